@@ -1,0 +1,747 @@
+/*
+ * aenet_oracle.c -- plain FP64 CPU oracle of the ANN-potential hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. The GPU product path never calls it
+ * and shares no code, header or table with it.
+ *
+ * What it evaluates, written as the paper defines it and in the paper's order:
+ *   - neighbours: every periodic image j+n within the cutoff of atom i,
+ *     excluding only (j = i, n = 0); by brute force over all atoms and images
+ *     (the definition), or through a cell list (checked against brute force);
+ *   - descriptor (Sec. II.B): radial Chebyshev expansion (Eq. radial) with the
+ *     recurrence for T_n and the cosine cutoff (Eq. cos-cutoff), angular
+ *     expansion (Eq. angular) over ORDERED pairs (j, k) of distinct image-atoms,
+ *     and the species-weighted copy of both sums (weights s_t of the neighbour
+ *     species; s_j s_k for the angular sum), concatenated as
+ *     G = [radial, angular, radial_w, angular_w];
+ *   - standardisation g = (G - shift) * scale (a frozen input transform);
+ *   - atomic energy E_i = ANN_t(g_i) (Sec. II.A, Eq. ANN-layer): tanh hidden
+ *     layers, linear output; total E = sum_i E_i (Behler-Parrinello sum);
+ *   - forces F = -dE/dr by back-propagation to dE/dG and the analytic
+ *     derivative of every pair and triplet term; virial
+ *     W_ab = -sum over displacement vectors d of d_a dE/dd_b;
+ *   - dE/dW, dE/db (back-propagation, Sec. II.C) summed over atoms;
+ *   - velocity-Verlet NVE integration in metal units.
+ *
+ * Derivative identities used (not printed in the paper, derived here):
+ *   dT_n/dx = n U_{n-1}(x), U_0 = 1, U_1 = 2x, U_{n+1} = 2x U_n - U_{n-1};
+ *   df_c/dr = -(pi / (2 R_c)) sin(pi r / R_c) for r <= R_c, else 0;
+ *   d cos(theta)/d d_j = (u_k - cos(theta) u_j) / r_j  (u = unit vectors).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_E_ARG -1
+#define ORC_E_NOMEM -7
+#define ORC_E_OVERLAP -5
+
+typedef struct {
+    int n_species;
+    const double *type_weight; /* [n_species] s_t of the weighted copy */
+    double rc_rad;
+    int order_rad;
+    double rc_ang;
+    int order_ang;
+    int n_layers;              /* number of weight layers, e.g. 3 for D-h-h-1 */
+    const int *widths;         /* [n_layers + 1]; widths[0] = D, widths[n_layers] = 1 */
+    const double *params;      /* [n_species][n_params]: W^1 b^1 W^2 b^2 ... (W row-major) */
+    const double *in_shift;    /* [n_species][D] or NULL */
+    const double *in_scale;    /* [n_species][D] or NULL */
+} orc_model;
+
+typedef struct {
+    int j;
+    int img[3];
+    double d[3];
+    double r;
+} orc_nb;
+
+static const double ORC_PI = 3.14159265358979323846;
+
+static int orc_D(const orc_model *m) { return 2 * (m->order_rad + 1 + m->order_ang + 1); }
+
+static int orc_nparams(const orc_model *m) {
+    int s = 0;
+    for (int l = 1; l <= m->n_layers; ++l) s += m->widths[l] * m->widths[l - 1] + m->widths[l];
+    return s;
+}
+
+/* ------------------------------------------------------------ basis pieces */
+
+/* Chebyshev T_0..T_n at x by the three-term recurrence (Sec. II.B). */
+static void cheb_T(int n, double x, double *T) {
+    T[0] = 1.0;
+    if (n >= 1) T[1] = x;
+    for (int a = 1; a < n; ++a) T[a + 1] = 2.0 * x * T[a] - T[a - 1];
+}
+
+/* dT_a/dx = a U_{a-1}(x), U of the second kind by its own recurrence. */
+static void cheb_dT(int n, double x, double *dT) {
+    double Um1 = 0.0, U = 1.0; /* U_{-1} = 0, U_0 = 1 */
+    dT[0] = 0.0;
+    for (int a = 1; a <= n; ++a) {
+        dT[a] = a * U; /* U holds U_{a-1} */
+        double Un = 2.0 * x * U - Um1;
+        Um1 = U;
+        U = Un;
+    }
+}
+
+/* Cosine cutoff (Eq. cos-cutoff) and its derivative. */
+static double cutoff_fc(double r, double rc) {
+    return (r <= rc) ? 0.5 * (cos(ORC_PI * r / rc) + 1.0) : 0.0;
+}
+static double cutoff_dfc(double r, double rc) {
+    return (r <= rc) ? -0.5 * ORC_PI / rc * sin(ORC_PI * r / rc) : 0.0;
+}
+
+/* ------------------------------------------------------------ neighbours */
+
+static double wrap1(double x, double L) {
+    double w = x - floor(x / L) * L;
+    if (w >= L) w -= L;
+    if (w < 0.0) w = 0.0;
+    return w;
+}
+
+typedef struct {
+    int nc[3];
+    double h[3];
+    int m[3];
+    int *start; /* [ncell + 1] */
+    int *atoms; /* [n] */
+} orc_cells;
+
+static void cells_free(orc_cells *c) {
+    free(c->start);
+    free(c->atoms);
+    c->start = c->atoms = NULL;
+}
+
+static int cells_build(orc_cells *c, int n, const double *wpos, const double *box, double rc) {
+    for (int a = 0; a < 3; ++a) {
+        int nc = (int)floor(box[a] / rc);
+        c->nc[a] = nc < 1 ? 1 : nc;
+        c->h[a] = box[a] / c->nc[a];
+        c->m[a] = (int)ceil(rc / c->h[a]);
+    }
+    int ncell = c->nc[0] * c->nc[1] * c->nc[2];
+    c->start = (int *)calloc((size_t)ncell + 1, sizeof(int));
+    c->atoms = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *cid = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!c->start || !c->atoms || !cid) {
+        free(cid);
+        cells_free(c);
+        return ORC_E_NOMEM;
+    }
+    for (int i = 0; i < n; ++i) {
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+            ci[a] = (int)floor(wpos[3 * i + a] / c->h[a]);
+            if (ci[a] >= c->nc[a]) ci[a] = c->nc[a] - 1;
+            if (ci[a] < 0) ci[a] = 0;
+        }
+        cid[i] = (ci[2] * c->nc[1] + ci[1]) * c->nc[0] + ci[0];
+        c->start[cid[i] + 1]++;
+    }
+    for (int k = 0; k < ncell; ++k) c->start[k + 1] += c->start[k];
+    int *fill = (int *)malloc(sizeof(int) * (size_t)ncell);
+    if (!fill) {
+        free(cid);
+        cells_free(c);
+        return ORC_E_NOMEM;
+    }
+    memcpy(fill, c->start, sizeof(int) * (size_t)ncell);
+    for (int i = 0; i < n; ++i) c->atoms[fill[cid[i]]++] = i;
+    free(fill);
+    free(cid);
+    return ORC_OK;
+}
+
+typedef struct {
+    orc_nb *v;
+    int n, cap;
+} nb_buf;
+
+static int nb_push(nb_buf *b, int j, const int img[3], const double d[3], double r) {
+    if (b->n == b->cap) {
+        int cap = b->cap ? 2 * b->cap : 256;
+        orc_nb *nv = (orc_nb *)realloc(b->v, sizeof(orc_nb) * (size_t)cap);
+        if (!nv) return ORC_E_NOMEM;
+        b->v = nv;
+        b->cap = cap;
+    }
+    orc_nb *e = &b->v[b->n++];
+    e->j = j;
+    e->r = r;
+    for (int a = 0; a < 3; ++a) {
+        e->img[a] = img[a];
+        e->d[a] = d[a];
+    }
+    return ORC_OK;
+}
+
+/* Brute force: every atom j and every periodic image n with |x_j + nL - x_i| <= rc,
+ * except (j = i, n = 0). x are wrapped into [0, L). */
+static int neighbours_brute(int i, int n, const double *wpos, const double *box, double rc, nb_buf *out) {
+    out->n = 0;
+    const double rc2 = rc * rc;
+    for (int j = 0; j < n; ++j) {
+        double del[3];
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            del[a] = wpos[3 * j + a] - wpos[3 * i + a];
+            lo[a] = (int)ceil((-rc - del[a]) / box[a]);
+            hi[a] = (int)floor((rc - del[a]) / box[a]);
+        }
+        int img[3];
+        for (img[0] = lo[0]; img[0] <= hi[0]; ++img[0])
+            for (img[1] = lo[1]; img[1] <= hi[1]; ++img[1])
+                for (img[2] = lo[2]; img[2] <= hi[2]; ++img[2]) {
+                    if (j == i && img[0] == 0 && img[1] == 0 && img[2] == 0) continue;
+                    double d[3], r2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = del[a] + img[a] * box[a];
+                        r2 += d[a] * d[a];
+                    }
+                    if (r2 > rc2) continue;
+                    int e = nb_push(out, j, img, d, sqrt(r2));
+                    if (e) return e;
+                }
+    }
+    return ORC_OK;
+}
+
+/* Cell list: cells of edge h >= rc (or one cell per axis), scanned over cell
+ * offsets -m..m with m = ceil(rc / h); the image index of the neighbour cell
+ * follows from floor division of the unwrapped cell index. */
+static int neighbours_cells(int i, const double *wpos, const double *box, double rc,
+                            const orc_cells *c, nb_buf *out) {
+    out->n = 0;
+    const double rc2 = rc * rc;
+    int ci[3];
+    for (int a = 0; a < 3; ++a) {
+        ci[a] = (int)floor(wpos[3 * i + a] / c->h[a]);
+        if (ci[a] >= c->nc[a]) ci[a] = c->nc[a] - 1;
+        if (ci[a] < 0) ci[a] = 0;
+    }
+    int off[3];
+    for (off[2] = -c->m[2]; off[2] <= c->m[2]; ++off[2])
+        for (off[1] = -c->m[1]; off[1] <= c->m[1]; ++off[1])
+            for (off[0] = -c->m[0]; off[0] <= c->m[0]; ++off[0]) {
+                int cc[3], img[3];
+                for (int a = 0; a < 3; ++a) {
+                    int u = ci[a] + off[a];
+                    int q = (int)floor((double)u / c->nc[a]);
+                    img[a] = q;
+                    cc[a] = u - q * c->nc[a];
+                }
+                int cell = (cc[2] * c->nc[1] + cc[1]) * c->nc[0] + cc[0];
+                for (int p = c->start[cell]; p < c->start[cell + 1]; ++p) {
+                    int j = c->atoms[p];
+                    if (j == i && img[0] == 0 && img[1] == 0 && img[2] == 0) continue;
+                    double d[3], r2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = wpos[3 * j + a] + img[a] * box[a] - wpos[3 * i + a];
+                        r2 += d[a] * d[a];
+                    }
+                    if (r2 > rc2) continue;
+                    int e = nb_push(out, j, img, d, sqrt(r2));
+                    if (e) return e;
+                }
+            }
+    return ORC_OK;
+}
+
+static double *wrapped_copy(int n, const double *pos, const double *box) {
+    double *w = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!w) return NULL;
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) w[3 * i + a] = wrap1(pos[3 * i + a], box[a]);
+    return w;
+}
+
+/* Neighbour lists for tests: counts[i] (and, when out_j != NULL, the entries at
+ * offsets[i]...) with image indices relative to the WRAPPED positions. */
+int orc_neighbour_lists(int mode, int n, const double *pos, const double *box, double rc,
+                        int *counts, const int64_t *offsets, int *out_j, int *out_img) {
+    if (n < 0 || !pos || !box || rc <= 0.0 || !counts) return ORC_E_ARG;
+    double *w = wrapped_copy(n, pos, box);
+    if (!w) return ORC_E_NOMEM;
+    orc_cells cells = {0};
+    int err = ORC_OK;
+    if (mode == 1) err = cells_build(&cells, n, w, box, rc);
+    nb_buf b = {0};
+    for (int i = 0; i < n && !err; ++i) {
+        err = (mode == 1) ? neighbours_cells(i, w, box, rc, &cells, &b)
+                          : neighbours_brute(i, n, w, box, rc, &b);
+        if (err) break;
+        counts[i] = b.n;
+        if (out_j) {
+            for (int k = 0; k < b.n; ++k) {
+                out_j[offsets[i] + k] = b.v[k].j;
+                for (int a = 0; a < 3; ++a) out_img[3 * (offsets[i] + k) + a] = b.v[k].img[a];
+            }
+        }
+    }
+    free(b.v);
+    if (mode == 1) cells_free(&cells);
+    free(w);
+    return err;
+}
+
+/* ------------------------------------------------------------ per-atom pass */
+
+typedef struct {
+    nb_buf nb;
+    double *G, *g, *dEdG, *acts, *dE_dd, *T, *dT;
+    int *ang; /* indices of angular neighbours in nb */
+    int ang_cap;
+} orc_work;
+
+static void work_free(orc_work *w) {
+    free(w->nb.v);
+    free(w->G);
+    free(w->g);
+    free(w->dEdG);
+    free(w->acts);
+    free(w->dE_dd);
+    free(w->T);
+    free(w->dT);
+    free(w->ang);
+    memset(w, 0, sizeof(*w));
+}
+
+static int work_init(orc_work *w, const orc_model *m) {
+    memset(w, 0, sizeof(*w));
+    int D = orc_D(m);
+    int tot = 0, nmax = 1;
+    for (int l = 0; l <= m->n_layers; ++l) {
+        tot += m->widths[l];
+        if (m->widths[l] > nmax) nmax = m->widths[l];
+    }
+    int ord = m->order_rad > m->order_ang ? m->order_rad : m->order_ang;
+    w->G = (double *)malloc(sizeof(double) * D);
+    w->g = (double *)malloc(sizeof(double) * D);
+    w->dEdG = (double *)malloc(sizeof(double) * D);
+    w->acts = (double *)malloc(sizeof(double) * (size_t)(2 * tot + 2 * nmax));
+    w->T = (double *)malloc(sizeof(double) * (ord + 2));
+    w->dT = (double *)malloc(sizeof(double) * (ord + 2));
+    if (!w->G || !w->g || !w->dEdG || !w->acts || !w->T || !w->dT) {
+        work_free(w);
+        return ORC_E_NOMEM;
+    }
+    return ORC_OK;
+}
+
+/* Descriptor of atom i from its neighbour list (Eqs. radial, angular, the
+ * weighted copy); fills w->G and the list of angular neighbours. */
+static int descriptor(const orc_model *m, const int *types, orc_work *w) {
+    const int Kr = m->order_rad + 1, Ka = m->order_ang + 1;
+    double *rad = w->G, *ang = w->G + Kr, *radw = w->G + Kr + Ka, *angw = w->G + 2 * Kr + Ka;
+    memset(w->G, 0, sizeof(double) * orc_D(m));
+    if (w->ang_cap < w->nb.n) {
+        int *na = (int *)realloc(w->ang, sizeof(int) * (size_t)w->nb.n);
+        if (!na) return ORC_E_NOMEM;
+        w->ang = na;
+        w->ang_cap = w->nb.n;
+    }
+    int n_ang = 0;
+    for (int p = 0; p < w->nb.n; ++p) {
+        const orc_nb *e = &w->nb.v[p];
+        if (e->r < 1e-8) return ORC_E_OVERLAP;
+        double s = m->type_weight[types[e->j]];
+        if (e->r <= m->rc_rad) {
+            double fc = cutoff_fc(e->r, m->rc_rad);
+            cheb_T(m->order_rad, 2.0 * e->r / m->rc_rad - 1.0, w->T);
+            for (int a = 0; a < Kr; ++a) {
+                rad[a] += w->T[a] * fc;
+                radw[a] += s * w->T[a] * fc;
+            }
+        }
+        if (e->r <= m->rc_ang) w->ang[n_ang++] = p;
+    }
+    for (int pa = 0; pa < n_ang; ++pa) {
+        const orc_nb *ej = &w->nb.v[w->ang[pa]];
+        double fj = cutoff_fc(ej->r, m->rc_ang), sj = m->type_weight[types[ej->j]];
+        for (int pb = 0; pb < n_ang; ++pb) {
+            if (pb == pa) continue; /* k != j as image-atoms; ordered pairs */
+            const orc_nb *ek = &w->nb.v[w->ang[pb]];
+            double fk = cutoff_fc(ek->r, m->rc_ang), sk = m->type_weight[types[ek->j]];
+            double cth = (ej->d[0] * ek->d[0] + ej->d[1] * ek->d[1] + ej->d[2] * ek->d[2]) / (ej->r * ek->r);
+            cheb_T(m->order_ang, cth, w->T);
+            for (int a = 0; a < Ka; ++a) {
+                ang[a] += w->T[a] * fj * fk;
+                angw[a] += sj * sk * w->T[a] * fj * fk;
+            }
+        }
+    }
+    return n_ang;
+}
+
+/* Network of species t: forward (Eq. ANN-layer, tanh hidden, linear output),
+ * then back-propagation of dE_i/dg; optional accumulation of dE/dW, dE/db. */
+static double network(const orc_model *m, int t, orc_work *w, double *dEdW_t) {
+    const int L = m->n_layers, D = orc_D(m);
+    const double *P = m->params + (size_t)t * orc_nparams(m);
+    const double *sh = m->in_shift ? m->in_shift + (size_t)t * D : NULL;
+    const double *sc = m->in_scale ? m->in_scale + (size_t)t * D : NULL;
+    /* activations x^0..x^L stored back to back */
+    int off[64];
+    off[0] = 0;
+    for (int l = 1; l <= L; ++l) off[l] = off[l - 1] + m->widths[l - 1];
+    double *x = w->acts;
+    for (int k = 0; k < D; ++k) x[k] = (w->G[k] - (sh ? sh[k] : 0.0)) * (sc ? sc[k] : 1.0);
+    const double *Wl = P;
+    const double *Wptr[64];
+    for (int l = 1; l <= L; ++l) {
+        int no = m->widths[l], ni = m->widths[l - 1];
+        const double *W = Wl, *b = Wl + (size_t)no * ni;
+        Wptr[l] = W;
+        for (int o = 0; o < no; ++o) {
+            double z = b[o];
+            for (int k = 0; k < ni; ++k) z += W[(size_t)o * ni + k] * x[off[l - 1] + k];
+            x[off[l] + o] = (l < L) ? tanh(z) : z;
+        }
+        Wl = b + no;
+    }
+    double E = x[off[L]];
+    /* back-propagation: delta^L = dE/dz^L = 1; two scratch vectors after x^L */
+    int nmax = 1;
+    for (int l = 0; l <= L; ++l)
+        if (m->widths[l] > nmax) nmax = m->widths[l];
+    double *dcur = w->acts + off[L] + m->widths[L], *dprev = dcur + nmax;
+    dcur[0] = 1.0;
+    size_t poff = 0;
+    size_t lay_off[64];
+    for (int l = 1; l <= L; ++l) {
+        lay_off[l] = poff;
+        poff += (size_t)m->widths[l] * m->widths[l - 1] + m->widths[l];
+    }
+    for (int l = L; l >= 1; --l) {
+        int no = m->widths[l], ni = m->widths[l - 1];
+        const double *W = Wptr[l];
+        if (dEdW_t) {
+            double *gW = dEdW_t + lay_off[l], *gb = gW + (size_t)no * ni;
+            for (int o = 0; o < no; ++o) {
+                gb[o] += dcur[o];
+                for (int k = 0; k < ni; ++k) gW[(size_t)o * ni + k] += dcur[o] * x[off[l - 1] + k];
+            }
+        }
+        for (int k = 0; k < ni; ++k) {
+            double s = 0.0;
+            for (int o = 0; o < no; ++o) s += W[(size_t)o * ni + k] * dcur[o];
+            if (l - 1 >= 1) {
+                double a = x[off[l - 1] + k];
+                s *= (1.0 - a * a);
+            }
+            dprev[k] = s;
+        }
+        double *tmp = dcur;
+        dcur = dprev;
+        dprev = tmp;
+    }
+    /* dcur now holds dE/dg; dE/dG = dE/dg * scale */
+    for (int k = 0; k < D; ++k) w->dEdG[k] = dcur[k] * (sc ? sc[k] : 1.0);
+    return E;
+}
+
+/* dE_i/dd for every neighbour entry of atom i, from dE_i/dG. */
+static void descriptor_grad(const orc_model *m, const int *types, orc_work *w, int n_ang) {
+    const int Kr = m->order_rad + 1, Ka = m->order_ang + 1;
+    const double *gr = w->dEdG, *ga = w->dEdG + Kr, *grw = w->dEdG + Kr + Ka, *gaw = w->dEdG + 2 * Kr + Ka;
+    double *G3 = w->dE_dd;
+    memset(G3, 0, sizeof(double) * 3 * (size_t)w->nb.n);
+    for (int p = 0; p < w->nb.n; ++p) {
+        const orc_nb *e = &w->nb.v[p];
+        if (e->r > m->rc_rad) continue;
+        double s = m->type_weight[types[e->j]];
+        double x = 2.0 * e->r / m->rc_rad - 1.0;
+        double fc = cutoff_fc(e->r, m->rc_rad), dfc = cutoff_dfc(e->r, m->rc_rad);
+        cheb_T(m->order_rad, x, w->T);
+        cheb_dT(m->order_rad, x, w->dT);
+        double dEdr = 0.0;
+        for (int a = 0; a < Kr; ++a) {
+            double coef = gr[a] + s * grw[a];
+            dEdr += coef * (w->dT[a] * (2.0 / m->rc_rad) * fc + w->T[a] * dfc);
+        }
+        for (int a = 0; a < 3; ++a) G3[3 * p + a] += dEdr * e->d[a] / e->r;
+    }
+    for (int pa = 0; pa < n_ang; ++pa) {
+        int ij = w->ang[pa];
+        const orc_nb *ej = &w->nb.v[ij];
+        double fj = cutoff_fc(ej->r, m->rc_ang), dfj = cutoff_dfc(ej->r, m->rc_ang);
+        double sj = m->type_weight[types[ej->j]];
+        double uj[3] = {ej->d[0] / ej->r, ej->d[1] / ej->r, ej->d[2] / ej->r};
+        for (int pb = 0; pb < n_ang; ++pb) {
+            if (pb == pa) continue;
+            int ik = w->ang[pb];
+            const orc_nb *ek = &w->nb.v[ik];
+            double fk = cutoff_fc(ek->r, m->rc_ang), dfk = cutoff_dfc(ek->r, m->rc_ang);
+            double sk = m->type_weight[types[ek->j]];
+            double uk[3] = {ek->d[0] / ek->r, ek->d[1] / ek->r, ek->d[2] / ek->r};
+            double cth = uj[0] * uk[0] + uj[1] * uk[1] + uj[2] * uk[2];
+            cheb_T(m->order_ang, cth, w->T);
+            cheb_dT(m->order_ang, cth, w->dT);
+            double S = 0.0, dS = 0.0;
+            for (int a = 0; a < Ka; ++a) {
+                double coef = ga[a] + sj * sk * gaw[a];
+                S += coef * w->T[a];
+                dS += coef * w->dT[a];
+            }
+            for (int a = 0; a < 3; ++a) {
+                double dcos_dj = (uk[a] - cth * uj[a]) / ej->r;
+                double dcos_dk = (uj[a] - cth * uk[a]) / ek->r;
+                G3[3 * ij + a] += dS * fj * fk * dcos_dj + S * dfj * fk * uj[a];
+                G3[3 * ik + a] += dS * fj * fk * dcos_dk + S * fj * dfk * uk[a];
+            }
+        }
+    }
+}
+
+static int check_model(const orc_model *m) {
+    if (!m || m->n_species < 1 || !m->type_weight || m->rc_rad <= 0.0 || m->rc_ang <= 0.0 ||
+        m->order_rad < 0 || m->order_ang < 0 || m->n_layers < 1 || m->n_layers > 60 || !m->widths ||
+        !m->params)
+        return ORC_E_ARG;
+    if (m->widths[0] != orc_D(m) || m->widths[m->n_layers] != 1) return ORC_E_ARG;
+    return ORC_OK;
+}
+
+/*
+ * Energy, forces, virial (and optionally per-atom energies, G, dE/dG, dE/dW)
+ * of one periodic orthorhombic structure.
+ *   mode        0 = brute-force neighbours, 1 = cell list
+ *   center_mask NULL = every atom is a centre; else only atoms with mask != 0
+ *               contribute E_i (and their force / virial terms)
+ *   outputs     any may be NULL; forces [n*3], virial [9] row-major,
+ *               e_atom [n], G and dEdG [n*D], dEdW [n_species*n_params]
+ */
+int orc_compute(const orc_model *m, int n, const double *pos, const int *types, const double *box,
+                int mode, int n_threads, const unsigned char *center_mask, double *energy, double *e_atom,
+                double *forces, double *virial, double *G_out, double *dEdG_out, double *dEdW) {
+    if (check_model(m) || n < 0 || (n > 0 && (!pos || !types)) || !box) return ORC_E_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0.0)) return ORC_E_ARG;
+    for (int i = 0; i < n; ++i)
+        if (types[i] < 0 || types[i] >= m->n_species) return ORC_E_ARG;
+    const int D = orc_D(m), NP = orc_nparams(m);
+    const double rc = m->rc_rad > m->rc_ang ? m->rc_rad : m->rc_ang;
+    double *w = wrapped_copy(n, pos, box);
+    if (!w) return ORC_E_NOMEM;
+    orc_cells cells = {0};
+    if (mode == 1 && cells_build(&cells, n, w, box, rc)) {
+        free(w);
+        return ORC_E_NOMEM;
+    }
+    int nt = 1;
+#ifdef _OPENMP
+    nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#endif
+    double *Fth = (double *)calloc((size_t)nt * 3 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    double *Wth = (double *)calloc((size_t)nt * 9, sizeof(double));
+    double *Eth = (double *)calloc((size_t)nt, sizeof(double));
+    double *gWth = dEdW ? (double *)calloc((size_t)nt * m->n_species * NP, sizeof(double)) : NULL;
+    int err = ORC_OK;
+    if (!Fth || !Wth || !Eth || (dEdW && !gWth)) err = ORC_E_NOMEM;
+
+#pragma omp parallel num_threads(nt) if (nt > 1)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        orc_work wk;
+        memset(&wk, 0, sizeof(wk));
+        int lerr = err ? err : work_init(&wk, m);
+        double *F = Fth ? Fth + (size_t)tid * 3 * n : NULL;
+        double *V = Wth ? Wth + 9 * tid : NULL;
+#pragma omp for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            if (lerr) continue;
+            if (center_mask && !center_mask[i]) {
+                if (e_atom) e_atom[i] = 0.0;
+                continue;
+            }
+            int e = (mode == 1) ? neighbours_cells(i, w, box, rc, &cells, &wk.nb)
+                                : neighbours_brute(i, n, w, box, rc, &wk.nb);
+            if (e) {
+                lerr = e;
+                continue;
+            }
+            int n_ang = descriptor(m, types, &wk);
+            if (n_ang < 0) {
+                lerr = n_ang;
+                continue;
+            }
+            double Ei = network(m, types[i], &wk, gWth ? gWth + ((size_t)tid * m->n_species + types[i]) * NP : NULL);
+            Eth[tid] += Ei;
+            if (e_atom) e_atom[i] = Ei;
+            if (G_out) memcpy(G_out + (size_t)i * D, wk.G, sizeof(double) * D);
+            if (dEdG_out) memcpy(dEdG_out + (size_t)i * D, wk.dEdG, sizeof(double) * D);
+            if (forces || virial) {
+                double *nd = (double *)realloc(wk.dE_dd, sizeof(double) * 3 * (size_t)(wk.nb.n > 0 ? wk.nb.n : 1));
+                if (!nd) {
+                    lerr = ORC_E_NOMEM;
+                    continue;
+                }
+                wk.dE_dd = nd;
+                descriptor_grad(m, types, &wk, n_ang);
+                for (int p = 0; p < wk.nb.n; ++p) {
+                    const orc_nb *q = &wk.nb.v[p];
+                    const double *g3 = wk.dE_dd + 3 * p;
+                    for (int a = 0; a < 3; ++a) {
+                        /* d = x_j + nL - x_i: dE/dx_j = +g, dE/dx_i = -g; F = -dE/dx */
+                        F[3 * q->j + a] -= g3[a];
+                        F[3 * i + a] += g3[a];
+                        for (int b = 0; b < 3; ++b) V[3 * a + b] -= q->d[a] * g3[b];
+                    }
+                }
+            }
+        }
+#pragma omp critical
+        {
+            if (lerr && !err) err = lerr;
+        }
+        work_free(&wk);
+    }
+    if (!err) {
+        double E = 0.0;
+        for (int t = 0; t < nt; ++t) E += Eth[t];
+        if (energy) *energy = E;
+        if (forces) {
+            for (size_t k = 0; k < 3 * (size_t)n; ++k) {
+                double s = 0.0;
+                for (int t = 0; t < nt; ++t) s += Fth[(size_t)t * 3 * n + k];
+                forces[k] = s;
+            }
+        }
+        if (virial) {
+            for (int k = 0; k < 9; ++k) {
+                double s = 0.0;
+                for (int t = 0; t < nt; ++t) s += Wth[9 * t + k];
+                virial[k] = s;
+            }
+        }
+        if (dEdW) {
+            for (size_t k = 0; k < (size_t)m->n_species * NP; ++k) {
+                double s = 0.0;
+                for (int t = 0; t < nt; ++t) s += gWth[(size_t)t * m->n_species * NP + k];
+                dEdW[k] = s;
+            }
+        }
+    }
+    free(Fth);
+    free(Wth);
+    free(Eth);
+    free(gWth);
+    if (mode == 1) cells_free(&cells);
+    free(w);
+    return err;
+}
+
+/* Forces on a few target atoms only: every atom within the largest cutoff of a
+ * target (any image) is a centre; the rest are skipped. */
+int orc_forces_subset(const orc_model *m, int n, const double *pos, const int *types, const double *box,
+                      int mode, int n_threads, int n_targets, const int *targets, double *forces_out,
+                      double *e_atom_out) {
+    if (check_model(m) || n <= 0 || n_targets < 0 || (n_targets > 0 && !targets) || !forces_out) return ORC_E_ARG;
+    const double rc = m->rc_rad > m->rc_ang ? m->rc_rad : m->rc_ang;
+    double *w = wrapped_copy(n, pos, box);
+    unsigned char *mask = (unsigned char *)calloc((size_t)n, 1);
+    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *Ea = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!w || !mask || !F || !Ea) {
+        free(w);
+        free(mask);
+        free(F);
+        free(Ea);
+        return ORC_E_NOMEM;
+    }
+    orc_cells cells = {0};
+    int err = (mode == 1) ? cells_build(&cells, n, w, box, rc) : ORC_OK;
+    nb_buf b = {0};
+    for (int t = 0; t < n_targets && !err; ++t) {
+        int i = targets[t];
+        if (i < 0 || i >= n) {
+            err = ORC_E_ARG;
+            break;
+        }
+        mask[i] = 1;
+        err = (mode == 1) ? neighbours_cells(i, w, box, rc, &cells, &b) : neighbours_brute(i, n, w, box, rc, &b);
+        for (int k = 0; k < b.n && !err; ++k) mask[b.v[k].j] = 1;
+    }
+    free(b.v);
+    if (mode == 1) cells_free(&cells);
+    free(w);
+    if (!err) err = orc_compute(m, n, pos, types, box, mode, n_threads, mask, NULL, Ea, F, NULL, NULL, NULL, NULL);
+    if (!err) {
+        for (int t = 0; t < n_targets; ++t) {
+            for (int a = 0; a < 3; ++a) forces_out[3 * t + a] = F[3 * targets[t] + a];
+            if (e_atom_out) e_atom_out[t] = Ea[targets[t]];
+        }
+    }
+    free(mask);
+    free(F);
+    free(Ea);
+    return err;
+}
+
+/*
+ * Velocity-Verlet NVE (metal units): v += dt/2 F/m c; x += dt v; F(x);
+ * v += dt/2 F/m c, with c = 9648.533212 (A/ps)^2 per eV/amu.
+ * pos, vel updated in place; e_pot, e_kin [n_steps + 1] (frame 0 first).
+ */
+int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *types,
+               const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
+               int n_threads, double *e_pot, double *e_kin) {
+    const double c = 9648.533212;
+    if (check_model(m) || n <= 0 || !pos || !vel || !mass_of_type || n_steps < 0) return ORC_E_ARG;
+    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    if (!F) return ORC_E_NOMEM;
+    double E = 0.0;
+    int err = orc_compute(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
+    for (int s = 0; s <= n_steps && !err; ++s) {
+        double K = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double mi = mass_of_type[types[i]];
+            for (int a = 0; a < 3; ++a) K += 0.5 * mi * vel[3 * i + a] * vel[3 * i + a] / c;
+        }
+        if (e_pot) e_pot[s] = E;
+        if (e_kin) e_kin[s] = K;
+        if (s == n_steps) break;
+        for (int i = 0; i < n; ++i) {
+            double k = 0.5 * dt * c / mass_of_type[types[i]];
+            for (int a = 0; a < 3; ++a) {
+                vel[3 * i + a] += k * F[3 * i + a];
+                pos[3 * i + a] += dt * vel[3 * i + a];
+            }
+        }
+        err = orc_compute(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
+        if (err) break;
+        for (int i = 0; i < n; ++i) {
+            double k = 0.5 * dt * c / mass_of_type[types[i]];
+            for (int a = 0; a < 3; ++a) vel[3 * i + a] += k * F[3 * i + a];
+        }
+    }
+    free(F);
+    return err;
+}
+
+/* Test hooks: the basis pieces on their own. */
+void orc_chebyshev(int n, double x, double *T, double *dT) {
+    cheb_T(n, x, T);
+    cheb_dT(n, x, dT);
+}
+
+void orc_cutoff(double r, double rc, double *fc_dfc) {
+    fc_dfc[0] = cutoff_fc(r, rc);
+    fc_dfc[1] = cutoff_dfc(r, rc);
+}
