@@ -1,0 +1,339 @@
+"""Benchmark of the ANN-potential MD hot path on GB300.
+
+Workload (default): the 4,096-molecule water box at 1.0 g/cm^3 (12,288 atoms,
+L = 49.669 A), water basis (radial order 16 / 6.0 A, angular order 8 / 4.0 A,
+D = 52), per-species 52-15-15-1 tanh networks with seeded N(0, 1/fan_in)
+weights, 300 K seeded velocities, velocity-Verlet NVE at dt = 0.5 fs.
+
+One benchmark step = one MD step of the whole path (kick + drift, cell list,
+descriptor, networks, forces + virial, FP64 reductions, kick), replayed from a
+captured CUDA graph on device-resident state. Between timed steps the L2 cache
+is flushed by writing a buffer larger than L2; each step is bracketed by CUDA
+events on the library's stream and the step times are summed.
+
+Metric: atom-steps/s (E+F). The JSON line also carries the end-to-end number
+through the C ABI with host buffers (host->device copy of positions, velocities
+and types, device->host copy of positions, velocities and energies, every
+step), the roofline of the dominant kernel, and the FP64 CPU oracle's
+throughput on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|bf16|bf16x3] [--workload water_12288|...]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (E+F) on 1 GB300, BF16 vs FP32 form at <=1 meV/A force err"
+DT_PS = 5e-4
+
+# FP32 operations per unit of the two fingerprint kernels (FMA = 2 flops):
+# per radial neighbour entry and per unordered angular pair, counted from the
+# arithmetic each unit needs (recurrences for T_a and U_a, coefficient
+# combination, chain rule, force scatter and virial); derivation in the design doc.
+def force_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
+    return (13 * (Kr - 1) + 38) * n_entries + (11 * (Ka - 1) + 52) * n_ang_pairs
+
+
+def descriptor_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
+    return (6 * (Kr - 1) + 10) * n_entries + (6 * (Ka - 1) + 10) * n_ang_pairs
+
+
+def workload(name):
+    from paper_2107_11311_gb300 import inputs
+    if name == "water_12288":
+        st, fam, vseed = inputs.water_12288(), "water", 12
+    elif name == "water_192":
+        st, fam, vseed = inputs.water_192(), "water", 2
+    elif name == "water_331776":
+        st, fam, vseed = inputs.water_331776(), "water", 42
+    elif name == "amorphous_27000":
+        st, fam, vseed = inputs.amorphous_27000(), "amorphous", 22
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    hidden = (32, 32) if name == "water_331776" else None
+    m = inputs.make_model(fam, hidden=hidden)
+    masses = m.masses[st.types] if fam == "water" else np.ones(st.n)
+    if fam != "water":
+        m.masses = np.ones(m.n_species)
+    v = inputs.maxwell_boltzmann(masses, 300.0, seed=vseed)
+    return st, m, v
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(n_sm, mhz):
+    """FP32 FMA pipe: 128 lanes per SM x 2 flops per FMA x clock."""
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(args, budget_s=12.0):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload:
+    E+F of the first frame evaluated for a contiguous block of centre atoms."""
+    from oracle import oracle
+    st, m, _ = workload(args.workload)
+    cores = os.cpu_count() or 1
+    n_cent = min(st.n, 2048)
+    mask = np.zeros(st.n, dtype=np.uint8)
+    mask[:n_cent] = 1
+    oracle.compute(m, st.pos, st.types, st.box, center_mask=mask, n_threads=cores)  # warm
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.compute(m, st.pos, st.types, st.box, center_mask=mask, n_threads=cores)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n_cent * reps / dt, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} E+F evaluations of {n_cent} centre atoms of {args.workload} "
+                      f"(FP64, OpenMP, {cores} threads)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle timed as the reference arm."""
+    if rank != 0:
+        return
+    from oracle import oracle
+    st, m, _ = workload(args.workload)
+    cores = os.cpu_count() or 1
+    n_cent = min(st.n, 1024)
+    mask = np.zeros(st.n, dtype=np.uint8)
+    mask[:n_cent] = 1
+    for _ in range(args.warmup):
+        oracle.compute(m, st.pos, st.types, st.box, center_mask=mask, n_threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.compute(m, st.pos, st.types, st.box, center_mask=mask, n_threads=cores)
+    dt = time.perf_counter() - t0
+    value = n_cent * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "atoms": st.n, "sample_centres": n_cent},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: E+F of {n_cent} centre atoms of {args.workload}"},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--workload", default="water_12288")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2107_11311_gb300.aenet import AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING, AenetGPU
+
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    st, m, v0 = workload(args.workload)
+    n = st.n
+
+    stream = torch.cuda.Stream(device=dev)
+    gpu = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+    pos = torch.tensor(st.pos, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    types = torch.tensor(st.types, device=dev)
+    # L2 flush buffer (> 129 MB L2)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    with torch.cuda.stream(stream):
+        gpu.md_nve(pos, vel, types, st.box, DT_PS, 1)  # initial forces + graph capture
+        flags = AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING
+        for _ in range(args.warmup):
+            flush.zero_()
+            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
+        gpu.check()
+        stats = gpu.neighbor_stats()
+
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stage_sum = None
+        kernels_per_step = 0
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
+            ends[k].record(stream)
+            ms, kernels_per_step = gpu.md_stage_times()  # synchronises: per-step stage times
+            stage_sum = ms if stage_sum is None else {s: stage_sum[s] + ms[s] for s in ms}
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        clk = clocks.stop()
+        gpu.check()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = world * n * args.steps / t_dev
+    stage_avg = {s: stage_sum[s] / args.steps for s in stage_sum}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hpos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    hvel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    htypes = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hep = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    hek = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    hpos.copy_(pos.cpu())
+    hvel.copy_(vel.cpu())
+    htypes.copy_(types.cpu())
+    e2 = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+    e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
+    for _ in range(3):
+        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * n * args.e2e_steps / t_e2e
+    h2d = hpos.numel() * 8 + hvel.numel() * 8 + htypes.numel() * 4
+    d2h = hpos.numel() * 8 + hvel.numel() * 8 + hep.numel() * 8 + hek.numel() * 8
+    e2.close()
+
+    if rank != 0:
+        gpu.close()
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (FP32 ALU bound)
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = measured_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    dom = max(("descriptor", "forces"), key=lambda s: stage_avg[s])
+    Kr, Ka = m.order_rad + 1, m.order_ang + 1
+    flops_force = force_kernel_flops(Kr, Ka, stats[0], stats[2])
+    flops_desc = descriptor_kernel_flops(Kr, Ka, stats[0], stats[2])
+    flops = flops_force if dom == "forces" else flops_desc
+    achieved = flops / (stage_avg[dom] * 1e-3) / 1e12
+    peak = fp32_alu_peak_tflops(props.multi_processor_count, max_mhz)
+    line = {
+        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "atoms": n, "box_A": float(st.box[0]), "dt_fs": DT_PS * 1e3,
+                   "precision": args.precision, "basis": f"rad {m.order_rad}/{m.rc_rad} A, ang {m.order_ang}/{m.rc_ang} A",
+                   "ann": "-".join(map(str, m.widths)), "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "neighbour_entries": stats[0], "angular_pairs": stats[2]},
+        "stage_ms": {s: round(v, 5) for s, v in stage_avg.items()},
+        "gpu_launches": kernels_per_step * args.steps,
+        "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
+                                   f"(SM clock max from MEASURED_PEAKS.json, {peak_kind})"},
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+    gpu.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * aenet_gpu.h -- C ABI of the GB300 (sm_103a) ANN-potential hot path.
+ *
+ * The library evaluates an atomic-energy-network potential of the
+ * Behler-Parrinello form E = sum_i ANN_{t_i}(g_i) (Sec. II.A, Eq. ANN-layer and
+ * the atomic-energy sum) on the Chebyshev descriptor of Sec. II.B (Eq. radial,
+ * Eq. angular, Eq. cos-cutoff and the species-weighted copy), plus the forces
+ * and virial that the MD engines of Sec. III consume and a velocity-Verlet NVE
+ * propagator (the MD cycle of Fig. 1). One context drives one GPU on one stream.
+ *
+ * Units: eV, Angstrom, amu, ps (LAMMPS "metal", Sec. III).
+ *
+ * Pointers: every array argument marked "host or device" may point to host
+ * memory or to device memory of the context's GPU; the library inspects it with
+ * cudaPointerGetAttributes and stages host data through its own device buffers.
+ * The caller owns all arrays it passes; the library copies what it keeps.
+ *
+ * Errors: every int-returning call returns an aenet_status. Nothing aborts or
+ * traps: device-side problems (neighbour-list overflow, coincident atoms,
+ * non-finite coordinates) are recorded in a device error word and reported by
+ * the next call that synchronises. aenet_last_error() gives a message.
+ *
+ * Thread safety: a context is not thread-safe; use one context per host thread
+ * and stream.
+ */
+#ifndef AENET_GPU_H
+#define AENET_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aenet_ctx aenet_ctx;
+
+typedef enum {
+    AENET_OK = 0,
+    AENET_E_ARG = -1,       /* invalid argument (sizes, NULL, types out of range, box) */
+    AENET_E_CUDA = -2,      /* a CUDA runtime call failed */
+    AENET_E_CAPACITY = -3,  /* a neighbour list exceeded its capacity even after one regrow */
+    AENET_E_NONFINITE = -4, /* non-finite coordinate */
+    AENET_E_OVERLAP = -5,   /* two image-atoms closer than 1e-6 A */
+    AENET_E_TIMEOUT = -6,   /* a bounded device wait gave up */
+    AENET_E_NOMEM = -7,     /* device allocation failed */
+    AENET_E_STATE = -8      /* call out of order (e.g. gradient before compute) */
+} aenet_status;
+
+typedef enum {
+    AENET_FP32 = 0,         /* network layers in FP32 on the CUDA cores */
+    AENET_BF16 = 1,         /* network layers as BF16 tensor-core products, FP32 accumulate */
+    AENET_BF16X3 = 2        /* split-BF16 (hi*hi + hi*lo + lo*hi) tensor-core products */
+} aenet_precision;
+
+/*
+ * Model description (copied at setup; the caller may free it afterwards).
+ *
+ * Descriptor (Sec. II.B): for atom i with neighbours j (all periodic images
+ * within the cutoff, excluding only the zero-shift self)
+ *   radial  c_a = sum_j T_a(2 r_ij / rc_rad - 1) f_c(r_ij),      a = 0..order_rad
+ *   angular c_a = sum_{j != k} T_a(cos theta_ijk) f_c(r_ij) f_c(r_ik), a = 0..order_ang
+ *             (ordered pairs of distinct image-atoms, f_c with rc_ang)
+ * and the same two sums with every neighbour term weighted by type_weight[t_j]
+ * (angular: type_weight[t_j] * type_weight[t_k]). G = [radial, angular,
+ * radial_w, angular_w], D = 2 (order_rad + 1 + order_ang + 1) <= 64.
+ * The network input is g = (G - in_shift[t]) * in_scale[t].
+ *
+ * Network (Eq. ANN-layer): widths[0] = D, widths[n_layers] = 1, hidden widths
+ * <= 64; tanh on hidden layers, linear output. params holds, per species, the
+ * concatenation W^1 b^1 W^2 b^2 ... with W^l row-major [widths[l] x widths[l-1]].
+ */
+typedef struct {
+    int n_species;               /* >= 1, <= 8 */
+    const double *type_weight;   /* [n_species] s_t of the weighted copy */
+    const double *mass;          /* [n_species] amu; NULL if no MD is run */
+    double rc_rad;               /* radial cutoff (A) */
+    int order_rad;               /* radial Chebyshev order N_r (0..31) */
+    double rc_ang;               /* angular cutoff (A) */
+    int order_ang;               /* angular Chebyshev order N_a (0..31) */
+    int n_layers;                /* weight layers, 2..5 (at least one hidden layer) */
+    const int *widths;           /* [n_layers + 1] */
+    const double *params;        /* [n_species * n_params] */
+    const double *in_shift;      /* [n_species * D] or NULL (zeros) */
+    const double *in_scale;      /* [n_species * D] or NULL (ones) */
+} aenet_model_desc;
+
+/*
+ * Create a context on the current CUDA device. `stream` is a cudaStream_t
+ * (NULL = legacy default stream); all work of the context is ordered on it.
+ * precision: an aenet_precision. Returns AENET_OK and *out, or an error and
+ * *out = NULL.
+ */
+int aenet_setup(aenet_ctx **out, const aenet_model_desc *model, int precision, void *stream);
+
+/* Change the stream of a context (the captured MD graph is rebuilt lazily). */
+int aenet_set_stream(aenet_ctx *ctx, void *stream);
+
+/*
+ * Energy, forces and virial of one periodic orthorhombic structure
+ * (the potential of Sec. II evaluated as the interface of Sec. III returns it).
+ *   n_atoms  >= 0
+ *   pos      [n_atoms * 3] double, host or device; any real coordinates (wrapped
+ *            internally into [0, box))
+ *   types    [n_atoms] int32, host or device; 0-based species index in setup
+ *            order (the species-order rule of the LAMMPS interface)
+ *   box      [3] double, HOST; box edge lengths (A), each > 0
+ *   energy   [1] double, host or device, or NULL: E = sum_i E_i (FP64 sum)
+ *   forces   [n_atoms * 3] double, host or device, or NULL: F = -dE/dr
+ *   virial   [9] double, host or device, or NULL: W_ab = -sum_d d_a dE/dd_b
+ *            over all displacement vectors d = x_j + nL - x_i (row-major)
+ *   e_atom   [n_atoms] double, host or device, or NULL: E_i
+ * Synchronises the stream before returning.
+ */
+int aenet_compute(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t *types,
+                  const double *box, double *energy, double *forces, double *virial,
+                  double *e_atom);
+
+/*
+ * Descriptor only (rows a1-a5 of the path): G [n_atoms * D] float32, host or
+ * device, row i = atom i in input order, layout [radial, angular, radial_w,
+ * angular_w] before standardisation. Synchronises.
+ */
+int aenet_descriptors(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t *types,
+                      const double *box, float *G);
+
+/*
+ * Velocity-Verlet NVE (the propagation cycle of Fig. 1; integration in FP64):
+ *   v += dt/2 F/m c;  x += dt v;  F = F(x);  v += dt/2 F/m c
+ * with c = 9648.533212 (A/ps)^2 per eV/amu. Requires model masses.
+ *   pos, vel [n_atoms * 3] double, host or device, updated in place
+ *   types    [n_atoms] int32, host or device; box [3] HOST
+ *   dt_ps    time step (ps); n_steps >= 0
+ *   e_pot, e_kin  [n_steps + 1] double, host or device, or NULL: potential and
+ *            kinetic energy of frames 0..n_steps
+ *   flags    bitwise OR of
+ *            AENET_MD_ASYNC: do not synchronise; then pos, vel, types, e_pot
+ *            and e_kin must be device pointers (or NULL) and device errors are
+ *            reported by the next synchronising call or aenet_check();
+ *            AENET_MD_CONTINUE: see below.
+ * Every step after the first is one replay of a captured CUDA graph.
+ */
+#define AENET_MD_ASYNC 1
+/* AENET_MD_CONTINUE: pos and vel are exactly as the previous aenet_md_nve call
+ * on this context left them (same buffers, nothing else run on the context in
+ * between); the forces and energy of that call's last frame are reused instead
+ * of being recomputed for frame 0. */
+#define AENET_MD_CONTINUE 2
+/* AENET_MD_TIMING: record CUDA events between the stages of every captured MD
+ * step; read them with aenet_md_stage_times(). */
+#define AENET_MD_TIMING 4
+int aenet_md_nve(aenet_ctx *ctx, int n_atoms, double *pos, double *vel, const int32_t *types,
+                 const double *box, double dt_ps, int n_steps, double *e_pot, double *e_kin,
+                 int flags);
+
+/*
+ * Neighbour statistics of the last descriptor evaluation on the context,
+ * summed over atoms: out[0] = image-atoms within the largest cutoff, out[1] =
+ * image-atoms within the angular cutoff, out[2] = unordered angular pairs
+ * (j < k) -- the pair and triplet counts that set the cost of Eqs. radial and
+ * angular. Synchronises.
+ */
+int aenet_neighbor_stats(aenet_ctx *ctx, int64_t out[3]);
+
+/*
+ * Device time (ms) of each stage of the last MD step run with
+ * AENET_MD_TIMING (CUDA events recorded inside the captured graph, on the
+ * context's stream): [kick + drift, cell list, descriptor, network, forces,
+ * reductions, kick], and the number of kernel launches in one MD step.
+ * Returns AENET_E_STATE if no timed step has run. Synchronises.
+ */
+int aenet_md_stage_times(aenet_ctx *ctx, float ms[7], int *kernels_per_step);
+
+/* Synchronise the context's stream and report any recorded device error. */
+int aenet_check(aenet_ctx *ctx);
+
+/* Last error message of the context (or of the last failed setup when ctx is NULL). */
+const char *aenet_last_error(const aenet_ctx *ctx);
+
+/* Free the context and all its device memory. NULL is a no-op. */
+void aenet_destroy(aenet_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AENET_GPU_H */

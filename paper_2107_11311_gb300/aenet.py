@@ -1,0 +1,221 @@
+"""Python binding of ``libaenet_gpu.so`` (C ABI in ``include/aenet_gpu.h``).
+
+Argument marshalling only: every step of the potential runs in the library's
+CUDA kernels. torch supplies device memory and the current CUDA stream; numpy
+arrays and CPU tensors are passed as host pointers (the library stages them).
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
+AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING = 1, 2, 4
+STAGES = ("kick_drift", "cell_list", "descriptor", "network", "forces", "reductions", "kick")
+PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
+
+STATUS = {0: "AENET_OK", -1: "AENET_E_ARG", -2: "AENET_E_CUDA", -3: "AENET_E_CAPACITY",
+          -4: "AENET_E_NONFINITE", -5: "AENET_E_OVERLAP", -6: "AENET_E_TIMEOUT", -7: "AENET_E_NOMEM",
+          -8: "AENET_E_STATE"}
+
+
+class AenetError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("type_weight", C.c_void_p), ("mass", C.c_void_p),
+                ("rc_rad", C.c_double), ("order_rad", C.c_int), ("rc_ang", C.c_double),
+                ("order_ang", C.c_int), ("n_layers", C.c_int), ("widths", C.c_void_p),
+                ("params", C.c_void_p), ("in_shift", C.c_void_p), ("in_scale", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the C-ABI library (building it with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run paper_2107_11311_gb300.build.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    lib.aenet_setup.argtypes = [C.POINTER(P), C.POINTER(ModelDesc), I, P]
+    lib.aenet_set_stream.argtypes = [P, P]
+    lib.aenet_compute.argtypes = [P, I, P, P, P, P, P, P, P]
+    lib.aenet_descriptors.argtypes = [P, I, P, P, P, P]
+    lib.aenet_md_nve.argtypes = [P, I, P, P, P, P, D, I, P, P, I]
+    lib.aenet_check.argtypes = [P]
+    lib.aenet_neighbor_stats.argtypes = [P, P]
+    lib.aenet_md_stage_times.argtypes = [P, P, P]
+    lib.aenet_last_error.argtypes = [P]
+    lib.aenet_last_error.restype = C.c_char_p
+    lib.aenet_destroy.argtypes = [P]
+    lib.aenet_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous numpy array or torch tensor (or None)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(x.ctypes.data)
+
+
+def _as(x, dtype):
+    """numpy inputs are converted to contiguous arrays of the ABI's type; torch
+    tensors must already have it (no hidden copies of device data)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if x.dtype != want:
+            raise TypeError(f"expected a {want} tensor, got {x.dtype}")
+        return x
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _current_stream():
+    import torch
+    if torch.cuda.is_available():
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+class AenetGPU:
+    """One library context: a model resident on the current GPU.
+
+    ``model`` is a :class:`paper_2107_11311_gb300.inputs.Model`.
+    """
+
+    def __init__(self, model, precision="fp32", stream=None):
+        self.lib = load()
+        self.model = model
+        self.D = int(model.widths[0])
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        keep = dict(
+            tw=np.ascontiguousarray(model.type_weights, dtype=np.float64),
+            mass=np.ascontiguousarray(model.masses, dtype=np.float64) if len(model.masses) else None,
+            widths=np.ascontiguousarray(model.widths, dtype=np.int32),
+            params=np.ascontiguousarray(model.params, dtype=np.float64),
+            shift=np.ascontiguousarray(model.in_shift, dtype=np.float64),
+            scale=np.ascontiguousarray(model.in_scale, dtype=np.float64))
+        desc = ModelDesc(model.n_species, keep["tw"].ctypes.data,
+                         None if keep["mass"] is None else keep["mass"].ctypes.data,
+                         float(model.rc_rad), int(model.order_rad), float(model.rc_ang), int(model.order_ang),
+                         len(model.widths) - 1, keep["widths"].ctypes.data, keep["params"].ctypes.data,
+                         keep["shift"].ctypes.data, keep["scale"].ctypes.data)
+        h = C.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        rc = self.lib.aenet_setup(C.byref(h), C.byref(desc), self.precision, st)
+        if rc != 0:
+            raise AenetError(rc, self.lib.aenet_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.aenet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise AenetError(rc, self.lib.aenet_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        self._check(self.lib.aenet_set_stream(self.h, stream))
+
+    def check(self):
+        self._check(self.lib.aenet_check(self.h))
+
+    @staticmethod
+    def _box(box):
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+
+    def compute(self, pos, types, box, energy=None, forces=None, virial=None, e_atom=None):
+        """Energy, forces, virial (and per-atom energies) of one structure.
+
+        With numpy inputs and no output buffers, returns numpy results. Output
+        buffers (numpy or torch, host or device) may be passed to avoid copies.
+        """
+        pos, types = _as(pos, np.float64), _as(types, np.int32)
+        n = int(pos.shape[0])
+        ret = energy is None and forces is None and virial is None and e_atom is None
+        if ret:
+            energy, forces, virial, e_atom = np.zeros(1), np.zeros((n, 3)), np.zeros((3, 3)), np.zeros(n)
+        box = self._box(box)
+        self._check(self.lib.aenet_compute(self.h, n, _ptr(pos), _ptr(types), _ptr(box), _ptr(energy),
+                                           _ptr(forces), _ptr(virial), _ptr(e_atom)))
+        if ret:
+            return dict(energy=float(energy[0]), forces=forces, virial=virial, e_atom=e_atom)
+        return None
+
+    def descriptors(self, pos, types, box, out=None):
+        pos, types = _as(pos, np.float64), _as(types, np.int32)
+        n = int(pos.shape[0])
+        G = np.zeros((n, self.D), dtype=np.float32) if out is None else out
+        box = self._box(box)
+        self._check(self.lib.aenet_descriptors(self.h, n, _ptr(pos), _ptr(types), _ptr(box), _ptr(G)))
+        return G
+
+    def md_nve(self, pos, vel, types, box, dt, n_steps, e_pot=None, e_kin=None, flags=0):
+        """Velocity-Verlet NVE in place on ``pos`` and ``vel`` (float64 arrays or
+        tensors; numpy arrays must already be float64 and contiguous)."""
+        types = _as(types, np.int32)
+        n = int(pos.shape[0])
+        box = self._box(box)
+        self._check(self.lib.aenet_md_nve(self.h, n, _ptr(pos), _ptr(vel), _ptr(types), _ptr(box),
+                                          float(dt), int(n_steps), _ptr(e_pot), _ptr(e_kin), int(flags)))
+
+    def neighbor_stats(self):
+        """(entries within the largest cutoff, angular entries, angular pairs) of
+        the last evaluation, summed over atoms."""
+        out = np.zeros(3, dtype=np.int64)
+        self._check(self.lib.aenet_neighbor_stats(self.h, _ptr(out)))
+        return tuple(int(x) for x in out)
+
+    def md_stage_times(self):
+        """Per-stage device milliseconds of the last AENET_MD_TIMING step and the
+        number of kernel launches per MD step."""
+        ms = np.zeros(7, dtype=np.float32)
+        k = C.c_int(0)
+        self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), C.byref(k)))
+        return dict(zip(STAGES, map(float, ms))), int(k.value)

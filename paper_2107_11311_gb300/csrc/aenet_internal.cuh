@@ -1,0 +1,167 @@
+// Internal declarations of the GB300 ANN-potential library: device model
+// constants, the cell grid, the context, and the launch wrappers of every
+// kernel. Only the .cu files of this library include it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "aenet_gpu.h"
+
+namespace aenet {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxD = 64;       // descriptor length handled by the 64-slot warp reduction
+constexpr int kMaxWidth = 64;   // hidden-layer width limit
+constexpr int kMaxLayers = 5;   // weight layers
+constexpr int kMaxOrder = 31;
+
+// Device error word bits (set by kernels, read by the host after a sync).
+constexpr unsigned kErrNbCap = 1u;      // neighbour list overflow
+constexpr unsigned kErrAngCap = 2u;     // angular list overflow
+constexpr unsigned kErrOverlap = 4u;    // |d| < 1e-6 A
+constexpr unsigned kErrNonfinite = 8u;  // non-finite coordinate
+constexpr unsigned kErrType = 16u;      // species index out of range
+
+// Descriptor basis and species constants, passed by value to the kernels.
+struct Basis {
+    int n_species;
+    int Kr, Ka, D;          // Kr = order_rad + 1, Ka = order_ang + 1, D = 2 (Kr + Ka)
+    float rc_rad, rc_ang, rc_max;
+    float type_weight[kMaxSpecies];
+};
+
+// Network shape (per species identical), passed by value.
+struct Net {
+    int n_species;
+    int n_layers;                  // weight layers
+    int widths[kMaxLayers + 1];
+    int n_params;                  // floats per species: W^1 b^1 W^2 b^2 ...
+    int act_len;                   // sum of widths (activation storage per atom)
+};
+
+// Cell grid of one orthorhombic box: nc cells per axis of edge h >= rc_max (or
+// a single cell when the box is shorter than the cutoff); neighbour cells are
+// scanned over offsets -m..m per axis, each offset one periodic image.
+struct Grid {
+    int nc[3];
+    int m[3];
+    int ncell;
+    int n_off;                     // prod(2 m + 1)
+    double box[3];
+    double h[3];
+    float hf[3];
+};
+
+// Capacities of the per-warp neighbour lists of the fingerprint kernels.
+struct Caps {
+    int nb;     // entries with r <= rc_max
+    int ang;    // entries with r <= rc_ang
+};
+
+struct Context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int precision = AENET_FP32;
+    Basis basis{};
+    Net net{};
+    std::vector<double> mass;      // [n_species], empty if none
+    std::string err;
+
+    // model on the device
+    float *d_params = nullptr;     // [n_species * n_params] FP32
+    float *d_shift = nullptr;      // [n_species * D]
+    float *d_scale = nullptr;      // [n_species * D]
+    uint16_t *d_wbf = nullptr;     // BF16 tensor-core operand tiles (hi, lo), see ann.cu
+    size_t wbf_elems = 0;
+    double *d_mass = nullptr;      // [n_species]
+
+    // work buffers (grown on demand)
+    int cap_atoms = 0;
+    int cap_cells = 0;
+    int cap_blocks = 0;
+    float4 *d_pos4 = nullptr;      // sorted cell-local coordinates, .w = species (int bits)
+    float4 *d_tmp4 = nullptr;      // same, input order
+    int *d_perm = nullptr;         // sorted slot -> input index
+    int *d_cell_of = nullptr;      // input index -> cell
+    int *d_slot = nullptr;         // input index -> rank inside its cell
+    int *d_cell_count = nullptr;   // [ncell]
+    int *d_cell_start = nullptr;   // [ncell + 1]
+    float *d_G = nullptr;          // [n * D] sorted order
+    float *d_dEdG = nullptr;       // [n * D] sorted order
+    float *d_eatom = nullptr;      // [n] sorted order
+    float4 *d_F4 = nullptr;        // [n] force accumulators, sorted order
+    double *d_vir_part = nullptr;  // [cells * 9]
+    double *d_e_part = nullptr;    // [blocks]
+    double *d_ke_part = nullptr;   // [blocks]
+    double *d_result = nullptr;    // [10]: energy, virial[9]
+    unsigned *d_err = nullptr;     // device error word
+    unsigned long long *d_stats = nullptr;  // [4] radial entries, angular entries, angular pairs
+    int *d_step = nullptr;         // MD record counter
+
+    // staging of host arrays
+    int cap_stage = 0;
+    double *d_pos = nullptr, *d_vel = nullptr, *d_forces = nullptr, *d_eatom_out = nullptr;
+    int32_t *d_types = nullptr;
+    int cap_rec = 0;
+    double *d_rec = nullptr;       // [2 * cap_rec] e_pot, e_kin records
+
+    Caps caps{};
+
+    // captured MD step
+    cudaGraphExec_t md_exec = nullptr;
+    struct {
+        int n = -1;
+        double *pos = nullptr, *vel = nullptr;
+        const int32_t *types = nullptr;
+        double box[3] = {0, 0, 0};
+        double dt = 0;
+        double *rec = nullptr;
+        cudaStream_t stream = nullptr;
+        Caps caps{};
+        bool timing = false;
+    } md_key;
+
+    // stage timing of the captured MD step (events recorded inside the graph)
+    static constexpr int kStages = 7;  // vv1, cells, descriptor, network, forces, reductions, vv2
+    cudaEvent_t ev[kStages + 1] = {};
+    int md_kernels = 0;                // kernel nodes in the captured step
+};
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on ctx.stream and return the launch status.
+
+// Wrap, bin and sort atoms by cell (rows a1, a2 of the path).
+cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
+
+// Descriptor of every atom into c.d_G (rows a3-a5).
+cudaError_t launch_fp_forward(Context &c, const Grid &g, int n);
+
+// Per-species networks: E_i and dE/dG_i (row a6), energy block partials.
+cudaError_t launch_ann(Context &c, int n);
+
+// Forces and virial partials from dE/dG (row a8).
+cudaError_t launch_fp_backward(Context &c, const Grid &g, int n);
+
+// Energy and virial reductions (row a7) and outputs in input order.
+cudaError_t launch_finalize(Context &c, const Grid &g, int n, double *forces, double *e_atom);
+
+// Descriptor rows to input order (float).
+cudaError_t launch_unsort_G(Context &c, int n, float *G);
+
+// Velocity Verlet (row a9).
+cudaError_t launch_vv_first(Context &c, int n, double dt, double *pos, double *vel, const double *F,
+                            const int32_t *types);
+cudaError_t launch_vv_second(Context &c, int n, double dt, double *vel, const double *F,
+                             const int32_t *types);
+cudaError_t launch_record(Context &c, int n, double *rec_pot, double *rec_kin);
+
+// Dynamic shared memory bytes of the fingerprint kernels for given capacities.
+size_t fp_smem_bytes(const Grid &g, const Caps &caps, bool backward);
+size_t ann_smem_bytes(const Context &c);
+
+}  // namespace aenet

@@ -1,0 +1,589 @@
+// C ABI of the library (declared in include/aenet_gpu.h): context set-up, the
+// energy/force/virial evaluation, the descriptor-only entry point and the
+// graph-captured velocity-Verlet NVE propagator.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "aenet_internal.cuh"
+
+struct aenet_ctx {
+    aenet::Context c;
+};
+
+namespace aenet {
+
+int ann_blocks(int n);
+cudaError_t prepare_bf16_weights(Context &c);
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+int fail(Context *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(Context *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_setup_error = buf;
+    return code;
+}
+
+int cuda_fail(Context *c, cudaError_t e, const char *where) {
+    return fail(c, AENET_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(&c, _e, where); \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t grow(T *&p, size_t have, size_t need) {
+    if (need <= have && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    return cudaMalloc(&p, sizeof(T) * (need > 0 ? need : 1));
+}
+
+int make_grid(Context &c, const double *box, Grid &g) {
+    const double rc = c.basis.rc_max;
+    g.ncell = 1;
+    g.n_off = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !isfinite(box[a])) return fail(&c, AENET_E_ARG, "box[%d] must be finite and > 0", a);
+        int nc = (int)floor(box[a] / rc);
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        g.nc[a] = nc;
+        g.box[a] = box[a];
+        g.h[a] = box[a] / nc;
+        g.hf[a] = (float)g.h[a];
+        g.m[a] = (int)ceil(rc / g.h[a]);
+        g.ncell *= nc;
+        g.n_off *= 2 * g.m[a] + 1;
+    }
+    if (g.n_off > 4096)
+        return fail(&c, AENET_E_ARG, "box too small for the cutoff: %d image cells per atom (limit 4096)", g.n_off);
+    return AENET_OK;
+}
+
+// Neighbour-list capacities from the mean density: 1.5x the expected count + 32,
+// rounded to a multiple of 32.
+Caps estimate_caps(const Context &c, int n, const Grid &g) {
+    const double V = g.box[0] * g.box[1] * g.box[2];
+    const double rho = n / V;
+    auto cap = [&](double rc) {
+        double e = rho * 4.18879020478639 * rc * rc * rc;
+        int k = (int)(1.5 * e + 32.0);
+        return ((k + 31) / 32) * 32;
+    };
+    Caps k;
+    k.nb = std::max(64, cap(c.basis.rc_max));
+    k.ang = std::max(32, cap(c.basis.rc_ang));
+    return k;
+}
+
+int ensure(Context &c, int n, const Grid &g) {
+    if (n > c.cap_atoms || !c.d_pos4) {
+        n = std::max(n, 1);
+        size_t N = (size_t)n;
+        const int D = c.basis.D;
+        CK(grow(c.d_pos4, 0, N), "cudaMalloc");
+        CK(grow(c.d_tmp4, 0, N), "cudaMalloc");
+        CK(grow(c.d_perm, 0, N), "cudaMalloc");
+        CK(grow(c.d_cell_of, 0, N), "cudaMalloc");
+        CK(grow(c.d_slot, 0, N), "cudaMalloc");
+        CK(grow(c.d_G, 0, N * D), "cudaMalloc");
+        CK(grow(c.d_dEdG, 0, N * D), "cudaMalloc");
+        CK(grow(c.d_eatom, 0, N), "cudaMalloc");
+        CK(grow(c.d_F4, 0, N), "cudaMalloc");
+        CK(grow(c.d_e_part, 0, (size_t)ann_blocks(n) + 1), "cudaMalloc");
+        CK(grow(c.d_ke_part, 0, (N + 255) / 256 + 1), "cudaMalloc");
+        c.cap_atoms = n;
+    }
+    if (g.ncell > c.cap_cells) {
+        CK(grow(c.d_cell_count, 0, (size_t)g.ncell), "cudaMalloc");
+        CK(grow(c.d_cell_start, 0, (size_t)g.ncell + 1), "cudaMalloc");
+        CK(grow(c.d_vir_part, 0, (size_t)g.ncell * 9), "cudaMalloc");
+        c.cap_cells = g.ncell;
+    }
+    return AENET_OK;
+}
+
+int ensure_stage(Context &c, int n) {
+    if (n > c.cap_stage || !c.d_pos) {
+        n = std::max(n, 1);
+        size_t N = (size_t)n;
+        CK(grow(c.d_pos, 0, 3 * N), "cudaMalloc");
+        CK(grow(c.d_vel, 0, 3 * N), "cudaMalloc");
+        CK(grow(c.d_forces, 0, 3 * N), "cudaMalloc");
+        CK(grow(c.d_eatom_out, 0, N), "cudaMalloc");
+        CK(grow(c.d_types, 0, N), "cudaMalloc");
+        c.cap_stage = n;
+    }
+    return AENET_OK;
+}
+
+int check_smem(Context &c, const Grid &g) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t need = fp_smem_bytes(g, c.caps, true);
+    if (optin > 0 && need > (size_t)optin)
+        return fail(&c, AENET_E_CAPACITY, "neighbour lists need %zu B of shared memory (limit %d B)", need, optin);
+    return AENET_OK;
+}
+
+// Timing event inside a captured graph (an event-record node) or eagerly.
+cudaError_t mark(Context &c, cudaEvent_t ev) {
+    if (!ev) return cudaSuccess;
+    return cudaEventRecordWithFlags(ev, c.stream, cudaEventRecordExternal);
+}
+
+// The whole path on device buffers, enqueued on c.stream (no synchronisation).
+// evs (optional): 5 events recorded after cells, descriptor, network, forces,
+// reductions.
+int enqueue_compute(Context &c, const Grid &g, int n, const double *pos, const int32_t *types, double *forces,
+                    double *e_atom, cudaEvent_t *evs = nullptr) {
+    int rc = check_smem(c, g);
+    if (rc) return rc;
+    CK(launch_cells(c, g, n, pos, types), "cell list");
+    if (evs) CK(mark(c, evs[0]), "event");
+    CK(launch_fp_forward(c, g, n), "descriptor kernel");
+    if (evs) CK(mark(c, evs[1]), "event");
+    CK(launch_ann(c, n), "network kernel");
+    if (evs) CK(mark(c, evs[2]), "event");
+    CK(launch_fp_backward(c, g, n), "force kernel");
+    if (evs) CK(mark(c, evs[3]), "event");
+    CK(launch_finalize(c, g, n, forces, e_atom), "reductions");
+    if (evs) CK(mark(c, evs[4]), "event");
+    return AENET_OK;
+}
+
+int read_error_word(Context &c) {
+    unsigned w = 0;
+    CK(cudaMemcpyAsync(&w, c.d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    if (w) CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
+    if (w & kErrType) return fail(&c, AENET_E_ARG, "species index out of range");
+    if (w & kErrNonfinite) return fail(&c, AENET_E_NONFINITE, "non-finite coordinate");
+    if (w & kErrOverlap) return fail(&c, AENET_E_OVERLAP, "two image-atoms closer than 1e-6 A");
+    if (w & (kErrNbCap | kErrAngCap))
+        return fail(&c, AENET_E_CAPACITY, "neighbour list overflow (capacity %d / %d)", c.caps.nb, c.caps.ang);
+    return AENET_OK;
+}
+
+// Stage a host-or-device array into a device buffer.
+template <class T>
+int stage_in(Context &c, const T *src, T *dev_buf, size_t count, const T **out) {
+    if (!src || count == 0) {
+        *out = src;
+        return AENET_OK;
+    }
+    if (is_device_ptr(src)) {
+        *out = src;
+        return AENET_OK;
+    }
+    CK(cudaMemcpyAsync(dev_buf, src, sizeof(T) * count, cudaMemcpyHostToDevice, c.stream), "cudaMemcpyAsync");
+    *out = dev_buf;
+    return AENET_OK;
+}
+
+int validate_types_host(Context &c, int n, const int32_t *types) {
+    if (is_device_ptr(types)) return AENET_OK;  // device arrays are range-checked by the binning kernel
+    for (int i = 0; i < n; ++i)
+        if (types[i] < 0 || types[i] >= c.basis.n_species)
+            return fail(&c, AENET_E_ARG, "types[%d] = %d out of range [0, %d)", i, types[i], c.basis.n_species);
+    return AENET_OK;
+}
+
+void destroy_graph(Context &c) {
+    if (c.md_exec) cudaGraphExecDestroy(c.md_exec);
+    c.md_exec = nullptr;
+    c.md_key.n = -1;
+}
+
+}  // namespace
+}  // namespace aenet
+
+using namespace aenet;
+
+extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int precision, void *stream) {
+    if (!out) return fail(nullptr, AENET_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!m) return fail(nullptr, AENET_E_ARG, "model is NULL");
+    if (m->n_species < 1 || m->n_species > kMaxSpecies)
+        return fail(nullptr, AENET_E_ARG, "n_species must be in [1, %d]", kMaxSpecies);
+    if (!m->type_weight || !m->widths || !m->params) return fail(nullptr, AENET_E_ARG, "NULL model array");
+    if (!(m->rc_rad > 0.0) || !(m->rc_ang > 0.0)) return fail(nullptr, AENET_E_ARG, "cutoffs must be > 0");
+    if (m->order_rad < 0 || m->order_ang < 0 || m->order_rad > kMaxOrder || m->order_ang > kMaxOrder)
+        return fail(nullptr, AENET_E_ARG, "orders must be in [0, %d]", kMaxOrder);
+    const int Kr = m->order_rad + 1, Ka = m->order_ang + 1, D = 2 * (Kr + Ka);
+    const bool supported = (Kr == 17 && Ka == 9) || (Kr == 21 && Ka == 7) || (Kr <= 20 && Ka <= 12) ||
+                           (Kr <= 24 && Ka <= 8);
+    if (!supported || D > kMaxD)
+        return fail(nullptr, AENET_E_ARG,
+                    "unsupported basis orders (%d, %d): need (N_r+1, N_a+1) <= (20, 12) or (24, 8)", Kr, Ka);
+    if (m->n_layers < 2 || m->n_layers > kMaxLayers)
+        return fail(nullptr, AENET_E_ARG, "n_layers must be in [2, %d]", kMaxLayers);
+    if (m->widths[0] != D) return fail(nullptr, AENET_E_ARG, "widths[0] = %d but D = %d", m->widths[0], D);
+    if (m->widths[m->n_layers] != 1) return fail(nullptr, AENET_E_ARG, "output width must be 1");
+    for (int l = 1; l < m->n_layers; ++l)
+        if (m->widths[l] < 1 || m->widths[l] > kMaxWidth)
+            return fail(nullptr, AENET_E_ARG, "hidden width %d out of [1, %d]", m->widths[l], kMaxWidth);
+    if (precision != AENET_FP32 && precision != AENET_BF16 && precision != AENET_BF16X3)
+        return fail(nullptr, AENET_E_ARG, "unknown precision %d", precision);
+
+    aenet_ctx *h = new (std::nothrow) aenet_ctx();
+    if (!h) return fail(nullptr, AENET_E_NOMEM, "host allocation failed");
+    Context &c = h->c;
+    cudaGetDevice(&c.device);
+    c.precision = precision;
+    c.stream = (cudaStream_t)stream;
+    if (!c.stream) {
+        cudaError_t e = cudaStreamCreate(&c.stream);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(nullptr, AENET_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        c.own_stream = true;
+    }
+    c.basis.n_species = m->n_species;
+    c.basis.Kr = Kr;
+    c.basis.Ka = Ka;
+    c.basis.D = D;
+    c.basis.rc_rad = (float)m->rc_rad;
+    c.basis.rc_ang = (float)m->rc_ang;
+    c.basis.rc_max = (float)std::max(m->rc_rad, m->rc_ang);
+    for (int t = 0; t < kMaxSpecies; ++t) c.basis.type_weight[t] = t < m->n_species ? (float)m->type_weight[t] : 0.f;
+    c.net.n_species = m->n_species;
+    c.net.n_layers = m->n_layers;
+    c.net.act_len = 0;
+    c.net.n_params = 0;
+    for (int l = 0; l <= kMaxLayers; ++l) c.net.widths[l] = l <= m->n_layers ? m->widths[l] : 0;
+    for (int l = 0; l <= m->n_layers; ++l) c.net.act_len += m->widths[l];
+    for (int l = 1; l <= m->n_layers; ++l) c.net.n_params += m->widths[l] * m->widths[l - 1] + m->widths[l];
+    if (m->mass) c.mass.assign(m->mass, m->mass + m->n_species);
+
+    const size_t NP = (size_t)m->n_species * c.net.n_params;
+    std::vector<float> P(NP), sh((size_t)m->n_species * D, 0.f), sc((size_t)m->n_species * D, 1.f);
+    for (size_t k = 0; k < NP; ++k) P[k] = (float)m->params[k];
+    for (size_t k = 0; k < sh.size(); ++k) {
+        if (m->in_shift) sh[k] = (float)m->in_shift[k];
+        if (m->in_scale) sc[k] = (float)m->in_scale[k];
+    }
+    auto setup_fail = [&](cudaError_t e, const char *what) {
+        g_setup_error = std::string(what) + ": " + cudaGetErrorString(e);
+        aenet_destroy(h);
+        return AENET_E_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&c.d_params, sizeof(float) * NP)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_shift, sizeof(float) * sh.size())) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_scale, sizeof(float) * sc.size())) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_err, sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_stats, sizeof(unsigned long long) * 4)) != cudaSuccess)
+        return setup_fail(e, "cudaMalloc");
+    for (int k = 0; k <= Context::kStages; ++k)
+        if ((e = cudaEventCreate(&c.ev[k])) != cudaSuccess) return setup_fail(e, "cudaEventCreate");
+    if ((e = cudaMalloc(&c.d_step, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_result, sizeof(double) * 10)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_mass, sizeof(double) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    double masses[kMaxSpecies] = {0};
+    for (int t = 0; t < m->n_species && m->mass; ++t) masses[t] = m->mass[t];
+    if ((e = cudaMemcpy(c.d_params, P.data(), sizeof(float) * NP, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c.d_shift, sh.data(), sizeof(float) * sh.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c.d_scale, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c.d_mass, masses, sizeof(masses), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c.d_err, 0, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(c.d_stats, 0, sizeof(unsigned long long) * 4)) != cudaSuccess ||
+        (e = cudaMemset(c.d_result, 0, sizeof(double) * 10)) != cudaSuccess)
+        return setup_fail(e, "cudaMemcpy");
+    if (precision != AENET_FP32) {
+        if ((e = prepare_bf16_weights(c)) != cudaSuccess) return setup_fail(e, "BF16 weights");
+    }
+    *out = h;
+    return AENET_OK;
+}
+
+extern "C" int aenet_set_stream(aenet_ctx *h, void *stream) {
+    if (!h) return AENET_E_ARG;
+    Context &c = h->c;
+    if (!stream) return fail(&c, AENET_E_ARG, "stream must not be NULL");
+    if (c.own_stream && c.stream) {
+        cudaStreamSynchronize(c.stream);
+        cudaStreamDestroy(c.stream);
+        c.own_stream = false;
+    }
+    c.stream = (cudaStream_t)stream;
+    destroy_graph(c);
+    return AENET_OK;
+}
+
+static int compute_impl(Context &c, int n, const double *pos, const int32_t *types, const double *box,
+                        double *energy, double *forces, double *virial, double *e_atom, float *G_out) {
+    cudaGetLastError();  // a stale error of an unrelated earlier call must not be reported as ours
+    if (n < 0) return fail(&c, AENET_E_ARG, "n_atoms < 0");
+    if (!box) return fail(&c, AENET_E_ARG, "box is NULL");
+    if (n > 0 && (!pos || !types)) return fail(&c, AENET_E_ARG, "pos/types NULL");
+    Grid g;
+    int rc = make_grid(c, box, g);
+    if (rc) return rc;
+    if ((rc = validate_types_host(c, n, types))) return rc;
+    if ((rc = ensure(c, n, g)) || (rc = ensure_stage(c, n))) return rc;
+    if (c.caps.nb == 0) c.caps = estimate_caps(c, n, g);
+    const double *dpos;
+    const int32_t *dtypes;
+    if ((rc = stage_in(c, pos, c.d_pos, 3 * (size_t)n, &dpos))) return rc;
+    if ((rc = stage_in(c, types, c.d_types, (size_t)n, &dtypes))) return rc;
+    const bool f_dev = is_device_ptr(forces), ea_dev = is_device_ptr(e_atom), G_dev = is_device_ptr(G_out);
+    double *dF = forces ? (f_dev ? forces : c.d_forces) : nullptr;
+    double *dE = e_atom ? (ea_dev ? e_atom : c.d_eatom_out) : nullptr;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
+        if (G_out) {
+            if ((rc = check_smem(c, g))) return rc;
+            CK(launch_cells(c, g, n, dpos, dtypes), "cell list");
+            CK(launch_fp_forward(c, g, n), "descriptor kernel");
+        } else {
+            if ((rc = enqueue_compute(c, g, n, dpos, dtypes, dF, dE))) return rc;
+        }
+        rc = read_error_word(c);
+        if (rc != AENET_E_CAPACITY || attempt == 1) break;
+        c.caps.nb *= 2;  // regrow once and retry
+        c.caps.ang *= 2;
+        destroy_graph(c);
+    }
+    if (rc) return rc;
+    if (G_out) {
+        if (G_dev) {
+            CK(launch_unsort_G(c, n, G_out), "unsort");
+        } else {
+            float *tmp = nullptr;
+            CK(cudaMalloc(&tmp, sizeof(float) * (size_t)n * c.basis.D + 4), "cudaMalloc");
+            cudaError_t e1 = launch_unsort_G(c, n, tmp);
+            cudaError_t e2 = e1 == cudaSuccess ? cudaMemcpyAsync(G_out, tmp, sizeof(float) * (size_t)n * c.basis.D,
+                                                                 cudaMemcpyDeviceToHost, c.stream)
+                                               : e1;
+            cudaError_t e3 = cudaStreamSynchronize(c.stream);
+            cudaFree(tmp);
+            if (e2 != cudaSuccess) return cuda_fail(&c, e2, "descriptor copy");
+            if (e3 != cudaSuccess) return cuda_fail(&c, e3, "cudaStreamSynchronize");
+        }
+        CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+        return AENET_OK;
+    }
+    if (energy) CK(cudaMemcpyAsync(energy, c.d_result, sizeof(double), cudaMemcpyDefault, c.stream), "energy copy");
+    if (virial)
+        CK(cudaMemcpyAsync(virial, c.d_result + 1, 9 * sizeof(double), cudaMemcpyDefault, c.stream), "virial copy");
+    if (forces && !f_dev)
+        CK(cudaMemcpyAsync(forces, c.d_forces, 3 * sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c.stream),
+           "forces copy");
+    if (e_atom && !ea_dev)
+        CK(cudaMemcpyAsync(e_atom, c.d_eatom_out, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c.stream),
+           "e_atom copy");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    return AENET_OK;
+}
+
+extern "C" int aenet_compute(aenet_ctx *h, int n, const double *pos, const int32_t *types, const double *box,
+                             double *energy, double *forces, double *virial, double *e_atom) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    return compute_impl(h->c, n, pos, types, box, energy, forces, virial, e_atom, nullptr);
+}
+
+extern "C" int aenet_descriptors(aenet_ctx *h, int n, const double *pos, const int32_t *types, const double *box,
+                                 float *G) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    if (!G) return fail(&h->c, AENET_E_ARG, "G is NULL");
+    return compute_impl(h->c, n, pos, types, box, nullptr, nullptr, nullptr, nullptr, G);
+}
+
+// One MD step on device buffers: kick + drift, forces at the new positions,
+// second kick (and kinetic energy), optional record of (E_pot, E_kin).
+static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
+                           const int32_t *types, double *rec, bool timing) {
+    cudaEvent_t *ev = timing ? c.ev : nullptr;
+    if (ev) CK(mark(c, ev[0]), "event");
+    CK(launch_vv_first(c, n, dt, pos, vel, c.d_forces, types), "vv first");
+    if (ev) CK(mark(c, ev[1]), "event");
+    int rc = enqueue_compute(c, g, n, pos, types, c.d_forces, nullptr, ev ? ev + 2 : nullptr);
+    if (rc) return rc;
+    CK(launch_vv_second(c, n, dt, vel, c.d_forces, types), "vv second");
+    if (ev) CK(mark(c, ev[7]), "event");
+    if (rec) CK(launch_record(c, n, rec, rec + c.cap_rec), "record");
+    return AENET_OK;
+}
+
+extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const int32_t *types,
+                            const double *box, double dt, int n_steps, double *e_pot, double *e_kin, int flags) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    cudaGetLastError();
+    if (c.mass.empty()) return fail(&c, AENET_E_ARG, "model has no masses");
+    if (n <= 0 || !pos || !vel || !types || !box) return fail(&c, AENET_E_ARG, "bad MD arguments");
+    if (n_steps < 0 || !isfinite(dt)) return fail(&c, AENET_E_ARG, "bad n_steps / dt");
+    const bool async = (flags & AENET_MD_ASYNC) != 0;
+    const bool cont = (flags & AENET_MD_CONTINUE) != 0;
+    const bool timing = (flags & AENET_MD_TIMING) != 0;
+    const bool pos_dev = is_device_ptr(pos), vel_dev = is_device_ptr(vel), typ_dev = is_device_ptr(types);
+    const bool rec_dev = (!e_pot || is_device_ptr(e_pot)) && (!e_kin || is_device_ptr(e_kin));
+    if (async && !(pos_dev && vel_dev && typ_dev && rec_dev))
+        return fail(&c, AENET_E_ARG, "AENET_MD_ASYNC needs device pointers");
+    Grid g;
+    int rc = make_grid(c, box, g);
+    if (rc) return rc;
+    if ((rc = validate_types_host(c, n, types))) return rc;
+    if ((rc = ensure(c, n, g)) || (rc = ensure_stage(c, n))) return rc;
+    if (c.caps.nb == 0) c.caps = estimate_caps(c, n, g);
+    double *dpos = pos_dev ? pos : c.d_pos;
+    double *dvel = vel_dev ? vel : c.d_vel;
+    const int32_t *dtypes = typ_dev ? types : c.d_types;
+    if (!pos_dev) CK(cudaMemcpyAsync(dpos, pos, 3 * sizeof(double) * n, cudaMemcpyHostToDevice, c.stream), "pos in");
+    if (!vel_dev) CK(cudaMemcpyAsync(dvel, vel, 3 * sizeof(double) * n, cudaMemcpyHostToDevice, c.stream), "vel in");
+    if (!typ_dev)
+        CK(cudaMemcpyAsync(c.d_types, types, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c.stream), "types in");
+    const bool want_rec = e_pot || e_kin;
+    if (want_rec && n_steps + 1 > c.cap_rec) {
+        if (c.d_rec) cudaFree(c.d_rec);
+        c.d_rec = nullptr;
+        c.cap_rec = 0;
+        CK(cudaMalloc(&c.d_rec, sizeof(double) * 2 * (size_t)(n_steps + 1)), "cudaMalloc");
+        c.cap_rec = n_steps + 1;
+        destroy_graph(c);
+    }
+    double *rec = want_rec ? c.d_rec : nullptr;
+    if (!async) CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
+    if (want_rec) CK(cudaMemsetAsync(c.d_step, 0, sizeof(int), c.stream), "cudaMemsetAsync");
+    // frame 0: forces at the initial positions (unless continuing), kinetic energy
+    if (!cont) {
+        if ((rc = enqueue_compute(c, g, n, dpos, dtypes, c.d_forces, nullptr))) return rc;
+    }
+    if (want_rec) {
+        CK(launch_vv_second(c, n, 0.0, dvel, c.d_forces, dtypes), "kinetic energy");
+        CK(launch_record(c, n, rec, rec + c.cap_rec), "record");
+    }
+    if (n_steps > 0) {
+        const bool same = c.md_exec && c.md_key.n == n && c.md_key.pos == dpos && c.md_key.vel == dvel &&
+                          c.md_key.types == dtypes && c.md_key.box[0] == box[0] && c.md_key.box[1] == box[1] &&
+                          c.md_key.box[2] == box[2] && c.md_key.dt == dt && c.md_key.rec == rec &&
+                          c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
+                          c.md_key.caps.ang == c.caps.ang && c.md_key.timing == timing;
+        if (!same) {
+            destroy_graph(c);
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            int src = enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec, timing);
+            cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
+            if (src) {
+                if (graph) cudaGraphDestroy(graph);
+                return src;
+            }
+            if (ce != cudaSuccess) return cuda_fail(&c, ce, "end capture");
+            size_t n_nodes = 0;
+            c.md_kernels = 0;
+            if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+                std::vector<cudaGraphNode_t> nodes(n_nodes);
+                if (cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess) {
+                    for (size_t k = 0; k < n_nodes; ++k) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                            ++c.md_kernels;
+                    }
+                }
+            }
+            ce = cudaGraphInstantiate(&c.md_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                c.md_exec = nullptr;
+                return cuda_fail(&c, ce, "graph instantiate");
+            }
+            c.md_key.n = n;
+            c.md_key.pos = dpos;
+            c.md_key.vel = dvel;
+            c.md_key.types = dtypes;
+            for (int a = 0; a < 3; ++a) c.md_key.box[a] = box[a];
+            c.md_key.dt = dt;
+            c.md_key.rec = rec;
+            c.md_key.stream = c.stream;
+            c.md_key.caps = c.caps;
+            c.md_key.timing = timing;
+        }
+        for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(c.md_exec, c.stream), "graph launch");
+    }
+    if (want_rec) {
+        if (e_pot) CK(cudaMemcpyAsync(e_pot, rec, sizeof(double) * (n_steps + 1), cudaMemcpyDefault, c.stream), "e_pot");
+        if (e_kin)
+            CK(cudaMemcpyAsync(e_kin, rec + c.cap_rec, sizeof(double) * (n_steps + 1), cudaMemcpyDefault, c.stream),
+               "e_kin");
+    }
+    if (!pos_dev) CK(cudaMemcpyAsync(pos, dpos, 3 * sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "pos out");
+    if (!vel_dev) CK(cudaMemcpyAsync(vel, dvel, 3 * sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "vel out");
+    if (async) return AENET_OK;
+    return read_error_word(c);
+}
+
+extern "C" int aenet_neighbor_stats(aenet_ctx *h, int64_t *out) {
+    if (!h || !out) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
+    Context &c = h->c;
+    unsigned long long st[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(st, c.d_stats, sizeof(st), cudaMemcpyDeviceToHost, c.stream), "stats copy");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    for (int k = 0; k < 3; ++k) out[k] = (int64_t)st[k];
+    return AENET_OK;
+}
+
+extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_step) {
+    if (!h || !ms) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
+    Context &c = h->c;
+    if (!c.md_exec || !c.md_key.timing) return fail(&c, AENET_E_STATE, "no MD step was run with AENET_MD_TIMING");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    for (int k = 0; k < Context::kStages; ++k) CK(cudaEventElapsedTime(&ms[k], c.ev[k], c.ev[k + 1]), "elapsed");
+    if (kernels_per_step) *kernels_per_step = c.md_kernels;
+    return AENET_OK;
+}
+
+extern "C" int aenet_check(aenet_ctx *h) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    return read_error_word(h->c);
+}
+
+extern "C" const char *aenet_last_error(const aenet_ctx *h) {
+    if (!h) return g_setup_error.c_str();
+    return h->c.err.c_str();
+}
+
+extern "C" void aenet_destroy(aenet_ctx *h) {
+    if (!h) return;
+    Context &c = h->c;
+    destroy_graph(c);
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    void *ptrs[] = {c.d_params, c.d_shift, c.d_scale, c.d_wbf, c.d_mass, c.d_pos4, c.d_tmp4, c.d_perm,
+                    c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
+                    c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_pos, c.d_vel,
+                    c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int k = 0; k <= Context::kStages; ++k)
+        if (c.ev[k]) cudaEventDestroy(c.ev[k]);
+    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+    delete h;
+}

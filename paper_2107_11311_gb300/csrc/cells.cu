@@ -1,0 +1,113 @@
+// Rows a1-a2 of the path: wrap FP64 positions into the box, bin them into the
+// cell grid (edge >= the largest cutoff) and sort them by cell.
+//
+// Every atom is stored as FP32 coordinates RELATIVE TO ITS CELL ORIGIN
+// (u = x_wrapped - c h, computed in FP64 and then rounded), so that a
+// displacement d = u_j + offset*h - u_i carries an absolute error of a few 1e-7 A
+// whatever the box size; absolute FP32 coordinates in a 150 A box would carry
+// ~1e-5 A.
+#include "aenet_internal.cuh"
+
+namespace aenet {
+
+__global__ void k_bin_count(int n, int n_species, const double *__restrict__ pos,
+                            const int32_t *__restrict__ types, Grid g,
+                            float4 *__restrict__ tmp4, int *__restrict__ cell_of, int *__restrict__ slot,
+                            int *__restrict__ cell_count, unsigned *__restrict__ err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int ci[3];
+    float u[3];
+    bool finite = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = pos[3 * i + a];
+        if (!isfinite(x)) {
+            finite = false;
+            x = 0.0;
+        }
+        double L = g.box[a];
+        double w = x - floor(x / L) * L;
+        if (w >= L) w -= L;
+        if (w < 0.0) w = 0.0;
+        int c = (int)floor(w / g.h[a]);
+        c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+        ci[a] = c;
+        u[a] = (float)(w - c * g.h[a]);
+    }
+    if (!finite) atomicOr(err, kErrNonfinite);
+    int t = types[i];
+    if (t < 0 || t >= n_species) {
+        atomicOr(err, kErrType);
+        t = 0;
+    }
+    int cell = (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
+    tmp4[i] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+    cell_of[i] = cell;
+    slot[i] = atomicAdd(&cell_count[cell], 1);
+}
+
+// Exclusive scan of the cell counts by one CTA (cell counts are O(1e4-1e5)).
+__global__ void k_scan_cells(int ncell, const int *__restrict__ count, int *__restrict__ start) {
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ncell; base += blockDim.x) {
+        int i = base + tid;
+        int v = i < ncell ? count[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int nw = blockDim.x >> 5;
+            int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            if (lane < nw) warp_sums[lane] = s;
+        }
+        __syncthreads();
+        int excl = carry + (wid ? warp_sums[wid - 1] : 0) + x - v;
+        if (i < ncell) start[i] = excl;
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (tid == 0) start[ncell] = carry;
+}
+
+__global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__restrict__ cell_of,
+                          const int *__restrict__ slot, const int *__restrict__ cell_start,
+                          float4 *__restrict__ pos4, int *__restrict__ perm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = cell_start[cell_of[i]] + slot[i];
+    pos4[s] = tmp4[i];
+    perm[s] = i;
+}
+
+cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types) {
+    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * g.ncell, c.stream);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_bin_count<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.basis.n_species, pos, types, g, c.d_tmp4, c.d_cell_of, c.d_slot,
+                                                           c.d_cell_count, c.d_err);
+    }
+    k_scan_cells<<<1, 1024, 0, c.stream>>>(g.ncell, c.d_cell_count, c.d_cell_start);
+    if (n > 0) {
+        k_scatter<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_tmp4, c.d_cell_of, c.d_slot, c.d_cell_start,
+                                                         c.d_pos4, c.d_perm);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace aenet

@@ -1,0 +1,293 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, plus the edge cases and error paths of the boundary.
+
+Tolerances (FP32 form, spec bound): energy |dE|/N <= 0.5 meV/atom and
+force RMS error <= 1 meV/A; virial within 1e-4 relative to its largest
+component. Descriptor columns: every coefficient is an FP32 sum of terms with
+|T_a| <= 1, so its rounding error is bounded by a small multiple of the FP32
+unit roundoff u = 6e-8 times the sum of |terms|; that sum is at most
+max|s|^p * G_0 of its block (G_0 = the a = 0 coefficient, p = 0 unweighted,
+1 weighted radial, 2 weighted angular). The test allows 32 u times that bound.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2107_11311_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E_TOL = 5e-4      # eV/atom
+F_RMS_TOL = 1e-3  # eV/A
+
+
+@pytest.fixture(scope="module")
+def gpu_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2107_11311_gb300 import aenet
+    return aenet
+
+
+def _cases():
+    return {
+        "water_192": ("water", inputs.water_192),
+        "water_small_box": ("water", lambda: inputs.water(8, 6.6, seed=3)),
+        "amorphous_small_box": ("amorphous", lambda: inputs.amorphous(32, seed=4)),
+        "amorphous_2000": ("amorphous", lambda: inputs.amorphous(2000, seed=5)),
+    }
+
+
+def _check_efw(ref, got, n, what):
+    de = abs(got["energy"] - ref["energy"]) / max(n, 1)
+    assert de <= E_TOL, f"{what}: |dE|/N = {de}"
+    if n:
+        df = got["forces"] - ref["forces"]
+        rms = float(np.sqrt((df ** 2).mean()))
+        assert rms <= F_RMS_TOL, f"{what}: force RMS error {rms}"
+        assert np.abs(df).max() <= 10 * F_RMS_TOL, f"{what}: max force error {np.abs(df).max()}"
+        np.testing.assert_allclose(got["e_atom"], ref["e_atom"], atol=2e-4 * (1 + np.abs(ref["e_atom"]).max()))
+    scale = max(1.0, np.abs(ref["virial"]).max())
+    np.testing.assert_allclose(got["virial"], ref["virial"], atol=1e-4 * scale)
+
+
+def _descriptor_tol(G, m):
+    Kr, Ka = m.order_rad + 1, m.order_ang + 1
+    smax = float(np.abs(m.type_weights).max())
+    B = np.empty_like(G)
+    B[:, :Kr] = G[:, [0]]
+    B[:, Kr:Kr + Ka] = G[:, [Kr]]
+    B[:, Kr + Ka:2 * Kr + Ka] = smax * G[:, [0]]
+    B[:, 2 * Kr + Ka:] = smax ** 2 * G[:, [Kr]]
+    return 32 * 6e-8 * np.abs(B) + 1e-6
+
+
+@pytest.mark.parametrize("case", list(_cases()))
+def test_descriptor_parity(gpu_mod, case):
+    fam, make = _cases()[case]
+    st = make()
+    m = inputs.make_model(fam)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    G = g.descriptors(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box, want_G=True, want_forces=False)["G"]
+    tol = _descriptor_tol(ref, m)
+    bad = np.abs(G - ref) > tol
+    assert not bad.any(), (f"{bad.sum()} coefficients off; worst excess "
+                           f"{(np.abs(G - ref) / tol).max():.2f}x the bound")
+
+
+@pytest.mark.parametrize("case", list(_cases()))
+def test_energy_force_virial_parity(gpu_mod, case):
+    fam, make = _cases()[case]
+    st = make()
+    m = inputs.make_model(fam)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    got = g.compute(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, got, st.n, case)
+
+
+def test_device_and_host_pointers_agree(gpu_mod):
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    host = g.compute(st.pos, st.types, st.box)
+    pos = torch.tensor(st.pos, device="cuda")
+    types = torch.tensor(st.types, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F = torch.zeros((st.n, 3), dtype=torch.float64, device="cuda")
+    W = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    Ea = torch.zeros(st.n, dtype=torch.float64, device="cuda")
+    g.compute(pos, types, st.box, energy=E, forces=F, virial=W, e_atom=Ea)
+    torch.cuda.synchronize()
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, dict(energy=E.item(), forces=F.cpu().numpy(), virial=W.cpu().numpy(),
+                         e_atom=Ea.cpu().numpy()), st.n, "device pointers")
+    assert abs(E.item() - host["energy"]) < 1e-6
+
+
+def test_full_size_water_12288(gpu_mod):
+    """The 4,096-molecule water box at 1.0 g/cm^3: every output against the oracle."""
+    st = inputs.water_12288()
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    got = g.compute(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, got, st.n, "water_12288")
+
+
+def test_full_size_amorphous_27000(gpu_mod):
+    st = inputs.amorphous_27000()
+    m = inputs.make_model("amorphous")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    got = g.compute(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, got, st.n, "amorphous_27000")
+
+
+def test_invariances_on_gpu(gpu_mod):
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    r0 = g.compute(st.pos, st.types, st.box)
+    r1 = g.compute(st.pos + np.array([1.7, -40.2, 3.3]), st.types, st.box)
+    p = np.random.default_rng(0).permutation(st.n)
+    r2 = g.compute(st.pos[p], st.types[p], st.box)
+    assert abs(r1["energy"] - r0["energy"]) / st.n < 1e-5
+    assert abs(r2["energy"] - r0["energy"]) / st.n < 1e-5
+    np.testing.assert_allclose(r2["forces"], r0["forces"][p], atol=1e-4)
+    np.testing.assert_allclose(r0["forces"].sum(0), 0.0, atol=1e-3)
+
+
+# ----------------------------------------------------------------- edge cases
+
+def test_empty_and_isolated(gpu_mod):
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    r = g.compute(np.zeros((0, 3)), np.zeros(0, dtype=np.int32), np.full(3, 10.0))
+    assert r["energy"] == 0.0
+    pos = np.array([[1.0, 2.0, 3.0]])
+    types = np.array([1], dtype=np.int32)
+    r = g.compute(pos, types, np.full(3, 30.0))
+    ref = O.compute(m, pos, types, np.full(3, 30.0))
+    assert abs(r["energy"] - ref["energy"]) < 1e-4
+    np.testing.assert_allclose(r["forces"], 0.0, atol=1e-7)
+
+
+@pytest.mark.parametrize("what", ["type", "nan", "overlap", "box"])
+def test_errors_are_reported(gpu_mod, what):
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    st = inputs.water_192()
+    pos, types, box = st.pos.copy(), st.types.copy(), st.box.copy()
+    code = {"type": -1, "nan": -4, "overlap": -5, "box": -1}[what]
+    if what == "type":
+        types[5] = 7
+    elif what == "nan":
+        pos[3, 1] = np.nan
+    elif what == "overlap":
+        pos[4] = pos[7]
+    else:
+        box[1] = -1.0
+    with pytest.raises(gpu_mod.AenetError) as ei:
+        g.compute(pos, types, box)
+    assert ei.value.code == code
+    # the context stays usable after a reported error
+    r = g.compute(st.pos, st.types, st.box)
+    assert np.isfinite(r["energy"])
+
+
+def test_device_types_out_of_range_reported(gpu_mod):
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    st = inputs.water_192()
+    types = torch.tensor(st.types, device="cuda")
+    types[10] = 5
+    with pytest.raises(gpu_mod.AenetError) as ei:
+        g.compute(torch.tensor(st.pos, device="cuda"), types, st.box,
+                  energy=torch.zeros(1, dtype=torch.float64, device="cuda"))
+    assert ei.value.code == -1
+
+
+# ------------------------------------------------------------------------ MD
+
+def test_md_matches_oracle_trajectory(gpu_mod):
+    """10 velocity-Verlet steps at 0.5 fs from seeded 300 K velocities: per-frame
+    energies and final positions against the oracle's own integration."""
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    xo, vo, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 10)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    pos, vel = st.pos.copy(), v0.copy()
+    ep, ek = np.zeros(11), np.zeros(11)
+    g.md_nve(pos, vel, st.types, st.box, 5e-4, 10, e_pot=ep, e_kin=ek)
+    assert np.abs(ep - epo).max() / st.n <= E_TOL
+    np.testing.assert_allclose(ek, eko, rtol=1e-5)
+    np.testing.assert_allclose(pos, xo, atol=1e-5)
+    np.testing.assert_allclose(vel, vo, atol=1e-2)
+
+
+def test_md_device_async_continue_equals_one_call(gpu_mod):
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    p1, v1 = torch.tensor(st.pos, device="cuda"), torch.tensor(v0, device="cuda")
+    types = torch.tensor(st.types, device="cuda")
+    g.md_nve(p1, v1, types, st.box, 5e-4, 6)
+    p2, v2 = torch.tensor(st.pos, device="cuda"), torch.tensor(v0, device="cuda")
+    g2 = gpu_mod.AenetGPU(m, "fp32")
+    g2.md_nve(p2, v2, types, st.box, 5e-4, 2)
+    for _ in range(4):
+        g2.md_nve(p2, v2, types, st.box, 5e-4, 1, flags=gpu_mod.AENET_MD_ASYNC | gpu_mod.AENET_MD_CONTINUE)
+    g2.check()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(p2.cpu().numpy(), p1.cpu().numpy(), atol=1e-9)
+
+
+def _md_gpu(gpu_mod, m, st, v0, dt, n_steps):
+    g = gpu_mod.AenetGPU(m, "fp32")
+    pos, vel = st.pos.copy(), v0.copy()
+    ep, ek = np.zeros(n_steps + 1), np.zeros(n_steps + 1)
+    g.md_nve(pos, vel, st.types, st.box, dt, n_steps, e_pot=ep, e_kin=ek)
+    return ep + ek
+
+
+def test_md_energy_error_scales_as_dt_squared_on_gpu(gpu_mod):
+    """Velocity Verlet on FP32 forces keeps the FP64 integrator's order: the
+    total-energy error over 10 fs drops ~4x when dt is halved."""
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    errs = []
+    for dt in (5e-4, 2.5e-4):
+        et = _md_gpu(gpu_mod, m, st, v0, dt, int(round(0.01 / dt)))
+        errs.append(np.abs(et - et[0]).max())
+    assert 2.5 < errs[0] / errs[1] < 6.0, errs
+
+
+def test_md_1000_steps_energy_error_matches_oracle(gpu_mod):
+    """1,000 steps at 0.5 fs of the 192-atom water box: the GPU's total-energy
+    error stays at the level of the FP64 oracle's own velocity-Verlet error on
+    the same trajectory start (the random-weight potential heats the lattice
+    start strongly, so both are far from zero)."""
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    _, _, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 1000)
+    eto = epo + eko
+    et = _md_gpu(gpu_mod, m, st, v0, 5e-4, 1000)
+    d_gpu = np.abs(et - et[0]).max() / st.n
+    d_ora = np.abs(eto - eto[0]).max() / st.n
+    print(f"max |E_tot - E_tot(0)|/N: GPU {d_gpu:.3e}, oracle {d_ora:.3e} eV/atom")
+    assert d_gpu <= 1.5 * d_ora + 2e-3
+
+
+def test_md_water_12288_1000_steps(gpu_mod):
+    """1,000 graph-replayed NVE steps (0.5 ps) of the 12,288-atom water box:
+    frame 0 against the oracle; the per-atom total-energy error of the whole run
+    stays at the level the oracle shows for the same potential and step."""
+    st = inputs.water_12288()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=12)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    pos = torch.tensor(st.pos, device="cuda")
+    vel = torch.tensor(v0, device="cuda")
+    types = torch.tensor(st.types, device="cuda")
+    ep = torch.zeros(1001, dtype=torch.float64, device="cuda")
+    ek = torch.zeros(1001, dtype=torch.float64, device="cuda")
+    g.md_nve(pos, vel, types, st.box, 5e-4, 1000, e_pot=ep, e_kin=ek)
+    et = (ep + ek).cpu().numpy()
+    assert np.isfinite(et).all() and np.isfinite(pos.cpu().numpy()).all()
+    drift = np.abs(et - et[0]).max() / st.n
+    # the oracle's error for this potential at 0.5 fs on the 192-atom box
+    s2 = inputs.water_192()
+    v2 = inputs.maxwell_boltzmann(m.masses[s2.types], 300.0, seed=2)
+    _, _, epo, eko = O.md_nve(m, s2.pos, v2, s2.types, s2.box, 5e-4, 1000)
+    ref = np.abs((epo + eko) - (epo[0] + eko[0])).max() / s2.n
+    print(f"water_12288: max |E_tot - E_tot(0)|/N = {drift:.3e} eV/atom (oracle, 192 atoms: {ref:.3e})")
+    assert drift <= 2.0 * ref + 5e-3
+    r0 = O.compute(m, st.pos, st.types, st.box)
+    assert abs(ep[0].item() - r0["energy"]) / st.n <= E_TOL
