@@ -263,30 +263,33 @@ def main():
     stage_avg = {s: stage_sum[s] / args.steps for s in stage_sum}
 
     # ---- end to end through the C ABI with pinned host buffers
-    hpos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
-    hvel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
-    htypes = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    hep = torch.empty(2, dtype=torch.float64, pin_memory=True)
-    hek = torch.empty(2, dtype=torch.float64, pin_memory=True)
-    hpos.copy_(pos.cpu())
-    hvel.copy_(vel.cpu())
-    htypes.copy_(types.cpu())
-    e2 = AenetGPU(m, args.precision, stream=stream.cuda_stream)
-    e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
-    for _ in range(3):
-        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = world * n * args.e2e_steps / t_e2e
-    h2d = hpos.numel() * 8 + hvel.numel() * 8 + htypes.numel() * 4
-    d2h = hpos.numel() * 8 + hvel.numel() * 8 + hep.numel() * 8 + hek.numel() * 8
-    e2.close()
+    e2e = None
+    if args.e2e_steps > 0:
+        hpos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        hvel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        htypes = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        hep = torch.empty(2, dtype=torch.float64, pin_memory=True)
+        hek = torch.empty(2, dtype=torch.float64, pin_memory=True)
+        hpos.copy_(pos.cpu())
+        hvel.copy_(vel.cpu())
+        htypes.copy_(types.cpu())
+        e2 = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
+        for _ in range(3):
+            e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = hpos.numel() * 8 + hvel.numel() * 8 + htypes.numel() * 4
+        d2h = hpos.numel() * 8 + hvel.numel() * 8 + hep.numel() * 8 + hek.numel() * 8
+        e2e = {"value": world * n * args.e2e_steps / t_e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+        e2.close()
 
     if rank != 0:
         gpu.close()
@@ -318,7 +321,7 @@ def main():
                    "neighbour_entries": stats[0], "angular_pairs": stats[2]},
         "stage_ms": {s: round(v, 5) for s, v in stage_avg.items()},
         "gpu_launches": kernels_per_step * args.steps,
-        "e2e": {"value": e2e_value, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
