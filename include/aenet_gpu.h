@@ -170,6 +170,40 @@ int aenet_neighbor_stats(aenet_ctx *ctx, int64_t out[3]);
  */
 int aenet_md_stage_times(aenet_ctx *ctx, float ms[7], int *kernels_per_step);
 
+/*
+ * Descriptor without a context and without any device allocation.
+ *
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc when they need descriptors -- a host program whose GPU memory
+ * is handed out only by its own fixed pool, code running while another
+ * component owns the allocator, or a plugin that must not grow the process's
+ * device footprint after start-up. It computes the same G as
+ * aenet_descriptors() (same kernels) and allocates nothing: its scratch is one
+ * fixed file-scope __device__ array of about 5.0 MB (cell-sorted coordinates,
+ * cell table, sorted descriptor rows, error word) that every GPU which loads
+ * this library holds until the process exits.
+ *   n_atoms      0 .. AENET_NOALLOC_MAX_ATOMS; larger systems return
+ *                AENET_E_CAPACITY (as do boxes with more than
+ *                AENET_NOALLOC_MAX_CELLS cells of edge >= the largest cutoff)
+ *   pos, types   DEVICE pointers, [n_atoms * 3] double and [n_atoms] int32
+ *   box          [3] double, HOST
+ *   n_species, type_weight (HOST [n_species]), rc_rad, order_rad, rc_ang,
+ *   order_ang    the basis, as in aenet_model_desc
+ *   G            DEVICE [n_atoms * D] float32 output, input order
+ *   stream       cudaStream_t (NULL = legacy default stream)
+ * The first call on a device looks up the device address of the scratch
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. Every call shares the one scratch array, so
+ * calls whose GPU work overlaps (other host threads, other streams) race and
+ * must be serialised by the caller. Synchronises `stream`. Messages are read
+ * with aenet_last_error(NULL).
+ */
+#define AENET_NOALLOC_MAX_ATOMS 16384
+#define AENET_NOALLOC_MAX_CELLS 16384
+int aenet_descriptors_noalloc(int n_atoms, const double *pos, const int32_t *types, const double *box,
+                              int n_species, const double *type_weight, double rc_rad, int order_rad,
+                              double rc_ang, int order_ang, float *G, void *stream);
+
 /* Synchronise the context's stream and report any recorded device error. */
 int aenet_check(aenet_ctx *ctx);
 

@@ -64,6 +64,7 @@ def load(build_if_missing: bool = True):
     lib.aenet_md_nve.argtypes = [P, I, P, P, P, P, D, I, P, P, I]
     lib.aenet_check.argtypes = [P]
     lib.aenet_neighbor_stats.argtypes = [P, P]
+    lib.aenet_descriptors_noalloc.argtypes = [I, P, P, P, I, P, D, I, D, I, P, P]
     lib.aenet_md_stage_times.argtypes = [P, P, P]
     lib.aenet_last_error.argtypes = [P]
     lib.aenet_last_error.restype = C.c_char_p
@@ -113,6 +114,26 @@ def _current_stream():
     if torch.cuda.is_available():
         return C.c_void_p(torch.cuda.current_stream().cuda_stream)
     return None
+
+
+NOALLOC_MAX_ATOMS = 16384
+
+
+def descriptors_noalloc(model, pos, types, box, out, stream=None):
+    """Descriptor through the allocation-free entry point (no context, no device
+    allocation; for callers that cannot call cudaMalloc). ``pos``, ``types`` and
+    ``out`` [n, D] float32 must be CUDA tensors; at most NOALLOC_MAX_ATOMS atoms."""
+    lib = load()
+    pos, types = _as(pos, np.float64), _as(types, np.int32)
+    box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    tw = np.ascontiguousarray(model.type_weights, dtype=np.float64)
+    st = stream if stream is not None else _current_stream()
+    rc = lib.aenet_descriptors_noalloc(int(pos.shape[0]), _ptr(pos), _ptr(types), _ptr(box), int(model.n_species),
+                                       _ptr(tw), float(model.rc_rad), int(model.order_rad), float(model.rc_ang),
+                                       int(model.order_ang), _ptr(out), st)
+    if rc != 0:
+        raise AenetError(rc, lib.aenet_last_error(None).decode())
+    return out
 
 
 class AenetGPU:

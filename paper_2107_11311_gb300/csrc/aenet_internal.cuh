@@ -160,6 +160,9 @@ cudaError_t launch_vv_second(Context &c, int n, double dt, double *vel, const do
                              const int32_t *types);
 cudaError_t launch_record(Context &c, int n, double *rec_pot, double *rec_kin);
 
+// Message reported by aenet_last_error(NULL) for calls made without a context.
+void set_context_free_error(const char *msg);
+
 // Dynamic shared memory bytes of the fingerprint kernels for given capacities.
 size_t fp_smem_bytes(const Grid &g, const Caps &caps, bool backward);
 size_t ann_smem_bytes(const Context &c);

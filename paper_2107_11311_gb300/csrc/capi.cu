@@ -222,6 +222,9 @@ void destroy_graph(Context &c) {
 }
 
 }  // namespace
+
+void set_context_free_error(const char *msg) { g_setup_error = msg; }
+
 }  // namespace aenet
 
 using namespace aenet;

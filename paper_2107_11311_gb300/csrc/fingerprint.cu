@@ -21,6 +21,8 @@
 //    FP64 partial.
 // Displacements are formed from cell-local FP32 coordinates plus the exact cell
 // offset, so their error does not grow with the box size.
+#include <stdio.h>
+
 #include "aenet_internal.cuh"
 
 namespace aenet {
@@ -602,3 +604,214 @@ cudaError_t launch_fp_backward(Context &c, const Grid &g, int n) {
 }
 
 }  // namespace aenet
+
+// ---------------------------------------------------------------------------
+// Allocation-free descriptor entry point (aenet_descriptors_noalloc).
+//
+// Some callers cannot allocate device memory at the time they need descriptors:
+// a host program that hands every allocation to its own fixed memory pool, code
+// that runs while another component owns the allocator, or a plugin that must
+// not grow the process's GPU footprint after start-up. For them this entry point
+// computes the same descriptor as aenet_descriptors() without a context and
+// without any cudaMalloc/cudaFree: its scratch (cell-sorted coordinates, cell
+// table, sorted descriptor rows, error word) is one file-scope __device__ array
+// of fixed size, which every GPU that loads this library holds until the
+// process exits. The caller passes device inputs and the device output.
+#include <mutex>
+
+namespace aenet {
+
+__global__ void k_bin_count(int n, int n_species, const double *__restrict__ pos,
+                            const int32_t *__restrict__ types, Grid g, float4 *__restrict__ tmp4,
+                            int *__restrict__ cell_of, int *__restrict__ slot, int *__restrict__ cell_count,
+                            unsigned *__restrict__ err);
+__global__ void k_scan_cells(int ncell, const int *__restrict__ count, int *__restrict__ start);
+__global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__restrict__ cell_of,
+                          const int *__restrict__ slot, const int *__restrict__ cell_start,
+                          float4 *__restrict__ pos4, int *__restrict__ perm);
+
+namespace {
+
+constexpr size_t kNaAlign = 256;
+constexpr size_t na_round(size_t x) { return (x + kNaAlign - 1) / kNaAlign * kNaAlign; }
+constexpr size_t kNaOffTmp4 = 0;
+constexpr size_t kNaOffPos4 = kNaOffTmp4 + na_round(sizeof(float4) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffPerm = kNaOffPos4 + na_round(sizeof(float4) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffCellOf = kNaOffPerm + na_round(sizeof(int) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffSlot = kNaOffCellOf + na_round(sizeof(int) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffCount = kNaOffSlot + na_round(sizeof(int) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffStart = kNaOffCount + na_round(sizeof(int) * AENET_NOALLOC_MAX_CELLS);
+constexpr size_t kNaOffG = kNaOffStart + na_round(sizeof(int) * (AENET_NOALLOC_MAX_CELLS + 1));
+constexpr size_t kNaOffErr = kNaOffG + na_round(sizeof(float) * kMaxD * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaBytes = kNaOffErr + na_round(sizeof(unsigned) + 4 * sizeof(unsigned long long));
+
+// The scratch itself. Host code must not pass this symbol to a kernel: on the
+// host it names a stand-in, not the device address (see na_scratch()).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current) and cached.
+cudaError_t na_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_na_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void k_na_unsort(int n, int D, const int *__restrict__ perm, const float *__restrict__ Gs,
+                            float *__restrict__ G) {
+    const size_t total = (size_t)n * D;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(k / D), c = (int)(k % D);
+        G[(size_t)perm[s] * D + c] = Gs[k];
+    }
+}
+
+template <int KRT, int KAT, bool EXACT>
+cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaStream_t st, const float4 *pos4,
+                         const int *cell_start, float *Gs, unsigned long long *stats, unsigned *err) {
+    const size_t smem = make_layout(g.n_off, caps.nb, caps.ang, false).total;
+    auto kern = k_fingerprint<KRT, KAT, EXACT, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<g.ncell, kThreads, smem, st>>>(B, g, caps, pos4, cell_start, Gs, nullptr, nullptr, nullptr, stats, err);
+    return cudaGetLastError();
+}
+
+int na_fail(int code, const char *msg) {
+    set_context_free_error(msg);
+    return code;
+}
+
+bool na_is_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace aenet
+
+extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t *types, const double *box,
+                                         int n_species, const double *type_weight, double rc_rad, int order_rad,
+                                         double rc_ang, int order_ang, float *G, void *stream) {
+    using namespace aenet;
+    cudaGetLastError();
+    if (n < 0 || n > AENET_NOALLOC_MAX_ATOMS) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "n_atoms = %d is outside [0, %d], the fixed scratch limit of this entry point", n,
+                 AENET_NOALLOC_MAX_ATOMS);
+        return na_fail(AENET_E_CAPACITY, msg);
+    }
+    if (!box || !type_weight || n_species < 1 || n_species > kMaxSpecies || !(rc_rad > 0.0) || !(rc_ang > 0.0) ||
+        order_rad < 0 || order_ang < 0)
+        return na_fail(AENET_E_ARG, "invalid basis arguments");
+    const int Kr = order_rad + 1, Ka = order_ang + 1, D = 2 * (Kr + Ka);
+    const bool supported = (Kr == 17 && Ka == 9) || (Kr == 21 && Ka == 7) || (Kr <= 20 && Ka <= 12) ||
+                           (Kr <= 24 && Ka <= 8);
+    if (!supported || D > kMaxD) return na_fail(AENET_E_ARG, "unsupported basis orders");
+    if (n > 0 && (!pos || !types || !G || !na_is_device(pos) || !na_is_device(types) || !na_is_device(G)))
+        return na_fail(AENET_E_ARG, "pos, types and G must be device pointers");
+    Basis B{};
+    B.n_species = n_species;
+    B.Kr = Kr;
+    B.Ka = Ka;
+    B.D = D;
+    B.rc_rad = (float)rc_rad;
+    B.rc_ang = (float)rc_ang;
+    B.rc_max = (float)(rc_rad > rc_ang ? rc_rad : rc_ang);
+    for (int t = 0; t < kMaxSpecies; ++t) B.type_weight[t] = t < n_species ? (float)type_weight[t] : 0.f;
+    Grid g{};
+    g.ncell = 1;
+    g.n_off = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !isfinite(box[a])) return na_fail(AENET_E_ARG, "box lengths must be finite and > 0");
+        int nc = (int)floor(box[a] / B.rc_max);
+        nc = nc < 1 ? 1 : (nc > 1024 ? 1024 : nc);
+        g.nc[a] = nc;
+        g.box[a] = box[a];
+        g.h[a] = box[a] / nc;
+        g.hf[a] = (float)g.h[a];
+        g.m[a] = (int)ceil(B.rc_max / g.h[a]);
+        g.ncell *= nc;
+        g.n_off *= 2 * g.m[a] + 1;
+    }
+    if (g.ncell > AENET_NOALLOC_MAX_CELLS)
+        return na_fail(AENET_E_CAPACITY, "the box has more cells than the fixed scratch of this entry point holds");
+    if (g.n_off > 4096) return na_fail(AENET_E_ARG, "box too small for the cutoff");
+    if (n == 0) return AENET_OK;
+
+    unsigned char *base = nullptr;
+    cudaError_t e = na_scratch(&base);
+    if (e != cudaSuccess) return na_fail(AENET_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+    float4 *tmp4 = reinterpret_cast<float4 *>(base + kNaOffTmp4);
+    float4 *pos4 = reinterpret_cast<float4 *>(base + kNaOffPos4);
+    int *perm = reinterpret_cast<int *>(base + kNaOffPerm);
+    int *cell_of = reinterpret_cast<int *>(base + kNaOffCellOf);
+    int *slot = reinterpret_cast<int *>(base + kNaOffSlot);
+    int *count = reinterpret_cast<int *>(base + kNaOffCount);
+    int *start = reinterpret_cast<int *>(base + kNaOffStart);
+    float *Gs = reinterpret_cast<float *>(base + kNaOffG);
+    unsigned *err = reinterpret_cast<unsigned *>(base + kNaOffErr);
+    unsigned long long *stats = reinterpret_cast<unsigned long long *>(base + kNaOffErr + 8);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // mean-density capacities (1.5x the expected count + 32), one regrow on overflow
+    const double rho = n / (box[0] * box[1] * box[2]);
+    auto cap = [&](double rc) {
+        int k = (int)(1.5 * rho * 4.18879020478639 * rc * rc * rc + 32.0);
+        return ((k + 31) / 32) * 32;
+    };
+    Caps caps{cap(B.rc_max) > 64 ? cap(B.rc_max) : 64, cap(B.rc_ang) > 32 ? cap(B.rc_ang) : 32};
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    unsigned w = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (optin > 0 && make_layout(g.n_off, caps.nb, caps.ang, false).total > (size_t)optin)
+            return na_fail(AENET_E_CAPACITY, "neighbour lists exceed the shared memory of one CTA");
+        // the scratch keeps the previous call's contents: clear what must start at zero
+        if ((e = cudaMemsetAsync(count, 0, sizeof(int) * g.ncell, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(err, 0, sizeof(unsigned) + 8 + 4 * sizeof(unsigned long long), st)) != cudaSuccess)
+            return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(n, n_species, pos, types, g, tmp4, cell_of, slot, count, err);
+        k_scan_cells<<<1, 1024, 0, st>>>(g.ncell, count, start);
+        k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, tmp4, cell_of, slot, start, pos4, perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        if (Kr == 17 && Ka == 9) e = na_launch_fp<17, 9, true>(B, g, caps, st, pos4, start, Gs, stats, err);
+        else if (Kr == 21 && Ka == 7) e = na_launch_fp<21, 7, true>(B, g, caps, st, pos4, start, Gs, stats, err);
+        else if (Kr <= 20 && Ka <= 12) e = na_launch_fp<20, 12, false>(B, g, caps, st, pos4, start, Gs, stats, err);
+        else e = na_launch_fp<24, 8, false>(B, g, caps, st, pos4, start, Gs, stats, err);
+        if (e != cudaSuccess) return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        if ((e = cudaMemcpyAsync(&w, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        if (!(w & (kErrNbCap | kErrAngCap))) break;
+        caps.nb *= 2;
+        caps.ang *= 2;
+    }
+    if (w & kErrType) return na_fail(AENET_E_ARG, "species index out of range");
+    if (w & kErrNonfinite) return na_fail(AENET_E_NONFINITE, "non-finite coordinate");
+    if (w & kErrOverlap) return na_fail(AENET_E_OVERLAP, "two image-atoms closer than 1e-6 A");
+    if (w & (kErrNbCap | kErrAngCap)) return na_fail(AENET_E_CAPACITY, "neighbour list overflow");
+    k_na_unsort<<<256, 256, 0, st>>>(n, D, perm, Gs, G);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+    return AENET_OK;
+}
