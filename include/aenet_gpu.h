@@ -164,11 +164,16 @@ int aenet_neighbor_stats(aenet_ctx *ctx, int64_t out[3]);
 /*
  * Device time (ms) of each stage of the last MD step run with
  * AENET_MD_TIMING (CUDA events recorded inside the captured graph, on the
- * context's stream): [kick + drift, cell list, descriptor, network, forces,
- * reductions, kick], and the number of kernel launches in one MD step.
- * Returns AENET_E_STATE if no timed step has run. Synchronises.
+ * context's stream): [kick + drift + binning, cell sort, descriptor, network,
+ * forces, closing kick + FP64 reductions]; the number of kernel launches in
+ * one MD step; and path flags: AENET_PATH_FUSED when descriptor, network and
+ * forces run as one fused kernel (the FP32 form with hidden widths <= 32),
+ * whose time is then all reported under "forces" (descriptor and network read
+ * ~0). Any output pointer except ms may be NULL. Returns AENET_E_STATE if no
+ * timed step has run. Synchronises.
  */
-int aenet_md_stage_times(aenet_ctx *ctx, float ms[7], int *kernels_per_step);
+#define AENET_PATH_FUSED 1
+int aenet_md_stage_times(aenet_ctx *ctx, float ms[6], int *kernels_per_step, int *path_flags);
 
 /*
  * Descriptor without a context and without any device allocation.

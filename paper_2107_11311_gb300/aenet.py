@@ -17,7 +17,7 @@ from . import build as _build
 
 AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
 AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING = 1, 2, 4
-STAGES = ("kick_drift", "cell_list", "descriptor", "network", "forces", "reductions", "kick")
+STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
 PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
 
 STATUS = {0: "AENET_OK", -1: "AENET_E_ARG", -2: "AENET_E_CUDA", -3: "AENET_E_CAPACITY",
@@ -65,7 +65,7 @@ def load(build_if_missing: bool = True):
     lib.aenet_check.argtypes = [P]
     lib.aenet_neighbor_stats.argtypes = [P, P]
     lib.aenet_descriptors_noalloc.argtypes = [I, P, P, P, I, P, D, I, D, I, P, P]
-    lib.aenet_md_stage_times.argtypes = [P, P, P]
+    lib.aenet_md_stage_times.argtypes = [P, P, P, P]
     lib.aenet_last_error.argtypes = [P]
     lib.aenet_last_error.restype = C.c_char_p
     lib.aenet_destroy.argtypes = [P]
@@ -234,9 +234,10 @@ class AenetGPU:
         return tuple(int(x) for x in out)
 
     def md_stage_times(self):
-        """Per-stage device milliseconds of the last AENET_MD_TIMING step and the
-        number of kernel launches per MD step."""
-        ms = np.zeros(7, dtype=np.float32)
+        """Per-stage device milliseconds of the last AENET_MD_TIMING step, the
+        number of kernel launches per MD step and whether the fused kernel ran."""
+        ms = np.zeros(len(STAGES), dtype=np.float32)
         k = C.c_int(0)
-        self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), C.byref(k)))
-        return dict(zip(STAGES, map(float, ms))), int(k.value)
+        f = C.c_int(0)
+        self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), C.byref(k), C.byref(f)))
+        return dict(zip(STAGES, map(float, ms))), int(k.value), bool(f.value & 1)

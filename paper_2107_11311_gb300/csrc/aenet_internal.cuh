@@ -53,13 +53,42 @@ struct Grid {
     int n_off;                     // prod(2 m + 1)
     double box[3];
     double h[3];
+    double inv_box[3];             // reciprocals: no FP64 division on the device
+    double inv_h[3];
     float hf[3];
 };
+
+// Wrap one position into [0, box) and bin it: returns the cell and the FP32
+// coordinates relative to the cell origin (computed in FP64, then rounded).
+// FP64 work is a short chain of multiplies and FMAs (no division): FP64 has a
+// long latency on this part.
+__device__ inline int bin_position(double x0, double x1, double x2, const Grid &g, float *u, bool &finite) {
+    const double xs[3] = {x0, x1, x2};
+    int ci[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = xs[a];
+        if (!isfinite(x)) {
+            finite = false;
+            x = 0.0;
+        }
+        const double L = g.box[a];
+        double w = fma(-floor(x * g.inv_box[a]), L, x);
+        if (w >= L) w -= L;
+        if (w < 0.0) w = 0.0;
+        int c = (int)(w * g.inv_h[a]);
+        c = c >= g.nc[a] ? g.nc[a] - 1 : c;
+        ci[a] = c;
+        u[a] = (float)fma(-(double)c, g.h[a], w);
+    }
+    return (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
+}
 
 // Capacities of the per-warp neighbour lists of the fingerprint kernels.
 struct Caps {
     int nb;     // entries with r <= rc_max
     int ang;    // entries with r <= rc_ang
+    int tile;   // staged neighbour-cell atoms per chunk (fused kernel)
 };
 
 struct Context {
@@ -102,6 +131,7 @@ struct Context {
     unsigned *d_err = nullptr;     // device error word
     unsigned long long *d_stats = nullptr;  // [4] radial entries, angular entries, angular pairs
     int *d_step = nullptr;         // MD record counter
+    unsigned *d_done = nullptr;    // last-CTA counter of the MD reduction (left at 0)
 
     // staging of host arrays
     int cap_stage = 0;
@@ -127,7 +157,7 @@ struct Context {
     } md_key;
 
     // stage timing of the captured MD step (events recorded inside the graph)
-    static constexpr int kStages = 7;  // vv1, cells, descriptor, network, forces, reductions, vv2
+    static constexpr int kStages = 6;  // kick+drift+bin, sort, descriptor, network, forces, kick+reductions
     cudaEvent_t ev[kStages + 1] = {};
     int md_kernels = 0;                // kernel nodes in the captured step
 };
@@ -137,6 +167,8 @@ struct Context {
 
 // Wrap, bin and sort atoms by cell (rows a1, a2 of the path).
 cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
+// The scan + scatter half of launch_cells (after the counts are in place).
+cudaError_t launch_sort(Context &c, const Grid &g, int n);
 
 // Descriptor of every atom into c.d_G (rows a3-a5).
 cudaError_t launch_fp_forward(Context &c, const Grid &g, int n);
@@ -147,18 +179,29 @@ cudaError_t launch_ann(Context &c, int n);
 // Forces and virial partials from dE/dG (row a8).
 cudaError_t launch_fp_backward(Context &c, const Grid &g, int n);
 
-// Energy and virial reductions (row a7) and outputs in input order.
-cudaError_t launch_finalize(Context &c, const Grid &g, int n, double *forces, double *e_atom);
+// Energy and virial reductions (row a7) over n_eparts energy partials and the
+// cells' virial partials, and outputs in input order.
+cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom);
+
+// Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
+bool fused_supported(const Context &c);
+size_t fused_smem_bytes(const Context &c, const Grid &g);
+cudaError_t launch_fused_potential(Context &c, const Grid &g, int n);
+int ann_blocks(int n);
 
 // Descriptor rows to input order (float).
 cudaError_t launch_unsort_G(Context &c, int n, float *G);
 
 // Velocity Verlet (row a9).
-cudaError_t launch_vv_first(Context &c, int n, double dt, double *pos, double *vel, const double *F,
-                            const int32_t *types);
-cudaError_t launch_vv_second(Context &c, int n, double dt, double *vel, const double *F,
-                             const int32_t *types);
-cudaError_t launch_record(Context &c, int n, double *rec_pot, double *rec_kin);
+// One MD half: kick (v += dt/2 F/m c) + drift (x += dt v) fused with the binning
+// of the new positions (rows a9 + a1-a2); the scan and scatter follow.
+cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
+                                     const int32_t *types);
+// The closing kick (v += dt/2 F/m c) with the kinetic energy, fused with the
+// FP64 reduction of energy, virial and kinetic energy (last-CTA pattern) into
+// c.d_result and, when rec_pot != NULL, the record of step *c.d_step.
+cudaError_t launch_md_kick_finish(Context &c, const Grid &g, int n, int n_eparts, double dt, double *vel,
+                                  const int32_t *types, double *rec_pot, double *rec_kin);
 
 // Message reported by aenet_last_error(NULL) for calls made without a context.
 void set_context_free_error(const char *msg);

@@ -17,7 +17,6 @@ struct aenet_ctx {
 
 namespace aenet {
 
-int ann_blocks(int n);
 cudaError_t prepare_bf16_weights(Context &c);
 
 namespace {
@@ -76,6 +75,8 @@ int make_grid(Context &c, const double *box, Grid &g) {
         g.box[a] = box[a];
         g.h[a] = box[a] / nc;
         g.hf[a] = (float)g.h[a];
+        g.inv_box[a] = 1.0 / g.box[a];
+        g.inv_h[a] = 1.0 / g.h[a];
         g.m[a] = (int)ceil(rc / g.h[a]);
         g.ncell *= nc;
         g.n_off *= 2 * g.m[a] + 1;
@@ -85,19 +86,24 @@ int make_grid(Context &c, const double *box, Grid &g) {
     return AENET_OK;
 }
 
-// Neighbour-list capacities from the mean density: 1.5x the expected count + 32,
-// rounded to a multiple of 32.
+// Neighbour-list capacities from the mean density: 1.3x the expected count plus
+// a margin, rounded to 16; the staging tile holds 1.25x the mean neighbourhood
+// of a cell (at most 1024 atoms; larger neighbourhoods are staged in chunks).
 Caps estimate_caps(const Context &c, int n, const Grid &g) {
     const double V = g.box[0] * g.box[1] * g.box[2];
     const double rho = n / V;
-    auto cap = [&](double rc) {
+    auto cap = [&](double rc, double margin) {
         double e = rho * 4.18879020478639 * rc * rc * rc;
-        int k = (int)(1.5 * e + 32.0);
-        return ((k + 31) / 32) * 32;
+        int k = (int)(1.3 * e + margin);
+        return ((k + 15) / 16) * 16;
     };
     Caps k;
-    k.nb = std::max(64, cap(c.basis.rc_max));
-    k.ang = std::max(32, cap(c.basis.rc_ang));
+    k.nb = std::max(64, cap(c.basis.rc_max, 32.0));
+    k.ang = std::max(32, cap(c.basis.rc_ang, 24.0));
+    const double per_cell = (double)n / g.ncell;
+    int tile = (int)(1.25 * per_cell * g.n_off + 64.0);
+    tile = ((tile + 31) / 32) * 32;
+    k.tile = std::min(1024, std::max(128, tile));
     return k;
 }
 
@@ -115,7 +121,6 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_dEdG, 0, N * D), "cudaMalloc");
         CK(grow(c.d_eatom, 0, N), "cudaMalloc");
         CK(grow(c.d_F4, 0, N), "cudaMalloc");
-        CK(grow(c.d_e_part, 0, (size_t)ann_blocks(n) + 1), "cudaMalloc");
         CK(grow(c.d_ke_part, 0, (N + 255) / 256 + 1), "cudaMalloc");
         c.cap_atoms = n;
     }
@@ -124,6 +129,11 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_cell_start, 0, (size_t)g.ncell + 1), "cudaMalloc");
         CK(grow(c.d_vir_part, 0, (size_t)g.ncell * 9), "cudaMalloc");
         c.cap_cells = g.ncell;
+    }
+    const int need_e = std::max(ann_blocks(std::max(n, 1)), g.ncell) + 1;
+    if (need_e > c.cap_blocks || !c.d_e_part) {
+        CK(grow(c.d_e_part, 0, (size_t)need_e), "cudaMalloc");
+        c.cap_blocks = need_e;
     }
     return AENET_OK;
 }
@@ -146,7 +156,7 @@ int check_smem(Context &c, const Grid &g) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t need = fp_smem_bytes(g, c.caps, true);
+    const size_t need = std::max(fp_smem_bytes(g, c.caps, true), fused_supported(c) ? fused_smem_bytes(c, g) : 0);
     if (optin > 0 && need > (size_t)optin)
         return fail(&c, AENET_E_CAPACITY, "neighbour lists need %zu B of shared memory (limit %d B)", need, optin);
     return AENET_OK;
@@ -158,23 +168,39 @@ cudaError_t mark(Context &c, cudaEvent_t ev) {
     return cudaEventRecordWithFlags(ev, c.stream, cudaEventRecordExternal);
 }
 
+// Descriptor, networks and forces after the cell list (fused kernel or the
+// three split kernels). evs (optional): 3 events after descriptor, network,
+// forces. *n_eparts = number of energy partials written.
+int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent_t *evs) {
+    if (fused_supported(c)) {
+        // descriptor, network and forces in one kernel: their stage events coincide
+        if (evs) CK(mark(c, evs[0]), "event");
+        if (evs) CK(mark(c, evs[1]), "event");
+        CK(launch_fused_potential(c, g, n), "potential kernel");
+        *n_eparts = g.ncell;
+    } else {
+        CK(launch_fp_forward(c, g, n), "descriptor kernel");
+        if (evs) CK(mark(c, evs[0]), "event");
+        CK(launch_ann(c, n), "network kernel");
+        if (evs) CK(mark(c, evs[1]), "event");
+        CK(launch_fp_backward(c, g, n), "force kernel");
+        *n_eparts = ann_blocks(n);
+    }
+    if (evs) CK(mark(c, evs[2]), "event");
+    return AENET_OK;
+}
+
 // The whole path on device buffers, enqueued on c.stream (no synchronisation).
-// evs (optional): 5 events recorded after cells, descriptor, network, forces,
-// reductions.
+// *n_eparts (optional) receives the number of energy partials.
 int enqueue_compute(Context &c, const Grid &g, int n, const double *pos, const int32_t *types, double *forces,
-                    double *e_atom, cudaEvent_t *evs = nullptr) {
+                    double *e_atom, int *n_eparts_out = nullptr) {
     int rc = check_smem(c, g);
     if (rc) return rc;
     CK(launch_cells(c, g, n, pos, types), "cell list");
-    if (evs) CK(mark(c, evs[0]), "event");
-    CK(launch_fp_forward(c, g, n), "descriptor kernel");
-    if (evs) CK(mark(c, evs[1]), "event");
-    CK(launch_ann(c, n), "network kernel");
-    if (evs) CK(mark(c, evs[2]), "event");
-    CK(launch_fp_backward(c, g, n), "force kernel");
-    if (evs) CK(mark(c, evs[3]), "event");
-    CK(launch_finalize(c, g, n, forces, e_atom), "reductions");
-    if (evs) CK(mark(c, evs[4]), "event");
+    int n_eparts = 0;
+    if ((rc = enqueue_potential(c, g, n, &n_eparts, nullptr))) return rc;
+    CK(launch_finalize(c, g, n, n_eparts, forces, e_atom), "reductions");
+    if (n_eparts_out) *n_eparts_out = n_eparts;
     return AENET_OK;
 }
 
@@ -308,7 +334,8 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
     for (int k = 0; k <= Context::kStages; ++k)
         if ((e = cudaEventCreate(&c.ev[k])) != cudaSuccess) return setup_fail(e, "cudaEventCreate");
     if ((e = cudaMalloc(&c.d_step, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&c.d_result, sizeof(double) * 10)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_done, sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_result, sizeof(double) * 11)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_mass, sizeof(double) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     double masses[kMaxSpecies] = {0};
     for (int t = 0; t < m->n_species && m->mass; ++t) masses[t] = m->mass[t];
@@ -317,8 +344,9 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
         (e = cudaMemcpy(c.d_scale, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c.d_mass, masses, sizeof(masses), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(c.d_err, 0, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(c.d_done, 0, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(c.d_stats, 0, sizeof(unsigned long long) * 4)) != cudaSuccess ||
-        (e = cudaMemset(c.d_result, 0, sizeof(double) * 10)) != cudaSuccess)
+        (e = cudaMemset(c.d_result, 0, sizeof(double) * 11)) != cudaSuccess)
         return setup_fail(e, "cudaMemcpy");
     if (precision != AENET_FP32) {
         if ((e = prepare_bf16_weights(c)) != cudaSuccess) return setup_fail(e, "BF16 weights");
@@ -373,6 +401,7 @@ static int compute_impl(Context &c, int n, const double *pos, const int32_t *typ
         if (rc != AENET_E_CAPACITY || attempt == 1) break;
         c.caps.nb *= 2;  // regrow once and retry
         c.caps.ang *= 2;
+        c.caps.tile = 1024;
         destroy_graph(c);
     }
     if (rc) return rc;
@@ -420,19 +449,24 @@ extern "C" int aenet_descriptors(aenet_ctx *h, int n, const double *pos, const i
     return compute_impl(h->c, n, pos, types, box, nullptr, nullptr, nullptr, nullptr, G);
 }
 
-// One MD step on device buffers: kick + drift, forces at the new positions,
-// second kick (and kinetic energy), optional record of (E_pot, E_kin).
+// One MD step on device buffers: kick + drift + binning, cell sort, forces at
+// the new positions, closing kick with the FP64 reductions (and the record of
+// (E_pot, E_kin) when rec != NULL). With timing, events bracket the 6 stages.
 static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
                            const int32_t *types, double *rec, bool timing) {
     cudaEvent_t *ev = timing ? c.ev : nullptr;
-    if (ev) CK(mark(c, ev[0]), "event");
-    CK(launch_vv_first(c, n, dt, pos, vel, c.d_forces, types), "vv first");
-    if (ev) CK(mark(c, ev[1]), "event");
-    int rc = enqueue_compute(c, g, n, pos, types, c.d_forces, nullptr, ev ? ev + 2 : nullptr);
+    int rc = check_smem(c, g);
     if (rc) return rc;
-    CK(launch_vv_second(c, n, dt, vel, c.d_forces, types), "vv second");
-    if (ev) CK(mark(c, ev[7]), "event");
-    if (rec) CK(launch_record(c, n, rec, rec + c.cap_rec), "record");
+    if (ev) CK(mark(c, ev[0]), "event");
+    CK(launch_md_kick_drift_bin(c, g, n, dt, pos, vel, types), "kick + drift + binning");
+    if (ev) CK(mark(c, ev[1]), "event");
+    CK(launch_sort(c, g, n), "cell sort");
+    if (ev) CK(mark(c, ev[2]), "event");
+    int n_eparts = 0;
+    if ((rc = enqueue_potential(c, g, n, &n_eparts, ev ? ev + 3 : nullptr))) return rc;
+    CK(launch_md_kick_finish(c, g, n, n_eparts, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr),
+       "kick + reductions");
+    if (ev) CK(mark(c, ev[6]), "event");
     return AENET_OK;
 }
 
@@ -476,20 +510,31 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
     double *rec = want_rec ? c.d_rec : nullptr;
     if (!async) CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
     if (want_rec) CK(cudaMemsetAsync(c.d_step, 0, sizeof(int), c.stream), "cudaMemsetAsync");
-    // frame 0: forces at the initial positions (unless continuing), kinetic energy
+    // frame 0: forces at the initial positions (unless continuing); a
+    // neighbour-list overflow here regrows the capacities once before capture
+    int n_eparts = fused_supported(c) ? g.ncell : ann_blocks(n);
     if (!cont) {
-        if ((rc = enqueue_compute(c, g, n, dpos, dtypes, c.d_forces, nullptr))) return rc;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if ((rc = enqueue_compute(c, g, n, dpos, dtypes, nullptr, nullptr, &n_eparts))) return rc;
+            if (async) break;
+            rc = read_error_word(c);
+            if (rc != AENET_E_CAPACITY || attempt == 1) break;
+            c.caps.nb *= 2;
+            c.caps.ang *= 2;
+            c.caps.tile = 1024;
+            destroy_graph(c);
+        }
+        if (rc) return rc;
     }
-    if (want_rec) {
-        CK(launch_vv_second(c, n, 0.0, dvel, c.d_forces, dtypes), "kinetic energy");
-        CK(launch_record(c, n, rec, rec + c.cap_rec), "record");
-    }
+    if (want_rec)  // kinetic energy and record of frame 0 (a kick with dt = 0)
+        CK(launch_md_kick_finish(c, g, n, n_eparts, 0.0, dvel, dtypes, rec, rec + c.cap_rec), "frame 0");
     if (n_steps > 0) {
         const bool same = c.md_exec && c.md_key.n == n && c.md_key.pos == dpos && c.md_key.vel == dvel &&
                           c.md_key.types == dtypes && c.md_key.box[0] == box[0] && c.md_key.box[1] == box[1] &&
                           c.md_key.box[2] == box[2] && c.md_key.dt == dt && c.md_key.rec == rec &&
                           c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
-                          c.md_key.caps.ang == c.caps.ang && c.md_key.timing == timing;
+                          c.md_key.caps.ang == c.caps.ang && c.md_key.caps.tile == c.caps.tile &&
+                          c.md_key.timing == timing;
         if (!same) {
             destroy_graph(c);
             cudaGraph_t graph = nullptr;
@@ -554,13 +599,14 @@ extern "C" int aenet_neighbor_stats(aenet_ctx *h, int64_t *out) {
     return AENET_OK;
 }
 
-extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_step) {
+extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_step, int *path_flags) {
     if (!h || !ms) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
     Context &c = h->c;
     if (!c.md_exec || !c.md_key.timing) return fail(&c, AENET_E_STATE, "no MD step was run with AENET_MD_TIMING");
     CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
     for (int k = 0; k < Context::kStages; ++k) CK(cudaEventElapsedTime(&ms[k], c.ev[k], c.ev[k + 1]), "elapsed");
     if (kernels_per_step) *kernels_per_step = c.md_kernels;
+    if (path_flags) *path_flags = fused_supported(c) ? AENET_PATH_FUSED : 0;
     return AENET_OK;
 }
 
@@ -581,7 +627,7 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
     if (c.stream) cudaStreamSynchronize(c.stream);
     void *ptrs[] = {c.d_params, c.d_shift, c.d_scale, c.d_wbf, c.d_mass, c.d_pos4, c.d_tmp4, c.d_perm,
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
-                    c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_pos, c.d_vel,
+                    c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);

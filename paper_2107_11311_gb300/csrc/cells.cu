@@ -16,32 +16,15 @@ __global__ void k_bin_count(int n, int n_species, const double *__restrict__ pos
                             int *__restrict__ cell_count, unsigned *__restrict__ err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int ci[3];
     float u[3];
     bool finite = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double x = pos[3 * i + a];
-        if (!isfinite(x)) {
-            finite = false;
-            x = 0.0;
-        }
-        double L = g.box[a];
-        double w = x - floor(x / L) * L;
-        if (w >= L) w -= L;
-        if (w < 0.0) w = 0.0;
-        int c = (int)floor(w / g.h[a]);
-        c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-        ci[a] = c;
-        u[a] = (float)(w - c * g.h[a]);
-    }
+    const int cell = bin_position(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], g, u, finite);
     if (!finite) atomicOr(err, kErrNonfinite);
     int t = types[i];
     if (t < 0 || t >= n_species) {
         atomicOr(err, kErrType);
         t = 0;
     }
-    int cell = (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
     tmp4[i] = make_float4(u[0], u[1], u[2], __int_as_float(t));
     cell_of[i] = cell;
     slot[i] = atomicAdd(&cell_count[cell], 1);
@@ -95,19 +78,25 @@ __global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__r
     perm[s] = i;
 }
 
-cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types) {
-    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * g.ncell, c.stream);
-    if (e != cudaSuccess) return e;
-    if (n > 0) {
-        k_bin_count<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.basis.n_species, pos, types, g, c.d_tmp4, c.d_cell_of, c.d_slot,
-                                                           c.d_cell_count, c.d_err);
-    }
+cudaError_t launch_sort(Context &c, const Grid &g, int n) {
     k_scan_cells<<<1, 1024, 0, c.stream>>>(g.ncell, c.d_cell_count, c.d_cell_start);
     if (n > 0) {
         k_scatter<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_tmp4, c.d_cell_of, c.d_slot, c.d_cell_start,
                                                          c.d_pos4, c.d_perm);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types) {
+    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * g.ncell, c.stream);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_bin_count<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.basis.n_species, pos, types, g, c.d_tmp4,
+                                                           c.d_cell_of, c.d_slot, c.d_cell_count, c.d_err);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_sort(c, g, n);
 }
 
 }  // namespace aenet

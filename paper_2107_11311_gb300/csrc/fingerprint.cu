@@ -24,6 +24,7 @@
 #include <stdio.h>
 
 #include "aenet_internal.cuh"
+#include "fp_common.cuh"
 
 namespace aenet {
 
@@ -32,10 +33,12 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kTile = 1024;  // staged atoms per chunk
-constexpr unsigned kFull = 0xffffffffu;
-constexpr int kShiftBit = 0x80000000;
-
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+using detail::align16;
+using detail::floor_div;
+using detail::kFull;
+using detail::kShiftBit;
+using detail::pair_advance;
+using detail::transpose_reduce64;
 
 struct SmemLayout {
     size_t off_start, off_count, off_prefix, off_shift, s_pos, s_idx, warp_base, warp_bytes, total;
@@ -83,40 +86,6 @@ __host__ __device__ inline SmemLayout make_layout(int n_off, int cap, int acap, 
     L.warp_bytes = q;
     L.total = p + q * kWarps;
     return L;
-}
-
-__device__ inline int floor_div(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-    return q;
-}
-
-// 64 per-lane partial sums -> lane l holds the warp totals of slots 2l, 2l+1.
-__device__ inline void transpose_reduce64(float (&v)[64], int lane) {
-#define AENET_STAGE(O, N)                                                   \
-    {                                                                       \
-        const bool up = (lane & (O)) != 0;                                  \
-        _Pragma("unroll") for (int k = 0; k < (N); ++k) {                   \
-            float send = up ? v[k] : v[k + (N)];                            \
-            float keep = up ? v[k + (N)] : v[k];                            \
-            v[k] = keep + __shfl_xor_sync(kFull, send, (O));                \
-        }                                                                   \
-    }
-    AENET_STAGE(16, 32)
-    AENET_STAGE(8, 16)
-    AENET_STAGE(4, 8)
-    AENET_STAGE(2, 4)
-    AENET_STAGE(1, 2)
-#undef AENET_STAGE
-}
-
-// Next (j, k) of the flattened unordered pair enumeration, k = j + 1 + rem.
-__device__ inline void pair_advance(int n, int step, int &j, int &rem) {
-    rem += step;
-    while (j < n - 1 && rem >= n - 1 - j) {
-        rem -= n - 1 - j;
-        ++j;
-    }
 }
 
 template <int KRT, int KAT, bool EXACT, bool BWD>
@@ -748,6 +717,8 @@ extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t
         g.box[a] = box[a];
         g.h[a] = box[a] / nc;
         g.hf[a] = (float)g.h[a];
+        g.inv_box[a] = 1.0 / g.box[a];
+        g.inv_h[a] = 1.0 / g.h[a];
         g.m[a] = (int)ceil(B.rc_max / g.h[a]);
         g.ncell *= nc;
         g.n_off *= 2 * g.m[a] + 1;

@@ -1,46 +1,69 @@
 // Rows a7 and a9 of the path: FP64 reductions of the total energy (the
 // Behler-Parrinello sum E = sum_i E_i) and the virial, outputs back in input
 // order, and the velocity-Verlet NVE update (the propagation step of the MD
-// cycle, Fig. 1) in FP64. All reductions are two-level and deterministic:
-// per-CTA partials are summed by one CTA in a fixed order.
+// cycle, Fig. 1) in FP64.
+//
+// FP64 arithmetic has a long latency on this part, so every FP64 reduction is a
+// wide tree (independent accumulators per thread, then shuffles) rather than a
+// serial chain, divisions are replaced by host-computed reciprocals, and the
+// MD step runs in two kernels around the potential: kick + drift + binning, and
+// closing kick + all reductions (the last CTA to finish sums every partial in a
+// fixed order, so results are deterministic).
 #include "aenet_internal.cuh"
 
 namespace aenet {
 
-int ann_blocks(int n);
-
 namespace {
 
 constexpr double kEvPerAmu = 9648.533212;  // (A/ps)^2 per eV/amu
+constexpr int kRedThreads = 256;
+constexpr int kMdThreads = 256;
 
-__device__ inline double block_sum(double v, double *sh) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Per-species kick factor dt/2 * c / m and kinetic factor m / (2 c).
+struct KickParams {
+    double k[kMaxSpecies];
+    double hm[kMaxSpecies];
+};
+
+__device__ inline double select_species(const double (&v)[kMaxSpecies], int t) {
+    double r = v[0];
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    }
-    __syncthreads();
-    return s;  // valid in thread 0
+    for (int s = 1; s < kMaxSpecies; ++s)
+        if (t == s) r = v[s];
+    return r;
 }
 
-// energy = sum of ANN-block partials; virial = sum of cell partials.
-__global__ void k_reduce(int n_eblocks, const double *__restrict__ e_part, int n_vblocks,
-                         const double *__restrict__ vir_part, double *__restrict__ result) {
-    __shared__ double sh[32];
-    double e = 0.0;
-    for (int k = threadIdx.x; k < n_eblocks; k += blockDim.x) e += e_part[k];
-    e = block_sum(e, sh);
-    if (threadIdx.x == 0) result[0] = e;
-    for (int c = 0; c < 9; ++c) {
-        double v = 0.0;
-        for (int k = threadIdx.x; k < n_vblocks; k += blockDim.x) v += vir_part[(size_t)k * 9 + c];
-        v = block_sum(v, sh);
-        if (threadIdx.x == 0) result[1 + c] = v;
+__device__ inline double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of n values x[k * stride] (read through L2) by one warp: four independent
+// accumulators per lane, then a shuffle tree. Result valid in every lane.
+__device__ inline double warp_reduce_strided(const double *x, int n, int stride, int lane) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = lane;
+    for (; k + 96 < n; k += 128) {
+        a0 += __ldcg(x + (size_t)k * stride);
+        a1 += __ldcg(x + (size_t)(k + 32) * stride);
+        a2 += __ldcg(x + (size_t)(k + 64) * stride);
+        a3 += __ldcg(x + (size_t)(k + 96) * stride);
     }
+    for (; k < n; k += 32) a0 += __ldcg(x + (size_t)k * stride);
+    return warp_sum_d((a0 + a1) + (a2 + a3));
+}
+
+// result[q] for q = 0 (energy, n_e partials) and 1..9 (virial, n_v x 9 partials):
+// one warp per quantity.
+__global__ void k_reduce(int n_e, const double *__restrict__ e_part, int n_v, const double *__restrict__ vir_part,
+                         double *__restrict__ result) {
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5);
+    if (q > 9) return;
+    const double v = q == 0 ? warp_reduce_strided(e_part, n_e, 1, lane)
+                            : warp_reduce_strided(vir_part + (q - 1), n_v, 9, lane);
+    if (lane == 0) result[q] = v;
 }
 
 __global__ void k_unsort_outputs(int n, const int *__restrict__ perm, const float4 *__restrict__ F4,
@@ -67,63 +90,118 @@ __global__ void k_unsort_G(int n, int D, const int *__restrict__ perm, const flo
     }
 }
 
-// v += dt/2 F/m c;  x += dt v
-__global__ void k_vv_first(int n, double dt, double *__restrict__ pos, double *__restrict__ vel,
-                           const double *__restrict__ F, const int32_t *__restrict__ types,
-                           const double *__restrict__ mass) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// v += dt/2 F/m c; x += dt v; then bin x (as k_bin_count). F comes from the
+// previous evaluation, in its cell-sorted order (cell_start/cell_of/slot of that
+// evaluation are still in place).
+__global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double dt, double *__restrict__ pos,
+                                    double *__restrict__ vel, const int32_t *__restrict__ types,
+                                    const float4 *__restrict__ F4, const int *__restrict__ cell_start, Grid g,
+                                    float4 *__restrict__ tmp4, int *__restrict__ cell_of, int *__restrict__ slot,
+                                    int *__restrict__ cell_count, unsigned *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double k = 0.5 * dt * kEvPerAmu / mass[types[i]];
+    int t = types[i];
+    if (t < 0 || t >= n_species) {
+        atomicOr(err, kErrType);
+        t = 0;
+    }
+    const float4 f = F4[cell_start[cell_of[i]] + slot[i]];
+    const double k = select_species(kp.k, t);
+    double x[3];
+    const float fa[3] = {f.x, f.y, f.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double v = vel[3 * i + a] + k * F[3 * i + a];
+        const double v = fma(k, (double)fa[a], vel[3 * i + a]);
         vel[3 * i + a] = v;
-        pos[3 * i + a] += dt * v;
+        x[a] = fma(dt, v, pos[3 * i + a]);
+        pos[3 * i + a] = x[a];
     }
+    float u[3];
+    bool finite = true;
+    const int cell = bin_position(x[0], x[1], x[2], g, u, finite);
+    if (!finite) atomicOr(err, kErrNonfinite);
+    tmp4[i] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+    cell_of[i] = cell;
+    slot[i] = atomicAdd(&cell_count[cell], 1);
 }
 
-// v += dt/2 F/m c, and the kinetic energy sum_i m v^2 / (2 c) as CTA partials
-__global__ void k_vv_second(int n, double dt, double *__restrict__ vel, const double *__restrict__ F,
-                            const int32_t *__restrict__ types, const double *__restrict__ mass,
-                            double *__restrict__ ke_part) {
-    __shared__ double sh[32];
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// v += dt/2 F/m c with F of the current evaluation; kinetic energy per CTA; the
+// last CTA reduces energy, virial and kinetic energy into result[0..10] and
+// appends (E_pot, E_kin) to the records.
+__global__ void __launch_bounds__(kMdThreads)
+    k_md_kick_finish(int n, KickParams kp, double *__restrict__ vel, const int32_t *__restrict__ types,
+                     const float4 *__restrict__ F4, const int *__restrict__ cell_start, const int *__restrict__ cell_of,
+                     const int *__restrict__ slot, int n_e, const double *__restrict__ e_part, int n_v,
+                     const double *__restrict__ vir_part, double *__restrict__ ke_part, unsigned *__restrict__ done,
+                     double *__restrict__ result, int *__restrict__ step, double *__restrict__ rec_pot,
+                     double *__restrict__ rec_kin) {
+    __shared__ double s_w[kMdThreads / 32];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i = blockIdx.x * blockDim.x + tid;
     double ke = 0.0;
     if (i < n) {
-        const double m = mass[types[i]];
-        const double k = 0.5 * dt * kEvPerAmu / m;
-        double v2 = 0.0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double v = vel[3 * i + a] + k * F[3 * i + a];
-            if (dt != 0.0) vel[3 * i + a] = v;
-            v2 += v * v;
-        }
-        ke = 0.5 * m * v2 / kEvPerAmu;
+        const int t = types[i];
+        const float4 f = F4[cell_start[cell_of[i]] + slot[i]];
+        const double k = select_species(kp.k, t);
+        const double vx = fma(k, (double)f.x, vel[3 * i + 0]);
+        const double vy = fma(k, (double)f.y, vel[3 * i + 1]);
+        const double vz = fma(k, (double)f.z, vel[3 * i + 2]);
+        vel[3 * i + 0] = vx;
+        vel[3 * i + 1] = vy;
+        vel[3 * i + 2] = vz;
+        ke = select_species(kp.hm, t) * fma(vx, vx, fma(vy, vy, vz * vz));
     }
-    ke = block_sum(ke, sh);
-    if (threadIdx.x == 0) ke_part[blockIdx.x] = ke;
+    ke = warp_sum_d(ke);
+    if (lane == 0) s_w[warp] = ke;
+    __syncthreads();
+    if (warp == 0) {
+        double v = lane < kMdThreads / 32 ? s_w[lane] : 0.0;
+        v = warp_sum_d(v);
+        if (lane == 0) {
+            ke_part[blockIdx.x] = v;
+            __threadfence();
+            s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last CTA: 11 quantities, one warp each (8 warps, so warps 0-2 take two)
+    for (int q = warp; q < 11; q += kMdThreads / 32) {
+        double v;
+        if (q == 0) v = warp_reduce_strided(e_part, n_e, 1, lane);
+        else if (q < 10) v = warp_reduce_strided(vir_part + (q - 1), n_v, 9, lane);
+        else v = warp_reduce_strided(ke_part, gridDim.x, 1, lane);
+        if (lane == 0) result[q] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *done = 0u;
+        if (rec_pot) {
+            const int s = *step;
+            rec_pot[s] = result[0];
+            rec_kin[s] = result[10];
+            *step = s + 1;
+        }
+    }
 }
 
-// rec_pot[step] = E, rec_kin[step] = sum of kinetic partials; step++.
-__global__ void k_record(int n_kblocks, const double *__restrict__ ke_part, const double *__restrict__ result,
-                         int *__restrict__ step, double *__restrict__ rec_pot, double *__restrict__ rec_kin) {
-    __shared__ double sh[32];
-    double ke = 0.0;
-    for (int k = threadIdx.x; k < n_kblocks; k += blockDim.x) ke += ke_part[k];
-    ke = block_sum(ke, sh);
-    if (threadIdx.x == 0) {
-        const int s = *step;
-        rec_pot[s] = result[0];
-        rec_kin[s] = ke;
-        *step = s + 1;
+KickParams kick_params(const Context &c, double dt) {
+    KickParams kp{};
+    for (int t = 0; t < kMaxSpecies; ++t) {
+        const double m = t < (int)c.mass.size() ? c.mass[t] : 1.0;
+        kp.k[t] = 0.5 * dt * kEvPerAmu / m;
+        kp.hm[t] = 0.5 * m / kEvPerAmu;
     }
+    return kp;
 }
 
 }  // namespace
 
-cudaError_t launch_finalize(Context &c, const Grid &g, int n, double *forces, double *e_atom) {
-    k_reduce<<<1, 1024, 0, c.stream>>>(ann_blocks(n), c.d_e_part, g.ncell, c.d_vir_part, c.d_result);
+cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom) {
+    k_reduce<<<(10 + kRedThreads / 32 - 1) / (kRedThreads / 32), kRedThreads, 0, c.stream>>>(
+        n_eparts, c.d_e_part, g.ncell, c.d_vir_part, c.d_result);
     if ((forces || e_atom) && n > 0)
         k_unsort_outputs<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_perm, c.d_F4, c.d_eatom, forces, e_atom);
     return cudaGetLastError();
@@ -135,21 +213,23 @@ cudaError_t launch_unsort_G(Context &c, int n, float *G) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_vv_first(Context &c, int n, double dt, double *pos, double *vel, const double *F,
-                            const int32_t *types) {
-    if (n <= 0) return cudaSuccess;
-    k_vv_first<<<(n + 255) / 256, 256, 0, c.stream>>>(n, dt, pos, vel, F, types, c.d_mass);
+cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
+                                     const int32_t *types) {
+    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * g.ncell, c.stream);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_md_kick_drift_bin<<<(n + kMdThreads - 1) / kMdThreads, kMdThreads, 0, c.stream>>>(
+        n, c.basis.n_species, kick_params(c, dt), dt, pos, vel, types, c.d_F4, c.d_cell_start, g, c.d_tmp4,
+        c.d_cell_of, c.d_slot, c.d_cell_count, c.d_err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_vv_second(Context &c, int n, double dt, double *vel, const double *F, const int32_t *types) {
-    if (n <= 0) return cudaSuccess;
-    k_vv_second<<<(n + 255) / 256, 256, 0, c.stream>>>(n, dt, vel, F, types, c.d_mass, c.d_ke_part);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_record(Context &c, int n, double *rec_pot, double *rec_kin) {
-    k_record<<<1, 1024, 0, c.stream>>>((n + 255) / 256, c.d_ke_part, c.d_result, c.d_step, rec_pot, rec_kin);
+cudaError_t launch_md_kick_finish(Context &c, const Grid &g, int n, int n_eparts, double dt, double *vel,
+                                  const int32_t *types, double *rec_pot, double *rec_kin) {
+    const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
+    k_md_kick_finish<<<blocks, kMdThreads, 0, c.stream>>>(n, kick_params(c, dt), vel, types, c.d_F4, c.d_cell_start,
+                                                          c.d_cell_of, c.d_slot, n_eparts, c.d_e_part, g.ncell,
+                                                          c.d_vir_part, c.d_ke_part, c.d_done, c.d_result, c.d_step,
+                                                          rec_pot, rec_kin);
     return cudaGetLastError();
 }
 

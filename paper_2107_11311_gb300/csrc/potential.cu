@@ -1,0 +1,811 @@
+// Fused potential kernel: rows a3-a8 of the path in one pass per atom.
+//
+// One CTA per cell, one warp per atom (atoms handed out dynamically inside the
+// CTA). For each atom the warp
+//   1. builds the neighbour list once, from the CTA's shared-memory tile of the
+//      (2m+1)^3 neighbour cells (image shifts applied when staging), storing per
+//      entry the displacement, r, 1/r, the radial cutoff f_c and f_c' and the
+//      species weight; angular entries additionally keep the unit vector and
+//      the angular f_c, f_c';
+//   2. evaluates the descriptor (Sec. II.B: Eq. radial, Eq. angular over
+//      unordered pairs doubled to the paper's ordered sum, the species-weighted
+//      copy) in registers and reduces it across the warp;
+//   3. runs its species' network (Sec. II.A, Eq. ANN-layer; tanh hidden layers,
+//      linear output) warp-cooperatively in FP32 -- one lane per neuron, weights
+//      in shared memory -- and back-propagates to dE/dG;
+//   4. applies the chain rule through every radial term and angular pair to
+//      forces (one FP32 vector atomic per neighbour entry) and the virial.
+// G and dE/dG never leave the SM, the list is never rebuilt and the pair loops
+// need no division or transcendental call. Energy and virial leave as FP64
+// per-CTA partials, reduced in a fixed order by the reduction kernel.
+#include "aenet_internal.cuh"
+#include "fp_common.cuh"
+
+namespace aenet {
+
+namespace {
+
+using namespace detail;
+
+constexpr int kPWarps = 8;
+constexpr int kPThreads = kPWarps * 32;
+constexpr int kSlots = 64;
+
+__host__ __device__ inline int odd(int x) { return x | 1; }
+
+// Per-species parameter block in shared memory (floats):
+//   W1T [64 slots][H1 | 1]  layer-1 weights indexed by descriptor slot
+//   b1  [H1]
+//   for hidden l = 2..L-1: W_l [H_l][H_{l-1} | 1], b_l [H_l]
+//   wL  [H_{L-1}], bL [1]
+//   shift [64 slots], scale [64 slots] (scale 0 on unused slots)
+struct FusedNet {
+    int L;                          // weight layers
+    int H[kMaxLayers + 1];          // widths
+    int offW[kMaxLayers + 1];       // offset of W_l in the block
+    int offB[kMaxLayers + 1];       // offset of b_l
+    int offShift, offScale, stride; // stride = floats per species (rounded to 4)
+    int srcOff[kMaxLayers + 1];     // offset of W_l in the canonical FP32 parameters
+    int n_params;                   // canonical floats per species
+    int Hlast, offWL, offBL, srcOffL;  // last hidden width and output-layer offsets (scalars:
+                                       // kernels never index the arrays above with runtime values)
+};
+
+FusedNet make_fused_net(const Net &net) {
+    FusedNet f{};
+    f.L = net.n_layers;
+    for (int l = 0; l <= net.n_layers; ++l) f.H[l] = net.widths[l];
+    int p = 0;
+    f.offW[1] = p;
+    p += kSlots * odd(f.H[1]);
+    f.offB[1] = p;
+    p += f.H[1];
+    for (int l = 2; l < f.L; ++l) {
+        f.offW[l] = p;
+        p += f.H[l] * odd(f.H[l - 1]);
+        f.offB[l] = p;
+        p += f.H[l];
+    }
+    f.offW[f.L] = p;
+    p += f.H[f.L - 1];
+    f.offB[f.L] = p;
+    p += 1;
+    f.offShift = p;
+    p += kSlots;
+    f.offScale = p;
+    p += kSlots;
+    f.stride = (p + 3) & ~3;
+    int q = 0;
+    for (int l = 1; l <= f.L; ++l) {
+        f.srcOff[l] = q;
+        q += f.H[l] * f.H[l - 1] + f.H[l];
+    }
+    f.n_params = q;
+    f.Hlast = f.H[f.L - 1];
+    f.offWL = f.offW[f.L];
+    f.offBL = f.offB[f.L];
+    f.srcOffL = f.srcOff[f.L];
+    return f;
+}
+
+struct PLayout {
+    size_t off_start, off_count, off_prefix, off_shift, s_pos, s_idx, params, warp_base, warp_bytes, total;
+    size_t e_d, e_c, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
+};
+
+__host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, int acap, int n_species, int stride) {
+    PLayout L{};
+    size_t p = 0;
+    L.off_start = p;
+    p = align16(p + sizeof(int) * n_off);
+    L.off_count = p;
+    p = align16(p + sizeof(int) * n_off);
+    L.off_prefix = p;
+    p = align16(p + sizeof(int) * (n_off + 1));
+    L.off_shift = p;
+    p = align16(p + sizeof(float4) * n_off);
+    L.s_pos = p;
+    p = align16(p + sizeof(float4) * tile);
+    L.s_idx = p;
+    p = align16(p + sizeof(int) * tile);
+    L.params = p;
+    p = align16(p + sizeof(float) * (size_t)n_species * stride);
+    L.warp_base = p;
+    size_t q = 0;
+    L.e_d = q;
+    q = align16(q + sizeof(float4) * cap);
+    L.e_c = q;
+    q = align16(q + sizeof(float2) * cap);
+    L.e_j = q;
+    q = align16(q + sizeof(int) * cap);
+    L.e_fx = q;
+    q = align16(q + sizeof(float) * cap);
+    L.e_fy = q;
+    q = align16(q + sizeof(float) * cap);
+    L.e_fz = q;
+    q = align16(q + sizeof(float) * cap);
+    L.a_u = q;
+    q = align16(q + sizeof(float4) * acap);
+    L.a_x = q;
+    q = align16(q + sizeof(float4) * acap);
+    L.coef = q;
+    q = align16(q + sizeof(float) * kSlots);
+    L.warp_bytes = q;
+    L.total = p + q * kPWarps;
+    return L;
+}
+
+// Descriptor slot -> G column (-1 if unused); slots are [rad | ang | rad_w | ang_w]
+// of compile-time widths KRT, KAT.
+template <int KRT, int KAT>
+__device__ inline int slot_col(int slot, int Kr, int Ka) {
+    if (slot < KRT) return slot < Kr ? slot : -1;
+    if (slot < KRT + KAT) return slot - KRT < Ka ? Kr + slot - KRT : -1;
+    if (slot < 2 * KRT + KAT) return slot - KRT - KAT < Kr ? Kr + Ka + slot - KRT - KAT : -1;
+    if (slot < 2 * KRT + 2 * KAT) return slot - 2 * KRT - KAT < Ka ? 2 * Kr + Ka + slot - 2 * KRT - KAT : -1;
+    return -1;
+}
+
+template <int KRT, int KAT>
+__device__ inline bool slot_is_angular(int slot) {
+    return (slot >= KRT && slot < KRT + KAT) || (slot >= 2 * KRT + KAT && slot < 2 * KRT + 2 * KAT);
+}
+
+struct WarpLists {
+    float4 *e_d, *a_u, *a_x;  // e_d: (dx, dy, dz, r)
+    float2 *e_c;              // (f_c, f_c') of the radial cutoff (0 beyond it)
+    int *e_j;                 // sorted neighbour index | species << 28
+    float *e_fx, *e_fy, *e_fz, *coef;
+};
+
+// Phase 1 of the list build: append the image-atoms of the staged tile that
+// lie within the largest cutoff of atom i, as (d, r^2) and index | species << 28.
+// Only a ballot compaction runs per 32 candidates; everything per neighbour is
+// deferred to the dense phase 2 (complete_list), so that the ~85% of lanes
+// whose candidate is out of range do not idle through it.
+__device__ __forceinline__ void scan_tile(const float4 *s_pos, const int *s_idx, int len, float4 ui, int i_s,
+                                          const Basis &B, const Caps &caps, const WarpLists &W, int lane,
+                                          int &nnb) {
+    const float rc2max = B.rc_max * B.rc_max;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        bool in = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        int jid = 0, typ = 0;
+        if (q < len) {
+            const float4 p = s_pos[q];
+            jid = s_idx[q];
+            dx = p.x - ui.x;
+            dy = p.y - ui.y;
+            dz = p.z - ui.z;
+            r2 = dx * dx + dy * dy + dz * dz;
+            typ = __float_as_int(p.w);
+            in = (r2 <= rc2max) && (jid != i_s);
+        }
+        const unsigned m = __ballot_sync(kFull, in);
+        if (in) {
+            const int slot = nnb + __popc(m & lt_mask);
+            if (slot < caps.nb) {
+                W.e_d[slot] = make_float4(dx, dy, dz, r2);
+                W.e_j[slot] = (jid & ~kShiftBit) | (typ << 28);
+            }
+        }
+        nnb += __popc(m);
+    }
+}
+
+// Phase 2 of the list build, dense over the nnb entries: r, the radial cutoff
+// f_c and f_c', and the angular sub-list (unit vector, 1/r, angular f_c, f_c',
+// species weight, index of the main entry).
+__device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw, const Caps &caps,
+                                              const WarpLists &W, int lane, int nnb, int &nang, unsigned *err) {
+    const float inv_rcr = 1.0f / B.rc_rad, inv_rca = 1.0f / B.rc_ang;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    nang = 0;
+    for (int base = 0; base < nnb; base += 32) {
+        const int k = base + lane;
+        bool ina = false;
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        float r = 0.f;
+        if (k < nnb) {
+            e = W.e_d[k];
+            r = sqrtf(e.w);
+            if (r < 1e-6f) {
+                atomicOr(err, kErrOverlap);
+                r = 1e-6f;
+            }
+            float fc = 0.f, dfc = 0.f;
+            if (r <= B.rc_rad) {
+                float sn, cs;
+                sincospif(r * inv_rcr, &sn, &cs);
+                fc = 0.5f * (cs + 1.0f);
+                dfc = -0.5f * 3.14159265358979f * inv_rcr * sn;
+            }
+            W.e_d[k].w = r;
+            W.e_c[k] = make_float2(fc, dfc);
+            ina = r <= B.rc_ang;
+        }
+        const unsigned ma = __ballot_sync(kFull, ina);
+        if (ina) {
+            const int aslot = nang + __popc(ma & lt_mask);
+            if (aslot < caps.ang) {
+                const float inv = 1.0f / r;
+                float sn, cs;
+                sincospif(r * inv_rca, &sn, &cs);
+                W.a_u[aslot] = make_float4(e.x * inv, e.y * inv, e.z * inv, 0.5f * (cs + 1.0f));
+                W.a_x[aslot] = make_float4(inv, -0.5f * 3.14159265358979f * inv_rca * sn, s_tw[W.e_j[k] >> 28],
+                                           __int_as_float(k));
+            }
+        }
+        nang += __popc(ma);
+    }
+}
+
+template <int KRT, int KAT, bool EXACT>
+__device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
+                                             const float *s_par, const float *s_tw,
+                             const WarpLists &W, int lane, const float4 *__restrict__ pos4, float4 *__restrict__ F4,
+                             float *__restrict__ eatom, double &e_acc, float (&vir)[9]) {
+    constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
+    const int Kr = EXACT ? KRT : B.Kr;
+    const int Ka = EXACT ? KAT : B.Ka;
+    const float inv_rcr = 1.0f / B.rc_rad;
+
+    // ---- descriptor
+    float acc[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+    for (int k = lane; k < nnb; k += 32) {
+        const float r = W.e_d[k].w;
+        if (r <= B.rc_rad) {
+            const float fc = W.e_c[k].x;
+            const float x = 2.0f * r * inv_rcr - 1.0f;
+            const float sfc = s_tw[W.e_j[k] >> 28] * fc;
+            float tm1 = 1.0f, t = x;
+            acc[0] += fc;
+            acc[SLOT_RADW] += sfc;
+#pragma unroll
+            for (int q = 1; q < KRT; ++q) {
+                if (q < Kr) {
+                    acc[q] = fmaf(t, fc, acc[q]);
+                    acc[SLOT_RADW + q] = fmaf(t, sfc, acc[SLOT_RADW + q]);
+                    const float tn = fmaf(2.0f * x, t, -tm1);
+                    tm1 = t;
+                    t = tn;
+                }
+            }
+        }
+    }
+    // angular (Eq. angular): every unordered pair once by the rotation schedule
+    // (see for the backward pass below); doubled to the ordered sum at the end
+    {
+        const int nbk = (nang + 31) >> 5;
+        for (int A = 0; A < nbk; ++A) {
+            const int nA = min(32, nang - 32 * A);
+            const bool vj = lane < nA;
+            const float4 uj = W.a_u[32 * A + (vj ? lane : 0)];
+            const float sj = W.a_x[32 * A + (vj ? lane : 0)].z;
+            for (int Bk = A; Bk < nbk; ++Bk) {
+                const int nB = min(32, nang - 32 * Bk);
+                const bool diag = Bk == A;
+                const int nt = diag ? nA / 2 : 32;
+                for (int it = 0; it < nt; ++it) {
+                    const int t = diag ? it + 1 : it;
+                    int cc;
+                    bool v;
+                    if (diag) {
+                        cc = lane + t >= nA ? lane + t - nA : lane + t;
+                        v = vj && !(2 * t == nA && lane >= t);
+                    } else {
+                        cc = (lane + t) & 31;
+                        v = vj && cc < nB;
+                    }
+                    if (v) {
+                        const float4 uk = W.a_u[32 * Bk + cc];
+                        const float sk = W.a_x[32 * Bk + cc].z;
+                        const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+                        const float w = uj.w * uk.w;
+                        const float ws = w * sj * sk;
+                        float tm1 = 1.0f, tt = c;
+                        acc[SLOT_ANG] += w;
+                        acc[SLOT_ANGW] += ws;
+#pragma unroll
+                        for (int q = 1; q < KAT; ++q) {
+                            if (q < Ka) {
+                                acc[SLOT_ANG + q] = fmaf(tt, w, acc[SLOT_ANG + q]);
+                                acc[SLOT_ANGW + q] = fmaf(tt, ws, acc[SLOT_ANGW + q]);
+                                const float tn = fmaf(2.0f * c, tt, -tm1);
+                                tm1 = tt;
+                                tt = tn;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    transpose_reduce64(acc, lane);
+
+    // ---- network of the atom's species (FP32, one lane per neuron)
+    const int t = __float_as_int(pos4[i_s].w);
+    const float *Pt = s_par + t * net.stride;
+    const int s0 = 2 * lane, s1 = 2 * lane + 1;
+    const float G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
+    const float G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
+    const float *sh = Pt + net.offShift, *sc = Pt + net.offScale;
+    const float x00 = (G0 - sh[s0]) * sc[s0];
+    const float x01 = (G1 - sh[s1]) * sc[s1];
+    const int H1 = net.H[1], H1p = odd(H1);
+    const float *W1T = Pt + net.offW[1];
+    float part[32];
+#pragma unroll
+    for (int o = 0; o < 32; ++o) part[o] = o < H1 ? fmaf(W1T[s0 * H1p + o], x00, W1T[s1 * H1p + o] * x01) : 0.f;
+    float z = transpose_reduce32(part, lane);
+    float xl[kMaxLayers];  // this lane's neuron of every hidden layer
+    xl[1] = lane < H1 ? tanhf(z + Pt[net.offB[1] + lane]) : 0.f;
+#pragma unroll
+    for (int l = 2; l < kMaxLayers; ++l) {
+        if (l < net.L) {
+            const int Hin = net.H[l - 1], Ho = net.H[l], Hinp = odd(Hin);
+            const float *Wl = Pt + net.offW[l];
+            const int o = lane < Ho ? lane : 0;
+            float zz = Pt[net.offB[l] + o];
+            for (int k = 0; k < Hin; ++k) zz = fmaf(Wl[o * Hinp + k], __shfl_sync(kFull, xl[l - 1], k), zz);
+            xl[l] = lane < Ho ? tanhf(zz) : 0.f;
+        }
+    }
+    const int Hlast = net.Hlast;
+    float xlast = 0.f;
+#pragma unroll
+    for (int l = 1; l < kMaxLayers; ++l)
+        if (l == net.L - 1) xlast = xl[l];
+    const float wL = lane < Hlast ? Pt[net.offWL + lane] : 0.f;
+    const float E = warp_sum(wL * xlast) + Pt[net.offBL];
+    // back-propagation: delta of the last hidden layer, then down to layer 1
+    float delta = (1.0f - xlast * xlast) * wL;
+#pragma unroll
+    for (int l = kMaxLayers - 1; l >= 2; --l) {
+        if (l < net.L) {
+            const int Hin = net.H[l - 1], Ho = net.H[l], Hinp = odd(Hin);
+            const float *Wl = Pt + net.offW[l];
+            const int k = lane < Hin ? lane : 0;
+            float dx = 0.f;
+            for (int o = 0; o < Ho; ++o) dx = fmaf(Wl[o * Hinp + k], __shfl_sync(kFull, delta, o), dx);
+            delta = lane < Hin ? (1.0f - xl[l - 1] * xl[l - 1]) * dx : 0.f;
+        }
+    }
+    float d0 = 0.f, d1 = 0.f;
+    for (int k = 0; k < H1; ++k) {
+        const float dk = __shfl_sync(kFull, delta, k);
+        d0 = fmaf(W1T[s0 * H1p + k], dk, d0);
+        d1 = fmaf(W1T[s1 * H1p + k], dk, d1);
+    }
+    W.coef[s0] = d0 * sc[s0];  // dE/dG = dE/dg * scale
+    W.coef[s1] = d1 * sc[s1];
+    if (lane == 0) {
+        e_acc += (double)E;
+        eatom[i_s] = E;
+    }
+    __syncwarp();
+
+    // ---- chain rule to forces
+    float cr[KRT], crw[KRT], ca[KAT], caw[KAT];
+#pragma unroll
+    for (int q = 0; q < KRT; ++q) {
+        cr[q] = W.coef[q];
+        crw[q] = W.coef[SLOT_RADW + q];
+    }
+#pragma unroll
+    for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
+        ca[q] = 2.0f * W.coef[SLOT_ANG + q];
+        caw[q] = 2.0f * W.coef[SLOT_ANGW + q];
+    }
+    const float k2 = 2.0f * inv_rcr;
+    for (int k = lane; k < nnb; k += 32) {
+        const float4 e = W.e_d[k];
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        if (e.w <= B.rc_rad) {
+            const float2 c = W.e_c[k];
+            const float s = s_tw[W.e_j[k] >> 28], fc = c.x, dfc = c.y;
+            const float x = 2.0f * e.w * inv_rcr - 1.0f;
+            // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c',  T_q' = q U_{q-1}
+            float dEdr = (cr[0] + s * crw[0]) * dfc;
+            float tm1 = 1.0f, tt = x, um1 = 0.0f, u = 1.0f;
+            const float k2fc = k2 * fc;
+#pragma unroll
+            for (int q = 1; q < KRT; ++q) {
+                if (q < Kr) {
+                    const float coef = fmaf(s, crw[q], cr[q]);
+                    dEdr = fmaf(coef, fmaf((float)q * u, k2fc, tt * dfc), dEdr);
+                    const float tn = fmaf(2.0f * x, tt, -tm1);
+                    tm1 = tt;
+                    tt = tn;
+                    const float un = fmaf(2.0f * x, u, -um1);
+                    um1 = u;
+                    u = un;
+                }
+            }
+            const float gr = __fdiv_rn(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
+            fx = -gr * e.x;
+            fy = -gr * e.y;
+            fz = -gr * e.z;
+        }
+        W.e_fx[k] = fx;
+        W.e_fy[k] = fy;
+        W.e_fz[k] = fz;
+    }
+    __syncwarp();
+    // Angular chain rule by the rotation schedule: the angular entries form
+    // blocks of 32 (lane l owns entries 32b + l). Inside a diagonal block, step t
+    // pairs lane l with entry (l + t) mod n_A (t = 1..n_A/2; at t = n_A/2 only the
+    // lower half of lanes, so each unordered pair is visited once); between
+    // blocks A < B, step t pairs lane l with column (l + t) mod 32 of B. The lane
+    // keeps dE/dd_j of its own entry in registers and hands dE/dd_k to the owner
+    // of k with one rotation shuffle; every entry is written only by its owner,
+    // so no atomics are needed. Coefficients carry the factor 2 of the ordered sum.
+    {
+        const int nbk = (nang + 31) >> 5;
+        for (int A = 0; A < nbk; ++A) {
+            const int nA = min(32, nang - 32 * A);
+            const bool vj = lane < nA;
+            const float4 uj = W.a_u[32 * A + (vj ? lane : 0)];
+            const float4 xj = W.a_x[32 * A + (vj ? lane : 0)];
+            for (int Bk = A; Bk < nbk; ++Bk) {
+                const int nB = min(32, nang - 32 * Bk);
+                const bool diag = Bk == A;
+                const int nt = diag ? nA / 2 : 32;
+                float jx = 0.f, jy = 0.f, jz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+                for (int it = 0; it < nt; ++it) {
+                    const int t = diag ? it + 1 : it;
+                    int cc, src;
+                    bool v;
+                    if (diag) {
+                        cc = lane + t >= nA ? lane + t - nA : lane + t;
+                        src = lane - t < 0 ? lane - t + nA : lane - t;
+                        v = vj && !(2 * t == nA && lane >= t);
+                    } else {
+                        cc = (lane + t) & 31;
+                        src = (lane - t) & 31;
+                        v = vj && cc < nB;
+                    }
+                    float gkx = 0.f, gky = 0.f, gkz = 0.f;
+                    if (v) {
+                        const float4 uk = W.a_u[32 * Bk + cc];
+                        const float4 xk = W.a_x[32 * Bk + cc];
+                        const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+                        const float w = xj.z * xk.z;
+                        float S = fmaf(w, caw[0], ca[0]);
+                        float dS = 0.f;
+                        float tm1 = 1.0f, tt = c, um1 = 0.0f, u = 1.0f;
+#pragma unroll
+                        for (int q = 1; q < KAT; ++q) {
+                            if (q < Ka) {
+                                const float b = fmaf(w, caw[q], ca[q]);
+                                S = fmaf(b, tt, S);
+                                dS = fmaf(b * (float)q, u, dS);
+                                const float tn = fmaf(2.0f * c, tt, -tm1);
+                                tm1 = tt;
+                                tt = tn;
+                                const float un = fmaf(2.0f * c, u, -um1);
+                                um1 = u;
+                                u = un;
+                            }
+                        }
+                        // d/dd_j [T(cos) f_j f_k] = T' f_j f_k (u_k - cos u_j)/r_j + T f_j' f_k u_j
+                        const float fj = uj.w, fk = uk.w;
+                        const float Af = dS * fj * fk;
+                        const float Aj = Af * xj.x, Ak = Af * xk.x;
+                        const float Bj = S * xj.y * fk, Bk2 = S * fj * xk.y;
+                        jx += Aj * (uk.x - c * uj.x) + Bj * uj.x;
+                        jy += Aj * (uk.y - c * uj.y) + Bj * uj.y;
+                        jz += Aj * (uk.z - c * uj.z) + Bj * uj.z;
+                        gkx = Ak * (uj.x - c * uk.x) + Bk2 * uk.x;
+                        gky = Ak * (uj.y - c * uk.y) + Bk2 * uk.y;
+                        gkz = Ak * (uj.z - c * uk.z) + Bk2 * uk.z;
+                    }
+                    kx += __shfl_sync(kFull, gkx, src);
+                    ky += __shfl_sync(kFull, gky, src);
+                    kz += __shfl_sync(kFull, gkz, src);
+                }
+                // force on neighbour = -dE_i/dd; each entry is touched by its owner lane only
+                if (vj) {
+                    const int sl = __float_as_int(xj.w);
+                    W.e_fx[sl] -= jx;
+                    W.e_fy[sl] -= jy;
+                    W.e_fz[sl] -= jz;
+                }
+                if (lane < nB) {
+                    const int sl = __float_as_int(W.a_x[32 * Bk + lane].w);
+                    W.e_fx[sl] -= kx;
+                    W.e_fy[sl] -= ky;
+                    W.e_fz[sl] -= kz;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    float fix = 0.f, fiy = 0.f, fiz = 0.f;
+    for (int k = lane; k < nnb; k += 32) {
+        const float fx = W.e_fx[k], fy = W.e_fy[k], fz = W.e_fz[k];
+        const float4 e = W.e_d[k];
+        atomicAdd(&F4[W.e_j[k] & 0x0fffffff], make_float4(fx, fy, fz, 0.f));
+        fix -= fx;
+        fiy -= fy;
+        fiz -= fz;
+        vir[0] = fmaf(e.x, fx, vir[0]);
+        vir[1] = fmaf(e.x, fy, vir[1]);
+        vir[2] = fmaf(e.x, fz, vir[2]);
+        vir[3] = fmaf(e.y, fx, vir[3]);
+        vir[4] = fmaf(e.y, fy, vir[4]);
+        vir[5] = fmaf(e.y, fz, vir[5]);
+        vir[6] = fmaf(e.z, fx, vir[6]);
+        vir[7] = fmaf(e.z, fy, vir[7]);
+        vir[8] = fmaf(e.z, fz, vir[8]);
+    }
+    fix = warp_sum(fix);
+    fiy = warp_sum(fiy);
+    fiz = warp_sum(fiz);
+    if (lane == 0) atomicAdd(&F4[i_s], make_float4(fix, fiy, fiz, 0.f));
+    __syncwarp();
+}
+
+template <int KRT, int KAT, bool EXACT>
+__global__ void __launch_bounds__(kPThreads, 2)
+    k_potential(Basis B, FusedNet net, Grid g, Caps caps, const float4 *__restrict__ pos4,
+                const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,
+                const float *__restrict__ scale, float4 *__restrict__ F4, float *__restrict__ eatom,
+                double *__restrict__ e_part, double *__restrict__ vir_part, unsigned long long *__restrict__ stats,
+                unsigned *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_tw[kMaxSpecies];
+    __shared__ float s_vir[kPWarps][9];
+    __shared__ double s_e[kPWarps];
+    __shared__ int s_next;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_off = g.n_off;
+    const int tile = caps.tile;
+    const PLayout L = make_playout(n_off, tile, caps.nb, caps.ang, B.n_species, net.stride);
+    int *off_start = reinterpret_cast<int *>(smem + L.off_start);
+    int *off_count = reinterpret_cast<int *>(smem + L.off_count);
+    int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);
+    float4 *off_shift = reinterpret_cast<float4 *>(smem + L.off_shift);
+    float4 *s_pos = reinterpret_cast<float4 *>(smem + L.s_pos);
+    int *s_idx = reinterpret_cast<int *>(smem + L.s_idx);
+    float *s_par = reinterpret_cast<float *>(smem + L.params);
+    unsigned char *wb = smem + L.warp_base + L.warp_bytes * warp;
+    WarpLists W;
+    W.e_d = reinterpret_cast<float4 *>(wb + L.e_d);
+    W.e_c = reinterpret_cast<float2 *>(wb + L.e_c);
+    W.e_j = reinterpret_cast<int *>(wb + L.e_j);
+    W.e_fx = reinterpret_cast<float *>(wb + L.e_fx);
+    W.e_fy = reinterpret_cast<float *>(wb + L.e_fy);
+    W.e_fz = reinterpret_cast<float *>(wb + L.e_fz);
+    W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
+    W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
+    W.coef = reinterpret_cast<float *>(wb + L.coef);
+
+#pragma unroll
+    for (int t = 0; t < kMaxSpecies; ++t)
+        if (tid == t) s_tw[t] = B.type_weight[t];
+    if (tid == 0) s_next = 0;
+    const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
+
+    // ---- network parameters of every species into the shared-memory layout
+    for (int t = 0; t < B.n_species; ++t) {
+        const float *src = params + (size_t)t * net.n_params;
+        float *dst = s_par + t * net.stride;
+        const int H1 = net.H[1], H1p = odd(H1);
+        for (int idx = tid; idx < kSlots * H1p; idx += kPThreads) {
+            const int slot = idx / H1p, o = idx % H1p;
+            const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
+            dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
+        }
+        for (int o = tid; o < H1; o += kPThreads) dst[net.offB[1] + o] = src[net.srcOff[1] + H1 * D + o];
+#pragma unroll
+        for (int l = 2; l < kMaxLayers; ++l) {
+            if (l >= net.L) break;
+            const int Hi = net.H[l - 1], Ho = net.H[l], Hip = odd(Hi);
+            for (int idx = tid; idx < Ho * Hip; idx += kPThreads) {
+                const int o = idx / Hip, k = idx % Hip;
+                dst[net.offW[l] + idx] = k < Hi ? src[net.srcOff[l] + o * Hi + k] : 0.f;
+            }
+            for (int o = tid; o < Ho; o += kPThreads) dst[net.offB[l] + o] = src[net.srcOff[l] + Ho * Hi + o];
+        }
+        const int Hl = net.Hlast;
+        for (int k = tid; k < Hl; k += kPThreads) dst[net.offWL + k] = src[net.srcOffL + k];
+        if (tid == 0) dst[net.offBL] = src[net.srcOffL + Hl];
+        for (int slot = tid; slot < kSlots; slot += kPThreads) {
+            const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
+            dst[net.offShift + slot] = col >= 0 ? shift[t * D + col] : 0.f;
+            dst[net.offScale + slot] = col >= 0 ? scale[t * D + col] : 0.f;
+        }
+    }
+
+    // ---- neighbour-cell table: start, count and image shift of every offset
+    const int cell = blockIdx.x;
+    const int cx = cell % g.nc[0], cy = (cell / g.nc[0]) % g.nc[1], cz = cell / (g.nc[0] * g.nc[1]);
+    const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
+    for (int o = tid; o < n_off; o += kPThreads) {
+        const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
+        const int ux = cx + ox, uy = cy + oy, uz = cz + oz;
+        const int vx = ux - floor_div(ux, g.nc[0]) * g.nc[0];
+        const int vy = uy - floor_div(uy, g.nc[1]) * g.nc[1];
+        const int vz = uz - floor_div(uz, g.nc[2]) * g.nc[2];
+        const int nc = (vz * g.nc[1] + vy) * g.nc[0] + vx;
+        const int s0 = cell_start[nc];
+        off_start[o] = s0;
+        off_count[o] = cell_start[nc + 1] - s0;
+        off_shift[o] = make_float4(ox * g.hf[0], oy * g.hf[1], oz * g.hf[2],
+                                   __int_as_float((ox | oy | oz) != 0 ? 1 : 0));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int carry = 0;
+        for (int base = 0; base < n_off; base += 32) {
+            const int o = base + lane;
+            const int v = o < n_off ? off_count[o] : 0;
+            int x = v;
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const int y = __shfl_up_sync(kFull, x, s);
+                if (lane >= s) x += y;
+            }
+            if (o < n_off) off_prefix[o] = carry + x - v;
+            carry += __shfl_sync(kFull, x, 31);
+        }
+        if (lane == 0) off_prefix[n_off] = carry;
+    }
+    __syncthreads();
+
+    const int total = off_prefix[n_off];
+    const int c0 = cell_start[cell];
+    const int cnt = cell_start[cell + 1] - c0;
+    const int n_chunks = (total + tile - 1) / tile;
+    auto stage = [&](int chunk) {
+        const int base = chunk * tile;
+        const int len = min(tile, total - base);
+        for (int t = tid; t < len; t += kPThreads) {
+            const int q = base + t;
+            int lo = 0, hi = n_off - 1;  // largest o with off_prefix[o] <= q
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (off_prefix[mid] <= q) lo = mid; else hi = mid - 1;
+            }
+            const int j = off_start[lo] + (q - off_prefix[lo]);
+            const float4 p = pos4[j];
+            const float4 sh = off_shift[lo];
+            s_pos[t] = make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w);
+            s_idx[t] = j | (__float_as_int(sh.w) ? kShiftBit : 0);
+        }
+    };
+
+    float vir[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vir[k] = 0.f;
+    double e_acc = 0.0;
+    unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
+
+    auto finish_list = [&](int &nnb, int &nang) {
+        if (nnb > caps.nb) {  // entries past the capacity were dropped
+            if (lane == 0) atomicOr(err, kErrNbCap);
+            nnb = caps.nb;
+        }
+        __syncwarp();
+        complete_list(B, s_tw, caps, W, lane, nnb, nang, err);
+        if (nang > caps.ang) {
+            if (lane == 0) atomicOr(err, kErrAngCap);
+            nang = caps.ang;
+        }
+        st_nb += nnb;
+        st_ang += nang;
+        st_pairs += (unsigned long long)(nang * (nang - 1) / 2);
+        __syncwarp();
+    };
+
+    if (n_chunks <= 1) {
+        if (total > 0) stage(0);
+        __syncthreads();
+        for (;;) {
+            int a = 0;
+            if (lane == 0) a = atomicAdd(&s_next, 1);
+            a = __shfl_sync(kFull, a, 0);
+            if (a >= cnt) break;
+            const int i_s = c0 + a;
+            const float4 ui = pos4[i_s];
+            int nnb = 0, nang = 0;
+            scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
+            finish_list(nnb, nang);
+            process_atom<KRT, KAT, EXACT>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom, e_acc, vir);
+        }
+    } else {
+        const int n_rounds = (cnt + kPWarps - 1) / kPWarps;
+        for (int round = 0; round < n_rounds; ++round) {
+            const int a = round * kPWarps + warp;
+            const bool active = a < cnt;
+            const int i_s = c0 + a;
+            const float4 ui = active ? pos4[i_s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            int nnb = 0, nang = 0;
+            for (int chunk = 0; chunk < n_chunks; ++chunk) {
+                __syncthreads();
+                stage(chunk);
+                __syncthreads();
+                if (active) scan_tile(s_pos, s_idx, min(tile, total - chunk * tile), ui, i_s, B, caps, W, lane, nnb);
+            }
+            if (active) {
+                finish_list(nnb, nang);
+                process_atom<KRT, KAT, EXACT>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom, e_acc, vir);
+            }
+        }
+    }
+
+    // ---- CTA partials: statistics, energy (FP64), virial (FP32 lanes -> FP64)
+    if (lane == 0 && st_nb) {
+        atomicAdd(&stats[0], st_nb);
+        atomicAdd(&stats[1], st_ang);
+        atomicAdd(&stats[2], st_pairs);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float v = warp_sum(vir[k]);
+        if (lane == 0) s_vir[warp][k] = v;
+    }
+    if (lane == 0) s_e[warp] = e_acc;
+    __syncthreads();
+    if (tid < 9) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kPWarps; ++w) s += (double)s_vir[w][tid];
+        vir_part[(size_t)blockIdx.x * 9 + tid] = s;
+    }
+    if (tid == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kPWarps; ++w) s += s_e[w];
+        e_part[blockIdx.x] = s;
+    }
+}
+
+template <int KRT, int KAT, bool EXACT>
+cudaError_t launch_fused(Context &c, const Grid &g, const FusedNet &net) {
+    const size_t smem =
+        make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
+    auto kern = k_potential<KRT, KAT, EXACT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, c.caps, c.d_pos4, c.d_cell_start, c.d_params,
+                                                 c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_e_part, c.d_vir_part,
+                                                 c.d_stats, c.d_err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_supported(const Context &c) {
+    if (c.precision != AENET_FP32) return false;
+    for (int l = 1; l < c.net.n_layers; ++l)
+        if (c.net.widths[l] > 32) return false;
+    return true;
+}
+
+size_t fused_smem_bytes(const Context &c, const Grid &g) {
+    const FusedNet net = make_fused_net(c.net);
+    return make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
+}
+
+cudaError_t launch_fused_potential(Context &c, const Grid &g, int n) {
+    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
+    if (e != cudaSuccess) return e;
+    const FusedNet net = make_fused_net(c.net);
+    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
+    if (Kr == 17 && Ka == 9) return launch_fused<17, 9, true>(c, g, net);
+    if (Kr == 21 && Ka == 7) return launch_fused<21, 7, true>(c, g, net);
+    if (Kr <= 20 && Ka <= 12) return launch_fused<20, 12, false>(c, g, net);
+    if (Kr <= 24 && Ka <= 8) return launch_fused<24, 8, false>(c, g, net);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace aenet
