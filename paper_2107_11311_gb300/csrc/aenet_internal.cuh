@@ -133,6 +133,14 @@ struct Context {
     int *d_step = nullptr;         // MD record counter
     unsigned *d_done = nullptr;    // last-CTA counter of the MD reduction (left at 0)
 
+    // species grouping of the BF16 network kernel
+    int *d_sp_cnt = nullptr;       // [kMaxSpecies], kept at 0 between evaluations
+    int *d_sp_off = nullptr;       // [kMaxSpecies]
+    int *d_sp_rank = nullptr;      // [n]
+    int *d_sp_list = nullptr;      // [n] sorted indices grouped by species
+    int4 *d_tiles = nullptr;       // [max tiles] (list offset, rows, species, 0)
+    int *d_n_tiles = nullptr;
+
     // staging of host arrays
     int cap_stage = 0;
     double *d_pos = nullptr, *d_vel = nullptr, *d_forces = nullptr, *d_eatom_out = nullptr;
@@ -170,22 +178,27 @@ cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, co
 // The scan + scatter half of launch_cells (after the counts are in place).
 cudaError_t launch_sort(Context &c, const Grid &g, int n);
 
-// Descriptor of every atom into c.d_G (rows a3-a5).
+// Descriptor of every atom into c.d_G (rows a3-a5; k_potential, descriptor mode).
 cudaError_t launch_fp_forward(Context &c, const Grid &g, int n);
 
 // Per-species networks: E_i and dE/dG_i (row a6), energy block partials.
 cudaError_t launch_ann(Context &c, int n);
 
-// Forces and virial partials from dE/dG (row a8).
+// Forces and virial partials from c.d_dEdG (row a8; k_potential, forces mode).
 cudaError_t launch_fp_backward(Context &c, const Grid &g, int n);
 
 // Energy and virial reductions (row a7) over n_eparts energy partials and the
 // cells' virial partials, and outputs in input order.
 cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom);
 
+// BF16 tensor-core network kernel (precision forms; two hidden layers <= 32).
+bool bf16_supported(const Net &net);
+int bf16_max_tiles(const Context &c, int n);
+int bf16_eparts(const Context &c, int n);
+cudaError_t launch_ann_bf16(Context &c, int n);
+
 // Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
 bool fused_supported(const Context &c);
-size_t fused_smem_bytes(const Context &c, const Grid &g);
 cudaError_t launch_fused_potential(Context &c, const Grid &g, int n);
 int ann_blocks(int n);
 
@@ -206,8 +219,8 @@ cudaError_t launch_md_kick_finish(Context &c, const Grid &g, int n, int n_eparts
 // Message reported by aenet_last_error(NULL) for calls made without a context.
 void set_context_free_error(const char *msg);
 
-// Dynamic shared memory bytes of the fingerprint kernels for given capacities.
-size_t fp_smem_bytes(const Grid &g, const Caps &caps, bool backward);
+// Dynamic shared memory bytes of the potential kernel in the context's mode.
+size_t potential_smem_bytes(const Context &c, const Grid &g);
 size_t ann_smem_bytes(const Context &c);
 
 }  // namespace aenet

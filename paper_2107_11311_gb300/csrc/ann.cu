@@ -130,11 +130,6 @@ size_t ann_smem_bytes(const Context &c) {
                             (size_t)kAnnThreads * ann_row_len(net));
 }
 
-cudaError_t prepare_bf16_weights(Context &c) {
-    (void)c;
-    return cudaErrorNotSupported;
-}
-
 int ann_blocks(int n) { return (n + kAnnThreads - 1) / kAnnThreads; }
 
 cudaError_t launch_ann(Context &c, int n) {

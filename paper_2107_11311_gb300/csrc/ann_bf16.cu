@@ -1,0 +1,436 @@
+// Row a6 of the path in the precision form: the per-species networks (Sec. II.A,
+// Eq. ANN-layer; two tanh hidden layers, linear output) and their
+// back-propagation to dE/dG as dense BF16 tensor-core products over atoms
+// grouped by species, accumulated in FP32.
+//
+// Atoms are grouped by species into 16-row tiles (one warp per tile). Each
+// layer is one small GEMM on mma.m16n8k16 (BF16 x BF16 -> FP32):
+//   forward   Z1 = g W1^T (K = D padded to 64), Z2 = X1 W2^T, E = X2 w3 + b3
+//   backward  dX1 = (delta2) W2, dE/dg = (delta1) W1
+// The accumulator fragment of two adjacent n8 tiles is the A fragment of the
+// next k16 step, so activations never leave registers. The standardisation
+// g = (G - shift) * scale and tanh' stay in FP32. AENET_BF16X3 splits every
+// operand into hi + lo BF16 parts and sums hi*hi + hi*lo + lo*hi.
+// Weights are packed once at set-up into fragment order (one 64-bit load per
+// lane per fragment).
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "aenet_internal.cuh"
+
+namespace aenet {
+
+namespace {
+
+constexpr int kKD = 64;       // padded descriptor length
+constexpr int kTileRows = 16;
+constexpr int kAnnWarps = 4;  // tiles per CTA
+
+// Packed-weight layout (uint32 words, each = 2 BF16), per species, per part
+// (hi, lo): for each GEMM a block of [k-steps][n-tiles][32 lanes][2 words].
+struct PackedNet {
+    int H1p, H2p;              // hidden widths padded to 16
+    int off_w1f, off_w2f, off_w2b, off_w1b;  // word offsets inside a species/part block
+    int words;                 // words per species/part block
+};
+
+__host__ __device__ inline int pad16(int x) { return (x + 15) & ~15; }
+
+PackedNet make_packed(int H1, int H2) {
+    PackedNet p{};
+    p.H1p = pad16(H1);
+    p.H2p = pad16(H2);
+    int w = 0;
+    p.off_w1f = w;  // K = 64, N = H1p
+    w += (kKD / 16) * (p.H1p / 8) * 64;
+    p.off_w2f = w;  // K = H1p, N = H2p
+    w += (p.H1p / 16) * (p.H2p / 8) * 64;
+    p.off_w2b = w;  // K = H2p, N = H1p
+    w += (p.H2p / 16) * (p.H1p / 8) * 64;
+    p.off_w1b = w;  // K = H1p, N = 64
+    w += (p.H1p / 16) * (kKD / 8) * 64;
+    p.words = w;
+    return p;
+}
+
+uint16_t f2bf(float x) {
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t *>(&b);
+}
+float bf2f(uint16_t u) {
+    __nv_bfloat16 b;
+    *reinterpret_cast<uint16_t *>(&b) = u;
+    return __bfloat162float(b);
+}
+
+// Pack B[k][n] (K x N, given by a functor) into mma B-fragment order, hi and lo.
+template <class F>
+void pack_b(F B, int K, int N, uint32_t *hi, uint32_t *lo) {
+    for (int ks = 0; ks < K / 16; ++ks)
+        for (int nt = 0; nt < N / 8; ++nt)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                const int n = nt * 8 + g;
+                for (int r = 0; r < 2; ++r) {
+                    const int k0 = ks * 16 + 2 * t + 8 * r;
+                    uint16_t h[2], l[2];
+                    for (int e = 0; e < 2; ++e) {
+                        const float v = B(k0 + e, n);
+                        h[e] = f2bf(v);
+                        l[e] = f2bf(v - bf2f(h[e]));
+                    }
+                    const size_t idx = ((size_t)(ks * (N / 8) + nt) * 32 + lane) * 2 + r;
+                    hi[idx] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+                    lo[idx] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+                }
+            }
+}
+
+__device__ inline uint32_t pack_bf2(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Split (a, b) into BF16 hi and lo parts.
+__device__ inline void split_bf2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = pack_bf2(a - hf.x, b - hf.y);
+}
+
+__device__ inline void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C[16 x NT*8] += A[16 x KS*16] * B, A given as hi/lo fragments per k-step.
+template <int KS, int NT, bool X3>
+__device__ inline void gemm(float (&C)[NT][4], const uint32_t (&Ah)[KS][4], const uint32_t (&Al)[KS][4],
+                            const uint2 *__restrict__ Bh, const uint2 *__restrict__ Bl, int lane) {
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const uint2 bh = Bh[(ks * NT + nt) * 32 + lane];
+            mma_bf16(C[nt], Ah[ks], bh.x, bh.y);
+            if (X3) {
+                const uint2 bl = Bl[(ks * NT + nt) * 32 + lane];
+                mma_bf16(C[nt], Ah[ks], bl.x, bl.y);
+                mma_bf16(C[nt], Al[ks], bh.x, bh.y);
+            }
+        }
+}
+
+// Accumulator tiles (FP32, 16 x NT*8) -> A fragments of the next GEMM (K = NT*8).
+template <int NT, bool X3>
+__device__ inline void to_a(const float (&C)[NT][4], uint32_t (&Ah)[NT / 2][4], uint32_t (&Al)[NT / 2][4]) {
+#pragma unroll
+    for (int ks = 0; ks < NT / 2; ++ks) {
+        const float *c0 = C[2 * ks], *c1 = C[2 * ks + 1];
+        if (X3) {
+            split_bf2(c0[0], c0[1], Ah[ks][0], Al[ks][0]);
+            split_bf2(c0[2], c0[3], Ah[ks][1], Al[ks][1]);
+            split_bf2(c1[0], c1[1], Ah[ks][2], Al[ks][2]);
+            split_bf2(c1[2], c1[3], Ah[ks][3], Al[ks][3]);
+        } else {
+            Ah[ks][0] = pack_bf2(c0[0], c0[1]);
+            Ah[ks][1] = pack_bf2(c0[2], c0[3]);
+            Ah[ks][2] = pack_bf2(c1[0], c1[1]);
+            Ah[ks][3] = pack_bf2(c1[2], c1[3]);
+        }
+    }
+}
+
+struct AnnBf16Args {
+    int n, D, n_species;
+    PackedNet pk;
+    int H1, H2;
+    const float *G;          // [n, D] sorted order
+    const int *list;         // atoms grouped by species
+    const int4 *tiles;       // (list offset, rows, species, 0)
+    const int *n_tiles;
+    const uint32_t *wpk;     // packed weights [species][2 parts][words]
+    const float *bias;       // [species][H1p + H2p + H2p + 1]: b1, b2, w3, b3 (FP32, zero padded)
+    const float *shift, *scale;  // [species][D]
+    float *dEdG, *eatom;
+    double *e_part;          // [max tiles]
+};
+
+template <int H1T, int H2T, bool X3>
+__global__ void __launch_bounds__(32 * kAnnWarps) k_ann_bf16(AnnBf16Args a) {
+    constexpr int NT1 = H1T / 8, NT2 = H2T / 8, KS1 = kKD / 16, KSH1 = H1T / 16, KSH2 = H2T / 16;
+    const int lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * kAnnWarps + (threadIdx.x >> 5);
+    const int g = lane >> 2, tq = lane & 3;
+    if (tile >= *a.n_tiles) {
+        if (lane == 0) a.e_part[tile] = 0.0;
+        return;
+    }
+    const int4 td = a.tiles[tile];
+    const int sp = td.z;
+    const int r0 = g, r1 = g + 8;
+    const bool v0 = r0 < td.y, v1 = r1 < td.y;
+    const int s0 = v0 ? a.list[td.x + r0] : -1, s1 = v1 ? a.list[td.x + r1] : -1;
+    const int D = a.D;
+    const float *sh = a.shift + sp * D, *sc = a.scale + sp * D;
+    const uint32_t *wbase = a.wpk + (size_t)sp * 2 * a.pk.words;
+    const uint2 *Wh = reinterpret_cast<const uint2 *>(wbase), *Wl = reinterpret_cast<const uint2 *>(wbase + a.pk.words);
+    const float *bias = a.bias + sp * (a.pk.H1p + 2 * a.pk.H2p + 1);
+
+    // ---- layer 1 input: standardised descriptor rows as A fragments (K = 64)
+    uint32_t A0h[KS1][4], A0l[KS1][4];
+#pragma unroll
+    for (int ks = 0; ks < KS1; ++ks) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {      // column half: +0 / +8
+            const int col = ks * 16 + 2 * tq + 8 * h;
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {  // row g / g + 8
+                const int s = rr ? s1 : s0;
+                float x0 = 0.f, x1 = 0.f;
+                if (s >= 0) {
+                    if (col < D) x0 = (a.G[(size_t)s * D + col] - sh[col]) * sc[col];
+                    if (col + 1 < D) x1 = (a.G[(size_t)s * D + col + 1] - sh[col + 1]) * sc[col + 1];
+                }
+                uint32_t hi, lo = 0;
+                if (X3) split_bf2(x0, x1, hi, lo); else hi = pack_bf2(x0, x1);
+                A0h[ks][2 * h + rr] = hi;
+                A0l[ks][2 * h + rr] = lo;
+            }
+        }
+    }
+    // ---- forward
+    float C1[NT1][4];
+#pragma unroll
+    for (int nt = 0; nt < NT1; ++nt) {
+        const float b0 = bias[nt * 8 + 2 * tq], b1 = bias[nt * 8 + 2 * tq + 1];
+        C1[nt][0] = b0; C1[nt][1] = b1; C1[nt][2] = b0; C1[nt][3] = b1;
+    }
+    gemm<KS1, NT1, X3>(C1, A0h, A0l, Wh + a.pk.off_w1f / 2, Wl + a.pk.off_w1f / 2, lane);
+#pragma unroll
+    for (int nt = 0; nt < NT1; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) C1[nt][e] = (nt * 8 + 2 * tq + (e & 1) < a.H1) ? tanhf(C1[nt][e]) : 0.f;
+    uint32_t A1h[KSH1][4], A1l[KSH1][4];
+    to_a<NT1, X3>(C1, A1h, A1l);
+    float C2[NT2][4];
+    const float *b2 = bias + a.pk.H1p;
+#pragma unroll
+    for (int nt = 0; nt < NT2; ++nt) {
+        const float b0 = b2[nt * 8 + 2 * tq], b1 = b2[nt * 8 + 2 * tq + 1];
+        C2[nt][0] = b0; C2[nt][1] = b1; C2[nt][2] = b0; C2[nt][3] = b1;
+    }
+    gemm<KSH1, NT2, X3>(C2, A1h, A1l, Wh + a.pk.off_w2f / 2, Wl + a.pk.off_w2f / 2, lane);
+    // output layer in FP32 on the accumulator fragments: E_row = sum_n w3_n x2_n + b3
+    const float *w3 = bias + a.pk.H1p + a.pk.H2p;
+    const float b3 = bias[a.pk.H1p + 2 * a.pk.H2p];
+    float e0 = 0.f, e1 = 0.f;
+    float D2[NT2][4];  // delta2 = (1 - x2^2) w3
+#pragma unroll
+    for (int nt = 0; nt < NT2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int col = nt * 8 + 2 * tq + (e & 1);
+            const float x = col < a.H2 ? tanhf(C2[nt][e]) : 0.f;
+            const float w = w3[col];
+            if (e < 2) e0 = fmaf(w, x, e0); else e1 = fmaf(w, x, e1);
+            D2[nt][e] = (1.0f - x * x) * w;
+        }
+    e0 += __shfl_xor_sync(0xffffffffu, e0, 1);
+    e0 += __shfl_xor_sync(0xffffffffu, e0, 2);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 1);
+    e1 += __shfl_xor_sync(0xffffffffu, e1, 2);
+    e0 += b3;
+    e1 += b3;
+    // ---- backward: dX1 = delta2 W2, delta1 = (1 - x1^2) dX1, dE/dg = delta1 W1
+    uint32_t A2h[KSH2][4], A2l[KSH2][4];
+    to_a<NT2, X3>(D2, A2h, A2l);
+    float C3[NT1][4];
+#pragma unroll
+    for (int nt = 0; nt < NT1; ++nt) C3[nt][0] = C3[nt][1] = C3[nt][2] = C3[nt][3] = 0.f;
+    gemm<KSH2, NT1, X3>(C3, A2h, A2l, Wh + a.pk.off_w2b / 2, Wl + a.pk.off_w2b / 2, lane);
+#pragma unroll
+    for (int nt = 0; nt < NT1; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) C3[nt][e] *= (1.0f - C1[nt][e] * C1[nt][e]);
+    uint32_t A3h[KSH1][4], A3l[KSH1][4];
+    to_a<NT1, X3>(C3, A3h, A3l);
+    float C4[kKD / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < kKD / 8; ++nt) C4[nt][0] = C4[nt][1] = C4[nt][2] = C4[nt][3] = 0.f;
+    gemm<KSH1, kKD / 8, X3>(C4, A3h, A3l, Wh + a.pk.off_w1b / 2, Wl + a.pk.off_w1b / 2, lane);
+    // ---- outputs: dE/dG = dE/dg * scale (FP32), E_i, tile energy partial
+#pragma unroll
+    for (int nt = 0; nt < kKD / 8; ++nt) {
+        const int col = nt * 8 + 2 * tq;
+        if (col < D) {
+            if (s0 >= 0) {
+                a.dEdG[(size_t)s0 * D + col] = C4[nt][0] * sc[col];
+                if (col + 1 < D) a.dEdG[(size_t)s0 * D + col + 1] = C4[nt][1] * sc[col + 1];
+            }
+            if (s1 >= 0) {
+                a.dEdG[(size_t)s1 * D + col] = C4[nt][2] * sc[col];
+                if (col + 1 < D) a.dEdG[(size_t)s1 * D + col + 1] = C4[nt][3] * sc[col + 1];
+            }
+        }
+    }
+    double et = 0.0;
+    if (tq == 0) {
+        if (s0 >= 0) {
+            a.eatom[s0] = e0;
+            et += e0;
+        }
+        if (s1 >= 0) {
+            a.eatom[s1] = e1;
+            et += e1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) et += __shfl_xor_sync(0xffffffffu, et, o);
+    if (lane == 0) a.e_part[tile] = et;
+}
+
+// ---- species grouping: count, scan into 16-row tiles, scatter
+__global__ void k_species_count(int n, const float4 *__restrict__ pos4, int *__restrict__ cnt, int *__restrict__ rank) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    rank[s] = atomicAdd(&cnt[__float_as_int(pos4[s].w)], 1);
+}
+
+// Species offsets and 16-row tiles: thread 0 scans the (<= 8) species counts,
+// then all threads write the tile table in parallel; counts are reset for the
+// next evaluation.
+__global__ void k_species_tiles(int n_species, int *__restrict__ cnt, int *__restrict__ off, int4 *__restrict__ tiles,
+                                int *__restrict__ n_tiles) {
+    __shared__ int s_cnt[kMaxSpecies], s_off[kMaxSpecies], s_t0[kMaxSpecies + 1];
+    if (threadIdx.x == 0) {
+        int o = 0, nt = 0;
+        for (int t = 0; t < n_species; ++t) {
+            s_cnt[t] = cnt[t];
+            s_off[t] = o;
+            s_t0[t] = nt;
+            off[t] = o;
+            o += s_cnt[t];
+            nt += (s_cnt[t] + kTileRows - 1) / kTileRows;
+        }
+        s_t0[n_species] = nt;
+        *n_tiles = nt;
+    }
+    __syncthreads();
+    const int total = s_t0[n_species];
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        int t = 0;
+        while (t + 1 < n_species && s_t0[t + 1] <= k) ++t;
+        const int r = (k - s_t0[t]) * kTileRows;
+        tiles[k] = make_int4(s_off[t] + r, min(kTileRows, s_cnt[t] - r), t, 0);
+    }
+    __syncthreads();
+    if (threadIdx.x < n_species) cnt[threadIdx.x] = 0;
+}
+
+__global__ void k_species_scatter(int n, const float4 *__restrict__ pos4, const int *__restrict__ off,
+                                  const int *__restrict__ rank, int *__restrict__ list) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    list[off[__float_as_int(pos4[s].w)] + rank[s]] = s;
+}
+
+template <int H1T, int H2T>
+cudaError_t launch_bf16_variant(const AnnBf16Args &a, int max_tiles, bool x3, cudaStream_t st) {
+    const int blocks = (max_tiles + kAnnWarps - 1) / kAnnWarps;
+    if (x3) k_ann_bf16<H1T, H2T, true><<<blocks, 32 * kAnnWarps, 0, st>>>(a);
+    else k_ann_bf16<H1T, H2T, false><<<blocks, 32 * kAnnWarps, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int bf16_max_tiles(const Context &c, int n) {
+    return (n + kTileRows - 1) / kTileRows + c.basis.n_species;
+}
+
+int bf16_eparts(const Context &c, int n) {
+    return (bf16_max_tiles(c, n) + kAnnWarps - 1) / kAnnWarps * kAnnWarps;
+}
+
+bool bf16_supported(const Net &net) {
+    return net.n_layers == 3 && net.widths[1] <= 32 && net.widths[2] <= 32 && net.widths[0] <= kKD;
+}
+
+cudaError_t prepare_bf16_weights(Context &c) {
+    if (!bf16_supported(c.net)) return cudaErrorInvalidValue;
+    const int D = c.net.widths[0], H1 = c.net.widths[1], H2 = c.net.widths[2];
+    const PackedNet pk = make_packed(H1, H2);
+    const int ns = c.net.n_species;
+    std::vector<float> P((size_t)ns * c.net.n_params);
+    cudaError_t e = cudaMemcpy(P.data(), c.d_params, sizeof(float) * P.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    std::vector<uint32_t> wpk((size_t)ns * 2 * pk.words, 0u);
+    const int nb = pk.H1p + 2 * pk.H2p + 1;
+    std::vector<float> bias((size_t)ns * nb, 0.f);
+    for (int t = 0; t < ns; ++t) {
+        const float *p = P.data() + (size_t)t * c.net.n_params;
+        const float *W1 = p, *b1 = W1 + H1 * D, *W2 = b1 + H1, *b2 = W2 + H2 * H1, *w3 = b2 + H2, *b3 = w3 + H2;
+        uint32_t *hi = wpk.data() + (size_t)t * 2 * pk.words, *lo = hi + pk.words;
+        auto W1f = [&](int k, int n) { return (k < D && n < H1) ? W1[n * D + k] : 0.f; };   // W1^T
+        auto W2f = [&](int k, int n) { return (k < H1 && n < H2) ? W2[n * H1 + k] : 0.f; };  // W2^T
+        auto W2b = [&](int k, int n) { return (k < H2 && n < H1) ? W2[k * H1 + n] : 0.f; };  // W2
+        auto W1b = [&](int k, int n) { return (k < H1 && n < D) ? W1[k * D + n] : 0.f; };    // W1
+        pack_b(W1f, kKD, pk.H1p, hi + pk.off_w1f, lo + pk.off_w1f);
+        pack_b(W2f, pk.H1p, pk.H2p, hi + pk.off_w2f, lo + pk.off_w2f);
+        pack_b(W2b, pk.H2p, pk.H1p, hi + pk.off_w2b, lo + pk.off_w2b);
+        pack_b(W1b, pk.H1p, kKD, hi + pk.off_w1b, lo + pk.off_w1b);
+        float *bt = bias.data() + (size_t)t * nb;
+        for (int k = 0; k < H1; ++k) bt[k] = b1[k];
+        for (int k = 0; k < H2; ++k) bt[pk.H1p + k] = b2[k];
+        for (int k = 0; k < H2; ++k) bt[pk.H1p + pk.H2p + k] = w3[k];
+        bt[pk.H1p + 2 * pk.H2p] = b3[0];
+    }
+    const size_t bytes = sizeof(uint32_t) * wpk.size() + sizeof(float) * bias.size();
+    if ((e = cudaMalloc(&c.d_wbf, bytes)) != cudaSuccess) return e;
+    c.wbf_elems = wpk.size();
+    if ((e = cudaMemcpy(c.d_wbf, wpk.data(), sizeof(uint32_t) * wpk.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    return cudaMemcpy(reinterpret_cast<uint32_t *>(c.d_wbf) + wpk.size(), bias.data(), sizeof(float) * bias.size(),
+                      cudaMemcpyHostToDevice);
+}
+
+cudaError_t launch_ann_bf16(Context &c, int n) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e;
+    k_species_count<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_pos4, c.d_sp_cnt, c.d_sp_rank);
+    k_species_tiles<<<1, 256, 0, c.stream>>>(c.basis.n_species, c.d_sp_cnt, c.d_sp_off, c.d_tiles, c.d_n_tiles);
+    k_species_scatter<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_pos4, c.d_sp_off, c.d_sp_rank, c.d_sp_list);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    AnnBf16Args a{};
+    a.n = n;
+    a.D = c.basis.D;
+    a.n_species = c.basis.n_species;
+    a.H1 = c.net.widths[1];
+    a.H2 = c.net.widths[2];
+    a.pk = make_packed(a.H1, a.H2);
+    a.G = c.d_G;
+    a.list = c.d_sp_list;
+    a.tiles = c.d_tiles;
+    a.n_tiles = c.d_n_tiles;
+    a.wpk = reinterpret_cast<const uint32_t *>(c.d_wbf);
+    a.bias = reinterpret_cast<const float *>(reinterpret_cast<const uint32_t *>(c.d_wbf) + c.wbf_elems);
+    a.shift = c.d_shift;
+    a.scale = c.d_scale;
+    a.dEdG = c.d_dEdG;
+    a.eatom = c.d_eatom;
+    a.e_part = c.d_e_part;
+    const bool x3 = c.precision == AENET_BF16X3;
+    const int mt = bf16_max_tiles(c, n);
+    if (a.pk.H1p == 16 && a.pk.H2p == 16) return launch_bf16_variant<16, 16>(a, mt, x3, c.stream);
+    if (a.pk.H1p == 32 && a.pk.H2p == 32) return launch_bf16_variant<32, 32>(a, mt, x3, c.stream);
+    if (a.pk.H1p == 16 && a.pk.H2p == 32) return launch_bf16_variant<16, 32>(a, mt, x3, c.stream);
+    return launch_bf16_variant<32, 16>(a, mt, x3, c.stream);
+}
+
+}  // namespace aenet

@@ -122,6 +122,9 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_eatom, 0, N), "cudaMalloc");
         CK(grow(c.d_F4, 0, N), "cudaMalloc");
         CK(grow(c.d_ke_part, 0, (N + 255) / 256 + 1), "cudaMalloc");
+        CK(grow(c.d_sp_rank, 0, N), "cudaMalloc");
+        CK(grow(c.d_sp_list, 0, N), "cudaMalloc");
+        CK(grow(c.d_tiles, 0, (size_t)bf16_max_tiles(c, n) + 1), "cudaMalloc");
         c.cap_atoms = n;
     }
     if (g.ncell > c.cap_cells) {
@@ -130,7 +133,7 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_vir_part, 0, (size_t)g.ncell * 9), "cudaMalloc");
         c.cap_cells = g.ncell;
     }
-    const int need_e = std::max(ann_blocks(std::max(n, 1)), g.ncell) + 1;
+    const int need_e = std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell), bf16_eparts(c, std::max(n, 1))) + 1;
     if (need_e > c.cap_blocks || !c.d_e_part) {
         CK(grow(c.d_e_part, 0, (size_t)need_e), "cudaMalloc");
         c.cap_blocks = need_e;
@@ -156,7 +159,7 @@ int check_smem(Context &c, const Grid &g) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t need = std::max(fp_smem_bytes(g, c.caps, true), fused_supported(c) ? fused_smem_bytes(c, g) : 0);
+    const size_t need = potential_smem_bytes(c, g);
     if (optin > 0 && need > (size_t)optin)
         return fail(&c, AENET_E_CAPACITY, "neighbour lists need %zu B of shared memory (limit %d B)", need, optin);
     return AENET_OK;
@@ -181,10 +184,15 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent
     } else {
         CK(launch_fp_forward(c, g, n), "descriptor kernel");
         if (evs) CK(mark(c, evs[0]), "event");
-        CK(launch_ann(c, n), "network kernel");
+        if (c.precision == AENET_FP32) {
+            CK(launch_ann(c, n), "network kernel");
+            *n_eparts = ann_blocks(n);
+        } else {
+            CK(launch_ann_bf16(c, n), "BF16 network kernel");
+            *n_eparts = bf16_eparts(c, n);
+        }
         if (evs) CK(mark(c, evs[1]), "event");
         CK(launch_fp_backward(c, g, n), "force kernel");
-        *n_eparts = ann_blocks(n);
     }
     if (evs) CK(mark(c, evs[2]), "event");
     return AENET_OK;
@@ -280,6 +288,8 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
             return fail(nullptr, AENET_E_ARG, "hidden width %d out of [1, %d]", m->widths[l], kMaxWidth);
     if (precision != AENET_FP32 && precision != AENET_BF16 && precision != AENET_BF16X3)
         return fail(nullptr, AENET_E_ARG, "unknown precision %d", precision);
+    if (precision != AENET_FP32 && !(m->n_layers == 3 && m->widths[1] <= 32 && m->widths[2] <= 32))
+        return fail(nullptr, AENET_E_ARG, "the BF16 forms need two hidden layers of width <= 32");
 
     aenet_ctx *h = new (std::nothrow) aenet_ctx();
     if (!h) return fail(nullptr, AENET_E_NOMEM, "host allocation failed");
@@ -335,6 +345,9 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
         if ((e = cudaEventCreate(&c.ev[k])) != cudaSuccess) return setup_fail(e, "cudaEventCreate");
     if ((e = cudaMalloc(&c.d_step, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_done, sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_sp_cnt, sizeof(int) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_sp_off, sizeof(int) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_n_tiles, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_result, sizeof(double) * 11)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_mass, sizeof(double) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     double masses[kMaxSpecies] = {0};
@@ -345,6 +358,7 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
         (e = cudaMemcpy(c.d_mass, masses, sizeof(masses), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(c.d_err, 0, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(c.d_done, 0, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMemset(c.d_sp_cnt, 0, sizeof(int) * kMaxSpecies)) != cudaSuccess ||
         (e = cudaMemset(c.d_stats, 0, sizeof(unsigned long long) * 4)) != cudaSuccess ||
         (e = cudaMemset(c.d_result, 0, sizeof(double) * 11)) != cudaSuccess)
         return setup_fail(e, "cudaMemcpy");
@@ -512,7 +526,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
     if (want_rec) CK(cudaMemsetAsync(c.d_step, 0, sizeof(int), c.stream), "cudaMemsetAsync");
     // frame 0: forces at the initial positions (unless continuing); a
     // neighbour-list overflow here regrows the capacities once before capture
-    int n_eparts = fused_supported(c) ? g.ncell : ann_blocks(n);
+    int n_eparts = fused_supported(c) ? g.ncell : (c.precision == AENET_FP32 ? ann_blocks(n) : bf16_eparts(c, n));
     if (!cont) {
         for (int attempt = 0; attempt < 2; ++attempt) {
             if ((rc = enqueue_compute(c, g, n, dpos, dtypes, nullptr, nullptr, &n_eparts))) return rc;
@@ -628,7 +642,8 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
     void *ptrs[] = {c.d_params, c.d_shift, c.d_scale, c.d_wbf, c.d_mass, c.d_pos4, c.d_tmp4, c.d_perm,
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
-                    c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats};
+                    c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,
+                    c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= Context::kStages; ++k)

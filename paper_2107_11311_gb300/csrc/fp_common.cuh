@@ -1,5 +1,5 @@
-// Device helpers shared by the descriptor/force kernels (fingerprint.cu) and
-// the fused potential kernel (potential.cu).
+// Device helpers of the potential kernel (potential.cu): warp reductions and
+// the flags of the staged neighbour tile.
 #pragma once
 
 #include "aenet_internal.cuh"

