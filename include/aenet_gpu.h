@@ -116,6 +116,24 @@ int aenet_compute(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t 
                   double *e_atom);
 
 /*
+ * Energies, forces and virials of many independent periodic structures in one
+ * evaluation (one binning, one potential launch over the cells of every
+ * structure, one per-structure reduction).
+ *   n_struct     >= 1
+ *   atom_offset  [n_struct + 1] int64, HOST: structure s holds atoms
+ *                atom_offset[s] .. atom_offset[s+1]-1; atom_offset[0] = 0
+ *   pos, types   [N * 3] double, [N] int32 (N = atom_offset[n_struct]), host or device
+ *   boxes        [n_struct * 3] double, HOST: orthorhombic box of each structure
+ *   energies     [n_struct] double, host or device, or NULL (FP64 sums of E_i)
+ *   forces       [N * 3] double, host or device, or NULL
+ *   virials      [n_struct * 9] double, host or device, or NULL
+ * Synchronises.
+ */
+int aenet_compute_batch(aenet_ctx *ctx, int n_struct, const int64_t *atom_offset, const double *pos,
+                        const int32_t *types, const double *boxes, double *energies, double *forces,
+                        double *virials);
+
+/*
  * Descriptor only (rows a1-a5 of the path): G [n_atoms * D] float32, host or
  * device, row i = atom i in input order, layout [radial, angular, radial_w,
  * angular_w] before standardisation. Synchronises.

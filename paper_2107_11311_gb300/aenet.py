@@ -61,6 +61,7 @@ def load(build_if_missing: bool = True):
     lib.aenet_set_stream.argtypes = [P, P]
     lib.aenet_compute.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_descriptors.argtypes = [P, I, P, P, P, P]
+    lib.aenet_compute_batch.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_md_nve.argtypes = [P, I, P, P, P, P, D, I, P, P, I]
     lib.aenet_check.argtypes = [P]
     lib.aenet_neighbor_stats.argtypes = [P, P]
@@ -207,6 +208,22 @@ class AenetGPU:
                                            _ptr(forces), _ptr(virial), _ptr(e_atom)))
         if ret:
             return dict(energy=float(energy[0]), forces=forces, virial=virial, e_atom=e_atom)
+        return None
+
+    def compute_batch(self, atom_offset, pos, types, boxes, energies=None, forces=None, virials=None):
+        """Energies [S], forces [N,3], virials [S,3,3] of S structures in one
+        evaluation; atom_offset [S+1] int64 and boxes [S,3] are host arrays."""
+        pos, types = _as(pos, np.float64), _as(types, np.int32)
+        off = np.ascontiguousarray(atom_offset, dtype=np.int64)
+        bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        S = len(off) - 1
+        ret = energies is None and forces is None and virials is None
+        if ret:
+            energies, forces, virials = np.zeros(S), np.zeros((int(off[-1]), 3)), np.zeros((S, 3, 3))
+        self._check(self.lib.aenet_compute_batch(self.h, S, _ptr(off), _ptr(pos), _ptr(types), _ptr(bx),
+                                                 _ptr(energies), _ptr(forces), _ptr(virials)))
+        if ret:
+            return dict(energies=energies, forces=forces, virials=virials)
         return None
 
     def descriptors(self, pos, types, box, out=None):

@@ -84,7 +84,15 @@ __device__ inline int bin_position(double x0, double x1, double x2, const Grid &
     return (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
 }
 
-// Capacities of the per-warp neighbour lists of the fingerprint kernels.
+// One structure of a batch: its own cell grid inside a global cell index space
+// (cells cell0 .. cell0 + ncell - 1) and its atoms (atom0 .. atom0 + natoms - 1
+// in input order).
+struct StructInfo {
+    Grid g;
+    int cell0, ncell, atom0, natoms;
+};
+
+// Capacities of the per-warp neighbour lists of the potential kernel.
 struct Caps {
     int nb;     // entries with r <= rc_max
     int ang;    // entries with r <= rc_ang
@@ -150,6 +158,13 @@ struct Context {
 
     Caps caps{};
 
+    // batched evaluation: per-structure grids (device), valid during a batch call
+    int cap_struct = 0;
+    StructInfo *d_sinfo = nullptr;     // [n_struct]
+    double *d_bres = nullptr;          // [n_struct * 10]: energy, virial[9]
+    const StructInfo *batch_sinfo = nullptr;  // non-NULL while a batch is enqueued
+    int batch_n = 0;
+
     // captured MD step
     cudaGraphExec_t md_exec = nullptr;
     struct {
@@ -177,6 +192,10 @@ struct Context {
 cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
 // The scan + scatter half of launch_cells (after the counts are in place).
 cudaError_t launch_sort(Context &c, const Grid &g, int n);
+// Binning of a batch: every atom into the cell grid of its structure.
+cudaError_t launch_cells_batch(Context &c, int n, int total_cells, const double *pos, const int32_t *types);
+// Per-structure energy (FP64 sum of E_i) and virial (FP64 sum of cell partials).
+cudaError_t launch_batch_reduce(Context &c);
 
 // Descriptor of every atom into c.d_G (rows a3-a5; k_potential, descriptor mode).
 cudaError_t launch_fp_forward(Context &c, const Grid &g, int n);
@@ -201,6 +220,9 @@ cudaError_t launch_ann_bf16(Context &c, int n);
 bool fused_supported(const Context &c);
 cudaError_t launch_fused_potential(Context &c, const Grid &g, int n);
 int ann_blocks(int n);
+
+// Forces to input order (FP64) only.
+cudaError_t launch_finalize_forces(Context &c, int n, double *forces);
 
 // Descriptor rows to input order (float).
 cudaError_t launch_unsort_G(Context &c, int n, float *G);

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <new>
 
 #include "aenet_internal.cuh"
@@ -456,6 +457,109 @@ extern "C" int aenet_compute(aenet_ctx *h, int n, const double *pos, const int32
     return compute_impl(h->c, n, pos, types, box, energy, forces, virial, e_atom, nullptr);
 }
 
+extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *atom_offset, const double *pos,
+                                   const int32_t *types, const double *boxes, double *energies, double *forces,
+                                   double *virials) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    cudaGetLastError();
+    if (n_struct < 1 || !atom_offset || !boxes) return fail(&c, AENET_E_ARG, "bad batch description");
+    if (atom_offset[0] != 0) return fail(&c, AENET_E_ARG, "atom_offset[0] must be 0");
+    for (int s = 0; s < n_struct; ++s)
+        if (atom_offset[s + 1] < atom_offset[s]) return fail(&c, AENET_E_ARG, "atom_offset must be non-decreasing");
+    if (atom_offset[n_struct] > INT32_MAX / 2) return fail(&c, AENET_E_ARG, "too many atoms");
+    const int n = (int)atom_offset[n_struct];
+    if (n > 0 && (!pos || !types)) return fail(&c, AENET_E_ARG, "pos/types NULL");
+    // per-structure grids in one global cell index space
+    std::vector<StructInfo> info((size_t)n_struct);
+    int total_cells = 0, max_off = 1;
+    double max_rho = 0.0, max_neigh = 0.0;
+    for (int s = 0; s < n_struct; ++s) {
+        int rc = make_grid(c, boxes + 3 * (size_t)s, info[s].g);
+        if (rc) return rc;
+        info[s].cell0 = total_cells;
+        info[s].ncell = info[s].g.ncell;
+        info[s].atom0 = (int)atom_offset[s];
+        info[s].natoms = (int)(atom_offset[s + 1] - atom_offset[s]);
+        total_cells += info[s].g.ncell;
+        max_off = std::max(max_off, info[s].g.n_off);
+        const double V = boxes[3 * s] * boxes[3 * s + 1] * boxes[3 * s + 2];
+        max_rho = std::max(max_rho, info[s].natoms / V);
+        max_neigh = std::max(max_neigh, (double)info[s].natoms / info[s].g.ncell * info[s].g.n_off);
+    }
+    Grid gall{};
+    gall.ncell = total_cells;
+    gall.n_off = max_off;
+    int rc = validate_types_host(c, n, types);
+    if (rc) return rc;
+    if ((rc = ensure(c, n, gall)) || (rc = ensure_stage(c, n))) return rc;
+    if (n_struct > c.cap_struct) {
+        CK(grow(c.d_sinfo, 0, (size_t)n_struct), "cudaMalloc");
+        CK(grow(c.d_bres, 0, (size_t)n_struct * 10), "cudaMalloc");
+        c.cap_struct = n_struct;
+    }
+    if (c.caps.nb == 0) {
+        Grid dens{};
+        dens.box[0] = dens.box[1] = dens.box[2] = 1.0;
+        dens.ncell = 1;
+        dens.n_off = 1;
+        c.caps = estimate_caps(c, 0, dens);
+        auto cap = [&](double rcut, double margin) {
+            const int k = (int)(1.3 * max_rho * 4.18879020478639 * rcut * rcut * rcut + margin);
+            return ((k + 15) / 16) * 16;
+        };
+        c.caps.nb = std::max(64, cap(c.basis.rc_max, 32.0));
+        c.caps.ang = std::max(32, cap(c.basis.rc_ang, 24.0));
+        c.caps.tile = std::min(1024, std::max(128, (((int)(1.25 * max_neigh + 64.0)) + 31) / 32 * 32));
+    }
+    const double *dpos;
+    const int32_t *dtypes;
+    if ((rc = stage_in(c, pos, c.d_pos, 3 * (size_t)n, &dpos))) return rc;
+    if ((rc = stage_in(c, types, c.d_types, (size_t)n, &dtypes))) return rc;
+    CK(cudaMemcpyAsync(c.d_sinfo, info.data(), sizeof(StructInfo) * n_struct, cudaMemcpyHostToDevice, c.stream),
+       "cudaMemcpyAsync");
+    const bool f_dev = is_device_ptr(forces);
+    double *dF = forces ? (f_dev ? forces : c.d_forces) : nullptr;
+    c.batch_sinfo = c.d_sinfo;
+    c.batch_n = n_struct;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
+        if ((rc = check_smem(c, gall))) break;
+        cudaError_t e = launch_cells_batch(c, n, total_cells, dpos, dtypes);
+        int n_eparts = 0;
+        if (e == cudaSuccess) rc = enqueue_potential(c, gall, n, &n_eparts, nullptr);
+        if (e == cudaSuccess && !rc) e = launch_batch_reduce(c);
+        if (e == cudaSuccess && !rc) e = launch_finalize_forces(c, n, dF);
+        if (e != cudaSuccess) rc = cuda_fail(&c, e, "batched evaluation");
+        if (rc) break;
+        rc = read_error_word(c);
+        if (rc != AENET_E_CAPACITY || attempt == 1) break;
+        c.caps.nb *= 2;
+        c.caps.ang *= 2;
+        c.caps.tile = 1024;
+        destroy_graph(c);
+    }
+    c.batch_sinfo = nullptr;
+    c.batch_n = 0;
+    if (rc) return rc;
+    // outputs: per-structure [energy, virial[9]] rows -> caller layout
+    std::vector<double> res((size_t)n_struct * 10);
+    CK(cudaMemcpyAsync(res.data(), c.d_bres, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, c.stream),
+       "result copy");
+    if (forces && !f_dev)
+        CK(cudaMemcpyAsync(forces, c.d_forces, 3 * sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c.stream),
+           "forces copy");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    std::vector<double> E((size_t)n_struct), W((size_t)n_struct * 9);
+    for (int s = 0; s < n_struct; ++s) {
+        E[s] = res[(size_t)s * 10];
+        for (int k = 0; k < 9; ++k) W[(size_t)s * 9 + k] = res[(size_t)s * 10 + 1 + k];
+    }
+    if (energies) CK(cudaMemcpy(energies, E.data(), sizeof(double) * E.size(), cudaMemcpyDefault), "energies");
+    if (virials) CK(cudaMemcpy(virials, W.data(), sizeof(double) * W.size(), cudaMemcpyDefault), "virials");
+    return AENET_OK;
+}
+
 extern "C" int aenet_descriptors(aenet_ctx *h, int n, const double *pos, const int32_t *types, const double *box,
                                  float *G) {
     if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
@@ -643,7 +747,7 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,
-                    c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles};
+                    c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= Context::kStages; ++k)

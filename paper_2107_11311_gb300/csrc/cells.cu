@@ -30,6 +30,34 @@ __global__ void k_bin_count(int n, int n_species, const double *__restrict__ pos
     slot[i] = atomicAdd(&cell_count[cell], 1);
 }
 
+// Batched binning: atom i belongs to the structure with the largest atom0 <= i
+// (binary search); its cell is offset into the global cell index space.
+__global__ void k_bin_count_batch(int n, int n_struct, int n_species, const double *__restrict__ pos,
+                                  const int32_t *__restrict__ types, const StructInfo *__restrict__ sinfo,
+                                  float4 *__restrict__ tmp4, int *__restrict__ cell_of, int *__restrict__ slot,
+                                  int *__restrict__ cell_count, unsigned *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_struct - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sinfo[mid].atom0 <= i) lo = mid; else hi = mid - 1;
+    }
+    const StructInfo &si = sinfo[lo];
+    float u[3];
+    bool finite = true;
+    const int cell = si.cell0 + bin_position(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], si.g, u, finite);
+    if (!finite) atomicOr(err, kErrNonfinite);
+    int t = types[i];
+    if (t < 0 || t >= n_species) {
+        atomicOr(err, kErrType);
+        t = 0;
+    }
+    tmp4[i] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+    cell_of[i] = cell;
+    slot[i] = atomicAdd(&cell_count[cell], 1);
+}
+
 // Exclusive scan of the cell counts by one CTA (cell counts are O(1e4-1e5)).
 __global__ void k_scan_cells(int ncell, const int *__restrict__ count, int *__restrict__ start) {
     __shared__ int warp_sums[32];
@@ -96,6 +124,21 @@ cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, co
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_sort(c, g, n);
+}
+
+cudaError_t launch_cells_batch(Context &c, int n, int total_cells, const double *pos, const int32_t *types) {
+    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * total_cells, c.stream);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_bin_count_batch<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.batch_n, c.basis.n_species, pos, types,
+                                                                 c.batch_sinfo, c.d_tmp4, c.d_cell_of, c.d_slot,
+                                                                 c.d_cell_count, c.d_err);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Grid g{};
+    g.ncell = total_cells;
     return launch_sort(c, g, n);
 }
 

@@ -187,6 +187,31 @@ __global__ void __launch_bounds__(kMdThreads)
     }
 }
 
+// One warp per structure of a batch: energy = FP64 sum of its atoms' E_i (its
+// atoms are contiguous in cell order), virial = FP64 sum of its cells' partials.
+__global__ void k_batch_reduce(int n_struct, const StructInfo *__restrict__ sinfo, const int *__restrict__ cell_start,
+                               const float *__restrict__ eatom, const double *__restrict__ vir_part,
+                               double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n_struct) return;
+    const int c0 = sinfo[s].cell0, c1 = c0 + sinfo[s].ncell;
+    const int a0 = cell_start[c0], a1 = cell_start[c1];
+    double e0 = 0.0, e1 = 0.0;
+    int k = a0 + lane;
+    for (; k + 32 < a1; k += 64) {
+        e0 += (double)eatom[k];
+        e1 += (double)eatom[k + 32];
+    }
+    if (k < a1) e0 += (double)eatom[k];
+    const double e = warp_sum_d(e0 + e1);
+    if (lane == 0) out[(size_t)s * 10] = e;
+    for (int q = 0; q < 9; ++q) {
+        const double v = warp_reduce_strided(vir_part + (size_t)c0 * 9 + q, c1 - c0, 9, lane);
+        if (lane == 0) out[(size_t)s * 10 + 1 + q] = v;
+    }
+}
+
 KickParams kick_params(const Context &c, double dt) {
     KickParams kp{};
     for (int t = 0; t < kMaxSpecies; ++t) {
@@ -207,9 +232,23 @@ cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, doub
     return cudaGetLastError();
 }
 
+cudaError_t launch_finalize_forces(Context &c, int n, double *forces) {
+    if (!forces || n <= 0) return cudaSuccess;
+    k_unsort_outputs<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_perm, c.d_F4, c.d_eatom, forces, nullptr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unsort_G(Context &c, int n, float *G) {
     if (n <= 0) return cudaSuccess;
     k_unsort_G<<<1024, 256, 0, c.stream>>>(n, c.basis.D, c.d_perm, c.d_G, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce(Context &c) {
+    const int per = kRedThreads / 32;
+    k_batch_reduce<<<(c.batch_n + per - 1) / per, kRedThreads, 0, c.stream>>>(c.batch_n, c.batch_sinfo,
+                                                                              c.d_cell_start, c.d_eatom,
+                                                                              c.d_vir_part, c.d_bres);
     return cudaGetLastError();
 }
 

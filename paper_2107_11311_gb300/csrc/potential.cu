@@ -579,9 +579,10 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     __syncwarp();
 }
 
-template <int KRT, int KAT, bool EXACT, int MODE>
+template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kPThreads, 2)
-    k_potential(Basis B, FusedNet net, Grid g, Caps caps, const float4 *__restrict__ pos4,
+    k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
+                const float4 *__restrict__ pos4,
                 const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,
                 const float *__restrict__ scale, float4 *__restrict__ F4, float *__restrict__ eatom,
                 float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
@@ -593,6 +594,19 @@ __global__ void __launch_bounds__(kPThreads, 2)
     __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the cell grid of this CTA's structure: the kernel parameter, or in a batch
+    // the grid of the structure that owns this cell (read in place, not copied)
+    int sidx = 0;
+    if constexpr (BATCH) {
+        int lo = 0, hi = n_struct - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sinfo[mid].cell0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        sidx = lo;
+    }
+    const Grid &g = BATCH ? sinfo[sidx].g : g_one;
+    const int cell0 = BATCH ? sinfo[sidx].cell0 : 0;
     const int n_off = g.n_off;
     const int tile = caps.tile;
     const PLayout L = make_playout(n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0, net.stride);
@@ -653,8 +667,9 @@ __global__ void __launch_bounds__(kPThreads, 2)
     }
 
     // ---- neighbour-cell table: start, count and image shift of every offset
-    const int cell = blockIdx.x;
-    const int cx = cell % g.nc[0], cy = (cell / g.nc[0]) % g.nc[1], cz = cell / (g.nc[0] * g.nc[1]);
+    const int cell = blockIdx.x;            // global cell
+    const int lcell = cell - cell0;         // cell inside its structure's grid
+    const int cx = lcell % g.nc[0], cy = (lcell / g.nc[0]) % g.nc[1], cz = lcell / (g.nc[0] * g.nc[1]);
     const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
     for (int o = tid; o < n_off; o += kPThreads) {
         const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
@@ -662,7 +677,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
         const int vx = ux - floor_div(ux, g.nc[0]) * g.nc[0];
         const int vy = uy - floor_div(uy, g.nc[1]) * g.nc[1];
         const int vz = uz - floor_div(uz, g.nc[2]) * g.nc[2];
-        const int nc = (vz * g.nc[1] + vy) * g.nc[0] + vx;
+        const int nc = cell0 + (vz * g.nc[1] + vy) * g.nc[0] + vx;
         const int s0 = cell_start[nc];
         off_start[o] = s0;
         off_count[o] = cell_start[nc + 1] - s0;
@@ -805,10 +820,11 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang,
                                      MODE == kFused ? c.basis.n_species : 0, net.stride)
                             .total;
-    auto kern = k_potential<KRT, KAT, EXACT, MODE>;
+    auto kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true> : k_potential<KRT, KAT, EXACT, MODE, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, c.caps, c.d_pos4, c.d_cell_start, c.d_params,
+    kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
+                                                 c.d_cell_start, c.d_params,
                                                  c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_G, c.d_dEdG,
                                                  c.d_e_part, c.d_vir_part, c.d_stats, c.d_err);
     return cudaGetLastError();
@@ -944,10 +960,11 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
                          const int *cell_start, float *Gs, unsigned long long *stats, unsigned *err) {
     const FusedNet net{};  // no network in descriptor mode
     const size_t smem = make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total;
-    auto kern = k_potential<KRT, KAT, EXACT, kDescriptor>;
+    auto kern = k_potential<KRT, KAT, EXACT, kDescriptor, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, caps, pos4, cell_start, nullptr, nullptr, nullptr, nullptr,
+    kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
+                                           nullptr,
                                            nullptr, Gs, nullptr, nullptr, nullptr, stats, err);
     return cudaGetLastError();
 }

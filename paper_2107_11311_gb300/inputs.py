@@ -317,3 +317,32 @@ def batch_sizes(n_struct: int = 512, lo: int = 32, hi: int = 2048, seed: int = 3
     """Log-uniform atom counts in [lo, hi] for the batched workload."""
     rng = np.random.default_rng(seed)
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_struct))).astype(np.int64)
+
+
+def batch_structures(n_struct: int = 512, lo: int = 32, hi: int = 2048, seed: int = 30, limit=None):
+    """The batched workload: log-uniform atom counts in [lo, hi]; the first half
+    water at 1.0 g/cm^3 (n_mol = round(N/3)), the second half the 4-species
+    amorphous solid; structure s uses seed 31 + s. Returns (water list,
+    amorphous list) of Structures; ``limit`` keeps only the first structures of
+    each half (for tests)."""
+    sizes = batch_sizes(n_struct, lo, hi, seed)
+    half = n_struct // 2
+    wat, amo = [], []
+    for s in range(n_struct):
+        if limit is not None and (s % half) >= limit:
+            continue
+        if s < half:
+            wat.append(water(max(1, int(round(sizes[s] / 3))), None, 31 + s))
+        else:
+            amo.append(amorphous(int(sizes[s]), 31 + s))
+    return wat, amo
+
+
+def concat(structures):
+    """Flatten a list of Structures into (atom_offset [S+1], pos [N,3], types [N], boxes [S,3])."""
+    off = np.zeros(len(structures) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([st.n for st in structures])
+    pos = np.concatenate([st.pos for st in structures]) if structures else np.zeros((0, 3))
+    types = np.concatenate([st.types for st in structures]).astype(np.int32) if structures else np.zeros(0, np.int32)
+    boxes = np.stack([st.box for st in structures]) if structures else np.zeros((0, 3))
+    return off, np.ascontiguousarray(pos), types, boxes
