@@ -188,6 +188,78 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """--workload batch_512: 512 independent periodic structures (log-uniform 32 ...
+    2,048 atoms; 256 water at 1.0 g/cm^3 with the water model, 256 of the
+    4-species solid with its model). One step = E+F+virial of every structure:
+    one aenet_compute_batch call per model family, against one aenet_compute call
+    per structure. Wall-clock time per step, L2 flushed between steps."""
+    import torch
+    from paper_2107_11311_gb300 import inputs
+    from paper_2107_11311_gb300.aenet import AenetGPU
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    wat, amo = inputs.batch_structures()
+    stream = torch.cuda.Stream(device=dev)
+    fams = []
+    for fam, structs in (("water", wat), ("amorphous", amo)):
+        m = inputs.make_model(fam)
+        off, pos, types, boxes = inputs.concat(structs)
+        g = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+        dpos, dtypes = torch.tensor(pos, device=dev), torch.tensor(types, device=dev)
+        E = torch.zeros(len(structs), dtype=torch.float64, device=dev)
+        F = torch.zeros((int(off[-1]), 3), dtype=torch.float64, device=dev)
+        V = torch.zeros((len(structs), 3, 3), dtype=torch.float64, device=dev)
+        single = [(torch.tensor(st.pos, device=dev), torch.tensor(st.types, device=dev), st.box) for st in structs]
+        fams.append((g, off, dpos, dtypes, boxes, E, F, V, single))
+    n_atoms = sum(int(f[1][-1]) for f in fams)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def batched():
+        for g, off, dpos, dtypes, boxes, E, F, V, _ in fams:
+            g.compute_batch(off, dpos, dtypes, boxes, energies=E, forces=F, virials=V)
+
+    e1 = torch.zeros(1, dtype=torch.float64, device=dev)
+    f1 = torch.zeros((2048, 3), dtype=torch.float64, device=dev)
+    v1 = torch.zeros((3, 3), dtype=torch.float64, device=dev)
+
+    def per_structure():
+        for g, *_rest, single in fams:
+            for p, t, b in single:
+                g.compute(p, t, b, energy=e1, forces=f1[:p.shape[0]], virial=v1)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            tot += time.perf_counter() - t0
+        return tot
+
+    with torch.cuda.stream(stream):
+        t_b = timed(batched, args.steps)
+        t_s = timed(per_structure, max(1, args.steps // 10))
+    steps_s = max(1, args.steps // 10)
+    if rank == 0:
+        line = {"metric": METRIC, "value": n_atoms * args.steps / t_b, "unit": "atom-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
+                "config": {"workload": "batch_512", "structures": 512, "atoms": n_atoms,
+                           "sizes": "log-uniform 32..2048; 256 water + 256 4-species solid",
+                           "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                           "timing": "wall clock per step around synchronous C-ABI calls"},
+                "per_structure_launches": {"value": n_atoms * steps_s / t_s, "ms_per_step": 1e3 * t_s / steps_s}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +279,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch_512":
+        run_batch(args, rank, world)
         return
 
     import torch

@@ -227,6 +227,33 @@ int aenet_descriptors_noalloc(int n_atoms, const double *pos, const int32_t *typ
                               int n_species, const double *type_weight, double rc_rad, int order_rad,
                               double rc_ang, int order_ang, float *G, void *stream);
 
+/*
+ * Context options. AENET_OPT_KEEP_ACTIVATIONS (value 0/1): when on, every
+ * aenet_compute / aenet_compute_batch keeps one activation record per atom
+ * (standardised descriptor g, and x_l, delta_l of every hidden layer) so that
+ * aenet_grad_weights can follow; costs (D + 2 sum H_l) floats per atom.
+ */
+#define AENET_OPT_KEEP_ACTIVATIONS 1
+int aenet_set_option(aenet_ctx *ctx, int option, int value);
+
+/*
+ * Energy gradient with respect to the network parameters (back-propagation,
+ * Sec. II.C), summed over all atoms of the last evaluation:
+ *   dE/dW^l[o][k] = sum_{i of species t} delta^l_i[o] x^{l-1}_i[k],
+ *   dE/db^l[o]    = sum_{i of species t} delta^l_i[o]     (delta^L = 1, x^0 = g)
+ * dEdW: [n_species * n_params] double, host or device, same layout as the
+ * model's params. FP64 sums of FP32 products, deterministic. Returns
+ * AENET_E_STATE if the last evaluation kept no activation records.
+ * Synchronises.
+ */
+int aenet_grad_weights(aenet_ctx *ctx, double *dEdW);
+
+/*
+ * Replace the network parameters ([n_species * n_params] double, HOST, same
+ * layout as at set-up). A captured MD step picks them up on its next replay.
+ */
+int aenet_set_params(aenet_ctx *ctx, const double *params);
+
 /* Synchronise the context's stream and report any recorded device error. */
 int aenet_check(aenet_ctx *ctx);
 

@@ -17,6 +17,7 @@ from . import build as _build
 
 AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
 AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING = 1, 2, 4
+AENET_OPT_KEEP_ACTIVATIONS = 1
 STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
 PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
 
@@ -62,6 +63,9 @@ def load(build_if_missing: bool = True):
     lib.aenet_compute.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_descriptors.argtypes = [P, I, P, P, P, P]
     lib.aenet_compute_batch.argtypes = [P, I, P, P, P, P, P, P, P]
+    lib.aenet_set_option.argtypes = [P, I, I]
+    lib.aenet_grad_weights.argtypes = [P, P]
+    lib.aenet_set_params.argtypes = [P, P]
     lib.aenet_md_nve.argtypes = [P, I, P, P, P, P, D, I, P, P, I]
     lib.aenet_check.argtypes = [P]
     lib.aenet_neighbor_stats.argtypes = [P, P]
@@ -243,6 +247,25 @@ class AenetGPU:
         self._check(self.lib.aenet_md_nve(self.h, n, _ptr(pos), _ptr(vel), _ptr(types), _ptr(box),
                                           float(dt), int(n_steps), _ptr(e_pot), _ptr(e_kin), int(flags)))
 
+    def set_option(self, option, value):
+        self._check(self.lib.aenet_set_option(self.h, int(option), int(value)))
+
+    def keep_activations(self, on=True):
+        """Keep per-atom activation records so that grad_weights() can follow."""
+        self.set_option(AENET_OPT_KEEP_ACTIVATIONS, 1 if on else 0)
+
+    def grad_weights(self, out=None):
+        """dE/dW [n_species, n_params] (FP64) of the last evaluation."""
+        if out is None:
+            out = np.zeros((self.model.n_species, self.model.n_params))
+        self._check(self.lib.aenet_grad_weights(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, params):
+        """Replace the network parameters ([n_species, n_params], host float64)."""
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        self._check(self.lib.aenet_set_params(self.h, _ptr(p)))
+
     def neighbor_stats(self):
         """(entries within the largest cutoff, angular entries, angular pairs) of
         the last evaluation, summed over atoms."""
@@ -258,3 +281,52 @@ class AenetGPU:
         f = C.c_int(0)
         self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), C.byref(k), C.byref(f)))
         return dict(zip(STAGES, map(float, ms))), int(k.value), bool(f.value & 1)
+
+
+def _energy_function():
+    import torch
+
+    class AenetEnergy(torch.autograd.Function):
+        """E(positions, parameters) with a hand-written backward: dE/dr = -F from
+        the force kernel, dE/dW from the weight-gradient kernel. Usage:
+        ``E = AenetEnergy.apply(pos, params, gpu, types, box)`` with ``gpu`` an
+        AenetGPU, ``pos`` [N,3] float64 and ``params`` [n_species, n_params]
+        float64 tensors."""
+
+        @staticmethod
+        def forward(ctx, pos, params, gpu, types, box):
+            want_w = params.requires_grad
+            gpu.set_params(params.detach().cpu().numpy())
+            gpu.keep_activations(want_w)
+            dev = pos.device
+            E = torch.zeros(1, dtype=torch.float64, device=dev)
+            F = torch.zeros_like(pos, dtype=torch.float64)
+            gpu.compute(pos.detach().contiguous(), types, box, energy=E, forces=F)
+            dW = None
+            if want_w:
+                dW = torch.zeros(params.shape, dtype=torch.float64, device=dev)
+                gpu.grad_weights(out=dW)
+            if dev.type == "cuda":
+                torch.cuda.current_stream(dev).synchronize()
+            ctx.save_for_backward(F, dW if dW is not None else torch.zeros(0))
+            ctx.want_w = want_w
+            return E[0]
+
+        @staticmethod
+        def backward(ctx, gE):
+            F, dW = ctx.saved_tensors
+            gp = -F * gE
+            gw = (dW * gE).to(dtype=torch.float64) if ctx.want_w else None
+            return gp, gw, None, None, None
+
+    return AenetEnergy
+
+
+def energy_function():
+    """The torch.autograd.Function class (built lazily so that torch stays optional)."""
+    global _AENET_ENERGY
+    try:
+        return _AENET_ENERGY
+    except NameError:
+        _AENET_ENERGY = _energy_function()
+        return _AENET_ENERGY

@@ -8,6 +8,7 @@
 
 #include <string>
 #include <vector>
+#include <vector_types.h>
 
 #include "aenet_gpu.h"
 
@@ -141,6 +142,17 @@ struct Context {
     int *d_step = nullptr;         // MD record counter
     unsigned *d_done = nullptr;    // last-CTA counter of the MD reduction (left at 0)
 
+    // per-atom activation records for dE/dW (optional)
+    bool keep_act = false;
+    bool act_valid = false;        // records of the last evaluation are in d_act
+    int act_atoms = 0;             // atoms of that evaluation
+    int cap_act = 0;
+    float *d_act = nullptr;        // [n * rec_len] sorted order
+    float *d_wpart = nullptr;      // dE/dW partial sums per (species, chunk)
+    size_t cap_wpart = 0;
+    int2 *d_wpairs = nullptr;      // [n_params] record indices of each weight's factors
+    double *d_dEdW = nullptr;      // [n_species * n_params]
+
     // species grouping of the BF16 network kernel
     int *d_sp_cnt = nullptr;       // [kMaxSpecies], kept at 0 between evaluations
     int *d_sp_off = nullptr;       // [kMaxSpecies]
@@ -215,6 +227,15 @@ bool bf16_supported(const Net &net);
 int bf16_max_tiles(const Context &c, int n);
 int bf16_eparts(const Context &c, int n);
 cudaError_t launch_ann_bf16(Context &c, int n);
+
+// Length of the per-atom activation record (g, then x_l and delta_l per hidden layer).
+int activation_record_len(const Net &net);
+// Group the sorted atoms by species (d_sp_list, d_sp_off).
+cudaError_t launch_species_group(Context &c, int n);
+// dE/dW and dE/db of every species from the activation records (FP64 result in d_dEdW).
+cudaError_t launch_grad_weights(Context &c, int n);
+std::vector<int2> grad_pairs(const Net &net);
+int grad_max_params();
 
 // Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
 bool fused_supported(const Context &c);

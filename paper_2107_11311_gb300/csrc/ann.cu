@@ -26,7 +26,8 @@ __host__ __device__ inline int ann_row_len(const Net &net) {
 __global__ void __launch_bounds__(kAnnThreads)
     k_ann_fp32(Net net, int n, const float4 *__restrict__ pos4, const float *__restrict__ G,
                const float *__restrict__ params, const float *__restrict__ shift, const float *__restrict__ scale,
-               float *__restrict__ dEdG, float *__restrict__ eatom, double *__restrict__ e_part) {
+               float *__restrict__ dEdG, float *__restrict__ eatom, double *__restrict__ e_part,
+               float *__restrict__ act, int rec_len) {
     extern __shared__ __align__(16) float sm[];
     const int D = net.widths[0];
     const int L = net.n_layers;
@@ -75,6 +76,17 @@ __global__ void __launch_bounds__(kAnnThreads)
         }
         E = x[xin];
         eatom[s] = E;
+        // optional activation record: g, then x_l and delta_l of every hidden layer
+        float *rec = act ? act + (size_t)s * rec_len : nullptr;
+        if (rec) {
+            for (int k = 0; k < D; ++k) rec[k] = x[k];
+            int r = D, a0 = D;
+            for (int l = 1; l < L; ++l) {
+                for (int k = 0; k < net.widths[l]; ++k) rec[r + k] = x[a0 + k];
+                r += 2 * net.widths[l];
+                a0 += net.widths[l];
+            }
+        }
         // back-propagation: delta^L = 1
         int maxw = 1;
         for (int l = 0; l <= L; ++l) maxw = net.widths[l] > maxw ? net.widths[l] : maxw;
@@ -99,6 +111,11 @@ __global__ void __launch_bounds__(kAnnThreads)
                     acc *= (1.0f - a * a);
                 }
                 dprev[k] = acc;
+            }
+            if (rec && l > 1) {  // dprev = delta of hidden layer l - 1
+                int r = D;
+                for (int m = 1; m < l - 1; ++m) r += 2 * net.widths[m];
+                for (int k = 0; k < ni; ++k) rec[r + net.widths[l - 1] + k] = dprev[k];
             }
             float *tmp = dcur;
             dcur = dprev;
@@ -138,7 +155,9 @@ cudaError_t launch_ann(Context &c, int n) {
     cudaError_t e = cudaFuncSetAttribute(k_ann_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_ann_fp32<<<ann_blocks(n), kAnnThreads, smem, c.stream>>>(c.net, n, c.d_pos4, c.d_G, c.d_params, c.d_shift,
-                                                               c.d_scale, c.d_dEdG, c.d_eatom, c.d_e_part);
+                                                               c.d_scale, c.d_dEdG, c.d_eatom, c.d_e_part,
+                                                               c.keep_act ? c.d_act : nullptr,
+                                                               activation_record_len(c.net));
     return cudaGetLastError();
 }
 

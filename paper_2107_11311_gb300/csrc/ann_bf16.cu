@@ -159,7 +159,24 @@ struct AnnBf16Args {
     const float *shift, *scale;  // [species][D]
     float *dEdG, *eatom;
     double *e_part;          // [max tiles]
+    float *act;              // optional activation records [n, rec_len]: g, x1, d1, x2, d2
+    int rec_len;
 };
+
+// Write an accumulator tile set (rows = the tile's atoms, cols = neurons < H) at
+// record offset `off` of each atom's activation record.
+template <int NT>
+__device__ inline void store_rows(const AnnBf16Args &a, const float (&C)[NT][4], int off, int H, int s0, int s1,
+                                  int tq) {
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int col = nt * 8 + 2 * tq + (e & 1);
+            const int s = e < 2 ? s0 : s1;
+            if (col < H && s >= 0) a.act[(size_t)s * a.rec_len + off + col] = C[nt][e];
+        }
+}
 
 template <int H1T, int H2T, bool X3>
 __global__ void __launch_bounds__(32 * kAnnWarps) k_ann_bf16(AnnBf16Args a) {
@@ -197,6 +214,11 @@ __global__ void __launch_bounds__(32 * kAnnWarps) k_ann_bf16(AnnBf16Args a) {
                     if (col < D) x0 = (a.G[(size_t)s * D + col] - sh[col]) * sc[col];
                     if (col + 1 < D) x1 = (a.G[(size_t)s * D + col + 1] - sh[col + 1]) * sc[col + 1];
                 }
+                if (a.act && s >= 0) {
+                    float *rec = a.act + (size_t)s * a.rec_len;
+                    if (col < D) rec[col] = x0;
+                    if (col + 1 < D) rec[col + 1] = x1;
+                }
                 uint32_t hi, lo = 0;
                 if (X3) split_bf2(x0, x1, hi, lo); else hi = pack_bf2(x0, x1);
                 A0h[ks][2 * h + rr] = hi;
@@ -216,6 +238,7 @@ __global__ void __launch_bounds__(32 * kAnnWarps) k_ann_bf16(AnnBf16Args a) {
     for (int nt = 0; nt < NT1; ++nt)
 #pragma unroll
         for (int e = 0; e < 4; ++e) C1[nt][e] = (nt * 8 + 2 * tq + (e & 1) < a.H1) ? tanhf(C1[nt][e]) : 0.f;
+    if (a.act) store_rows<NT1>(a, C1, D, a.H1, s0, s1, tq);  // x1
     uint32_t A1h[KSH1][4], A1l[KSH1][4];
     to_a<NT1, X3>(C1, A1h, A1l);
     float C2[NT2][4];
@@ -247,6 +270,18 @@ __global__ void __launch_bounds__(32 * kAnnWarps) k_ann_bf16(AnnBf16Args a) {
     e1 += __shfl_xor_sync(0xffffffffu, e1, 2);
     e0 += b3;
     e1 += b3;
+    if (a.act) {
+        float X2[NT2][4];
+#pragma unroll
+        for (int nt = 0; nt < NT2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = nt * 8 + 2 * tq + (e & 1);
+                X2[nt][e] = col < a.H2 ? tanhf(C2[nt][e]) : 0.f;
+            }
+        store_rows<NT2>(a, X2, D + 2 * a.H1, a.H2, s0, s1, tq);           // x2
+        store_rows<NT2>(a, D2, D + 2 * a.H1 + a.H2, a.H2, s0, s1, tq);    // delta2
+    }
     // ---- backward: dX1 = delta2 W2, delta1 = (1 - x1^2) dX1, dE/dg = delta1 W1
     uint32_t A2h[KSH2][4], A2l[KSH2][4];
     to_a<NT2, X3>(D2, A2h, A2l);
@@ -258,6 +293,7 @@ __global__ void __launch_bounds__(32 * kAnnWarps) k_ann_bf16(AnnBf16Args a) {
     for (int nt = 0; nt < NT1; ++nt)
 #pragma unroll
         for (int e = 0; e < 4; ++e) C3[nt][e] *= (1.0f - C1[nt][e] * C1[nt][e]);
+    if (a.act) store_rows<NT1>(a, C3, D + a.H1, a.H1, s0, s1, tq);  // delta1
     uint32_t A3h[KSH1][4], A3l[KSH1][4];
     to_a<NT1, X3>(C3, A3h, A3l);
     float C4[kKD / 8][4];
@@ -392,7 +428,7 @@ cudaError_t prepare_bf16_weights(Context &c) {
         bt[pk.H1p + 2 * pk.H2p] = b3[0];
     }
     const size_t bytes = sizeof(uint32_t) * wpk.size() + sizeof(float) * bias.size();
-    if ((e = cudaMalloc(&c.d_wbf, bytes)) != cudaSuccess) return e;
+    if (!c.d_wbf && (e = cudaMalloc(&c.d_wbf, bytes)) != cudaSuccess) return e;  // reused on a parameter update
     c.wbf_elems = wpk.size();
     if ((e = cudaMemcpy(c.d_wbf, wpk.data(), sizeof(uint32_t) * wpk.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
@@ -400,13 +436,18 @@ cudaError_t prepare_bf16_weights(Context &c) {
                       cudaMemcpyHostToDevice);
 }
 
-cudaError_t launch_ann_bf16(Context &c, int n) {
+cudaError_t launch_species_group(Context &c, int n) {
     if (n <= 0) return cudaSuccess;
-    cudaError_t e;
     k_species_count<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_pos4, c.d_sp_cnt, c.d_sp_rank);
     k_species_tiles<<<1, 256, 0, c.stream>>>(c.basis.n_species, c.d_sp_cnt, c.d_sp_off, c.d_tiles, c.d_n_tiles);
     k_species_scatter<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_pos4, c.d_sp_off, c.d_sp_rank, c.d_sp_list);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ann_bf16(Context &c, int n) {
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = launch_species_group(c, n)) != cudaSuccess) return e;
     AnnBf16Args a{};
     a.n = n;
     a.D = c.basis.D;
@@ -425,6 +466,8 @@ cudaError_t launch_ann_bf16(Context &c, int n) {
     a.dEdG = c.d_dEdG;
     a.eatom = c.d_eatom;
     a.e_part = c.d_e_part;
+    a.act = c.keep_act ? c.d_act : nullptr;
+    a.rec_len = activation_record_len(c.net);
     const bool x3 = c.precision == AENET_BF16X3;
     const int mt = bf16_max_tiles(c, n);
     if (a.pk.H1p == 16 && a.pk.H2p == 16) return launch_bf16_variant<16, 16>(a, mt, x3, c.stream);

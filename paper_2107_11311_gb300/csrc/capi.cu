@@ -134,6 +134,10 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_vir_part, 0, (size_t)g.ncell * 9), "cudaMalloc");
         c.cap_cells = g.ncell;
     }
+    if (c.keep_act && (n > c.cap_act || !c.d_act)) {
+        CK(grow(c.d_act, 0, (size_t)std::max(n, 1) * activation_record_len(c.net)), "cudaMalloc");
+        c.cap_act = std::max(n, 1);
+    }
     const int need_e = std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell), bf16_eparts(c, std::max(n, 1))) + 1;
     if (need_e > c.cap_blocks || !c.d_e_part) {
         CK(grow(c.d_e_part, 0, (size_t)need_e), "cudaMalloc");
@@ -366,6 +370,14 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
     if (precision != AENET_FP32) {
         if ((e = prepare_bf16_weights(c)) != cudaSuccess) return setup_fail(e, "BF16 weights");
     }
+    {
+        const std::vector<int2> pairs = grad_pairs(c.net);
+        if ((e = cudaMalloc(&c.d_wpairs, sizeof(int2) * pairs.size())) != cudaSuccess ||
+            (e = cudaMemcpy(c.d_wpairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMalloc(&c.d_dEdW, sizeof(double) * NP)) != cudaSuccess)
+            return setup_fail(e, "gradient tables");
+    }
     *out = h;
     return AENET_OK;
 }
@@ -438,6 +450,8 @@ static int compute_impl(Context &c, int n, const double *pos, const int32_t *typ
         CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
         return AENET_OK;
     }
+    c.act_valid = c.keep_act;
+    c.act_atoms = n;
     if (energy) CK(cudaMemcpyAsync(energy, c.d_result, sizeof(double), cudaMemcpyDefault, c.stream), "energy copy");
     if (virial)
         CK(cudaMemcpyAsync(virial, c.d_result + 1, 9 * sizeof(double), cudaMemcpyDefault, c.stream), "virial copy");
@@ -542,6 +556,8 @@ extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *at
     c.batch_sinfo = nullptr;
     c.batch_n = 0;
     if (rc) return rc;
+    c.act_valid = c.keep_act;
+    c.act_atoms = n;
     // outputs: per-structure [energy, virial[9]] rows -> caller layout
     std::vector<double> res((size_t)n_struct * 10);
     CK(cudaMemcpyAsync(res.data(), c.d_bres, sizeof(double) * res.size(), cudaMemcpyDeviceToHost, c.stream),
@@ -597,6 +613,14 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
     if (n <= 0 || !pos || !vel || !types || !box) return fail(&c, AENET_E_ARG, "bad MD arguments");
     if (n_steps < 0 || !isfinite(dt)) return fail(&c, AENET_E_ARG, "bad n_steps / dt");
     const bool async = (flags & AENET_MD_ASYNC) != 0;
+    const bool keep_act = c.keep_act;  // MD steps keep no activation records
+    c.keep_act = false;
+    c.act_valid = false;
+    struct Restore {
+        Context &c;
+        bool v;
+        ~Restore() { c.keep_act = v; }
+    } restore{c, keep_act};
     const bool cont = (flags & AENET_MD_CONTINUE) != 0;
     const bool timing = (flags & AENET_MD_TIMING) != 0;
     const bool pos_dev = is_device_ptr(pos), vel_dev = is_device_ptr(vel), typ_dev = is_device_ptr(types);
@@ -728,6 +752,47 @@ extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_st
     return AENET_OK;
 }
 
+extern "C" int aenet_set_option(aenet_ctx *h, int option, int value) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (option == AENET_OPT_KEEP_ACTIVATIONS) {
+        c.keep_act = value != 0;
+        c.act_valid = false;
+        return AENET_OK;
+    }
+    return fail(&c, AENET_E_ARG, "unknown option %d", option);
+}
+
+extern "C" int aenet_grad_weights(aenet_ctx *h, double *dEdW) {
+    if (!h || !dEdW) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
+    Context &c = h->c;
+    cudaGetLastError();
+    if (!c.act_valid)
+        return fail(&c, AENET_E_STATE, "no activation records: set AENET_OPT_KEEP_ACTIVATIONS and evaluate first");
+    if (c.net.n_params > grad_max_params())
+        return fail(&c, AENET_E_ARG, "network has more than %d parameters per species", grad_max_params());
+    CK(launch_grad_weights(c, c.act_atoms), "weight gradient");
+    CK(cudaMemcpyAsync(dEdW, c.d_dEdW, sizeof(double) * c.basis.n_species * c.net.n_params, cudaMemcpyDefault,
+                       c.stream),
+       "dE/dW copy");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    return AENET_OK;
+}
+
+extern "C" int aenet_set_params(aenet_ctx *h, const double *params) {
+    if (!h || !params) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
+    Context &c = h->c;
+    cudaGetLastError();
+    const size_t NP = (size_t)c.basis.n_species * c.net.n_params;
+    std::vector<float> P(NP);
+    for (size_t k = 0; k < NP; ++k) P[k] = (float)params[k];
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    CK(cudaMemcpy(c.d_params, P.data(), sizeof(float) * NP, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (c.precision != AENET_FP32) CK(prepare_bf16_weights(c), "BF16 weights");
+    c.act_valid = false;
+    return AENET_OK;
+}
+
 extern "C" int aenet_check(aenet_ctx *h) {
     if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
     return read_error_word(h->c);
@@ -747,7 +812,8 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,
-                    c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres};
+                    c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres, c.d_act,
+                    c.d_wpart, c.d_wpairs, c.d_dEdW};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= Context::kStages; ++k)

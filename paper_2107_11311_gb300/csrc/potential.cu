@@ -62,6 +62,9 @@ struct FusedNet {
     int n_params;                   // canonical floats per species
     int Hlast, offWL, offBL, srcOffL;  // last hidden width and output-layer offsets (scalars:
                                        // kernels never index the arrays above with runtime values)
+    // per-atom activation record (for dE/dW): g [D], then x_l [H_l], delta_l [H_l]
+    // for every hidden layer l
+    int rec_len, rec_x[kMaxLayers], rec_d[kMaxLayers], rec_dlast;
 };
 
 FusedNet make_fused_net(const Net &net) {
@@ -94,6 +97,14 @@ FusedNet make_fused_net(const Net &net) {
         q += f.H[l] * f.H[l - 1] + f.H[l];
     }
     f.n_params = q;
+    int r = f.H[0];
+    for (int l = 1; l < f.L; ++l) {
+        f.rec_x[l] = r;
+        f.rec_d[l] = r + f.H[l];
+        r += 2 * f.H[l];
+    }
+    f.rec_len = r;
+    f.rec_dlast = f.rec_d[f.L - 1];
     f.Hlast = f.H[f.L - 1];
     f.offWL = f.offW[f.L];
     f.offBL = f.offB[f.L];
@@ -357,6 +368,13 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     const float *sh = Pt + net.offShift, *sc = Pt + net.offScale;
     const float x00 = (G0 - sh[s0]) * sc[s0];
     const float x01 = (G1 - sh[s1]) * sc[s1];
+    // optional activation record of this atom (G_out holds records in this mode)
+    float *rec = G_out ? G_out + (size_t)i_s * net.rec_len : nullptr;
+    if (rec) {
+        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
+        if (c0 >= 0) rec[c0] = x00;
+        if (c1 >= 0) rec[c1] = x01;
+    }
     const int H1 = net.H[1], H1p = odd(H1);
     const float *W1T = Pt + net.offW[1];
     float part[32];
@@ -365,6 +383,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     float z = transpose_reduce32(part, lane);
     float xl[kMaxLayers];  // this lane's neuron of every hidden layer
     xl[1] = lane < H1 ? tanhf(z + Pt[net.offB[1] + lane]) : 0.f;
+    if (rec && lane < H1) rec[net.rec_x[1] + lane] = xl[1];
 #pragma unroll
     for (int l = 2; l < kMaxLayers; ++l) {
         if (l < net.L) {
@@ -374,6 +393,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
             float zz = Pt[net.offB[l] + o];
             for (int k = 0; k < Hin; ++k) zz = fmaf(Wl[o * Hinp + k], __shfl_sync(kFull, xl[l - 1], k), zz);
             xl[l] = lane < Ho ? tanhf(zz) : 0.f;
+            if (rec && lane < Ho) rec[net.rec_x[l] + lane] = xl[l];
         }
     }
     const int Hlast = net.Hlast;
@@ -385,6 +405,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     const float E = warp_sum(wL * xlast) + Pt[net.offBL];
     // back-propagation: delta of the last hidden layer, then down to layer 1
     float delta = (1.0f - xlast * xlast) * wL;
+    if (rec && lane < Hlast) rec[net.rec_dlast + lane] = delta;
 #pragma unroll
     for (int l = kMaxLayers - 1; l >= 2; --l) {
         if (l < net.L) {
@@ -394,6 +415,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
             float dx = 0.f;
             for (int o = 0; o < Ho; ++o) dx = fmaf(Wl[o * Hinp + k], __shfl_sync(kFull, delta, o), dx);
             delta = lane < Hin ? (1.0f - xl[l - 1] * xl[l - 1]) * dx : 0.f;
+            if (rec && lane < Hin) rec[net.rec_d[l - 1] + lane] = delta;
         }
     }
     float d0 = 0.f, d1 = 0.f;
@@ -823,9 +845,10 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     auto kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true> : k_potential<KRT, KAT, EXACT, MODE, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    float *rows = MODE == kFused ? (c.keep_act ? c.d_act : nullptr) : c.d_G;  // activation records / G rows
     kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
                                                  c.d_cell_start, c.d_params,
-                                                 c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_G, c.d_dEdG,
+                                                 c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
                                                  c.d_e_part, c.d_vir_part, c.d_stats, c.d_err);
     return cudaGetLastError();
 }
@@ -1101,3 +1124,7 @@ extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t
         return na_fail(AENET_E_CUDA, cudaGetErrorString(e));
     return AENET_OK;
 }
+
+namespace aenet {
+int activation_record_len(const Net &net) { return make_fused_net(net).rec_len; }
+}  // namespace aenet
