@@ -57,6 +57,36 @@ def network_flops(widths, n_atoms):
     return 4 * sum(widths[l] * widths[l - 1] for l in range(1, len(widths))) * n_atoms
 
 
+# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
+# profiles/k_potential_water_12288.md; reported only while the kernel source is the
+# one the counters were taken on (first 16 hex digits of its SHA-256).
+TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha256_16": "8e87fcc066be1018",
+                   "bytes": 494848}
+
+
+def captured_traffic(workload_name, precision):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", "potential.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    c = TRAFFIC_CAPTURE
+    if workload_name == c["workload"] and precision == c["precision"] and sha == c["source_sha256_16"]:
+        return c["bytes"]
+    return None
+
+
+def max_over_ranks(value, world):
+    """Largest value over all ranks (the timing rule of the multi-GPU contract)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name):
     from paper_2107_11311_gb300 import inputs
     if name == "water_12288":
@@ -335,11 +365,7 @@ def main():
         clk = clocks.stop()
         gpu.check()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_dev = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
+    t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
     value = world * n * args.steps / t_dev
     stage_avg = {s: stage_sum[s] / args.steps for s in stage_sum}
 
@@ -361,11 +387,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
         h2d = hpos.numel() * 8 + hvel.numel() * 8 + htypes.numel() * 4
         d2h = hpos.numel() * 8 + hvel.numel() * 8 + hep.numel() * 8 + hek.numel() * 8
         e2e = {"value": world * n * args.e2e_steps / t_e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
@@ -411,7 +433,8 @@ def main():
         "gpu_launches": kernels_per_step * args.steps,
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": captured_traffic(args.workload, args.precision) if fused else None,
                      "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
                                    f"(SM clock max from MEASURED_PEAKS.json, {peak_kind})"},
         "clocks": clk,
