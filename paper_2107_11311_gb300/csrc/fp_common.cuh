@@ -37,6 +37,26 @@ __device__ inline void transpose_reduce64(float (&v)[64], int lane) {
 #undef AENET_STAGE
 }
 
+// 16 per-lane partial sums -> lanes 2q and 2q+1 each hold the total of slot q
+// over the 16 lanes that share their bit 0 (one more xor-1 shuffle completes it).
+__device__ inline float transpose_reduce16(float (&v)[16], int lane) {
+#define AENET_STAGE(O, N)                                                   \
+    {                                                                       \
+        const bool up = (lane & (O)) != 0;                                  \
+        _Pragma("unroll") for (int k = 0; k < (N); ++k) {                   \
+            float send = up ? v[k] : v[k + (N)];                            \
+            float keep = up ? v[k + (N)] : v[k];                            \
+            v[k] = keep + __shfl_xor_sync(kFull, send, (O));                \
+        }                                                                   \
+    }
+    AENET_STAGE(16, 8)
+    AENET_STAGE(8, 4)
+    AENET_STAGE(4, 2)
+    AENET_STAGE(2, 1)
+#undef AENET_STAGE
+    return v[0];
+}
+
 // 32 per-lane partial sums -> lane l holds the warp total of slot l.
 __device__ inline float transpose_reduce32(float (&v)[32], int lane) {
 #define AENET_STAGE(O, N)                                                   \

@@ -44,16 +44,19 @@ enum Mode : int {
     kForces = 2       // forces and virial from given dE/dG rows (sorted order)
 };
 
-__host__ __device__ inline int odd(int x) { return x | 1; }
-
-// Per-species parameter block in shared memory (floats):
-//   W1T [64 slots][H1 | 1]  layer-1 weights indexed by descriptor slot
-//   b1  [H1]
-//   for hidden l = 2..L-1: W_l [H_l][H_{l-1} | 1], b_l [H_l]
-//   wL  [H_{L-1}], bL [1]
+// Per-species parameter block in shared memory (floats), every hidden layer
+// zero-padded to the compile-time width bound hb (16 or 32) so the network
+// loops run a fixed trip count with no masks; padded neurons see zero weights
+// and biases, so they stay at tanh(0) = 0 and contribute nothing:
+//   W1P [32 slot pairs][hb + 1] float2   layer-1 weights of slots (2p, 2p+1)
+//   b1  [hb]
+//   for hidden l = 2..L-1: W_l [hb][hb + 1], b_l [hb]
+//   wL  [hb], bL [1]
 //   shift [64 slots], scale [64 slots] (scale 0 on unused slots)
+// The odd row strides keep the lane-strided reads free of bank conflicts.
 struct FusedNet {
     int L;                          // weight layers
+    int hb;                         // hidden-width bound of the layout (16 or 32)
     int H[kMaxLayers + 1];          // widths
     int offW[kMaxLayers + 1];       // offset of W_l in the block
     int offB[kMaxLayers + 1];       // offset of b_l
@@ -67,23 +70,31 @@ struct FusedNet {
     int rec_len, rec_x[kMaxLayers], rec_d[kMaxLayers], rec_dlast;
 };
 
+int hidden_bound(const Net &net) {
+    int h = 0;
+    for (int l = 1; l < net.n_layers; ++l) h = h > net.widths[l] ? h : net.widths[l];
+    return h <= 16 ? 16 : 32;
+}
+
 FusedNet make_fused_net(const Net &net) {
     FusedNet f{};
     f.L = net.n_layers;
+    f.hb = hidden_bound(net);
+    const int hb = f.hb;
     for (int l = 0; l <= net.n_layers; ++l) f.H[l] = net.widths[l];
     int p = 0;
     f.offW[1] = p;
-    p += kSlots * odd(f.H[1]);
+    p += kSlots * (hb + 1);
     f.offB[1] = p;
-    p += f.H[1];
+    p += hb;
     for (int l = 2; l < f.L; ++l) {
         f.offW[l] = p;
-        p += f.H[l] * odd(f.H[l - 1]);
+        p += hb * (hb + 1);
         f.offB[l] = p;
-        p += f.H[l];
+        p += hb;
     }
     f.offW[f.L] = p;
-    p += f.H[f.L - 1];
+    p += hb;
     f.offB[f.L] = p;
     p += 1;
     f.offShift = p;
@@ -266,7 +277,7 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
     }
 }
 
-template <int KRT, int KAT, bool EXACT, int MODE>
+template <int KRT, int KAT, bool EXACT, int MODE, int HB>
 __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
                                              const float *s_par, const float *s_tw, const WarpLists &W, int lane,
                                              const float4 *__restrict__ pos4, float4 *__restrict__ F4,
@@ -375,55 +386,86 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         if (c0 >= 0) rec[c0] = x00;
         if (c1 >= 0) rec[c1] = x01;
     }
-    const int H1 = net.H[1], H1p = odd(H1);
-    const float *W1T = Pt + net.offW[1];
-    float part[32];
+    // Lanes own neurons: o = lane for hb = 32; for hb = 16 both half-warps hold
+    // neurons 0..15 (o = lane & 15) and split every sum over k into even and odd
+    // terms (half h takes k = 2j + h), joined by one shuffle.
+    const int o = lane & (HB - 1), h = HB == 16 ? lane >> 4 : 0;
+    const float2 *W1P = reinterpret_cast<const float2 *>(Pt + net.offW[1]) + lane * (HB + 1);
+    float part[HB];
 #pragma unroll
-    for (int o = 0; o < 32; ++o) part[o] = o < H1 ? fmaf(W1T[s0 * H1p + o], x00, W1T[s1 * H1p + o] * x01) : 0.f;
-    float z = transpose_reduce32(part, lane);
+    for (int q = 0; q < HB; ++q) {
+        const float2 w = W1P[q];
+        part[q] = fmaf(w.x, x00, w.y * x01);
+    }
+    float z;
+    if constexpr (HB == 16) {
+        z = transpose_reduce16(part, lane);  // lanes 2q, 2q+1: halves of neuron q
+        z += __shfl_xor_sync(kFull, z, 1);
+        z = __shfl_sync(kFull, z, 2 * o);
+    } else {
+        z = transpose_reduce32(part, lane);
+    }
     float xl[kMaxLayers];  // this lane's neuron of every hidden layer
-    xl[1] = lane < H1 ? tanhf(z + Pt[net.offB[1] + lane]) : 0.f;
-    if (rec && lane < H1) rec[net.rec_x[1] + lane] = xl[1];
+    xl[1] = tanhf(z + Pt[net.offB[1] + o]);
+    if (rec && lane < net.H[1]) rec[net.rec_x[1] + lane] = xl[1];
 #pragma unroll
     for (int l = 2; l < kMaxLayers; ++l) {
         if (l < net.L) {
-            const int Hin = net.H[l - 1], Ho = net.H[l], Hinp = odd(Hin);
-            const float *Wl = Pt + net.offW[l];
-            const int o = lane < Ho ? lane : 0;
-            float zz = Pt[net.offB[l] + o];
-            for (int k = 0; k < Hin; ++k) zz = fmaf(Wl[o * Hinp + k], __shfl_sync(kFull, xl[l - 1], k), zz);
-            xl[l] = lane < Ho ? tanhf(zz) : 0.f;
-            if (rec && lane < Ho) rec[net.rec_x[l] + lane] = xl[l];
+            const float *Wl = Pt + net.offW[l] + o * (HB + 1);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll(HB == 16 ? 4 : 2)
+            for (int j = 0; j < (HB == 16 ? 8 : 32); j += 2) {
+                const int k0 = HB == 16 ? 2 * j + h : j, k1 = HB == 16 ? 2 * j + 2 + h : j + 1;
+                a0 = fmaf(Wl[k0], __shfl_sync(kFull, xl[l - 1], k0), a0);
+                a1 = fmaf(Wl[k1], __shfl_sync(kFull, xl[l - 1], k1), a1);
+            }
+            float zz = a0 + a1;
+            if constexpr (HB == 16) zz += __shfl_xor_sync(kFull, zz, 16);
+            xl[l] = tanhf(zz + Pt[net.offB[l] + o]);
+            if (rec && lane < net.H[l]) rec[net.rec_x[l] + lane] = xl[l];
         }
     }
-    const int Hlast = net.Hlast;
     float xlast = 0.f;
 #pragma unroll
     for (int l = 1; l < kMaxLayers; ++l)
         if (l == net.L - 1) xlast = xl[l];
-    const float wL = lane < Hlast ? Pt[net.offWL + lane] : 0.f;
-    const float E = warp_sum(wL * xlast) + Pt[net.offBL];
+    const float wL = Pt[net.offWL + o];
+    float E = wL * xlast;
+#pragma unroll
+    for (int m = HB / 2; m >= 1; m >>= 1) E += __shfl_xor_sync(kFull, E, m);
+    E += Pt[net.offBL];
     // back-propagation: delta of the last hidden layer, then down to layer 1
     float delta = (1.0f - xlast * xlast) * wL;
-    if (rec && lane < Hlast) rec[net.rec_dlast + lane] = delta;
+    if (rec && lane < net.Hlast) rec[net.rec_dlast + lane] = delta;
 #pragma unroll
     for (int l = kMaxLayers - 1; l >= 2; --l) {
         if (l < net.L) {
-            const int Hin = net.H[l - 1], Ho = net.H[l], Hinp = odd(Hin);
-            const float *Wl = Pt + net.offW[l];
-            const int k = lane < Hin ? lane : 0;
-            float dx = 0.f;
-            for (int o = 0; o < Ho; ++o) dx = fmaf(Wl[o * Hinp + k], __shfl_sync(kFull, delta, o), dx);
-            delta = lane < Hin ? (1.0f - xl[l - 1] * xl[l - 1]) * dx : 0.f;
-            if (rec && lane < Hin) rec[net.rec_d[l - 1] + lane] = delta;
+            const float *Wl = Pt + net.offW[l] + o;  // column o: weights from input neuron o
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll(HB == 16 ? 4 : 2)
+            for (int j = 0; j < (HB == 16 ? 8 : 32); j += 2) {
+                const int q0 = HB == 16 ? 2 * j + h : j, q1 = HB == 16 ? 2 * j + 2 + h : j + 1;
+                a0 = fmaf(Wl[q0 * (HB + 1)], __shfl_sync(kFull, delta, q0), a0);
+                a1 = fmaf(Wl[q1 * (HB + 1)], __shfl_sync(kFull, delta, q1), a1);
+            }
+            float dx = a0 + a1;
+            if constexpr (HB == 16) dx += __shfl_xor_sync(kFull, dx, 16);
+            delta = (1.0f - xl[l - 1] * xl[l - 1]) * dx;
+            if (rec && lane < net.H[l - 1]) rec[net.rec_d[l - 1] + lane] = delta;
         }
     }
-    float d0 = 0.f, d1 = 0.f;
-    for (int k = 0; k < H1; ++k) {
-        const float dk = __shfl_sync(kFull, delta, k);
-        d0 = fmaf(W1T[s0 * H1p + k], dk, d0);
-        d1 = fmaf(W1T[s1 * H1p + k], dk, d1);
+    float d0 = 0.f, d1 = 0.f, e0 = 0.f, e1 = 0.f;
+#pragma unroll(HB == 16 ? 8 : 2)
+    for (int q = 0; q < HB; q += 2) {
+        const float dq = __shfl_sync(kFull, delta, q), dr = __shfl_sync(kFull, delta, q + 1);
+        const float2 wq = W1P[q], wr = W1P[q + 1];
+        d0 = fmaf(wq.x, dq, d0);
+        d1 = fmaf(wq.y, dq, d1);
+        e0 = fmaf(wr.x, dr, e0);
+        e1 = fmaf(wr.y, dr, e1);
     }
+    d0 += e0;
+    d1 += e1;
     W.coef[s0] = d0 * sc[s0];  // dE/dG = dE/dg * scale
     W.coef[s1] = d1 * sc[s1];
     if (lane == 0) {
@@ -601,7 +643,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     __syncwarp();
 }
 
-template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH>
+template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB>
 __global__ void __launch_bounds__(kPThreads, 2)
     k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
                 const float4 *__restrict__ pos4,
@@ -661,25 +703,26 @@ __global__ void __launch_bounds__(kPThreads, 2)
     for (int t = 0; t < (MODE == kFused ? B.n_species : 0); ++t) {
         const float *src = params + (size_t)t * net.n_params;
         float *dst = s_par + t * net.stride;
-        const int H1 = net.H[1], H1p = odd(H1);
-        for (int idx = tid; idx < kSlots * H1p; idx += kPThreads) {
-            const int slot = idx / H1p, o = idx % H1p;
-            const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
+        const int H1 = net.H[1], hb = net.hb;
+        for (int idx = tid; idx < kSlots * (hb + 1); idx += kPThreads) {  // W1P: (pair, o, slot parity)
+            const int pair = idx / (2 * (hb + 1)), rem = idx % (2 * (hb + 1)), o = rem >> 1;
+            const int col = slot_col<KRT, KAT>(2 * pair + (rem & 1), Kr, Ka);
             dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
         }
-        for (int o = tid; o < H1; o += kPThreads) dst[net.offB[1] + o] = src[net.srcOff[1] + H1 * D + o];
+        for (int o = tid; o < hb; o += kPThreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
 #pragma unroll
         for (int l = 2; l < kMaxLayers; ++l) {
             if (l >= net.L) break;
-            const int Hi = net.H[l - 1], Ho = net.H[l], Hip = odd(Hi);
-            for (int idx = tid; idx < Ho * Hip; idx += kPThreads) {
-                const int o = idx / Hip, k = idx % Hip;
-                dst[net.offW[l] + idx] = k < Hi ? src[net.srcOff[l] + o * Hi + k] : 0.f;
+            const int Hi = net.H[l - 1], Ho = net.H[l];
+            for (int idx = tid; idx < hb * (hb + 1); idx += kPThreads) {
+                const int o = idx / (hb + 1), k = idx % (hb + 1);
+                dst[net.offW[l] + idx] = (o < Ho && k < Hi) ? src[net.srcOff[l] + o * Hi + k] : 0.f;
             }
-            for (int o = tid; o < Ho; o += kPThreads) dst[net.offB[l] + o] = src[net.srcOff[l] + Ho * Hi + o];
+            for (int o = tid; o < hb; o += kPThreads)
+                dst[net.offB[l] + o] = o < Ho ? src[net.srcOff[l] + Ho * Hi + o] : 0.f;
         }
         const int Hl = net.Hlast;
-        for (int k = tid; k < Hl; k += kPThreads) dst[net.offWL + k] = src[net.srcOffL + k];
+        for (int k = tid; k < hb; k += kPThreads) dst[net.offWL + k] = k < Hl ? src[net.srcOffL + k] : 0.f;
         if (tid == 0) dst[net.offBL] = src[net.srcOffL + Hl];
         for (int slot = tid; slot < kSlots; slot += kPThreads) {
             const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
@@ -783,7 +826,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
             int nnb = 0, nang = 0;
             scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
             finish_list(nnb, nang);
-            process_atom<KRT, KAT, EXACT, MODE>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+            process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
                                                 G_out, dEdG_in, e_acc, vir);
         }
     } else {
@@ -802,7 +845,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
             }
             if (active) {
                 finish_list(nnb, nang);
-                process_atom<KRT, KAT, EXACT, MODE>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+                process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
                                                     G_out, dEdG_in, e_acc, vir);
             }
         }
@@ -842,7 +885,13 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang,
                                      MODE == kFused ? c.basis.n_species : 0, net.stride)
                             .total;
-    auto kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true> : k_potential<KRT, KAT, EXACT, MODE, false>;
+    // the network's hidden-width bound is a template argument of the fused form only
+    auto kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 32> : k_potential<KRT, KAT, EXACT, MODE, false, 32>;
+    if constexpr (MODE == kFused) {
+        if (net.hb == 16)
+            kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 16>
+                                 : k_potential<KRT, KAT, EXACT, MODE, false, 16>;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     float *rows = MODE == kFused ? (c.keep_act ? c.d_act : nullptr) : c.d_G;  // activation records / G rows
@@ -983,7 +1032,7 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
                          const int *cell_start, float *Gs, unsigned long long *stats, unsigned *err) {
     const FusedNet net{};  // no network in descriptor mode
     const size_t smem = make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total;
-    auto kern = k_potential<KRT, KAT, EXACT, kDescriptor, false>;
+    auto kern = k_potential<KRT, KAT, EXACT, kDescriptor, false, 32>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
