@@ -134,6 +134,51 @@ int aenet_compute_batch(aenet_ctx *ctx, int n_struct, const int64_t *atom_offset
                         double *virials);
 
 /*
+ * Prepared batch: the batched evaluation above (row a11 of the path; the
+ * energy of each structure is the Behler-Parrinello sum of Sec. II.A, its
+ * forces the chain rule of Sec. II.C) made replayable for repeated
+ * evaluation of one batch layout with new coordinates (an MD or screening
+ * loop over many structures).
+ * aenet_batch_prepare fixes the layout (atom_offset, boxes: HOST, as in
+ * aenet_compute_batch) and the DEVICE buffers the evaluation reads (pos
+ * [N * 3], types [N]) and writes (energies [n_struct], forces [N * 3],
+ * virials [n_struct * 9]; each output may be NULL). It evaluates the batch on
+ * the current contents of pos, and with flags & AENET_BATCH_AUTOTUNE times
+ * candidate launches of the potential kernel on them: one CTA per cell in
+ * cell order, or one resident (persistent) CTA per SM slot taking cells from
+ * a global counter heaviest first, each with staging tiles of 256, 512, 1024
+ * and 2048 image-atoms. It keeps the fastest and captures the whole evaluation
+ * (binning, cell sort, potential, per-structure reductions, forces) in one
+ * CUDA graph. Without the flag it uses the persistent form and the current
+ * tile. The caller keeps the buffers alive and at the same addresses until
+ * the next prepare or aenet_destroy. Synchronises.
+ * Errors: AENET_E_ARG for host buffers or a bad layout, AENET_E_CAPACITY if a
+ * neighbour list overflows twice, the device error codes of aenet_compute.
+ */
+#define AENET_BATCH_AUTOTUNE 1
+int aenet_batch_prepare(aenet_ctx *ctx, int n_struct, const int64_t *atom_offset, const double *boxes,
+                        const double *pos, const int32_t *types, double *energies, double *forces,
+                        double *virials, int flags);
+
+/*
+ * Replays the prepared evaluation on the context's stream: reads pos/types
+ * and writes the outputs given to aenet_batch_prepare. Asynchronous: device
+ * errors (e.g. a neighbour list overflowing on new coordinates) are reported
+ * by the next aenet_check. If the context's work buffers, stream or list
+ * capacities changed since the capture (another call on the same context),
+ * the graph is captured again first. AENET_E_STATE without a prepared batch.
+ */
+int aenet_batch_run(aenet_ctx *ctx);
+
+/*
+ * The launch aenet_batch_prepare chose: persistent (1) or one CTA per cell
+ * (0), staging tile, CTAs of the potential launch, kernel nodes in the
+ * captured graph, and the measured time of one evaluation (ms). Any output
+ * may be NULL. AENET_E_STATE without a prepared batch.
+ */
+int aenet_batch_tuning(aenet_ctx *ctx, int *persistent, int *tile, int *ctas, int *kernels, float *ms);
+
+/*
  * Descriptor only (rows a1-a5 of the path): G [n_atoms * D] float32, host or
  * device, row i = atom i in input order, layout [radial, angular, radial_w,
  * angular_w] before standardisation. Synchronises.

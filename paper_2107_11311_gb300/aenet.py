@@ -18,6 +18,7 @@ from . import build as _build
 AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
 AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING = 1, 2, 4
 AENET_OPT_KEEP_ACTIVATIONS = 1
+AENET_BATCH_AUTOTUNE = 1
 STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
 PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
 
@@ -63,6 +64,9 @@ def load(build_if_missing: bool = True):
     lib.aenet_compute.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_descriptors.argtypes = [P, I, P, P, P, P]
     lib.aenet_compute_batch.argtypes = [P, I, P, P, P, P, P, P, P]
+    lib.aenet_batch_prepare.argtypes = [P, I, P, P, P, P, P, P, P, I]
+    lib.aenet_batch_run.argtypes = [P]
+    lib.aenet_batch_tuning.argtypes = [P, P, P, P, P, P]
     lib.aenet_set_option.argtypes = [P, I, I]
     lib.aenet_grad_weights.argtypes = [P, P]
     lib.aenet_set_params.argtypes = [P, P]
@@ -229,6 +233,32 @@ class AenetGPU:
         if ret:
             return dict(energies=energies, forces=forces, virials=virials)
         return None
+
+    def batch_prepare(self, atom_offset, boxes, pos, types, energies=None, forces=None, virials=None,
+                      autotune=True):
+        """Fix a batch layout and its device buffers (torch CUDA tensors: pos
+        [N,3] float64, types [N] int32, energies [S], forces [N,3], virials
+        [S,3,3] float64), tune the potential launch on the current pos and
+        capture the evaluation in a CUDA graph. Returns batch_tuning()."""
+        off = np.ascontiguousarray(atom_offset, dtype=np.int64)
+        bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        S = len(off) - 1
+        self._batch_keep = (off, bx, pos, types, energies, forces, virials)
+        self._check(self.lib.aenet_batch_prepare(self.h, S, _ptr(off), _ptr(bx), _ptr(pos), _ptr(types),
+                                                 _ptr(energies), _ptr(forces), _ptr(virials),
+                                                 AENET_BATCH_AUTOTUNE if autotune else 0))
+        return self.batch_tuning()
+
+    def batch_run(self):
+        """Replay the prepared batch on the context's stream (asynchronous)."""
+        self._check(self.lib.aenet_batch_run(self.h))
+
+    def batch_tuning(self):
+        p, t, g, k = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ms = C.c_float()
+        self._check(self.lib.aenet_batch_tuning(self.h, C.byref(p), C.byref(t), C.byref(g), C.byref(k),
+                                                C.byref(ms)))
+        return dict(persistent=bool(p.value), tile=t.value, ctas=g.value, kernels=k.value, ms=ms.value)
 
     def descriptors(self, pos, types, box, out=None):
         pos, types = _as(pos, np.float64), _as(types, np.int32)

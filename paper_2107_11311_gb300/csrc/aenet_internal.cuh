@@ -177,6 +177,42 @@ struct Context {
     const StructInfo *batch_sinfo = nullptr;  // non-NULL while a batch is enqueued
     int batch_n = 0;
 
+    // Generation of the work buffers: bumped whenever one is reallocated, so a
+    // captured graph (which holds their addresses) knows it must be re-captured.
+    unsigned buf_gen = 0;
+
+    // persistent form of the potential kernel (used by the batched evaluation)
+    int n_sm = 0;                      // SMs of the device
+    bool persist = false;              // CTAs take cells from a global counter (batches only)
+    int persist_ctas = 0;              // CTAs of the persistent launch (0 = all resident)
+    unsigned *d_work = nullptr;        // [1] the counter (zeroed before each launch)
+    const int *batch_order = nullptr;  // cell order of the batch being enqueued, heaviest first
+    int *d_order = nullptr;            // [cap_order] that order for aenet_compute_batch
+    int cap_order = 0;
+    int last_grid = 0;                 // CTAs of the last potential launch
+
+    // prepared batch (aenet_batch_prepare): its own layout buffers, the tuned
+    // launch and the captured evaluation
+    cudaGraphExec_t batch_exec = nullptr;
+    StructInfo *d_psinfo = nullptr;    // [n_struct]
+    int *d_porder = nullptr;           // [total_cells]
+    struct {
+        bool valid = false;
+        int n_struct = 0, n_atoms = 0, total_cells = 0;
+        Grid gall{};
+        const double *pos = nullptr;
+        const int32_t *types = nullptr;
+        double *energies = nullptr, *forces = nullptr, *virials = nullptr;
+        bool persist = false;
+        int tile = 0, ctas = 0, kernels = 0;
+        float ms = 0.f;
+        Caps caps{};
+        unsigned gen = 0;
+        cudaStream_t stream = nullptr;
+    } plan;
+    std::vector<StructInfo> plan_layout;  // host copy of the prepared layout
+    std::vector<int> plan_order;
+
     // captured MD step
     cudaGraphExec_t md_exec = nullptr;
     struct {
@@ -189,6 +225,7 @@ struct Context {
         cudaStream_t stream = nullptr;
         Caps caps{};
         bool timing = false;
+        unsigned gen = 0;
     } md_key;
 
     // stage timing of the captured MD step (events recorded inside the graph)
@@ -196,6 +233,22 @@ struct Context {
     cudaEvent_t ev[kStages + 1] = {};
     int md_kernels = 0;                // kernel nodes in the captured step
 };
+
+// Allow a kernel the device's largest dynamic shared memory. Launches of one
+// kernel with different sizes (captured graphs among them) then never depend on
+// which size was set last; each launcher still checks its own size.
+template <class K>
+inline cudaError_t allow_max_smem(K kern) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);  // static shared memory counts against the limit
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    return e;
+}
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on ctx.stream and return the launch status.
@@ -206,8 +259,9 @@ cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, co
 cudaError_t launch_sort(Context &c, const Grid &g, int n);
 // Binning of a batch: every atom into the cell grid of its structure.
 cudaError_t launch_cells_batch(Context &c, int n, int total_cells, const double *pos, const int32_t *types);
-// Per-structure energy (FP64 sum of E_i) and virial (FP64 sum of cell partials).
-cudaError_t launch_batch_reduce(Context &c);
+// Per-structure energy (FP64 sum of E_i) and virial (FP64 sum of cell partials)
+// into c.d_bres rows, or (when given) straight into energies[S], virials[S*9].
+cudaError_t launch_batch_reduce(Context &c, double *energies = nullptr, double *virials = nullptr);
 
 // Descriptor of every atom into c.d_G (rows a3-a5; k_potential, descriptor mode).
 cudaError_t launch_fp_forward(Context &c, const Grid &g, int n);

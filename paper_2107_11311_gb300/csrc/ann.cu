@@ -152,7 +152,7 @@ int ann_blocks(int n) { return (n + kAnnThreads - 1) / kAnnThreads; }
 cudaError_t launch_ann(Context &c, int n) {
     if (n <= 0) return cudaSuccess;
     const size_t smem = ann_smem_bytes(c);
-    cudaError_t e = cudaFuncSetAttribute(k_ann_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(k_ann_fp32);
     if (e != cudaSuccess) return e;
     k_ann_fp32<<<ann_blocks(n), kAnnThreads, smem, c.stream>>>(c.net, n, c.d_pos4, c.d_G, c.d_params, c.d_shift,
                                                                c.d_scale, c.d_dEdG, c.d_eatom, c.d_e_part,

@@ -127,21 +127,25 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_sp_list, 0, N), "cudaMalloc");
         CK(grow(c.d_tiles, 0, (size_t)bf16_max_tiles(c, n) + 1), "cudaMalloc");
         c.cap_atoms = n;
+        ++c.buf_gen;
     }
     if (g.ncell > c.cap_cells) {
         CK(grow(c.d_cell_count, 0, (size_t)g.ncell), "cudaMalloc");
         CK(grow(c.d_cell_start, 0, (size_t)g.ncell + 1), "cudaMalloc");
         CK(grow(c.d_vir_part, 0, (size_t)g.ncell * 9), "cudaMalloc");
         c.cap_cells = g.ncell;
+        ++c.buf_gen;
     }
     if (c.keep_act && (n > c.cap_act || !c.d_act)) {
         CK(grow(c.d_act, 0, (size_t)std::max(n, 1) * activation_record_len(c.net)), "cudaMalloc");
         c.cap_act = std::max(n, 1);
+        ++c.buf_gen;
     }
     const int need_e = std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell), bf16_eparts(c, std::max(n, 1))) + 1;
     if (need_e > c.cap_blocks || !c.d_e_part) {
         CK(grow(c.d_e_part, 0, (size_t)need_e), "cudaMalloc");
         c.cap_blocks = need_e;
+        ++c.buf_gen;
     }
     return AENET_OK;
 }
@@ -156,6 +160,7 @@ int ensure_stage(Context &c, int n) {
         CK(grow(c.d_eatom_out, 0, N), "cudaMalloc");
         CK(grow(c.d_types, 0, N), "cudaMalloc");
         c.cap_stage = n;
+        ++c.buf_gen;
     }
     return AENET_OK;
 }
@@ -164,7 +169,7 @@ int check_smem(Context &c, const Grid &g) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t need = potential_smem_bytes(c, g);
+    const size_t need = potential_smem_bytes(c, g) + 1024;  // + the kernel's static shared memory
     if (optin > 0 && need > (size_t)optin)
         return fail(&c, AENET_E_CAPACITY, "neighbour lists need %zu B of shared memory (limit %d B)", need, optin);
     return AENET_OK;
@@ -355,6 +360,9 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
     if ((e = cudaMalloc(&c.d_n_tiles, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_result, sizeof(double) * 11)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_mass, sizeof(double) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_work, sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, c.device)) != cudaSuccess)
+        return setup_fail(e, "cudaDeviceGetAttribute");
     double masses[kMaxSpecies] = {0};
     for (int t = 0; t < m->n_species && m->mass; ++t) masses[t] = m->mass[t];
     if ((e = cudaMemcpy(c.d_params, P.data(), sizeof(float) * NP, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -471,47 +479,66 @@ extern "C" int aenet_compute(aenet_ctx *h, int n, const double *pos, const int32
     return compute_impl(h->c, n, pos, types, box, energy, forces, virial, e_atom, nullptr);
 }
 
-extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *atom_offset, const double *pos,
-                                   const int32_t *types, const double *boxes, double *energies, double *forces,
-                                   double *virials) {
-    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
-    Context &c = h->c;
-    cudaGetLastError();
+// ------------------------------------------------------------ batched form
+// Many periodic structures in one evaluation: per-structure cell grids in one
+// global cell index space; one launch of each kernel over all cells.
+namespace aenet {
+namespace {
+
+struct BatchLayout {
+    std::vector<StructInfo> info;  // per structure
+    std::vector<int> order;        // cells, heaviest first
+    Grid gall{};                   // ncell = all cells, n_off = largest image table
+    int n = 0;                     // atoms
+    double max_rho = 0.0, max_neigh = 0.0;
+};
+
+int batch_layout(Context &c, int n_struct, const int64_t *atom_offset, const double *boxes, BatchLayout &L) {
     if (n_struct < 1 || !atom_offset || !boxes) return fail(&c, AENET_E_ARG, "bad batch description");
     if (atom_offset[0] != 0) return fail(&c, AENET_E_ARG, "atom_offset[0] must be 0");
     for (int s = 0; s < n_struct; ++s)
         if (atom_offset[s + 1] < atom_offset[s]) return fail(&c, AENET_E_ARG, "atom_offset must be non-decreasing");
     if (atom_offset[n_struct] > INT32_MAX / 2) return fail(&c, AENET_E_ARG, "too many atoms");
-    const int n = (int)atom_offset[n_struct];
-    if (n > 0 && (!pos || !types)) return fail(&c, AENET_E_ARG, "pos/types NULL");
-    // per-structure grids in one global cell index space
-    std::vector<StructInfo> info((size_t)n_struct);
+    L.n = (int)atom_offset[n_struct];
+    L.info.assign((size_t)n_struct, StructInfo{});
     int total_cells = 0, max_off = 1;
-    double max_rho = 0.0, max_neigh = 0.0;
+    std::vector<double> work_of((size_t)n_struct);
     for (int s = 0; s < n_struct; ++s) {
-        int rc = make_grid(c, boxes + 3 * (size_t)s, info[s].g);
+        StructInfo &si = L.info[s];
+        int rc = make_grid(c, boxes + 3 * (size_t)s, si.g);
         if (rc) return rc;
-        info[s].cell0 = total_cells;
-        info[s].ncell = info[s].g.ncell;
-        info[s].atom0 = (int)atom_offset[s];
-        info[s].natoms = (int)(atom_offset[s + 1] - atom_offset[s]);
-        total_cells += info[s].g.ncell;
-        max_off = std::max(max_off, info[s].g.n_off);
+        if ((long long)total_cells + si.g.ncell > INT32_MAX / 2) return fail(&c, AENET_E_ARG, "too many cells");
+        si.cell0 = total_cells;
+        si.ncell = si.g.ncell;
+        si.atom0 = (int)atom_offset[s];
+        si.natoms = (int)(atom_offset[s + 1] - atom_offset[s]);
+        total_cells += si.g.ncell;
+        max_off = std::max(max_off, si.g.n_off);
         const double V = boxes[3 * s] * boxes[3 * s + 1] * boxes[3 * s + 2];
-        max_rho = std::max(max_rho, info[s].natoms / V);
-        max_neigh = std::max(max_neigh, (double)info[s].natoms / info[s].g.ncell * info[s].g.n_off);
+        const double per_cell = (double)si.natoms / si.g.ncell;
+        L.max_rho = std::max(L.max_rho, si.natoms / V);
+        L.max_neigh = std::max(L.max_neigh, per_cell * si.g.n_off);
+        // work of one cell ~ its atoms x the image-atoms each of them scans
+        work_of[s] = per_cell * (per_cell * si.g.n_off);
     }
-    Grid gall{};
-    gall.ncell = total_cells;
-    gall.n_off = max_off;
-    int rc = validate_types_host(c, n, types);
-    if (rc) return rc;
-    if ((rc = ensure(c, n, gall)) || (rc = ensure_stage(c, n))) return rc;
-    if (n_struct > c.cap_struct) {
-        CK(grow(c.d_sinfo, 0, (size_t)n_struct), "cudaMalloc");
-        CK(grow(c.d_bres, 0, (size_t)n_struct * 10), "cudaMalloc");
-        c.cap_struct = n_struct;
-    }
+    L.gall = Grid{};
+    L.gall.ncell = total_cells;
+    L.gall.n_off = max_off;
+    L.order.resize((size_t)total_cells);
+    std::vector<int> sorder((size_t)n_struct);
+    for (int s = 0; s < n_struct; ++s) sorder[s] = s;
+    std::stable_sort(sorder.begin(), sorder.end(), [&](int a, int b) { return work_of[a] > work_of[b]; });
+    int k = 0;
+    for (int s : sorder)
+        for (int q = 0; q < L.info[s].ncell; ++q) L.order[k++] = L.info[s].cell0 + q;
+    return AENET_OK;
+}
+
+// Work buffers and neighbour-list capacities for a batch (capacities from the
+// densest structure, staging tile from the largest neighbourhood of a cell).
+int batch_buffers(Context &c, const BatchLayout &L) {
+    int rc;
+    if ((rc = ensure(c, L.n, L.gall)) || (rc = ensure_stage(c, L.n))) return rc;
     if (c.caps.nb == 0) {
         Grid dens{};
         dens.box[0] = dens.box[1] = dens.box[2] = 1.0;
@@ -519,33 +546,90 @@ extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *at
         dens.n_off = 1;
         c.caps = estimate_caps(c, 0, dens);
         auto cap = [&](double rcut, double margin) {
-            const int k = (int)(1.3 * max_rho * 4.18879020478639 * rcut * rcut * rcut + margin);
+            const int k = (int)(1.3 * L.max_rho * 4.18879020478639 * rcut * rcut * rcut + margin);
             return ((k + 15) / 16) * 16;
         };
         c.caps.nb = std::max(64, cap(c.basis.rc_max, 32.0));
         c.caps.ang = std::max(32, cap(c.basis.rc_ang, 24.0));
-        c.caps.tile = std::min(1024, std::max(128, (((int)(1.25 * max_neigh + 64.0)) + 31) / 32 * 32));
+        c.caps.tile = std::min(1024, std::max(128, (((int)(1.25 * L.max_neigh + 64.0)) + 31) / 32 * 32));
     }
+    return AENET_OK;
+}
+
+// The batched evaluation on device buffers, enqueued on c.stream: binning,
+// cell sort, potential (persistent when c.persist), per-structure reductions,
+// forces back in input order. sinfo/order: the layout on the device.
+int batch_enqueue(Context &c, const BatchLayout &L, const StructInfo *sinfo, const int *order, const double *dpos,
+                  const int32_t *dtypes, double *dF, double *energies, double *virials) {
+    int rc = check_smem(c, L.gall);
+    if (rc) return rc;
+    c.batch_sinfo = sinfo;
+    c.batch_order = order;
+    c.batch_n = (int)L.info.size();
+    cudaError_t e = launch_cells_batch(c, L.n, L.gall.ncell, dpos, dtypes);
+    int n_eparts = 0;
+    if (e == cudaSuccess) rc = enqueue_potential(c, L.gall, L.n, &n_eparts, nullptr);
+    if (e == cudaSuccess && !rc) e = launch_batch_reduce(c, energies, virials);
+    if (e == cudaSuccess && !rc) e = launch_finalize_forces(c, L.n, dF);
+    c.batch_sinfo = nullptr;
+    c.batch_order = nullptr;
+    c.batch_n = 0;
+    if (e != cudaSuccess) return cuda_fail(&c, e, "batched evaluation");
+    return rc;
+}
+
+int grow_order(Context &c, int cells) {
+    if (cells > c.cap_order || !c.d_order) {
+        CK(grow(c.d_order, 0, (size_t)cells), "cudaMalloc");
+        c.cap_order = cells;
+        ++c.buf_gen;
+    }
+    return AENET_OK;
+}
+
+}  // namespace
+}  // namespace aenet
+
+extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *atom_offset, const double *pos,
+                                   const int32_t *types, const double *boxes, double *energies, double *forces,
+                                   double *virials) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    cudaGetLastError();
+    BatchLayout L;
+    int rc = batch_layout(c, n_struct, atom_offset, boxes, L);
+    if (rc) return rc;
+    const int n = L.n;
+    if (n > 0 && (!pos || !types)) return fail(&c, AENET_E_ARG, "pos/types NULL");
+    if ((rc = validate_types_host(c, n, types))) return rc;
+    if ((rc = batch_buffers(c, L))) return rc;
+    if (n_struct > c.cap_struct) {
+        CK(grow(c.d_sinfo, 0, (size_t)n_struct), "cudaMalloc");
+        CK(grow(c.d_bres, 0, (size_t)n_struct * 10), "cudaMalloc");
+        c.cap_struct = n_struct;
+        ++c.buf_gen;
+    }
+    if ((rc = grow_order(c, L.gall.ncell))) return rc;
     const double *dpos;
     const int32_t *dtypes;
     if ((rc = stage_in(c, pos, c.d_pos, 3 * (size_t)n, &dpos))) return rc;
     if ((rc = stage_in(c, types, c.d_types, (size_t)n, &dtypes))) return rc;
-    CK(cudaMemcpyAsync(c.d_sinfo, info.data(), sizeof(StructInfo) * n_struct, cudaMemcpyHostToDevice, c.stream),
+    CK(cudaMemcpyAsync(c.d_sinfo, L.info.data(), sizeof(StructInfo) * n_struct, cudaMemcpyHostToDevice, c.stream),
+       "cudaMemcpyAsync");
+    CK(cudaMemcpyAsync(c.d_order, L.order.data(), sizeof(int) * L.order.size(), cudaMemcpyHostToDevice, c.stream),
        "cudaMemcpyAsync");
     const bool f_dev = is_device_ptr(forces);
     double *dF = forces ? (f_dev ? forces : c.d_forces) : nullptr;
-    c.batch_sinfo = c.d_sinfo;
-    c.batch_n = n_struct;
+    const bool persist = c.persist;
+    c.persist = true;  // heaviest cells first, resident CTAs
+    struct Restore {
+        Context &c;
+        bool v;
+        ~Restore() { c.persist = v; }
+    } restore{c, persist};
     for (int attempt = 0; attempt < 2; ++attempt) {
         CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
-        if ((rc = check_smem(c, gall))) break;
-        cudaError_t e = launch_cells_batch(c, n, total_cells, dpos, dtypes);
-        int n_eparts = 0;
-        if (e == cudaSuccess) rc = enqueue_potential(c, gall, n, &n_eparts, nullptr);
-        if (e == cudaSuccess && !rc) e = launch_batch_reduce(c);
-        if (e == cudaSuccess && !rc) e = launch_finalize_forces(c, n, dF);
-        if (e != cudaSuccess) rc = cuda_fail(&c, e, "batched evaluation");
-        if (rc) break;
+        if ((rc = batch_enqueue(c, L, c.d_sinfo, c.d_order, dpos, dtypes, dF, nullptr, nullptr))) break;
         rc = read_error_word(c);
         if (rc != AENET_E_CAPACITY || attempt == 1) break;
         c.caps.nb *= 2;
@@ -553,8 +637,6 @@ extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *at
         c.caps.tile = 1024;
         destroy_graph(c);
     }
-    c.batch_sinfo = nullptr;
-    c.batch_n = 0;
     if (rc) return rc;
     c.act_valid = c.keep_act;
     c.act_atoms = n;
@@ -573,6 +655,211 @@ extern "C" int aenet_compute_batch(aenet_ctx *h, int n_struct, const int64_t *at
     }
     if (energies) CK(cudaMemcpy(energies, E.data(), sizeof(double) * E.size(), cudaMemcpyDefault), "energies");
     if (virials) CK(cudaMemcpy(virials, W.data(), sizeof(double) * W.size(), cudaMemcpyDefault), "virials");
+    return AENET_OK;
+}
+
+// ------------------------------------------------------------ prepared batch
+namespace aenet {
+namespace {
+
+// Capture the prepared batch's evaluation into c.batch_exec.
+int batch_capture(Context &c, const BatchLayout &L) {
+    if (c.batch_exec) cudaGraphExecDestroy(c.batch_exec);
+    c.batch_exec = nullptr;
+    const bool persist = c.persist;
+    c.persist = c.plan.persist;
+    c.persist_ctas = c.plan.ctas;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int rc = batch_enqueue(c, L, c.d_psinfo, c.d_porder, c.plan.pos, c.plan.types, c.plan.forces, c.plan.energies,
+                           c.plan.virials);
+    cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
+    c.persist = persist;
+    c.persist_ctas = 0;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(&c, ce, "end capture");
+    size_t n_nodes = 0;
+    c.plan.kernels = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess)
+            for (size_t k = 0; k < n_nodes; ++k) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                    ++c.plan.kernels;
+            }
+    }
+    ce = cudaGraphInstantiate(&c.batch_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        c.batch_exec = nullptr;
+        return cuda_fail(&c, ce, "graph instantiate");
+    }
+    c.plan.gen = c.buf_gen;
+    c.plan.stream = c.stream;
+    c.plan.caps = c.caps;
+    return AENET_OK;
+}
+
+}  // namespace
+}  // namespace aenet
+
+extern "C" int aenet_batch_prepare(aenet_ctx *h, int n_struct, const int64_t *atom_offset, const double *boxes,
+                                   const double *pos, const int32_t *types, double *energies, double *forces,
+                                   double *virials, int flags) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    cudaGetLastError();
+    c.plan.valid = false;
+    if (c.batch_exec) cudaGraphExecDestroy(c.batch_exec);
+    c.batch_exec = nullptr;
+    BatchLayout L;
+    int rc = batch_layout(c, n_struct, atom_offset, boxes, L);
+    if (rc) return rc;
+    const int n = L.n;
+    if (n > 0 && (!is_device_ptr(pos) || !is_device_ptr(types)))
+        return fail(&c, AENET_E_ARG, "a prepared batch needs device pos and types");
+    if ((forces && !is_device_ptr(forces)) || (energies && !is_device_ptr(energies)) ||
+        (virials && !is_device_ptr(virials)))
+        return fail(&c, AENET_E_ARG, "a prepared batch needs device output buffers");
+    if ((rc = batch_buffers(c, L))) return rc;
+    // the plan's own layout buffers
+    if (c.d_psinfo) cudaFree(c.d_psinfo);
+    if (c.d_porder) cudaFree(c.d_porder);
+    c.d_psinfo = nullptr;
+    c.d_porder = nullptr;
+    CK(cudaMalloc(&c.d_psinfo, sizeof(StructInfo) * (size_t)n_struct), "cudaMalloc");
+    CK(cudaMalloc(&c.d_porder, sizeof(int) * std::max<size_t>(1, L.order.size())), "cudaMalloc");
+    CK(cudaMemcpyAsync(c.d_psinfo, L.info.data(), sizeof(StructInfo) * n_struct, cudaMemcpyHostToDevice, c.stream),
+       "cudaMemcpyAsync");
+    CK(cudaMemcpyAsync(c.d_porder, L.order.data(), sizeof(int) * L.order.size(), cudaMemcpyHostToDevice, c.stream),
+       "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    c.plan.n_struct = n_struct;
+    c.plan.n_atoms = n;
+    c.plan.total_cells = L.gall.ncell;
+    c.plan.gall = L.gall;
+    c.plan.pos = pos;
+    c.plan.types = types;
+    c.plan.energies = energies;
+    c.plan.forces = forces;
+    c.plan.virials = virials;
+
+    // Candidate launches: one CTA per cell in index order, or persistent CTAs
+    // taking cells heaviest first; staging tiles of 256 ... 2048 image-atoms.
+    struct Cand {
+        bool persist;
+        int tile;
+        float ms;
+    };
+    std::vector<Cand> cands;
+    const bool tune = (flags & AENET_BATCH_AUTOTUNE) != 0;
+    if (tune) {
+        for (int p = 0; p < 2; ++p)
+            for (int tile : {256, 512, 1024, 2048}) cands.push_back({p == 1, tile, 0.f});
+    } else {
+        cands.push_back({true, c.caps.tile, 0.f});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev_guard{e0, e1};
+    const bool persist0 = c.persist;
+    int best = -1;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        Cand &cd = cands[k];
+        c.caps.tile = cd.tile;
+        c.persist = cd.persist;
+        if (check_smem(c, L.gall)) {  // does not fit: skip
+            cd.ms = -1.f;
+            continue;
+        }
+        for (int attempt = 0; attempt < 2; ++attempt) {  // warm-up run; regrow the lists once on overflow
+            CK(cudaMemsetAsync(c.d_err, 0, sizeof(unsigned), c.stream), "cudaMemsetAsync");
+            if ((rc = batch_enqueue(c, L, c.d_psinfo, c.d_porder, pos, types, forces, energies, virials))) break;
+            rc = read_error_word(c);
+            if (rc != AENET_E_CAPACITY || attempt == 1) break;
+            c.caps.nb *= 2;
+            c.caps.ang *= 2;
+        }
+        if (rc) {
+            c.persist = persist0;
+            return rc;
+        }
+        const int reps = tune ? 3 : 1;
+        CK(cudaEventRecord(e0, c.stream), "cudaEventRecord");
+        for (int r = 0; r < reps && !rc; ++r)
+            rc = batch_enqueue(c, L, c.d_psinfo, c.d_porder, pos, types, forces, energies, virials);
+        CK(cudaEventRecord(e1, c.stream), "cudaEventRecord");
+        CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        if (rc) {
+            c.persist = persist0;
+            return rc;
+        }
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        cd.ms = ms / reps;
+        if (best < 0 || cd.ms < cands[best].ms) best = (int)k;
+    }
+    c.persist = persist0;
+    if (best < 0) return fail(&c, AENET_E_CAPACITY, "no staging tile fits in shared memory");
+    if ((rc = read_error_word(c))) return rc;
+    c.plan.persist = cands[best].persist;
+    c.plan.tile = cands[best].tile;
+    c.plan.ctas = 0;
+    c.plan.ms = cands[best].ms;
+    c.caps.tile = c.plan.tile;
+    if ((rc = batch_capture(c, L))) return rc;
+    c.plan.ctas = c.plan.persist ? c.last_grid : L.gall.ncell;
+    c.plan.valid = true;
+    c.plan_layout = L.info;
+    c.plan_order = L.order;
+    return AENET_OK;
+}
+
+extern "C" int aenet_batch_run(aenet_ctx *h) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    cudaGetLastError();
+    if (!c.plan.valid || !c.batch_exec) return fail(&c, AENET_E_STATE, "no prepared batch");
+    if (c.plan.gen != c.buf_gen || c.plan.stream != c.stream || c.plan.caps.nb != c.caps.nb ||
+        c.plan.caps.ang != c.caps.ang) {
+        // work buffers, stream or list capacities changed since the capture
+        BatchLayout L;
+        L.info = c.plan_layout;
+        L.order = c.plan_order;
+        L.gall = c.plan.gall;
+        L.n = c.plan.n_atoms;
+        int rc = batch_buffers(c, L);
+        if (rc) return rc;
+        const int tile = c.caps.tile;
+        c.caps.tile = c.plan.tile;
+        rc = batch_capture(c, L);
+        c.caps.tile = tile;
+        if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(c.batch_exec, c.stream), "graph launch");
+    return AENET_OK;
+}
+
+extern "C" int aenet_batch_tuning(aenet_ctx *h, int *persistent, int *tile, int *ctas, int *kernels, float *ms) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (!c.plan.valid) return fail(&c, AENET_E_STATE, "no prepared batch");
+    if (persistent) *persistent = c.plan.persist ? 1 : 0;
+    if (tile) *tile = c.plan.tile;
+    if (ctas) *ctas = c.plan.ctas;
+    if (kernels) *kernels = c.plan.kernels;
+    if (ms) *ms = c.plan.ms;
     return AENET_OK;
 }
 
@@ -647,6 +934,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
         c.cap_rec = 0;
         CK(cudaMalloc(&c.d_rec, sizeof(double) * 2 * (size_t)(n_steps + 1)), "cudaMalloc");
         c.cap_rec = n_steps + 1;
+        ++c.buf_gen;
         destroy_graph(c);
     }
     double *rec = want_rec ? c.d_rec : nullptr;
@@ -676,7 +964,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
                           c.md_key.box[2] == box[2] && c.md_key.dt == dt && c.md_key.rec == rec &&
                           c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
                           c.md_key.caps.ang == c.caps.ang && c.md_key.caps.tile == c.caps.tile &&
-                          c.md_key.timing == timing;
+                          c.md_key.timing == timing && c.md_key.gen == c.buf_gen;
         if (!same) {
             destroy_graph(c);
             cudaGraph_t graph = nullptr;
@@ -716,6 +1004,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
             c.md_key.stream = c.stream;
             c.md_key.caps = c.caps;
             c.md_key.timing = timing;
+            c.md_key.gen = c.buf_gen;
         }
         for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(c.md_exec, c.stream), "graph launch");
     }
@@ -807,13 +1096,15 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
     if (!h) return;
     Context &c = h->c;
     destroy_graph(c);
+    if (c.batch_exec) cudaGraphExecDestroy(c.batch_exec);
+    c.batch_exec = nullptr;
     if (c.stream) cudaStreamSynchronize(c.stream);
     void *ptrs[] = {c.d_params, c.d_shift, c.d_scale, c.d_wbf, c.d_mass, c.d_pos4, c.d_tmp4, c.d_perm,
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,
                     c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres, c.d_act,
-                    c.d_wpart, c.d_wpairs, c.d_dEdW};
+                    c.d_wpart, c.d_wpairs, c.d_dEdW, c.d_work, c.d_order, c.d_psinfo, c.d_porder};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= Context::kStages; ++k)

@@ -122,9 +122,7 @@ cudaError_t launch_grad_weights(Context &c, int n) {
     }
     if ((e = launch_species_group(c, n)) != cudaSuccess) return e;
     const size_t smem = sizeof(float) * kGTile * rec;
-    if ((e = cudaFuncSetAttribute(k_dEdW_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
+    if ((e = allow_max_smem(k_dEdW_partial)) != cudaSuccess) return e;
     k_dEdW_partial<<<dim3(n_chunks, ns), kGThreads, smem, c.stream>>>(
         n, ns, np, rec, c.d_sp_list, c.d_sp_off, c.d_act, c.d_wpairs, c.d_wpart, n_chunks);
     k_dEdW_reduce<<<(ns * np + 255) / 256, 256, 0, c.stream>>>(ns, np, n_chunks, c.d_wpart, c.d_dEdW);

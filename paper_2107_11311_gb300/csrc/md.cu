@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(kMdThreads)
 // atoms are contiguous in cell order), virial = FP64 sum of its cells' partials.
 __global__ void k_batch_reduce(int n_struct, const StructInfo *__restrict__ sinfo, const int *__restrict__ cell_start,
                                const float *__restrict__ eatom, const double *__restrict__ vir_part,
-                               double *__restrict__ out) {
+                               double *__restrict__ out, double *__restrict__ energies,
+                               double *__restrict__ virials) {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= n_struct) return;
@@ -205,10 +206,16 @@ __global__ void k_batch_reduce(int n_struct, const StructInfo *__restrict__ sinf
     }
     if (k < a1) e0 += (double)eatom[k];
     const double e = warp_sum_d(e0 + e1);
-    if (lane == 0) out[(size_t)s * 10] = e;
+    if (lane == 0) {
+        if (out) out[(size_t)s * 10] = e;
+        if (energies) energies[s] = e;
+    }
     for (int q = 0; q < 9; ++q) {
         const double v = warp_reduce_strided(vir_part + (size_t)c0 * 9 + q, c1 - c0, 9, lane);
-        if (lane == 0) out[(size_t)s * 10 + 1 + q] = v;
+        if (lane == 0) {
+            if (out) out[(size_t)s * 10 + 1 + q] = v;
+            if (virials) virials[(size_t)s * 9 + q] = v;
+        }
     }
 }
 
@@ -244,11 +251,11 @@ cudaError_t launch_unsort_G(Context &c, int n, float *G) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_reduce(Context &c) {
+cudaError_t launch_batch_reduce(Context &c, double *energies, double *virials) {
     const int per = kRedThreads / 32;
-    k_batch_reduce<<<(c.batch_n + per - 1) / per, kRedThreads, 0, c.stream>>>(c.batch_n, c.batch_sinfo,
-                                                                              c.d_cell_start, c.d_eatom,
-                                                                              c.d_vir_part, c.d_bres);
+    double *rows = (energies || virials) ? nullptr : c.d_bres;
+    k_batch_reduce<<<(c.batch_n + per - 1) / per, kRedThreads, 0, c.stream>>>(
+        c.batch_n, c.batch_sinfo, c.d_cell_start, c.d_eatom, c.d_vir_part, rows, energies, virials);
     return cudaGetLastError();
 }
 

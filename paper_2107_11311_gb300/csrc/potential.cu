@@ -24,6 +24,8 @@
 // the G rows, kForces reads dE/dG rows and applies steps 1 and 4 only.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "aenet_internal.cuh"
 #include "fp_common.cuh"
 
@@ -650,30 +652,20 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,
                 const float *__restrict__ scale, float4 *__restrict__ F4, float *__restrict__ eatom,
                 float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
-                double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err) {
+                double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
+                unsigned *__restrict__ work, const int *__restrict__ order, int n_items) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
     __shared__ float s_vir[kPWarps][9];
     __shared__ double s_e[kPWarps];
-    __shared__ int s_next;
+    __shared__ int s_next, s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // the cell grid of this CTA's structure: the kernel parameter, or in a batch
-    // the grid of the structure that owns this cell (read in place, not copied)
-    int sidx = 0;
-    if constexpr (BATCH) {
-        int lo = 0, hi = n_struct - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sinfo[mid].cell0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-        }
-        sidx = lo;
-    }
-    const Grid &g = BATCH ? sinfo[sidx].g : g_one;
-    const int cell0 = BATCH ? sinfo[sidx].cell0 : 0;
-    const int n_off = g.n_off;
     const int tile = caps.tile;
-    const PLayout L = make_playout(n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0, net.stride);
+    // one layout for every cell: sized for the largest image-offset table
+    // (g_one.n_off is that maximum in a batch)
+    const PLayout L = make_playout(g_one.n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0,
+                                   net.stride);
     int *off_start = reinterpret_cast<int *>(smem + L.off_start);
     int *off_count = reinterpret_cast<int *>(smem + L.off_count);
     int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);
@@ -696,7 +688,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
         if (tid == t) s_tw[t] = B.type_weight[t];
-    if (tid == 0) s_next = 0;
     const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
 
     // ---- network parameters of every species into the shared-memory layout
@@ -731,8 +722,40 @@ __global__ void __launch_bounds__(kPThreads, 2)
         }
     }
 
+    unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
+    // Work items are cells: one per CTA (work == NULL), or, in the persistent
+    // form, taken from a global counter in the order given by `order` (heaviest
+    // cells first), so that CTAs stay resident and the tail stays short.
+    for (int item_pass = 0;; ++item_pass) {
+    int cell;
+    if (work) {
+        __syncthreads();  // the previous cell's shared-memory use is over
+        if (tid == 0) s_item = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        cell = order ? order[item] : item;
+    } else {
+        if (item_pass) break;
+        cell = blockIdx.x;
+    }
+    // the cell grid of this cell's structure: the kernel parameter, or in a batch
+    // the grid of the structure that owns the cell (read in place, not copied)
+    int sidx = 0;
+    if constexpr (BATCH) {
+        int lo = 0, hi = n_struct - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sinfo[mid].cell0 <= cell) lo = mid; else hi = mid - 1;
+        }
+        sidx = lo;
+    }
+    const Grid &g = BATCH ? sinfo[sidx].g : g_one;
+    const int cell0 = BATCH ? sinfo[sidx].cell0 : 0;
+    const int n_off = g.n_off;
+    if (tid == 0) s_next = 0;
+
     // ---- neighbour-cell table: start, count and image shift of every offset
-    const int cell = blockIdx.x;            // global cell
     const int lcell = cell - cell0;         // cell inside its structure's grid
     const int cx = lcell % g.nc[0], cy = (lcell / g.nc[0]) % g.nc[1], cz = lcell / (g.nc[0] * g.nc[1]);
     const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
@@ -794,7 +817,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
     double e_acc = 0.0;
-    unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
 
     auto finish_list = [&](int &nnb, int &nang) {
         if (nnb > caps.nb) {  // entries past the capacity were dropped
@@ -851,12 +873,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
         }
     }
 
-    // ---- CTA partials: statistics, energy (FP64), virial (FP32 lanes -> FP64)
-    if (MODE != kForces && lane == 0 && st_nb) {
-        atomicAdd(&stats[0], st_nb);
-        atomicAdd(&stats[1], st_ang);
-        atomicAdd(&stats[2], st_pairs);
-    }
+    // ---- cell partials: energy (FP64), virial (FP32 lanes -> FP64)
     if constexpr (MODE != kDescriptor) {
     #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -869,14 +886,20 @@ __global__ void __launch_bounds__(kPThreads, 2)
             float s = 0.f;
     #pragma unroll
             for (int w = 0; w < kPWarps; ++w) s += s_vir[w][tid];
-            vir_part[(size_t)blockIdx.x * 9 + tid] = (double)s;
+            vir_part[(size_t)cell * 9 + tid] = (double)s;
         }
         if (MODE == kFused && warp == 0) {  // FP64 tree over the warps' energies
             double v = lane < kPWarps ? s_e[lane] : 0.0;
     #pragma unroll
             for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0) e_part[blockIdx.x] = v;
+            if (lane == 0) e_part[cell] = v;
         }
+    }
+    }  // work items
+    if (MODE != kForces && lane == 0 && st_nb) {  // statistics
+        atomicAdd(&stats[0], st_nb);
+        atomicAdd(&stats[1], st_ang);
+        atomicAdd(&stats[2], st_pairs);
     }
 }
 
@@ -892,13 +915,27 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
             kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 16>
                                  : k_potential<KRT, KAT, EXACT, MODE, false, 16>;
     }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
     float *rows = MODE == kFused ? (c.keep_act ? c.d_act : nullptr) : c.d_G;  // activation records / G rows
-    kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
-                                                 c.d_cell_start, c.d_params,
-                                                 c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
-                                                 c.d_e_part, c.d_vir_part, c.d_stats, c.d_err);
+    int grid = g.ncell;
+    unsigned *work = nullptr;
+    if (c.persist && c.batch_sinfo && c.d_work && g.ncell > 0) {
+        // persistent form: as many CTAs as stay resident (or the tuned count)
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem)) != cudaSuccess)
+            return e;
+        const int resident = std::max(1, per_sm) * c.n_sm;
+        grid = std::min(g.ncell, c.persist_ctas > 0 ? std::min(c.persist_ctas, resident) : resident);
+        work = c.d_work;
+        if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
+    }
+    kern<<<grid, kPThreads, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
+                                              c.d_cell_start, c.d_params,
+                                              c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
+                                              c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,
+                                              work ? c.batch_order : nullptr, g.ncell);
+    c.last_grid = grid;
     return cudaGetLastError();
 }
 
@@ -1033,11 +1070,12 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
     const FusedNet net{};  // no network in descriptor mode
     const size_t smem = make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total;
     auto kern = k_potential<KRT, KAT, EXACT, kDescriptor, false, 32>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
     kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
                                            nullptr,
-                                           nullptr, Gs, nullptr, nullptr, nullptr, stats, err);
+                                           nullptr, Gs, nullptr, nullptr, nullptr, stats, err, nullptr, nullptr,
+                                           g.ncell);
     return cudaGetLastError();
 }
 
