@@ -279,6 +279,73 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
     }
 }
 
+// Step it of the rotation schedule over one block pair of angular entries:
+// lane l pairs its entry with column cc of block B. Inside a diagonal block
+// (A = B, n_A entries) step it uses the shift t = it + 1 and pairs l with
+// (l + t) mod n_A, for t = 1 .. n_A/2, the last shift only from the lower half
+// of the lanes when n_A is even, so each unordered pair is visited once; across
+// blocks step it pairs l with (l + it) mod 32. v: a real pair (step inside the
+// range, both entries present).
+__device__ __forceinline__ void rotation_step(bool diag, int it, int nt, int nA, int nB, int lane, bool vj, int &cc,
+                                              bool &v) {
+    if (diag) {
+        const int t = it + 1;
+        cc = lane + t >= nA ? lane + t - nA : lane + t;
+        v = vj && it < nt && !(2 * t == nA && lane >= t);
+    } else {
+        cc = (lane + it) & 31;
+        v = vj && it < nt && cc < nB;
+    }
+}
+
+// The lane whose partner in step it is this lane's entry (inverse rotation).
+__device__ __forceinline__ int rotation_source(bool diag, int it, int nA, int lane) {
+    if (diag) {
+        const int t = it + 1;
+        return lane - t < 0 ? lane - t + nA : lane - t;
+    }
+    return (lane - it) & 31;
+}
+
+// Chain rule through one angular term T(cos th) f_c(r_j) f_c(r_k) weighted by
+// b_q = ca_q + (s_j s_k) caw_q: adds dE/dd_j to (jx, jy, jz) and returns dE/dd_k
+// in (gx, gy, gz); nothing when v is false (uk, xk then hold any valid entry).
+//   d/dd_j [T(cos) f_j f_k] = T' f_j f_k (u_k - cos u_j) / r_j + T f_j' f_k u_j
+template <int KAT, bool EXACT>
+__device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj, const float4 uk, const float4 xk,
+                                              bool v, const float (&ca)[KAT], const float (&caw)[KAT], int Ka,
+                                              float &jx, float &jy, float &jz, float &gx, float &gy, float &gz) {
+    const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
+    const float w = xj.z * xk.z;
+    float S = fmaf(w, caw[0], ca[0]);
+    float dS = 0.f;
+    float tm1 = 1.0f, tt = c, um1 = 0.0f, u = 1.0f;
+#pragma unroll
+    for (int q = 1; q < KAT; ++q) {
+        if (q < Ka) {
+            const float b = fmaf(w, caw[q], ca[q]);
+            S = fmaf(b, tt, S);
+            dS = fmaf(b * (float)q, u, dS);
+            const float tn = fmaf(2.0f * c, tt, -tm1);
+            tm1 = tt;
+            tt = tn;
+            const float un = fmaf(2.0f * c, u, -um1);
+            um1 = u;
+            u = un;
+        }
+    }
+    const float fj = uj.w, fk = uk.w;
+    const float Af = v ? dS * fj * fk : 0.f;
+    const float Aj = Af * xj.x, Ak = Af * xk.x;
+    const float Bj = v ? S * xj.y * fk : 0.f, Bk = v ? S * fj * xk.y : 0.f;
+    jx += Aj * (uk.x - c * uj.x) + Bj * uj.x;
+    jy += Aj * (uk.y - c * uj.y) + Bj * uj.y;
+    jz += Aj * (uk.z - c * uj.z) + Bj * uj.z;
+    gx = Ak * (uj.x - c * uk.x) + Bk * uk.x;
+    gy = Ak * (uj.y - c * uk.y) + Bk * uk.y;
+    gz = Ak * (uj.z - c * uk.z) + Bk * uk.z;
+}
+
 template <int KRT, int KAT, bool EXACT, int MODE, int HB>
 __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
                                              const float *s_par, const float *s_tw, const WarpLists &W, int lane,
@@ -324,41 +391,41 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         for (int A = 0; A < nbk; ++A) {
             const int nA = min(32, nang - 32 * A);
             const bool vj = lane < nA;
-            const float4 uj = W.a_u[32 * A + (vj ? lane : 0)];
-            const float sj = W.a_x[32 * A + (vj ? lane : 0)].z;
+            const int self = 32 * A + (vj ? lane : 0);  // a valid entry: stands in for masked partners
+            const float4 uj = W.a_u[self];
+            const float sj = W.a_x[self].z;
             for (int Bk = A; Bk < nbk; ++Bk) {
                 const int nB = min(32, nang - 32 * Bk);
                 const bool diag = Bk == A;
                 const int nt = diag ? nA / 2 : 32;
-                for (int it = 0; it < nt; ++it) {
-                    const int t = diag ? it + 1 : it;
-                    int cc;
-                    bool v;
-                    if (diag) {
-                        cc = lane + t >= nA ? lane + t - nA : lane + t;
-                        v = vj && !(2 * t == nA && lane >= t);
-                    } else {
-                        cc = (lane + t) & 31;
-                        v = vj && cc < nB;
-                    }
-                    if (v) {
-                        const float4 uk = W.a_u[32 * Bk + cc];
-                        const float sk = W.a_x[32 * Bk + cc].z;
-                        const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-                        const float w = uj.w * uk.w;
-                        const float ws = w * sj * sk;
-                        float tm1 = 1.0f, tt = c;
-                        acc[SLOT_ANG] += w;
-                        acc[SLOT_ANGW] += ws;
+                // two rotation steps per iteration: their Chebyshev recurrences
+                // are independent, which hides the FMA latency of each chain;
+                // every accumulator still takes step it before step it + 1
+                for (int it = 0; it < nt; it += 2) {
+                    int ccA, ccB;
+                    bool vA, vB;
+                    rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
+                    rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
+                    const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
+                    const float4 ukA = W.a_u[kA], ukB = W.a_u[kB];
+                    const float skA = W.a_x[kA].z, skB = W.a_x[kB].z;
+                    const float cA = uj.x * ukA.x + uj.y * ukA.y + uj.z * ukA.z;
+                    const float cB = uj.x * ukB.x + uj.y * ukB.y + uj.z * ukB.z;
+                    const float wA = vA ? uj.w * ukA.w : 0.f, wB = vB ? uj.w * ukB.w : 0.f;
+                    const float wsA = wA * sj * skA, wsB = wB * sj * skB;
+                    float tA1 = 1.0f, tA = cA, tB1 = 1.0f, tB = cB;
+                    acc[SLOT_ANG] = (acc[SLOT_ANG] + wA) + wB;
+                    acc[SLOT_ANGW] = (acc[SLOT_ANGW] + wsA) + wsB;
 #pragma unroll
-                        for (int q = 1; q < KAT; ++q) {
-                            if (q < Ka) {
-                                acc[SLOT_ANG + q] = fmaf(tt, w, acc[SLOT_ANG + q]);
-                                acc[SLOT_ANGW + q] = fmaf(tt, ws, acc[SLOT_ANGW + q]);
-                                const float tn = fmaf(2.0f * c, tt, -tm1);
-                                tm1 = tt;
-                                tt = tn;
-                            }
+                    for (int q = 1; q < KAT; ++q) {
+                        if (q < Ka) {
+                            acc[SLOT_ANG + q] = fmaf(tB, wB, fmaf(tA, wA, acc[SLOT_ANG + q]));
+                            acc[SLOT_ANGW + q] = fmaf(tB, wsB, fmaf(tA, wsA, acc[SLOT_ANGW + q]));
+                            const float tnA = fmaf(2.0f * cA, tA, -tA1), tnB = fmaf(2.0f * cB, tB, -tB1);
+                            tA1 = tA;
+                            tA = tnA;
+                            tB1 = tB;
+                            tB = tnB;
                         }
                     }
                 }
@@ -544,64 +611,34 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         for (int A = 0; A < nbk; ++A) {
             const int nA = min(32, nang - 32 * A);
             const bool vj = lane < nA;
-            const float4 uj = W.a_u[32 * A + (vj ? lane : 0)];
-            const float4 xj = W.a_x[32 * A + (vj ? lane : 0)];
+            const int self = 32 * A + (vj ? lane : 0);
+            const float4 uj = W.a_u[self];
+            const float4 xj = W.a_x[self];
             for (int Bk = A; Bk < nbk; ++Bk) {
                 const int nB = min(32, nang - 32 * Bk);
                 const bool diag = Bk == A;
                 const int nt = diag ? nA / 2 : 32;
                 float jx = 0.f, jy = 0.f, jz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
-                for (int it = 0; it < nt; ++it) {
-                    const int t = diag ? it + 1 : it;
-                    int cc, src;
-                    bool v;
-                    if (diag) {
-                        cc = lane + t >= nA ? lane + t - nA : lane + t;
-                        src = lane - t < 0 ? lane - t + nA : lane - t;
-                        v = vj && !(2 * t == nA && lane >= t);
-                    } else {
-                        cc = (lane + t) & 31;
-                        src = (lane - t) & 31;
-                        v = vj && cc < nB;
-                    }
-                    float gkx = 0.f, gky = 0.f, gkz = 0.f;
-                    if (v) {
-                        const float4 uk = W.a_u[32 * Bk + cc];
-                        const float4 xk = W.a_x[32 * Bk + cc];
-                        const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-                        const float w = xj.z * xk.z;
-                        float S = fmaf(w, caw[0], ca[0]);
-                        float dS = 0.f;
-                        float tm1 = 1.0f, tt = c, um1 = 0.0f, u = 1.0f;
-#pragma unroll
-                        for (int q = 1; q < KAT; ++q) {
-                            if (q < Ka) {
-                                const float b = fmaf(w, caw[q], ca[q]);
-                                S = fmaf(b, tt, S);
-                                dS = fmaf(b * (float)q, u, dS);
-                                const float tn = fmaf(2.0f * c, tt, -tm1);
-                                tm1 = tt;
-                                tt = tn;
-                                const float un = fmaf(2.0f * c, u, -um1);
-                                um1 = u;
-                                u = un;
-                            }
-                        }
-                        // d/dd_j [T(cos) f_j f_k] = T' f_j f_k (u_k - cos u_j)/r_j + T f_j' f_k u_j
-                        const float fj = uj.w, fk = uk.w;
-                        const float Af = dS * fj * fk;
-                        const float Aj = Af * xj.x, Ak = Af * xk.x;
-                        const float Bj = S * xj.y * fk, Bk2 = S * fj * xk.y;
-                        jx += Aj * (uk.x - c * uj.x) + Bj * uj.x;
-                        jy += Aj * (uk.y - c * uj.y) + Bj * uj.y;
-                        jz += Aj * (uk.z - c * uj.z) + Bj * uj.z;
-                        gkx = Ak * (uj.x - c * uk.x) + Bk2 * uk.x;
-                        gky = Ak * (uj.y - c * uk.y) + Bk2 * uk.y;
-                        gkz = Ak * (uj.z - c * uk.z) + Bk2 * uk.z;
-                    }
-                    kx += __shfl_sync(kFull, gkx, src);
-                    ky += __shfl_sync(kFull, gky, src);
-                    kz += __shfl_sync(kFull, gkz, src);
+                for (int it = 0; it < nt; it += 2) {  // two independent steps per iteration (ILP)
+                    int ccA, ccB;
+                    bool vA, vB;
+                    rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
+                    rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
+                    const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
+                    float gAx, gAy, gAz, gBx, gBy, gBz;
+                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kA], W.a_x[kA], vA, ca, caw, Ka, jx, jy, jz, gAx, gAy,
+                                              gAz);
+                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kB], W.a_x[kB], vB, ca, caw, Ka, jx, jy, jz, gBx, gBy,
+                                              gBz);
+                    // dE/dd_k goes to the lane that owns k: it sits t lanes to the left
+                    const int srcA = rotation_source(diag, it, nA, lane);
+                    const int srcB = rotation_source(diag, it + 1, nA, lane);
+                    kx += __shfl_sync(kFull, gAx, srcA);
+                    ky += __shfl_sync(kFull, gAy, srcA);
+                    kz += __shfl_sync(kFull, gAz, srcA);
+                    kx += __shfl_sync(kFull, gBx, srcB);
+                    ky += __shfl_sync(kFull, gBy, srcB);
+                    kz += __shfl_sync(kFull, gBz, srcB);
                 }
                 // force on neighbour = -dE_i/dd; each entry is touched by its owner lane only
                 if (vj) {

@@ -83,7 +83,8 @@ def test_prepared_batch_equals_eager_batch_and_survives_reallocation(gpu_mod):
     g.batch_run()
     torch.cuda.synchronize()
     eager = g.compute_batch(off, d["pos"].cpu().numpy(), d["types"].cpu().numpy(), boxes)
-    np.testing.assert_allclose(d["energies"].cpu().numpy(), eager["energies"], rtol=0, atol=1e-6 * len(off))
+    # equal up to the run-dependent order of FP32 sums (atom order inside a cell)
+    np.testing.assert_allclose(d["energies"].cpu().numpy(), eager["energies"], rtol=2e-7, atol=1e-6)
     np.testing.assert_allclose(d["forces"].cpu().numpy(), eager["forces"], atol=1e-4)
     # a larger system on the same context regrows the work buffers; the next
     # replay must capture again instead of using the old addresses
@@ -95,7 +96,7 @@ def test_prepared_batch_equals_eager_batch_and_survives_reallocation(gpu_mod):
     torch.cuda.synchronize()
     g.check()
     # same layout, same coordinates: equal up to the run-dependent order of FP32 sums
-    torch.testing.assert_close(d["energies"], E_before, rtol=1e-7, atol=1e-6)
+    torch.testing.assert_close(d["energies"], E_before, rtol=2e-7, atol=1e-6)
 
 
 def test_prepared_batch_errors(gpu_mod):
