@@ -116,6 +116,23 @@ int aenet_compute(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t 
                   double *e_atom);
 
 /*
+ * Verlet neighbour list for aenet_md_nve (the LAMMPS-style list with a skin
+ * that the paper credits for ænet-LAMMPS's speed over ænet-TINKER, Sec. IV.B).
+ * skin (A) >= 0; 0 (the default) rebuilds the cell list in every step. With
+ * skin > 0 (FP32 form; the other forms ignore it) each MD step reuses a list
+ * of the image-atoms within rc_max + skin of every atom and rebuilds it inside
+ * the captured step only when some atom moved more than skin/2 since the last
+ * build (a CUDA-graph conditional node set on the device). Energies and forces
+ * are those of the cell path. The list costs (rc_max + skin)^3 / rc_max^3 more
+ * candidate pairs per step and one 4-byte entry per candidate.
+ * Errors: AENET_E_ARG for a negative or non-finite skin.
+ */
+int aenet_set_skin(aenet_ctx *ctx, double skin);
+
+/* Number of Verlet-list builds so far on this context (synchronises). */
+int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
+
+/*
  * Energies, forces and virials of many independent periodic structures in one
  * evaluation (one binning, one potential launch over the cells of every
  * structure, one per-structure reduction).

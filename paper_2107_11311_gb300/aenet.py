@@ -66,6 +66,8 @@ def load(build_if_missing: bool = True):
     lib.aenet_compute_batch.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_batch_prepare.argtypes = [P, I, P, P, P, P, P, P, P, I]
     lib.aenet_batch_run.argtypes = [P]
+    lib.aenet_set_skin.argtypes = [P, D]
+    lib.aenet_md_list_builds.argtypes = [P, P]
     lib.aenet_batch_tuning.argtypes = [P, P, P, P, P, P]
     lib.aenet_set_option.argtypes = [P, I, I]
     lib.aenet_grad_weights.argtypes = [P, P]
@@ -276,6 +278,16 @@ class AenetGPU:
         box = self._box(box)
         self._check(self.lib.aenet_md_nve(self.h, n, _ptr(pos), _ptr(vel), _ptr(types), _ptr(box),
                                           float(dt), int(n_steps), _ptr(e_pot), _ptr(e_kin), int(flags)))
+
+    def set_skin(self, skin):
+        """Verlet-list skin (A) for md_nve; 0 rebuilds the cell list every step."""
+        self._check(self.lib.aenet_set_skin(self.h, float(skin)))
+
+    def md_list_builds(self):
+        """Verlet-list builds so far on this context."""
+        out = np.zeros(1, dtype=np.int64)
+        self._check(self.lib.aenet_md_list_builds(self.h, _ptr(out)))
+        return int(out[0])
 
     def set_option(self, option, value):
         self._check(self.lib.aenet_set_option(self.h, int(option), int(value)))

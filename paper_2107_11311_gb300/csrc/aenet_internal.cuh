@@ -63,7 +63,8 @@ struct Grid {
 // coordinates relative to the cell origin (computed in FP64, then rounded).
 // FP64 work is a short chain of multiplies and FMAs (no division): FP64 has a
 // long latency on this part.
-__device__ inline int bin_position(double x0, double x1, double x2, const Grid &g, float *u, bool &finite) {
+__device__ inline int bin_position(double x0, double x1, double x2, const Grid &g, float *u, bool &finite,
+                                   double *ud = nullptr) {
     const double xs[3] = {x0, x1, x2};
     int ci[3];
 #pragma unroll
@@ -80,7 +81,9 @@ __device__ inline int bin_position(double x0, double x1, double x2, const Grid &
         int c = (int)(w * g.inv_h[a]);
         c = c >= g.nc[a] ? g.nc[a] - 1 : c;
         ci[a] = c;
-        u[a] = (float)fma(-(double)c, g.h[a], w);
+        const double ua = fma(-(double)c, g.h[a], w);
+        u[a] = (float)ua;
+        if (ud) ud[a] = ua;  // FP64 cell-relative coordinate (the Verlet list keeps its origin)
     }
     return (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
 }
@@ -93,11 +96,15 @@ struct StructInfo {
     int cell0, ncell, atom0, natoms;
 };
 
-// Capacities of the per-warp neighbour lists of the potential kernel.
+// Capacities of the per-warp neighbour lists of the potential kernel, and the
+// shape of the Verlet list (MD with a skin).
 struct Caps {
     int nb;     // entries with r <= rc_max
     int ang;    // entries with r <= rc_ang
     int tile;   // staged neighbour-cell atoms per chunk (fused kernel)
+    int vl_cap = 0;        // Verlet-list entries per atom (r <= rc_max + skin at the build)
+    int vl_jbits = 0;      // bits of the sorted atom index in an entry; the rest: image-offset code
+    float rc_list = 0.f;   // rc_max + skin
 };
 
 struct Context {
@@ -177,6 +184,28 @@ struct Context {
     const StructInfo *batch_sinfo = nullptr;  // non-NULL while a batch is enqueued
     int batch_n = 0;
 
+    // Verlet neighbour list with a skin (MD steps of the fused FP32 form; skin 0 =
+    // the cell list every step). Entries: sorted index | image-offset code << jbits,
+    // built by k_potential's list mode, rebuilt inside the captured step (a graph
+    // conditional node) whenever an atom moved more than skin/2 since the build.
+    double skin = 0.0;
+    int cap_vl_atoms = 0;
+    long long cap_vl_entries = 0;
+    int *d_vl = nullptr;               // [atoms * vl_cap] sorted order
+    int *d_vl_count = nullptr;         // [atoms]
+    double *d_vl_origin = nullptr;     // [atoms * 3] origin of atom i's FP32 coordinates (input order)
+    double *d_vl_ref = nullptr;        // [atoms * 3] positions at the last build (input order)
+    unsigned *d_vl_flag = nullptr;     // [2]: rebuild flag, last-CTA counter
+    unsigned long long *d_vl_builds = nullptr;  // list builds so far
+    double *d_vl_epart = nullptr;      // [4 * SMs] energy partials of the list-mode kernel
+    double *d_vl_vpart = nullptr;      // [4 * SMs * 9] virial partials
+    bool vl_valid = false;             // list, origins and cell maps describe the MD state
+    cudaStream_t aux_stream = nullptr; // captures the body of the rebuild conditional
+    int maps_n = -1;                   // atoms of the evaluation that last wrote the cell maps
+    // partials of the last potential evaluation (read by the MD reductions)
+    const double *last_epart = nullptr, *last_vpart = nullptr;
+    int last_eparts = 0, last_vparts = 0;
+
     // Generation of the work buffers: bumped whenever one is reallocated, so a
     // captured graph (which holds their addresses) knows it must be re-captured.
     unsigned buf_gen = 0;
@@ -226,6 +255,7 @@ struct Context {
         Caps caps{};
         bool timing = false;
         unsigned gen = 0;
+        double skin = 0.0;
     } md_key;
 
     // stage timing of the captured MD step (events recorded inside the graph)
@@ -309,9 +339,27 @@ cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt
                                      const int32_t *types);
 // The closing kick (v += dt/2 F/m c) with the kinetic energy, fused with the
 // FP64 reduction of energy, virial and kinetic energy (last-CTA pattern) into
-// c.d_result and, when rec_pot != NULL, the record of step *c.d_step.
-cudaError_t launch_md_kick_finish(Context &c, const Grid &g, int n, int n_eparts, double dt, double *vel,
-                                  const int32_t *types, double *rec_pot, double *rec_kin);
+// c.d_result and, when rec_pot != NULL, the record of step *c.d_step. The
+// partials are those of the last potential evaluation (c.last_*). With
+// clear_vl, the last CTA also counts a list build and clears the rebuild flag.
+cudaError_t launch_md_kick_finish(Context &c, int n, double dt, double *vel, const int32_t *types,
+                                  double *rec_pot, double *rec_kin, bool clear_vl = false);
+
+// Verlet form of the opening half-kick and drift (no binning): refresh the FP32
+// coordinates relative to the origins of the last list build, raise the rebuild
+// flag if an atom moved more than skin/2, and set the graph conditional.
+cudaError_t launch_md_vl_kick_drift(Context &c, int n, double dt, double *pos, double *vel, const int32_t *types,
+                                    cudaGraphConditionalHandle cond);
+// Rebuild, part 1: bin the current positions, record each atom's origin and
+// reference position (then launch_sort and launch_vl_build).
+cudaError_t launch_md_vl_bin(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
+// Rebuild, part 2: the Verlet list of every atom (k_potential, list-build mode).
+cudaError_t launch_vl_build(Context &c, const Grid &g, int n);
+// The fused potential over the Verlet list (persistent CTAs, atoms from a
+// counter); sets c.last_* to its partials.
+cudaError_t launch_potential_list(Context &c, const Grid &g, int n);
+// Largest CTA count of launch_potential_list (sizes its partial buffers).
+int potential_list_max_ctas(const Context &c);
 
 // Message reported by aenet_last_error(NULL) for calls made without a context.
 void set_context_free_error(const char *msg);

@@ -63,8 +63,10 @@ cudaError_t grow(T *&p, size_t have, size_t need) {
     return cudaMalloc(&p, sizeof(T) * (need > 0 ? need : 1));
 }
 
-int make_grid(Context &c, const double *box, Grid &g) {
-    const double rc = c.basis.rc_max;
+// Cell grid of a box: cells of edge >= rc_cut (default: the largest cutoff) and
+// the (2m+1)^3 image-cell window that covers rc_cut.
+int make_grid(Context &c, const double *box, Grid &g, double rc_cut = 0.0) {
+    const double rc = rc_cut > 0.0 ? rc_cut : c.basis.rc_max;
     g.ncell = 1;
     g.n_off = 1;
     for (int a = 0; a < 3; ++a) {
@@ -191,6 +193,10 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent
         if (evs) CK(mark(c, evs[1]), "event");
         CK(launch_fused_potential(c, g, n), "potential kernel");
         *n_eparts = g.ncell;
+        c.last_epart = c.d_e_part;
+        c.last_eparts = g.ncell;
+        c.last_vpart = c.d_vir_part;
+        c.last_vparts = g.ncell;
     } else {
         CK(launch_fp_forward(c, g, n), "descriptor kernel");
         if (evs) CK(mark(c, evs[0]), "event");
@@ -203,7 +209,13 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent
         }
         if (evs) CK(mark(c, evs[1]), "event");
         CK(launch_fp_backward(c, g, n), "force kernel");
+        c.last_epart = c.d_e_part;
+        c.last_eparts = *n_eparts;
+        c.last_vpart = c.d_vir_part;
+        c.last_vparts = g.ncell;
     }
+    c.maps_n = n;          // the cell maps now describe this evaluation
+    c.vl_valid = false;    // and no Verlet list matches them
     if (evs) CK(mark(c, evs[2]), "event");
     return AENET_OK;
 }
@@ -848,6 +860,8 @@ extern "C" int aenet_batch_run(aenet_ctx *h) {
         if (rc) return rc;
     }
     CK(cudaGraphLaunch(c.batch_exec, c.stream), "graph launch");
+    c.maps_n = c.plan.n_atoms;  // the replay rewrote the cell maps
+    c.vl_valid = false;
     return AENET_OK;
 }
 
@@ -885,9 +899,104 @@ static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *
     if (ev) CK(mark(c, ev[2]), "event");
     int n_eparts = 0;
     if ((rc = enqueue_potential(c, g, n, &n_eparts, ev ? ev + 3 : nullptr))) return rc;
-    CK(launch_md_kick_finish(c, g, n, n_eparts, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr),
+    CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr), "kick + reductions");
+    if (ev) CK(mark(c, ev[6]), "event");
+    return AENET_OK;
+}
+
+// One MD step with the Verlet list, enqueued while c.stream is being captured:
+// kick + drift (refreshing the FP32 coordinates, setting the rebuild
+// conditional), a conditional node whose body rebuilds the list (binning, cell
+// sort, list build; captured on the auxiliary stream), the potential over the
+// list, and the closing kick with the reductions. Events bracket the stages.
+static int enqueue_md_step_verlet(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
+                                  const int32_t *types, double *rec, bool timing) {
+    cudaEvent_t *ev = timing ? c.ev : nullptr;
+    int rc = check_smem(c, g);
+    if (rc) return rc;
+    cudaStreamCaptureStatus status;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamGetCaptureInfo(c.stream, &status, nullptr, &graph, nullptr, nullptr, nullptr), "capture info");
+    if (status != cudaStreamCaptureStatusActive || !graph) return fail(&c, AENET_E_STATE, "stream is not capturing");
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault), "conditional handle");
+    if (ev) CK(mark(c, ev[0]), "event");
+    CK(launch_md_vl_kick_drift(c, n, dt, pos, vel, types, cond), "kick + drift");
+    if (ev) CK(mark(c, ev[1]), "event");
+    // the conditional node after everything captured so far
+    const cudaGraphNode_t *deps = nullptr;
+    size_t n_deps = 0;
+    CK(cudaStreamGetCaptureInfo(c.stream, &status, nullptr, &graph, &deps, nullptr, &n_deps), "capture info");
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, graph, deps, nullptr, n_deps, &cp), "conditional node");
+    CK(cudaStreamUpdateCaptureDependencies(c.stream, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies),
+       "capture dependencies");
+    // its body: the rebuild, captured on the auxiliary stream
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(c.aux_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+       "body capture");
+    cudaStream_t main_stream = c.stream;
+    c.stream = c.aux_stream;
+    cudaError_t be = launch_md_vl_bin(c, g, n, pos, types);
+    if (be == cudaSuccess) be = launch_sort(c, g, n);
+    if (be == cudaSuccess) be = launch_vl_build(c, g, n);
+    c.stream = main_stream;
+    cudaGraph_t body_out = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c.aux_stream, &body_out);
+    if (be != cudaSuccess) return cuda_fail(&c, be, "list rebuild");
+    if (ee != cudaSuccess) return cuda_fail(&c, ee, "body capture");
+    if (ev) CK(mark(c, ev[2]), "event");
+    if (ev) CK(mark(c, ev[3]), "event");
+    if (ev) CK(mark(c, ev[4]), "event");
+    CK(launch_potential_list(c, g, n), "potential kernel (Verlet list)");
+    if (ev) CK(mark(c, ev[5]), "event");
+    CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr, true),
        "kick + reductions");
     if (ev) CK(mark(c, ev[6]), "event");
+    return AENET_OK;
+}
+
+// Buffers and list shape of the Verlet path for n atoms on grid g.
+static int ensure_verlet(Context &c, int n, const Grid &g) {
+    if (!c.aux_stream) CK(cudaStreamCreateWithFlags(&c.aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    int code_bits = 0;
+    while ((1 << code_bits) < g.n_off) ++code_bits;
+    const int jbits = 31 - code_bits;
+    if (jbits < 1 || n >= (1 << jbits) || n >= (1 << 28))
+        return fail(&c, AENET_E_CAPACITY, "Verlet list: %d atoms x %d image offsets do not fit a 31-bit entry", n,
+                    g.n_off);
+    const double V = g.box[0] * g.box[1] * g.box[2];
+    const double rl = c.caps.rc_list;
+    const int need_cap =
+        std::max(64, (((int)(1.3 * (n / V) * 4.18879020478639 * rl * rl * rl + 32.0)) + 15) / 16 * 16);
+    if (c.caps.vl_cap < need_cap) c.caps.vl_cap = need_cap;
+    c.caps.vl_jbits = jbits;
+    const size_t N = (size_t)std::max(n, 1);
+    if (n > c.cap_vl_atoms || !c.d_vl || (size_t)c.caps.vl_cap * N > (size_t)c.cap_vl_entries) {
+        CK(grow(c.d_vl, 0, N * c.caps.vl_cap), "cudaMalloc");
+        CK(grow(c.d_vl_count, 0, N), "cudaMalloc");
+        CK(grow(c.d_vl_origin, 0, 3 * N), "cudaMalloc");
+        CK(grow(c.d_vl_ref, 0, 3 * N), "cudaMalloc");
+        c.cap_vl_atoms = n;
+        c.cap_vl_entries = (long long)N * c.caps.vl_cap;
+        c.vl_valid = false;
+        ++c.buf_gen;
+    }
+    if (!c.d_vl_flag) {
+        const size_t P = (size_t)potential_list_max_ctas(c);
+        CK(grow(c.d_vl_flag, 0, 2), "cudaMalloc");
+        CK(grow(c.d_vl_builds, 0, 1), "cudaMalloc");
+        CK(grow(c.d_vl_epart, 0, P + 1), "cudaMalloc");
+        CK(grow(c.d_vl_vpart, 0, 9 * P + 9), "cudaMalloc");
+        CK(cudaMemsetAsync(c.d_vl_flag, 0, 2 * sizeof(unsigned), c.stream), "cudaMemsetAsync");
+        CK(cudaMemsetAsync(c.d_vl_builds, 0, sizeof(unsigned long long), c.stream), "cudaMemsetAsync");
+        ++c.buf_gen;
+    }
     return AENET_OK;
 }
 
@@ -908,18 +1017,25 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
         bool v;
         ~Restore() { c.keep_act = v; }
     } restore{c, keep_act};
-    const bool cont = (flags & AENET_MD_CONTINUE) != 0;
+    // continuing needs the cell maps and forces of an evaluation of these n atoms
+    const bool cont = (flags & AENET_MD_CONTINUE) != 0 && c.maps_n == n;
     const bool timing = (flags & AENET_MD_TIMING) != 0;
+    const bool verlet = c.skin > 0.0 && fused_supported(c);
     const bool pos_dev = is_device_ptr(pos), vel_dev = is_device_ptr(vel), typ_dev = is_device_ptr(types);
     const bool rec_dev = (!e_pot || is_device_ptr(e_pot)) && (!e_kin || is_device_ptr(e_kin));
     if (async && !(pos_dev && vel_dev && typ_dev && rec_dev))
         return fail(&c, AENET_E_ARG, "AENET_MD_ASYNC needs device pointers");
     Grid g;
-    int rc = make_grid(c, box, g);
+    // with a Verlet list the cells must cover the list cutoff rc_max + skin
+    int rc = make_grid(c, box, g, verlet ? c.basis.rc_max + c.skin : 0.0);
     if (rc) return rc;
     if ((rc = validate_types_host(c, n, types))) return rc;
     if ((rc = ensure(c, n, g)) || (rc = ensure_stage(c, n))) return rc;
     if (c.caps.nb == 0) c.caps = estimate_caps(c, n, g);
+    if (verlet) {
+        c.caps.rc_list = (float)(c.basis.rc_max + c.skin);
+        if ((rc = ensure_verlet(c, n, g))) return rc;
+    }
     double *dpos = pos_dev ? pos : c.d_pos;
     double *dvel = vel_dev ? vel : c.d_vel;
     const int32_t *dtypes = typ_dev ? types : c.d_types;
@@ -942,10 +1058,9 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
     if (want_rec) CK(cudaMemsetAsync(c.d_step, 0, sizeof(int), c.stream), "cudaMemsetAsync");
     // frame 0: forces at the initial positions (unless continuing); a
     // neighbour-list overflow here regrows the capacities once before capture
-    int n_eparts = fused_supported(c) ? g.ncell : (c.precision == AENET_FP32 ? ann_blocks(n) : bf16_eparts(c, n));
     if (!cont) {
         for (int attempt = 0; attempt < 2; ++attempt) {
-            if ((rc = enqueue_compute(c, g, n, dpos, dtypes, nullptr, nullptr, &n_eparts))) return rc;
+            if ((rc = enqueue_compute(c, g, n, dpos, dtypes, nullptr, nullptr))) return rc;
             if (async) break;
             rc = read_error_word(c);
             if (rc != AENET_E_CAPACITY || attempt == 1) break;
@@ -957,19 +1072,21 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
         if (rc) return rc;
     }
     if (want_rec)  // kinetic energy and record of frame 0 (a kick with dt = 0)
-        CK(launch_md_kick_finish(c, g, n, n_eparts, 0.0, dvel, dtypes, rec, rec + c.cap_rec), "frame 0");
+        CK(launch_md_kick_finish(c, n, 0.0, dvel, dtypes, rec, rec + c.cap_rec), "frame 0");
     if (n_steps > 0) {
         const bool same = c.md_exec && c.md_key.n == n && c.md_key.pos == dpos && c.md_key.vel == dvel &&
                           c.md_key.types == dtypes && c.md_key.box[0] == box[0] && c.md_key.box[1] == box[1] &&
                           c.md_key.box[2] == box[2] && c.md_key.dt == dt && c.md_key.rec == rec &&
                           c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
                           c.md_key.caps.ang == c.caps.ang && c.md_key.caps.tile == c.caps.tile &&
-                          c.md_key.timing == timing && c.md_key.gen == c.buf_gen;
+                          c.md_key.timing == timing && c.md_key.gen == c.buf_gen && c.md_key.skin == c.skin &&
+                          c.md_key.caps.vl_cap == c.caps.vl_cap;
         if (!same) {
             destroy_graph(c);
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            int src = enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec, timing);
+            int src = verlet ? enqueue_md_step_verlet(c, g, n, dt, dpos, dvel, dtypes, rec, timing)
+                             : enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec, timing);
             cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
             if (src) {
                 if (graph) cudaGraphDestroy(graph);
@@ -1005,8 +1122,14 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
             c.md_key.caps = c.caps;
             c.md_key.timing = timing;
             c.md_key.gen = c.buf_gen;
+            c.md_key.skin = c.skin;
         }
+        // the first step after any other evaluation (or a new list shape) builds the list
+        if (verlet && (!cont || !c.vl_valid))
+            CK(cudaMemsetAsync(c.d_vl_flag, 0xff, sizeof(unsigned), c.stream), "cudaMemsetAsync");
         for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(c.md_exec, c.stream), "graph launch");
+        c.maps_n = n;
+        c.vl_valid = verlet;
     }
     if (want_rec) {
         if (e_pot) CK(cudaMemcpyAsync(e_pot, rec, sizeof(double) * (n_steps + 1), cudaMemcpyDefault, c.stream), "e_pot");
@@ -1104,11 +1227,39 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,
                     c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres, c.d_act,
-                    c.d_wpart, c.d_wpairs, c.d_dEdW, c.d_work, c.d_order, c.d_psinfo, c.d_porder};
+                    c.d_wpart, c.d_wpairs, c.d_dEdW, c.d_work, c.d_order, c.d_psinfo, c.d_porder,
+                    c.d_vl, c.d_vl_count, c.d_vl_origin, c.d_vl_ref, c.d_vl_flag, c.d_vl_builds,
+                    c.d_vl_epart, c.d_vl_vpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= Context::kStages; ++k)
         if (c.ev[k]) cudaEventDestroy(c.ev[k]);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+    if (c.aux_stream) cudaStreamDestroy(c.aux_stream);
     delete h;
+}
+
+extern "C" int aenet_set_skin(aenet_ctx *h, double skin) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (!(skin >= 0.0) || !isfinite(skin)) return fail(&c, AENET_E_ARG, "skin must be finite and >= 0");
+    if (skin != c.skin) {
+        c.skin = skin;
+        c.vl_valid = false;
+        c.caps.vl_cap = 0;
+        destroy_graph(c);
+    }
+    return AENET_OK;
+}
+
+extern "C" int aenet_md_list_builds(aenet_ctx *h, int64_t *builds) {
+    if (!h || !builds) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
+    Context &c = h->c;
+    unsigned long long v = 0;
+    if (c.d_vl_builds) {
+        CK(cudaMemcpyAsync(&v, c.d_vl_builds, sizeof(v), cudaMemcpyDeviceToHost, c.stream), "cudaMemcpyAsync");
+        CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    }
+    *builds = (int64_t)v;
+    return AENET_OK;
 }

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(kMdThreads)
                      const int *__restrict__ slot, int n_e, const double *__restrict__ e_part, int n_v,
                      const double *__restrict__ vir_part, double *__restrict__ ke_part, unsigned *__restrict__ done,
                      double *__restrict__ result, int *__restrict__ step, double *__restrict__ rec_pot,
-                     double *__restrict__ rec_kin) {
+                     double *__restrict__ rec_kin, unsigned *__restrict__ vl_flag,
+                     unsigned long long *__restrict__ vl_builds) {
     __shared__ double s_w[kMdThreads / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -178,6 +179,10 @@ __global__ void __launch_bounds__(kMdThreads)
     __syncthreads();
     if (tid == 0) {
         *done = 0u;
+        if (vl_flag && vl_flag[0]) {  // this step rebuilt the Verlet list
+            ++*vl_builds;
+            vl_flag[0] = 0u;
+        }
         if (rec_pot) {
             const int s = *step;
             rec_pot[s] = result[0];
@@ -185,6 +190,97 @@ __global__ void __launch_bounds__(kMdThreads)
             *step = s + 1;
         }
     }
+}
+
+// Verlet form of v += dt/2 F/m c; x += dt v (the list is kept, nothing is
+// binned). The FP32 coordinate of atom i is refreshed relative to the origin of
+// its cell at the last list build, u = x - origin, and written to its sorted
+// slot of that build, so the list's image offsets stay valid. An atom that moved
+// more than skin/2 since the build (or is not finite) raises flag[0]; the last
+// CTA to finish turns the flag into the value of the graph conditional that
+// guards the rebuild.
+__global__ void k_md_vl_kick_drift(int n, int n_species, KickParams kp, double dt, double half_skin2,
+                                   double *__restrict__ pos, double *__restrict__ vel,
+                                   const int32_t *__restrict__ types, const float4 *__restrict__ F4,
+                                   const int *__restrict__ cell_start, const int *__restrict__ cell_of,
+                                   const int *__restrict__ slot, const double *__restrict__ origin,
+                                   const double *__restrict__ ref, float4 *__restrict__ pos4,
+                                   unsigned *__restrict__ flag, cudaGraphConditionalHandle cond,
+                                   unsigned *__restrict__ err) {
+    __shared__ bool s_last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool moved = false;
+    if (i < n) {
+        int t = types[i];
+        if (t < 0 || t >= n_species) {
+            atomicOr(err, kErrType);
+            t = 0;
+        }
+        const int s = cell_start[cell_of[i]] + slot[i];
+        const float4 f = F4[s];
+        const double k = select_species(kp.k, t);
+        const float fa[3] = {f.x, f.y, f.z};
+        double x[3], d2 = 0.0;
+        float u[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double v = fma(k, (double)fa[a], vel[3 * i + a]);
+            vel[3 * i + a] = v;
+            x[a] = fma(dt, v, pos[3 * i + a]);
+            pos[3 * i + a] = x[a];
+            u[a] = (float)(x[a] - origin[3 * i + a]);
+            const double dx = x[a] - ref[3 * i + a];
+            d2 = fma(dx, dx, d2);
+        }
+        moved = !(d2 <= half_skin2);  // also true for a non-finite position
+        pos4[s] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+    }
+    if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) {
+        atomicOr(&flag[0], 1u);
+        __threadfence();  // ordered before this CTA's arrival below
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&flag[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned rebuild = atomicOr(&flag[0], 0u);
+        cudaGraphSetConditional(cond, rebuild ? 1u : 0u);
+        flag[1] = 0u;
+    }
+}
+
+// Rebuild of the Verlet list, binning: as k_bin_count, plus the origin of each
+// atom's FP32 coordinates (x - u in FP64) and its reference position x.
+__global__ void k_md_vl_bin(int n, int n_species, const double *__restrict__ pos,
+                            const int32_t *__restrict__ types, Grid g, float4 *__restrict__ tmp4,
+                            int *__restrict__ cell_of, int *__restrict__ slot, int *__restrict__ cell_count,
+                            double *__restrict__ origin, double *__restrict__ ref, unsigned *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x0 = pos[3 * i], x1 = pos[3 * i + 1], x2 = pos[3 * i + 2];
+    float u[3];
+    double ud[3];
+    bool finite = true;
+    const int cell = bin_position(x0, x1, x2, g, u, finite, ud);
+    if (!finite) atomicOr(err, kErrNonfinite);
+    int t = types[i];
+    if (t < 0 || t >= n_species) {
+        atomicOr(err, kErrType);
+        t = 0;
+    }
+    const double xs[3] = {x0, x1, x2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        origin[3 * i + a] = xs[a] - ud[a];
+        ref[3 * i + a] = xs[a];
+    }
+    tmp4[i] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+    cell_of[i] = cell;
+    slot[i] = atomicAdd(&cell_count[cell], 1);
 }
 
 // One warp per structure of a batch: energy = FP64 sum of its atoms' E_i (its
@@ -269,13 +365,32 @@ cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt
     return cudaGetLastError();
 }
 
-cudaError_t launch_md_kick_finish(Context &c, const Grid &g, int n, int n_eparts, double dt, double *vel,
-                                  const int32_t *types, double *rec_pot, double *rec_kin) {
+cudaError_t launch_md_kick_finish(Context &c, int n, double dt, double *vel, const int32_t *types,
+                                  double *rec_pot, double *rec_kin, bool clear_vl) {
     const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
-    k_md_kick_finish<<<blocks, kMdThreads, 0, c.stream>>>(n, kick_params(c, dt), vel, types, c.d_F4, c.d_cell_start,
-                                                          c.d_cell_of, c.d_slot, n_eparts, c.d_e_part, g.ncell,
-                                                          c.d_vir_part, c.d_ke_part, c.d_done, c.d_result, c.d_step,
-                                                          rec_pot, rec_kin);
+    k_md_kick_finish<<<blocks, kMdThreads, 0, c.stream>>>(
+        n, kick_params(c, dt), vel, types, c.d_F4, c.d_cell_start, c.d_cell_of, c.d_slot, c.last_eparts,
+        c.last_epart, c.last_vparts, c.last_vpart, c.d_ke_part, c.d_done, c.d_result, c.d_step, rec_pot, rec_kin,
+        clear_vl ? c.d_vl_flag : nullptr, c.d_vl_builds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_vl_kick_drift(Context &c, int n, double dt, double *pos, double *vel, const int32_t *types,
+                                    cudaGraphConditionalHandle cond) {
+    const double h = 0.5 * c.skin;
+    const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
+    k_md_vl_kick_drift<<<blocks, kMdThreads, 0, c.stream>>>(
+        n, c.basis.n_species, kick_params(c, dt), dt, h * h, pos, vel, types, c.d_F4, c.d_cell_start, c.d_cell_of,
+        c.d_slot, c.d_vl_origin, c.d_vl_ref, c.d_pos4, c.d_vl_flag, cond, c.d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_vl_bin(Context &c, const Grid &g, int n, const double *pos, const int32_t *types) {
+    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * g.ncell, c.stream);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_md_vl_bin<<<(n + kMdThreads - 1) / kMdThreads, kMdThreads, 0, c.stream>>>(
+        n, c.basis.n_species, pos, types, g, c.d_tmp4, c.d_cell_of, c.d_slot, c.d_cell_count, c.d_vl_origin,
+        c.d_vl_ref, c.d_err);
     return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ constexpr int kSlots = 64;
 enum Mode : int {
     kFused = 0,       // descriptor -> FP32 network -> forces, energy and virial
     kDescriptor = 1,  // descriptor only: G rows (sorted order)
-    kForces = 2       // forces and virial from given dE/dG rows (sorted order)
+    kForces = 2,      // forces and virial from given dE/dG rows (sorted order)
+    kBuildList = 3    // Verlet list: every image-atom within rc_max + skin (no potential)
 };
 
 // Per-species parameter block in shared memory (floats), every hidden layer
@@ -276,6 +277,76 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
             }
         }
         nang += __popc(ma);
+    }
+}
+
+// Verlet-list build: append the staged image-atoms within rc_list of atom i
+// (their staged entries, index | image-offset code) to the atom's row of the
+// global list; entries past the capacity are counted but not stored.
+__device__ __forceinline__ void scan_tile_build(const float4 *s_pos, const int *s_idx, int len, float4 ui, int self,
+                                                float rc2, int *__restrict__ row, int cap, int lane, int &nnb) {
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        bool in = false;
+        int e = 0;
+        if (q < len) {
+            const float4 p = s_pos[q];
+            e = s_idx[q];
+            const float dx = p.x - ui.x, dy = p.y - ui.y, dz = p.z - ui.z;
+            in = (dx * dx + dy * dy + dz * dz <= rc2) && (e != self);
+        }
+        const unsigned m = __ballot_sync(kFull, in);
+        if (in) {
+            const int slot = nnb + __popc(m & lt_mask);
+            if (slot < cap) row[slot] = e;
+        }
+        nnb += __popc(m);
+    }
+}
+
+__device__ __forceinline__ void store_list_count(int *vl_count, int i_s, int nnb, int cap, int lane, unsigned *err) {
+    if (lane == 0) {
+        vl_count[i_s] = nnb < cap ? nnb : cap;
+        if (nnb > cap) atomicOr(err, kErrNbCap);
+    }
+}
+
+// Phase 1 of the list build from the Verlet list: the entries of atom i that
+// now lie within the largest cutoff, with the displacement computed exactly as
+// from the staged tile, (u_j + offset) - u_i.
+__device__ __forceinline__ void scan_list(const int *__restrict__ row, int cnt, const float4 *__restrict__ pos4,
+                                          const float4 *off_shift, float4 ui, int jbits, const Basis &B,
+                                          const Caps &caps, const WarpLists &W, int lane, int &nnb) {
+    const float rc2max = B.rc_max * B.rc_max;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int jmask = (1 << jbits) - 1;
+    for (int base = 0; base < cnt; base += 32) {
+        const int k = base + lane;
+        bool in = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        int j = 0, typ = 0;
+        if (k < cnt) {
+            const int e = __ldg(row + k);
+            j = e & jmask;
+            const float4 sh = off_shift[e >> jbits];
+            const float4 p = pos4[j];
+            dx = (p.x + sh.x) - ui.x;
+            dy = (p.y + sh.y) - ui.y;
+            dz = (p.z + sh.z) - ui.z;
+            r2 = dx * dx + dy * dy + dz * dz;
+            typ = __float_as_int(p.w);
+            in = r2 <= rc2max;
+        }
+        const unsigned m = __ballot_sync(kFull, in);
+        if (in) {
+            const int slot = nnb + __popc(m & lt_mask);
+            if (slot < caps.nb) {
+                W.e_d[slot] = make_float4(dx, dy, dz, r2);
+                W.e_j[slot] = j | (typ << 28);
+            }
+        }
+        nnb += __popc(m);
     }
 }
 
@@ -682,6 +753,45 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     __syncwarp();
 }
 
+// The network parameters of every species into the shared-memory layout of
+// FusedNet (zero-padded to the width bound; slots mapped to G columns).
+template <int KRT, int KAT, bool EXACT>
+__device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &net, const float *__restrict__ params,
+                                                const float *__restrict__ shift, const float *__restrict__ scale,
+                                                float *s_par, int tid) {
+    const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
+    for (int t = 0; t < B.n_species; ++t) {
+        const float *src = params + (size_t)t * net.n_params;
+        float *dst = s_par + t * net.stride;
+        const int H1 = net.H[1], hb = net.hb;
+        for (int idx = tid; idx < kSlots * (hb + 1); idx += kPThreads) {  // W1P: (pair, o, slot parity)
+            const int pair = idx / (2 * (hb + 1)), rem = idx % (2 * (hb + 1)), o = rem >> 1;
+            const int col = slot_col<KRT, KAT>(2 * pair + (rem & 1), Kr, Ka);
+            dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
+        }
+        for (int o = tid; o < hb; o += kPThreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
+#pragma unroll
+        for (int l = 2; l < kMaxLayers; ++l) {
+            if (l >= net.L) break;
+            const int Hi = net.H[l - 1], Ho = net.H[l];
+            for (int idx = tid; idx < hb * (hb + 1); idx += kPThreads) {
+                const int o = idx / (hb + 1), k = idx % (hb + 1);
+                dst[net.offW[l] + idx] = (o < Ho && k < Hi) ? src[net.srcOff[l] + o * Hi + k] : 0.f;
+            }
+            for (int o = tid; o < hb; o += kPThreads)
+                dst[net.offB[l] + o] = o < Ho ? src[net.srcOff[l] + Ho * Hi + o] : 0.f;
+        }
+        const int Hl = net.Hlast;
+        for (int k = tid; k < hb; k += kPThreads) dst[net.offWL + k] = k < Hl ? src[net.srcOffL + k] : 0.f;
+        if (tid == 0) dst[net.offBL] = src[net.srcOffL + Hl];
+        for (int slot = tid; slot < kSlots; slot += kPThreads) {
+            const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
+            dst[net.offShift + slot] = col >= 0 ? shift[t * D + col] : 0.f;
+            dst[net.offScale + slot] = col >= 0 ? scale[t * D + col] : 0.f;
+        }
+    }
+}
+
 template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB>
 __global__ void __launch_bounds__(kPThreads, 2)
     k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
@@ -690,7 +800,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 const float *__restrict__ scale, float4 *__restrict__ F4, float *__restrict__ eatom,
                 float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
                 double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
-                unsigned *__restrict__ work, const int *__restrict__ order, int n_items) {
+                unsigned *__restrict__ work, const int *__restrict__ order, int n_items, int *__restrict__ vl_out,
+                int *__restrict__ vl_count) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
     __shared__ float s_vir[kPWarps][9];
@@ -725,39 +836,9 @@ __global__ void __launch_bounds__(kPThreads, 2)
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
         if (tid == t) s_tw[t] = B.type_weight[t];
-    const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
 
     // ---- network parameters of every species into the shared-memory layout
-    for (int t = 0; t < (MODE == kFused ? B.n_species : 0); ++t) {
-        const float *src = params + (size_t)t * net.n_params;
-        float *dst = s_par + t * net.stride;
-        const int H1 = net.H[1], hb = net.hb;
-        for (int idx = tid; idx < kSlots * (hb + 1); idx += kPThreads) {  // W1P: (pair, o, slot parity)
-            const int pair = idx / (2 * (hb + 1)), rem = idx % (2 * (hb + 1)), o = rem >> 1;
-            const int col = slot_col<KRT, KAT>(2 * pair + (rem & 1), Kr, Ka);
-            dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
-        }
-        for (int o = tid; o < hb; o += kPThreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
-#pragma unroll
-        for (int l = 2; l < kMaxLayers; ++l) {
-            if (l >= net.L) break;
-            const int Hi = net.H[l - 1], Ho = net.H[l];
-            for (int idx = tid; idx < hb * (hb + 1); idx += kPThreads) {
-                const int o = idx / (hb + 1), k = idx % (hb + 1);
-                dst[net.offW[l] + idx] = (o < Ho && k < Hi) ? src[net.srcOff[l] + o * Hi + k] : 0.f;
-            }
-            for (int o = tid; o < hb; o += kPThreads)
-                dst[net.offB[l] + o] = o < Ho ? src[net.srcOff[l] + Ho * Hi + o] : 0.f;
-        }
-        const int Hl = net.Hlast;
-        for (int k = tid; k < hb; k += kPThreads) dst[net.offWL + k] = k < Hl ? src[net.srcOffL + k] : 0.f;
-        if (tid == 0) dst[net.offBL] = src[net.srcOffL + Hl];
-        for (int slot = tid; slot < kSlots; slot += kPThreads) {
-            const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
-            dst[net.offShift + slot] = col >= 0 ? shift[t * D + col] : 0.f;
-            dst[net.offScale + slot] = col >= 0 ? scale[t * D + col] : 0.f;
-        }
-    }
+    if constexpr (MODE == kFused) load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid);
 
     unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
     // Work items are cells: one per CTA (work == NULL), or, in the persistent
@@ -846,9 +927,15 @@ __global__ void __launch_bounds__(kPThreads, 2)
             const float4 p = pos4[j];
             const float4 sh = off_shift[lo];
             s_pos[t] = make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w);
-            s_idx[t] = j | (__float_as_int(sh.w) ? kShiftBit : 0);
+            if constexpr (MODE == kBuildList)
+                s_idx[t] = j | (lo << caps.vl_jbits);  // the Verlet-list entry: index and image offset
+            else
+                s_idx[t] = j | (__float_as_int(sh.w) ? kShiftBit : 0);
         }
     };
+    // list-build mode: the entry of the atom itself (zero image offset) is excluded
+    const int self_code = (g.m[0] + wx * (g.m[1] + wy * g.m[2])) << caps.vl_jbits;
+    const float rc2list = caps.rc_list * caps.rc_list;
 
     float vir[9];
 #pragma unroll
@@ -883,10 +970,16 @@ __global__ void __launch_bounds__(kPThreads, 2)
             const int i_s = c0 + a;
             const float4 ui = pos4[i_s];
             int nnb = 0, nang = 0;
-            scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
-            finish_list(nnb, nang);
-            process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
-                                                G_out, dEdG_in, e_acc, vir);
+            if constexpr (MODE == kBuildList) {
+                scan_tile_build(s_pos, s_idx, total, ui, i_s | self_code, rc2list,
+                                vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
+                store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
+            } else {
+                scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
+                finish_list(nnb, nang);
+                process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
+                                                        eatom, G_out, dEdG_in, e_acc, vir);
+            }
         }
     } else {
         const int n_rounds = (cnt + kPWarps - 1) / kPWarps;
@@ -900,18 +993,29 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 __syncthreads();
                 stage(chunk);
                 __syncthreads();
-                if (active) scan_tile(s_pos, s_idx, min(tile, total - chunk * tile), ui, i_s, B, caps, W, lane, nnb);
+                if (active) {
+                    const int len = min(tile, total - chunk * tile);
+                    if constexpr (MODE == kBuildList)
+                        scan_tile_build(s_pos, s_idx, len, ui, i_s | self_code, rc2list,
+                                        vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
+                    else
+                        scan_tile(s_pos, s_idx, len, ui, i_s, B, caps, W, lane, nnb);
+                }
             }
             if (active) {
-                finish_list(nnb, nang);
-                process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
-                                                    G_out, dEdG_in, e_acc, vir);
+                if constexpr (MODE == kBuildList) {
+                    store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
+                } else {
+                    finish_list(nnb, nang);
+                    process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
+                                                            eatom, G_out, dEdG_in, e_acc, vir);
+                }
             }
         }
     }
 
     // ---- cell partials: energy (FP64), virial (FP32 lanes -> FP64)
-    if constexpr (MODE != kDescriptor) {
+    if constexpr (MODE == kFused || MODE == kForces) {
     #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const float v = warp_sum(vir[k]);
@@ -971,8 +1075,148 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
                                               c.d_cell_start, c.d_params,
                                               c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
                                               c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,
-                                              work ? c.batch_order : nullptr, g.ncell);
+                                              work ? c.batch_order : nullptr, g.ncell, nullptr, nullptr);
     c.last_grid = grid;
+    return cudaGetLastError();
+}
+
+// The fused potential over the Verlet list (MD steps between list builds).
+// Persistent CTAs (the network parameters are staged once per CTA); each warp
+// takes the next sorted atom from a global counter, forms its neighbour list
+// from its Verlet-list row (scan_list) and then runs the same descriptor,
+// network and chain rule as k_potential. Energy and virial partials per CTA.
+template <int KRT, int KAT, bool EXACT, int HB>
+__global__ void __launch_bounds__(kPThreads, 2)
+    k_potential_list(Basis B, FusedNet net, Grid g, Caps caps, int n, const float4 *__restrict__ pos4,
+                     const int *__restrict__ vl, const int *__restrict__ vl_count, const float *__restrict__ params,
+                     const float *__restrict__ shift, const float *__restrict__ scale, float4 *__restrict__ F4,
+                     float *__restrict__ eatom, double *__restrict__ e_part, double *__restrict__ vir_part,
+                     unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
+                     unsigned *__restrict__ work) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_tw[kMaxSpecies];
+    __shared__ float s_vir[kPWarps][9];
+    __shared__ double s_e[kPWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const PLayout L = make_playout(g.n_off, 0, caps.nb, caps.ang, B.n_species, net.stride);
+    float4 *off_shift = reinterpret_cast<float4 *>(smem + L.off_shift);
+    float *s_par = reinterpret_cast<float *>(smem + L.params);
+    unsigned char *wb = smem + L.warp_base + L.warp_bytes * warp;
+    WarpLists W;
+    W.e_d = reinterpret_cast<float4 *>(wb + L.e_d);
+    W.e_c = reinterpret_cast<float2 *>(wb + L.e_c);
+    W.e_j = reinterpret_cast<int *>(wb + L.e_j);
+    W.e_fx = reinterpret_cast<float *>(wb + L.e_fx);
+    W.e_fy = reinterpret_cast<float *>(wb + L.e_fy);
+    W.e_fz = reinterpret_cast<float *>(wb + L.e_fz);
+    W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
+    W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
+    W.coef = reinterpret_cast<float *>(wb + L.coef);
+#pragma unroll
+    for (int t = 0; t < kMaxSpecies; ++t)
+        if (tid == t) s_tw[t] = B.type_weight[t];
+    load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid);
+    const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
+    for (int o = tid; o < g.n_off; o += kPThreads) {  // image offset of every list code
+        const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
+        off_shift[o] = make_float4(ox * g.hf[0], oy * g.hf[1], oz * g.hf[2], 0.f);
+    }
+    __syncthreads();
+
+    float vir[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vir[k] = 0.f;
+    double e_acc = 0.0;
+    unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
+    for (;;) {
+        int a = 0;
+        if (lane == 0) a = (int)atomicAdd(work, 1u);
+        a = __shfl_sync(kFull, a, 0);
+        if (a >= n) break;
+        const int i_s = a;
+        const float4 ui = pos4[i_s];
+        int nnb = 0, nang = 0;
+        scan_list(vl + (size_t)i_s * caps.vl_cap, vl_count[i_s], pos4, off_shift, ui, caps.vl_jbits, B, caps, W,
+                  lane, nnb);
+        if (nnb > caps.nb) {
+            if (lane == 0) atomicOr(err, kErrNbCap);
+            nnb = caps.nb;
+        }
+        __syncwarp();
+        complete_list(B, s_tw, caps, W, lane, nnb, nang, err);
+        if (nang > caps.ang) {
+            if (lane == 0) atomicOr(err, kErrAngCap);
+            nang = caps.ang;
+        }
+        st_nb += nnb;
+        st_ang += nang;
+        st_pairs += (unsigned long long)(nang * (nang - 1) / 2);
+        __syncwarp();
+        process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+                                                  nullptr, nullptr, e_acc, vir);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float v = warp_sum(vir[k]);
+        if (lane == 0) s_vir[warp][k] = v;
+    }
+    if (lane == 0) s_e[warp] = e_acc;
+    if (lane == 0 && st_nb) {
+        atomicAdd(&stats[0], st_nb);
+        atomicAdd(&stats[1], st_ang);
+        atomicAdd(&stats[2], st_pairs);
+    }
+    __syncthreads();
+    if (tid < 9) {
+        float sv = 0.f;
+#pragma unroll
+        for (int w = 0; w < kPWarps; ++w) sv += s_vir[w][tid];
+        vir_part[(size_t)blockIdx.x * 9 + tid] = (double)sv;
+    }
+    if (warp == 0) {
+        double v = lane < kPWarps ? s_e[lane] : 0.0;
+#pragma unroll
+        for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) e_part[blockIdx.x] = v;
+    }
+}
+
+template <int KRT, int KAT, bool EXACT>
+cudaError_t launch_build(Context &c, const Grid &g) {
+    const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, 0, 0).total;
+    auto kern = k_potential<KRT, KAT, EXACT, kBuildList, false, 32>;
+    cudaError_t e = allow_max_smem(kern);
+    if (e != cudaSuccess) return e;
+    const FusedNet net{};
+    kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, nullptr, 0, c.caps, c.d_pos4, c.d_cell_start,
+                                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, nullptr, c.d_stats, c.d_err, nullptr, nullptr, g.ncell,
+                                                 c.d_vl, c.d_vl_count);
+    return cudaGetLastError();
+}
+
+size_t potential_list_smem(const Context &c, const Grid &g, const FusedNet &net) {
+    return make_playout(g.n_off, 0, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
+}
+
+template <int KRT, int KAT, bool EXACT>
+cudaError_t launch_list(Context &c, const Grid &g, int n) {
+    const FusedNet net = make_fused_net(c.net);
+    const size_t smem = potential_list_smem(c, g, net);
+    auto kern = net.hb == 16 ? k_potential_list<KRT, KAT, EXACT, 16> : k_potential_list<KRT, KAT, EXACT, 32>;
+    cudaError_t e = allow_max_smem(kern);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem)) != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(std::min(std::max(1, per_sm), 4) * c.n_sm, (n + kPWarps - 1) / kPWarps));
+    if ((e = cudaMemsetAsync(c.d_work, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
+    kern<<<grid, kPThreads, smem, c.stream>>>(c.basis, net, g, c.caps, n, c.d_pos4, c.d_vl, c.d_vl_count, c.d_params,
+                                              c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_vl_epart, c.d_vl_vpart,
+                                              c.d_stats, c.d_err, c.d_work);
+    c.last_epart = c.d_vl_epart;
+    c.last_vpart = c.d_vl_vpart;
+    c.last_eparts = grid;
+    c.last_vparts = grid;
     return cudaGetLastError();
 }
 
@@ -1016,6 +1260,31 @@ cudaError_t launch_fp_forward(Context &c, const Grid &g, int n) {
     cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
     if (e != cudaSuccess) return e;
     return dispatch<kDescriptor>(c, g);
+}
+
+int potential_list_max_ctas(const Context &c) { return 4 * std::max(1, c.n_sm); }
+
+cudaError_t launch_vl_build(Context &c, const Grid &g, int n) {
+    (void)n;
+    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
+    if (Kr == 17 && Ka == 9) return launch_build<17, 9, true>(c, g);
+    if (Kr == 21 && Ka == 7) return launch_build<21, 7, true>(c, g);
+    if (Kr <= 20 && Ka <= 12) return launch_build<20, 12, false>(c, g);
+    if (Kr <= 24 && Ka <= 8) return launch_build<24, 8, false>(c, g);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_potential_list(Context &c, const Grid &g, int n) {
+    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
+    if (e != cudaSuccess) return e;
+    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
+    if (Kr == 17 && Ka == 9) return launch_list<17, 9, true>(c, g, n);
+    if (Kr == 21 && Ka == 7) return launch_list<21, 7, true>(c, g, n);
+    if (Kr <= 20 && Ka <= 12) return launch_list<20, 12, false>(c, g, n);
+    if (Kr <= 24 && Ka <= 8) return launch_list<24, 8, false>(c, g, n);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fp_backward(Context &c, const Grid &g, int n) {
@@ -1112,7 +1381,7 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
     kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
                                            nullptr,
                                            nullptr, Gs, nullptr, nullptr, nullptr, stats, err, nullptr, nullptr,
-                                           g.ncell);
+                                           g.ncell, nullptr, nullptr);
     return cudaGetLastError();
 }
 
