@@ -109,9 +109,12 @@ def workload(name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons, sampled every 20 ms from a process
+    started before the warm-up; stop() keeps the samples taken inside the timed
+    window [mark(), stop()] (and, for a window shorter than the sampling period,
+    the first sample after it opened)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -119,6 +122,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = None
 
     def start(self):
         try:
@@ -126,32 +130,55 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark(self):
+        """Opening of the timed window."""
+        self.t0 = time.time()
+
+    def _rows(self):
+        import datetime
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            rows.append((ts, parts[1:]))
+        return rows
 
     def stop(self):
         if self.proc is None:
             return None
+        t1 = time.time()
+        t0 = self.t0 if self.t0 is not None else t1
+        deadline = t1 + 1.0
+        while time.time() < deadline and not any(ts >= t0 for ts, _ in self._rows()):
+            time.sleep(0.02)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = self._rows()
         os.unlink(self.path)
-        if not rows:
+        inside = [r for ts, r in rows if t0 <= ts <= t1]
+        if not inside:
+            after = [r for ts, r in rows if ts >= t0]
+            inside = after[:1]
+        if not inside:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside), "period_ms": 20}
 
 
 def measured_peaks():
@@ -292,6 +319,8 @@ def run_batch(args, rank, world):
             tot += time.perf_counter() - t0
         return tot
 
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
@@ -299,8 +328,7 @@ def run_batch(args, rank, world):
         torch.cuda.synchronize()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-        clocks.start()
+        clocks.mark()
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
@@ -358,6 +386,8 @@ def main():
     ap.add_argument("--workload", default="water_12288")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skin", type=float, default=1.0,
+                    help="Verlet-list skin in A for the MD step (0: cell list every step)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -385,12 +415,15 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     gpu = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+    gpu.set_skin(args.skin)
     pos = torch.tensor(st.pos, device=dev)
     vel = torch.tensor(v0, device=dev)
     types = torch.tensor(st.types, device=dev)
     # L2 flush buffer (> 129 MB L2)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
+    clocks = ClockSampler(local)
+    clocks.start()  # running before the warm-up, so the timed window is sampled
     with torch.cuda.stream(stream):
         gpu.md_nve(pos, vel, types, st.box, DT_PS, 1)  # initial forces + graph capture
         flags = AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING
@@ -405,11 +438,11 @@ def main():
         stage_sum = None
         kernels_per_step = 0
         fused = False
+        builds0 = gpu.md_list_builds()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        clocks = ClockSampler(local)
-        clocks.start()
+        clocks.mark()
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
@@ -422,6 +455,7 @@ def main():
         wall = time.perf_counter() - wall0
         clk = clocks.stop()
         gpu.check()
+        builds = gpu.md_list_builds() - builds0
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
     value = world * n * args.steps / t_dev
@@ -439,6 +473,7 @@ def main():
         hvel.copy_(vel.cpu())
         htypes.copy_(types.cpu())
         e2 = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+        e2.set_skin(args.skin)
         e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
         for _ in range(3):
             e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
@@ -469,7 +504,8 @@ def main():
     if fused:
         # descriptor, networks and forces run as one kernel, timed under "forces"
         dom = "forces"
-        kernel_name = "k_potential (fused descriptor + network + forces)"
+        kernel_name = ("k_potential_list (fused descriptor + network + forces over the Verlet list)"
+                       if args.skin > 0 else "k_potential (fused descriptor + network + forces)")
         flops = flops_force + flops_desc + network_flops(m.widths, n)
     else:
         dom = max(("descriptor", "forces"), key=lambda s: stage_avg[s])
@@ -486,9 +522,12 @@ def main():
                    "precision": args.precision, "basis": f"rad {m.order_rad}/{m.rc_rad} A, ang {m.order_ang}/{m.rc_ang} A",
                    "ann": "-".join(map(str, m.widths)), "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "neighbour_entries": stats[0], "angular_pairs": stats[2]},
+                   "neighbour_entries": stats[0], "angular_pairs": stats[2],
+                   "skin_A": args.skin, "list_builds": builds if args.skin > 0 else None},
         "stage_ms": {s: round(v, 5) for s, v in stage_avg.items()},
-        "gpu_launches": kernels_per_step * args.steps,
+        # kernel nodes of the step graph, plus the 4 kernels of each list rebuild
+        # (the body of the graph's conditional node) that ran in the timed steps
+        "gpu_launches": kernels_per_step * args.steps + (4 * builds if args.skin > 0 else 0),
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
