@@ -1,1048 +1,17 @@
-// Fused potential kernel: rows a3-a8 of the path in one pass per atom.
-//
-// One CTA per cell, one warp per atom (atoms handed out dynamically inside the
-// CTA). For each atom the warp
-//   1. builds the neighbour list once, from the CTA's shared-memory tile of the
-//      (2m+1)^3 neighbour cells (image shifts applied when staging), storing per
-//      entry the displacement, r, 1/r, the radial cutoff f_c and f_c' and the
-//      species weight; angular entries additionally keep the unit vector and
-//      the angular f_c, f_c';
-//   2. evaluates the descriptor (Sec. II.B: Eq. radial, Eq. angular over
-//      unordered pairs doubled to the paper's ordered sum, the species-weighted
-//      copy) in registers and reduces it across the warp;
-//   3. runs its species' network (Sec. II.A, Eq. ANN-layer; tanh hidden layers,
-//      linear output) warp-cooperatively in FP32 -- one lane per neuron, weights
-//      in shared memory -- and back-propagates to dE/dG;
-//   4. applies the chain rule through every radial term and angular pair to
-//      forces (one FP32 vector atomic per neighbour entry) and the virial.
-// G and dE/dG never leave the SM, the list is never rebuilt and the pair loops
-// need no division or transcendental call. Energy and virial leave as FP64
-// per-CTA partials, reduced in a fixed order by the reduction kernel.
-//
-// The same kernel in two other modes serves the split path (the BF16 network
-// forms, networks wider than 32, the descriptor-only API): kDescriptor writes
-// the G rows, kForces reads dE/dG rows and applies steps 1 and 4 only.
+// Cell-list evaluation with the potential kernel: launch of its fused,
+// descriptor-only and forces-only forms (single structures and batches), and
+// the allocation-free descriptor entry point. The kernels themselves are in
+// potential_kernels.cuh.
 #include <stdio.h>
 
 #include <algorithm>
 
-#include "aenet_internal.cuh"
-#include "fp_common.cuh"
+#include "potential_kernels.cuh"
 
 namespace aenet {
-
 namespace {
 
 using namespace detail;
-
-constexpr int kPWarps = 8;
-constexpr int kPThreads = kPWarps * 32;
-constexpr int kSlots = 64;
-
-// What one launch of k_potential computes.
-enum Mode : int {
-    kFused = 0,       // descriptor -> FP32 network -> forces, energy and virial
-    kDescriptor = 1,  // descriptor only: G rows (sorted order)
-    kForces = 2,      // forces and virial from given dE/dG rows (sorted order)
-    kBuildList = 3    // Verlet list: every image-atom within rc_max + skin (no potential)
-};
-
-// Per-species parameter block in shared memory (floats), every hidden layer
-// zero-padded to the compile-time width bound hb (16 or 32) so the network
-// loops run a fixed trip count with no masks; padded neurons see zero weights
-// and biases, so they stay at tanh(0) = 0 and contribute nothing:
-//   W1P [32 slot pairs][hb + 1] float2   layer-1 weights of slots (2p, 2p+1)
-//   b1  [hb]
-//   for hidden l = 2..L-1: W_l [hb][hb + 1], b_l [hb]
-//   wL  [hb], bL [1]
-//   shift [64 slots], scale [64 slots] (scale 0 on unused slots)
-// The odd row strides keep the lane-strided reads free of bank conflicts.
-struct FusedNet {
-    int L;                          // weight layers
-    int hb;                         // hidden-width bound of the layout (16 or 32)
-    int H[kMaxLayers + 1];          // widths
-    int offW[kMaxLayers + 1];       // offset of W_l in the block
-    int offB[kMaxLayers + 1];       // offset of b_l
-    int offShift, offScale, stride; // stride = floats per species (rounded to 4)
-    int srcOff[kMaxLayers + 1];     // offset of W_l in the canonical FP32 parameters
-    int n_params;                   // canonical floats per species
-    int Hlast, offWL, offBL, srcOffL;  // last hidden width and output-layer offsets (scalars:
-                                       // kernels never index the arrays above with runtime values)
-    // per-atom activation record (for dE/dW): g [D], then x_l [H_l], delta_l [H_l]
-    // for every hidden layer l
-    int rec_len, rec_x[kMaxLayers], rec_d[kMaxLayers], rec_dlast;
-};
-
-int hidden_bound(const Net &net) {
-    int h = 0;
-    for (int l = 1; l < net.n_layers; ++l) h = h > net.widths[l] ? h : net.widths[l];
-    return h <= 16 ? 16 : 32;
-}
-
-FusedNet make_fused_net(const Net &net) {
-    FusedNet f{};
-    f.L = net.n_layers;
-    f.hb = hidden_bound(net);
-    const int hb = f.hb;
-    for (int l = 0; l <= net.n_layers; ++l) f.H[l] = net.widths[l];
-    int p = 0;
-    f.offW[1] = p;
-    p += kSlots * (hb + 1);
-    f.offB[1] = p;
-    p += hb;
-    for (int l = 2; l < f.L; ++l) {
-        f.offW[l] = p;
-        p += hb * (hb + 1);
-        f.offB[l] = p;
-        p += hb;
-    }
-    f.offW[f.L] = p;
-    p += hb;
-    f.offB[f.L] = p;
-    p += 1;
-    f.offShift = p;
-    p += kSlots;
-    f.offScale = p;
-    p += kSlots;
-    f.stride = (p + 3) & ~3;
-    int q = 0;
-    for (int l = 1; l <= f.L; ++l) {
-        f.srcOff[l] = q;
-        q += f.H[l] * f.H[l - 1] + f.H[l];
-    }
-    f.n_params = q;
-    int r = f.H[0];
-    for (int l = 1; l < f.L; ++l) {
-        f.rec_x[l] = r;
-        f.rec_d[l] = r + f.H[l];
-        r += 2 * f.H[l];
-    }
-    f.rec_len = r;
-    f.rec_dlast = f.rec_d[f.L - 1];
-    f.Hlast = f.H[f.L - 1];
-    f.offWL = f.offW[f.L];
-    f.offBL = f.offB[f.L];
-    f.srcOffL = f.srcOff[f.L];
-    return f;
-}
-
-struct PLayout {
-    size_t off_start, off_count, off_prefix, off_shift, s_pos, s_idx, params, warp_base, warp_bytes, total;
-    size_t e_d, e_c, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
-};
-
-__host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, int acap, int n_species, int stride) {
-    PLayout L{};
-    size_t p = 0;
-    L.off_start = p;
-    p = align16(p + sizeof(int) * n_off);
-    L.off_count = p;
-    p = align16(p + sizeof(int) * n_off);
-    L.off_prefix = p;
-    p = align16(p + sizeof(int) * (n_off + 1));
-    L.off_shift = p;
-    p = align16(p + sizeof(float4) * n_off);
-    L.s_pos = p;
-    p = align16(p + sizeof(float4) * tile);
-    L.s_idx = p;
-    p = align16(p + sizeof(int) * tile);
-    L.params = p;
-    p = align16(p + sizeof(float) * (size_t)n_species * stride);
-    L.warp_base = p;
-    size_t q = 0;
-    L.e_d = q;
-    q = align16(q + sizeof(float4) * cap);
-    L.e_c = q;
-    q = align16(q + sizeof(float2) * cap);
-    L.e_j = q;
-    q = align16(q + sizeof(int) * cap);
-    L.e_fx = q;
-    q = align16(q + sizeof(float) * cap);
-    L.e_fy = q;
-    q = align16(q + sizeof(float) * cap);
-    L.e_fz = q;
-    q = align16(q + sizeof(float) * cap);
-    L.a_u = q;
-    q = align16(q + sizeof(float4) * acap);
-    L.a_x = q;
-    q = align16(q + sizeof(float4) * acap);
-    L.coef = q;
-    q = align16(q + sizeof(float) * kSlots);
-    L.warp_bytes = q;
-    L.total = p + q * kPWarps;
-    return L;
-}
-
-// Descriptor slot -> G column (-1 if unused); slots are [rad | ang | rad_w | ang_w]
-// of compile-time widths KRT, KAT.
-template <int KRT, int KAT>
-__device__ inline int slot_col(int slot, int Kr, int Ka) {
-    if (slot < KRT) return slot < Kr ? slot : -1;
-    if (slot < KRT + KAT) return slot - KRT < Ka ? Kr + slot - KRT : -1;
-    if (slot < 2 * KRT + KAT) return slot - KRT - KAT < Kr ? Kr + Ka + slot - KRT - KAT : -1;
-    if (slot < 2 * KRT + 2 * KAT) return slot - 2 * KRT - KAT < Ka ? 2 * Kr + Ka + slot - 2 * KRT - KAT : -1;
-    return -1;
-}
-
-template <int KRT, int KAT>
-__device__ inline bool slot_is_angular(int slot) {
-    return (slot >= KRT && slot < KRT + KAT) || (slot >= 2 * KRT + KAT && slot < 2 * KRT + 2 * KAT);
-}
-
-struct WarpLists {
-    float4 *e_d, *a_u, *a_x;  // e_d: (dx, dy, dz, r)
-    float2 *e_c;              // (f_c, f_c') of the radial cutoff (0 beyond it)
-    int *e_j;                 // sorted neighbour index | species << 28
-    float *e_fx, *e_fy, *e_fz, *coef;
-};
-
-// Phase 1 of the list build: append the image-atoms of the staged tile that
-// lie within the largest cutoff of atom i, as (d, r^2) and index | species << 28.
-// Only a ballot compaction runs per 32 candidates; everything per neighbour is
-// deferred to the dense phase 2 (complete_list), so that the ~85% of lanes
-// whose candidate is out of range do not idle through it.
-__device__ __forceinline__ void scan_tile(const float4 *s_pos, const int *s_idx, int len, float4 ui, int i_s,
-                                          const Basis &B, const Caps &caps, const WarpLists &W, int lane,
-                                          int &nnb) {
-    const float rc2max = B.rc_max * B.rc_max;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int base = 0; base < len; base += 32) {
-        const int q = base + lane;
-        bool in = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        int jid = 0, typ = 0;
-        if (q < len) {
-            const float4 p = s_pos[q];
-            jid = s_idx[q];
-            dx = p.x - ui.x;
-            dy = p.y - ui.y;
-            dz = p.z - ui.z;
-            r2 = dx * dx + dy * dy + dz * dz;
-            typ = __float_as_int(p.w);
-            in = (r2 <= rc2max) && (jid != i_s);
-        }
-        const unsigned m = __ballot_sync(kFull, in);
-        if (in) {
-            const int slot = nnb + __popc(m & lt_mask);
-            if (slot < caps.nb) {
-                W.e_d[slot] = make_float4(dx, dy, dz, r2);
-                W.e_j[slot] = (jid & ~kShiftBit) | (typ << 28);
-            }
-        }
-        nnb += __popc(m);
-    }
-}
-
-// Phase 2 of the list build, dense over the nnb entries: r, the radial cutoff
-// f_c and f_c', and the angular sub-list (unit vector, 1/r, angular f_c, f_c',
-// species weight, index of the main entry).
-__device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw, const Caps &caps,
-                                              const WarpLists &W, int lane, int nnb, int &nang, unsigned *err) {
-    const float inv_rcr = 1.0f / B.rc_rad, inv_rca = 1.0f / B.rc_ang;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    nang = 0;
-    for (int base = 0; base < nnb; base += 32) {
-        const int k = base + lane;
-        bool ina = false;
-        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        float r = 0.f;
-        if (k < nnb) {
-            e = W.e_d[k];
-            r = sqrtf(e.w);
-            if (r < 1e-6f) {
-                atomicOr(err, kErrOverlap);
-                r = 1e-6f;
-            }
-            float fc = 0.f, dfc = 0.f;
-            if (r <= B.rc_rad) {
-                float sn, cs;
-                sincospif(r * inv_rcr, &sn, &cs);
-                fc = 0.5f * (cs + 1.0f);
-                dfc = -0.5f * 3.14159265358979f * inv_rcr * sn;
-            }
-            W.e_d[k].w = r;
-            W.e_c[k] = make_float2(fc, dfc);
-            ina = r <= B.rc_ang;
-        }
-        const unsigned ma = __ballot_sync(kFull, ina);
-        if (ina) {
-            const int aslot = nang + __popc(ma & lt_mask);
-            if (aslot < caps.ang) {
-                const float inv = 1.0f / r;
-                float sn, cs;
-                sincospif(r * inv_rca, &sn, &cs);
-                W.a_u[aslot] = make_float4(e.x * inv, e.y * inv, e.z * inv, 0.5f * (cs + 1.0f));
-                W.a_x[aslot] = make_float4(inv, -0.5f * 3.14159265358979f * inv_rca * sn, s_tw[W.e_j[k] >> 28],
-                                           __int_as_float(k));
-            }
-        }
-        nang += __popc(ma);
-    }
-}
-
-// Verlet-list build: append the staged image-atoms within rc_list of atom i
-// (their staged entries, index | image-offset code) to the atom's row of the
-// global list; entries past the capacity are counted but not stored.
-__device__ __forceinline__ void scan_tile_build(const float4 *s_pos, const int *s_idx, int len, float4 ui, int self,
-                                                float rc2, int *__restrict__ row, int cap, int lane, int &nnb) {
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int base = 0; base < len; base += 32) {
-        const int q = base + lane;
-        bool in = false;
-        int e = 0;
-        if (q < len) {
-            const float4 p = s_pos[q];
-            e = s_idx[q];
-            const float dx = p.x - ui.x, dy = p.y - ui.y, dz = p.z - ui.z;
-            in = (dx * dx + dy * dy + dz * dz <= rc2) && (e != self);
-        }
-        const unsigned m = __ballot_sync(kFull, in);
-        if (in) {
-            const int slot = nnb + __popc(m & lt_mask);
-            if (slot < cap) row[slot] = e;
-        }
-        nnb += __popc(m);
-    }
-}
-
-__device__ __forceinline__ void store_list_count(int *vl_count, int i_s, int nnb, int cap, int lane, unsigned *err) {
-    if (lane == 0) {
-        vl_count[i_s] = nnb < cap ? nnb : cap;
-        if (nnb > cap) atomicOr(err, kErrNbCap);
-    }
-}
-
-// Phase 1 of the list build from the Verlet list: the entries of atom i that
-// now lie within the largest cutoff, with the displacement computed exactly as
-// from the staged tile, (u_j + offset) - u_i.
-__device__ __forceinline__ void scan_list(const int *__restrict__ row, int cnt, const float4 *__restrict__ pos4,
-                                          const float4 *off_shift, float4 ui, int jbits, const Basis &B,
-                                          const Caps &caps, const WarpLists &W, int lane, int &nnb) {
-    const float rc2max = B.rc_max * B.rc_max;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int jmask = (1 << jbits) - 1;
-    for (int base = 0; base < cnt; base += 32) {
-        const int k = base + lane;
-        bool in = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        int j = 0, typ = 0;
-        if (k < cnt) {
-            const int e = __ldg(row + k);
-            j = e & jmask;
-            const float4 sh = off_shift[e >> jbits];
-            const float4 p = pos4[j];
-            dx = (p.x + sh.x) - ui.x;
-            dy = (p.y + sh.y) - ui.y;
-            dz = (p.z + sh.z) - ui.z;
-            r2 = dx * dx + dy * dy + dz * dz;
-            typ = __float_as_int(p.w);
-            in = r2 <= rc2max;
-        }
-        const unsigned m = __ballot_sync(kFull, in);
-        if (in) {
-            const int slot = nnb + __popc(m & lt_mask);
-            if (slot < caps.nb) {
-                W.e_d[slot] = make_float4(dx, dy, dz, r2);
-                W.e_j[slot] = j | (typ << 28);
-            }
-        }
-        nnb += __popc(m);
-    }
-}
-
-// Step it of the rotation schedule over one block pair of angular entries:
-// lane l pairs its entry with column cc of block B. Inside a diagonal block
-// (A = B, n_A entries) step it uses the shift t = it + 1 and pairs l with
-// (l + t) mod n_A, for t = 1 .. n_A/2, the last shift only from the lower half
-// of the lanes when n_A is even, so each unordered pair is visited once; across
-// blocks step it pairs l with (l + it) mod 32. v: a real pair (step inside the
-// range, both entries present).
-__device__ __forceinline__ void rotation_step(bool diag, int it, int nt, int nA, int nB, int lane, bool vj, int &cc,
-                                              bool &v) {
-    if (diag) {
-        const int t = it + 1;
-        cc = lane + t >= nA ? lane + t - nA : lane + t;
-        v = vj && it < nt && !(2 * t == nA && lane >= t);
-    } else {
-        cc = (lane + it) & 31;
-        v = vj && it < nt && cc < nB;
-    }
-}
-
-// The lane whose partner in step it is this lane's entry (inverse rotation).
-__device__ __forceinline__ int rotation_source(bool diag, int it, int nA, int lane) {
-    if (diag) {
-        const int t = it + 1;
-        return lane - t < 0 ? lane - t + nA : lane - t;
-    }
-    return (lane - it) & 31;
-}
-
-// Chain rule through one angular term T(cos th) f_c(r_j) f_c(r_k) weighted by
-// b_q = ca_q + (s_j s_k) caw_q: adds dE/dd_j to (jx, jy, jz) and returns dE/dd_k
-// in (gx, gy, gz); nothing when v is false (uk, xk then hold any valid entry).
-//   d/dd_j [T(cos) f_j f_k] = T' f_j f_k (u_k - cos u_j) / r_j + T f_j' f_k u_j
-template <int KAT, bool EXACT>
-__device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj, const float4 uk, const float4 xk,
-                                              bool v, const float (&ca)[KAT], const float (&caw)[KAT], int Ka,
-                                              float &jx, float &jy, float &jz, float &gx, float &gy, float &gz) {
-    const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-    const float w = xj.z * xk.z;
-    float S = fmaf(w, caw[0], ca[0]);
-    float dS = 0.f;
-    float tm1 = 1.0f, tt = c, um1 = 0.0f, u = 1.0f;
-#pragma unroll
-    for (int q = 1; q < KAT; ++q) {
-        if (q < Ka) {
-            const float b = fmaf(w, caw[q], ca[q]);
-            S = fmaf(b, tt, S);
-            dS = fmaf(b * (float)q, u, dS);
-            const float tn = fmaf(2.0f * c, tt, -tm1);
-            tm1 = tt;
-            tt = tn;
-            const float un = fmaf(2.0f * c, u, -um1);
-            um1 = u;
-            u = un;
-        }
-    }
-    const float fj = uj.w, fk = uk.w;
-    const float Af = v ? dS * fj * fk : 0.f;
-    const float Aj = Af * xj.x, Ak = Af * xk.x;
-    const float Bj = v ? S * xj.y * fk : 0.f, Bk = v ? S * fj * xk.y : 0.f;
-    jx += Aj * (uk.x - c * uj.x) + Bj * uj.x;
-    jy += Aj * (uk.y - c * uj.y) + Bj * uj.y;
-    jz += Aj * (uk.z - c * uj.z) + Bj * uj.z;
-    gx = Ak * (uj.x - c * uk.x) + Bk * uk.x;
-    gy = Ak * (uj.y - c * uk.y) + Bk * uk.y;
-    gz = Ak * (uj.z - c * uk.z) + Bk * uk.z;
-}
-
-template <int KRT, int KAT, bool EXACT, int MODE, int HB>
-__device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
-                                             const float *s_par, const float *s_tw, const WarpLists &W, int lane,
-                                             const float4 *__restrict__ pos4, float4 *__restrict__ F4,
-                                             float *__restrict__ eatom, float *__restrict__ G_out,
-                                             const float *__restrict__ dEdG_in, double &e_acc, float (&vir)[9]) {
-    constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
-    const int Kr = EXACT ? KRT : B.Kr;
-    const int Ka = EXACT ? KAT : B.Ka;
-    const float inv_rcr = 1.0f / B.rc_rad;
-
-    const int s0 = 2 * lane, s1 = 2 * lane + 1;
-    if constexpr (MODE != kForces) {
-    // ---- descriptor
-    float acc[64];
-#pragma unroll
-    for (int k = 0; k < 64; ++k) acc[k] = 0.f;
-    for (int k = lane; k < nnb; k += 32) {
-        const float r = W.e_d[k].w;
-        if (r <= B.rc_rad) {
-            const float fc = W.e_c[k].x;
-            const float x = 2.0f * r * inv_rcr - 1.0f;
-            const float sfc = s_tw[W.e_j[k] >> 28] * fc;
-            float tm1 = 1.0f, t = x;
-            acc[0] += fc;
-            acc[SLOT_RADW] += sfc;
-#pragma unroll
-            for (int q = 1; q < KRT; ++q) {
-                if (q < Kr) {
-                    acc[q] = fmaf(t, fc, acc[q]);
-                    acc[SLOT_RADW + q] = fmaf(t, sfc, acc[SLOT_RADW + q]);
-                    const float tn = fmaf(2.0f * x, t, -tm1);
-                    tm1 = t;
-                    t = tn;
-                }
-            }
-        }
-    }
-    // angular (Eq. angular): every unordered pair once by the rotation schedule
-    // (see for the backward pass below); doubled to the ordered sum at the end
-    {
-        const int nbk = (nang + 31) >> 5;
-        for (int A = 0; A < nbk; ++A) {
-            const int nA = min(32, nang - 32 * A);
-            const bool vj = lane < nA;
-            const int self = 32 * A + (vj ? lane : 0);  // a valid entry: stands in for masked partners
-            const float4 uj = W.a_u[self];
-            const float sj = W.a_x[self].z;
-            for (int Bk = A; Bk < nbk; ++Bk) {
-                const int nB = min(32, nang - 32 * Bk);
-                const bool diag = Bk == A;
-                const int nt = diag ? nA / 2 : 32;
-                // two rotation steps per iteration: their Chebyshev recurrences
-                // are independent, which hides the FMA latency of each chain;
-                // every accumulator still takes step it before step it + 1
-                for (int it = 0; it < nt; it += 2) {
-                    int ccA, ccB;
-                    bool vA, vB;
-                    rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
-                    rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
-                    const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
-                    const float4 ukA = W.a_u[kA], ukB = W.a_u[kB];
-                    const float skA = W.a_x[kA].z, skB = W.a_x[kB].z;
-                    const float cA = uj.x * ukA.x + uj.y * ukA.y + uj.z * ukA.z;
-                    const float cB = uj.x * ukB.x + uj.y * ukB.y + uj.z * ukB.z;
-                    const float wA = vA ? uj.w * ukA.w : 0.f, wB = vB ? uj.w * ukB.w : 0.f;
-                    const float wsA = wA * sj * skA, wsB = wB * sj * skB;
-                    float tA1 = 1.0f, tA = cA, tB1 = 1.0f, tB = cB;
-                    acc[SLOT_ANG] = (acc[SLOT_ANG] + wA) + wB;
-                    acc[SLOT_ANGW] = (acc[SLOT_ANGW] + wsA) + wsB;
-#pragma unroll
-                    for (int q = 1; q < KAT; ++q) {
-                        if (q < Ka) {
-                            acc[SLOT_ANG + q] = fmaf(tB, wB, fmaf(tA, wA, acc[SLOT_ANG + q]));
-                            acc[SLOT_ANGW + q] = fmaf(tB, wsB, fmaf(tA, wsA, acc[SLOT_ANGW + q]));
-                            const float tnA = fmaf(2.0f * cA, tA, -tA1), tnB = fmaf(2.0f * cB, tB, -tB1);
-                            tA1 = tA;
-                            tA = tnA;
-                            tB1 = tB;
-                            tB = tnB;
-                        }
-                    }
-                }
-            }
-        }
-    }
-    transpose_reduce64(acc, lane);
-    const float G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
-    const float G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
-    if constexpr (MODE == kDescriptor) {
-        const int D = 2 * (Kr + Ka);
-        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
-        if (c0 >= 0) G_out[(size_t)i_s * D + c0] = G0;
-        if (c1 >= 0) G_out[(size_t)i_s * D + c1] = G1;
-        return;
-    } else {
-    // ---- network of the atom's species (FP32, one lane per neuron)
-    const int t = __float_as_int(pos4[i_s].w);
-    const float *Pt = s_par + t * net.stride;
-    const float *sh = Pt + net.offShift, *sc = Pt + net.offScale;
-    const float x00 = (G0 - sh[s0]) * sc[s0];
-    const float x01 = (G1 - sh[s1]) * sc[s1];
-    // optional activation record of this atom (G_out holds records in this mode)
-    float *rec = G_out ? G_out + (size_t)i_s * net.rec_len : nullptr;
-    if (rec) {
-        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
-        if (c0 >= 0) rec[c0] = x00;
-        if (c1 >= 0) rec[c1] = x01;
-    }
-    // Lanes own neurons: o = lane for hb = 32; for hb = 16 both half-warps hold
-    // neurons 0..15 (o = lane & 15) and split every sum over k into even and odd
-    // terms (half h takes k = 2j + h), joined by one shuffle.
-    const int o = lane & (HB - 1), h = HB == 16 ? lane >> 4 : 0;
-    const float2 *W1P = reinterpret_cast<const float2 *>(Pt + net.offW[1]) + lane * (HB + 1);
-    float part[HB];
-#pragma unroll
-    for (int q = 0; q < HB; ++q) {
-        const float2 w = W1P[q];
-        part[q] = fmaf(w.x, x00, w.y * x01);
-    }
-    float z;
-    if constexpr (HB == 16) {
-        z = transpose_reduce16(part, lane);  // lanes 2q, 2q+1: halves of neuron q
-        z += __shfl_xor_sync(kFull, z, 1);
-        z = __shfl_sync(kFull, z, 2 * o);
-    } else {
-        z = transpose_reduce32(part, lane);
-    }
-    float xl[kMaxLayers];  // this lane's neuron of every hidden layer
-    xl[1] = tanhf(z + Pt[net.offB[1] + o]);
-    if (rec && lane < net.H[1]) rec[net.rec_x[1] + lane] = xl[1];
-#pragma unroll
-    for (int l = 2; l < kMaxLayers; ++l) {
-        if (l < net.L) {
-            const float *Wl = Pt + net.offW[l] + o * (HB + 1);
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll(HB == 16 ? 4 : 2)
-            for (int j = 0; j < (HB == 16 ? 8 : 32); j += 2) {
-                const int k0 = HB == 16 ? 2 * j + h : j, k1 = HB == 16 ? 2 * j + 2 + h : j + 1;
-                a0 = fmaf(Wl[k0], __shfl_sync(kFull, xl[l - 1], k0), a0);
-                a1 = fmaf(Wl[k1], __shfl_sync(kFull, xl[l - 1], k1), a1);
-            }
-            float zz = a0 + a1;
-            if constexpr (HB == 16) zz += __shfl_xor_sync(kFull, zz, 16);
-            xl[l] = tanhf(zz + Pt[net.offB[l] + o]);
-            if (rec && lane < net.H[l]) rec[net.rec_x[l] + lane] = xl[l];
-        }
-    }
-    float xlast = 0.f;
-#pragma unroll
-    for (int l = 1; l < kMaxLayers; ++l)
-        if (l == net.L - 1) xlast = xl[l];
-    const float wL = Pt[net.offWL + o];
-    float E = wL * xlast;
-#pragma unroll
-    for (int m = HB / 2; m >= 1; m >>= 1) E += __shfl_xor_sync(kFull, E, m);
-    E += Pt[net.offBL];
-    // back-propagation: delta of the last hidden layer, then down to layer 1
-    float delta = (1.0f - xlast * xlast) * wL;
-    if (rec && lane < net.Hlast) rec[net.rec_dlast + lane] = delta;
-#pragma unroll
-    for (int l = kMaxLayers - 1; l >= 2; --l) {
-        if (l < net.L) {
-            const float *Wl = Pt + net.offW[l] + o;  // column o: weights from input neuron o
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll(HB == 16 ? 4 : 2)
-            for (int j = 0; j < (HB == 16 ? 8 : 32); j += 2) {
-                const int q0 = HB == 16 ? 2 * j + h : j, q1 = HB == 16 ? 2 * j + 2 + h : j + 1;
-                a0 = fmaf(Wl[q0 * (HB + 1)], __shfl_sync(kFull, delta, q0), a0);
-                a1 = fmaf(Wl[q1 * (HB + 1)], __shfl_sync(kFull, delta, q1), a1);
-            }
-            float dx = a0 + a1;
-            if constexpr (HB == 16) dx += __shfl_xor_sync(kFull, dx, 16);
-            delta = (1.0f - xl[l - 1] * xl[l - 1]) * dx;
-            if (rec && lane < net.H[l - 1]) rec[net.rec_d[l - 1] + lane] = delta;
-        }
-    }
-    float d0 = 0.f, d1 = 0.f, e0 = 0.f, e1 = 0.f;
-#pragma unroll(HB == 16 ? 8 : 2)
-    for (int q = 0; q < HB; q += 2) {
-        const float dq = __shfl_sync(kFull, delta, q), dr = __shfl_sync(kFull, delta, q + 1);
-        const float2 wq = W1P[q], wr = W1P[q + 1];
-        d0 = fmaf(wq.x, dq, d0);
-        d1 = fmaf(wq.y, dq, d1);
-        e0 = fmaf(wr.x, dr, e0);
-        e1 = fmaf(wr.y, dr, e1);
-    }
-    d0 += e0;
-    d1 += e1;
-    W.coef[s0] = d0 * sc[s0];  // dE/dG = dE/dg * scale
-    W.coef[s1] = d1 * sc[s1];
-    if (lane == 0) {
-        e_acc += (double)E;
-        eatom[i_s] = E;
-    }
-    }  // MODE == kFused
-    }  // MODE != kForces
-    if constexpr (MODE == kForces) {  // dE/dG given: scatter the row into the slot layout
-        const int D = 2 * (Kr + Ka);
-        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
-        W.coef[s0] = c0 >= 0 ? dEdG_in[(size_t)i_s * D + c0] : 0.f;
-        W.coef[s1] = c1 >= 0 ? dEdG_in[(size_t)i_s * D + c1] : 0.f;
-    }
-    __syncwarp();
-
-    // ---- chain rule to forces
-    float cr[KRT], crw[KRT], ca[KAT], caw[KAT];
-#pragma unroll
-    for (int q = 0; q < KRT; ++q) {
-        cr[q] = W.coef[q];
-        crw[q] = W.coef[SLOT_RADW + q];
-    }
-#pragma unroll
-    for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
-        ca[q] = 2.0f * W.coef[SLOT_ANG + q];
-        caw[q] = 2.0f * W.coef[SLOT_ANGW + q];
-    }
-    const float k2 = 2.0f * inv_rcr;
-    for (int k = lane; k < nnb; k += 32) {
-        const float4 e = W.e_d[k];
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        if (e.w <= B.rc_rad) {
-            const float2 c = W.e_c[k];
-            const float s = s_tw[W.e_j[k] >> 28], fc = c.x, dfc = c.y;
-            const float x = 2.0f * e.w * inv_rcr - 1.0f;
-            // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c',  T_q' = q U_{q-1}
-            float dEdr = (cr[0] + s * crw[0]) * dfc;
-            float tm1 = 1.0f, tt = x, um1 = 0.0f, u = 1.0f;
-            const float k2fc = k2 * fc;
-#pragma unroll
-            for (int q = 1; q < KRT; ++q) {
-                if (q < Kr) {
-                    const float coef = fmaf(s, crw[q], cr[q]);
-                    dEdr = fmaf(coef, fmaf((float)q * u, k2fc, tt * dfc), dEdr);
-                    const float tn = fmaf(2.0f * x, tt, -tm1);
-                    tm1 = tt;
-                    tt = tn;
-                    const float un = fmaf(2.0f * x, u, -um1);
-                    um1 = u;
-                    u = un;
-                }
-            }
-            const float gr = __fdiv_rn(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
-            fx = -gr * e.x;
-            fy = -gr * e.y;
-            fz = -gr * e.z;
-        }
-        W.e_fx[k] = fx;
-        W.e_fy[k] = fy;
-        W.e_fz[k] = fz;
-    }
-    __syncwarp();
-    // Angular chain rule by the rotation schedule: the angular entries form
-    // blocks of 32 (lane l owns entries 32b + l). Inside a diagonal block, step t
-    // pairs lane l with entry (l + t) mod n_A (t = 1..n_A/2; at t = n_A/2 only the
-    // lower half of lanes, so each unordered pair is visited once); between
-    // blocks A < B, step t pairs lane l with column (l + t) mod 32 of B. The lane
-    // keeps dE/dd_j of its own entry in registers and hands dE/dd_k to the owner
-    // of k with one rotation shuffle; every entry is written only by its owner,
-    // so no atomics are needed. Coefficients carry the factor 2 of the ordered sum.
-    {
-        const int nbk = (nang + 31) >> 5;
-        for (int A = 0; A < nbk; ++A) {
-            const int nA = min(32, nang - 32 * A);
-            const bool vj = lane < nA;
-            const int self = 32 * A + (vj ? lane : 0);
-            const float4 uj = W.a_u[self];
-            const float4 xj = W.a_x[self];
-            for (int Bk = A; Bk < nbk; ++Bk) {
-                const int nB = min(32, nang - 32 * Bk);
-                const bool diag = Bk == A;
-                const int nt = diag ? nA / 2 : 32;
-                float jx = 0.f, jy = 0.f, jz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
-                for (int it = 0; it < nt; it += 2) {  // two independent steps per iteration (ILP)
-                    int ccA, ccB;
-                    bool vA, vB;
-                    rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
-                    rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
-                    const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
-                    float gAx, gAy, gAz, gBx, gBy, gBz;
-                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kA], W.a_x[kA], vA, ca, caw, Ka, jx, jy, jz, gAx, gAy,
-                                              gAz);
-                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kB], W.a_x[kB], vB, ca, caw, Ka, jx, jy, jz, gBx, gBy,
-                                              gBz);
-                    // dE/dd_k goes to the lane that owns k: it sits t lanes to the left
-                    const int srcA = rotation_source(diag, it, nA, lane);
-                    const int srcB = rotation_source(diag, it + 1, nA, lane);
-                    kx += __shfl_sync(kFull, gAx, srcA);
-                    ky += __shfl_sync(kFull, gAy, srcA);
-                    kz += __shfl_sync(kFull, gAz, srcA);
-                    kx += __shfl_sync(kFull, gBx, srcB);
-                    ky += __shfl_sync(kFull, gBy, srcB);
-                    kz += __shfl_sync(kFull, gBz, srcB);
-                }
-                // force on neighbour = -dE_i/dd; each entry is touched by its owner lane only
-                if (vj) {
-                    const int sl = __float_as_int(xj.w);
-                    W.e_fx[sl] -= jx;
-                    W.e_fy[sl] -= jy;
-                    W.e_fz[sl] -= jz;
-                }
-                if (lane < nB) {
-                    const int sl = __float_as_int(W.a_x[32 * Bk + lane].w);
-                    W.e_fx[sl] -= kx;
-                    W.e_fy[sl] -= ky;
-                    W.e_fz[sl] -= kz;
-                }
-            }
-        }
-    }
-    __syncwarp();
-    float fix = 0.f, fiy = 0.f, fiz = 0.f;
-    for (int k = lane; k < nnb; k += 32) {
-        const float fx = W.e_fx[k], fy = W.e_fy[k], fz = W.e_fz[k];
-        const float4 e = W.e_d[k];
-        atomicAdd(&F4[W.e_j[k] & 0x0fffffff], make_float4(fx, fy, fz, 0.f));
-        fix -= fx;
-        fiy -= fy;
-        fiz -= fz;
-        vir[0] = fmaf(e.x, fx, vir[0]);
-        vir[1] = fmaf(e.x, fy, vir[1]);
-        vir[2] = fmaf(e.x, fz, vir[2]);
-        vir[3] = fmaf(e.y, fx, vir[3]);
-        vir[4] = fmaf(e.y, fy, vir[4]);
-        vir[5] = fmaf(e.y, fz, vir[5]);
-        vir[6] = fmaf(e.z, fx, vir[6]);
-        vir[7] = fmaf(e.z, fy, vir[7]);
-        vir[8] = fmaf(e.z, fz, vir[8]);
-    }
-    fix = warp_sum(fix);
-    fiy = warp_sum(fiy);
-    fiz = warp_sum(fiz);
-    if (lane == 0) atomicAdd(&F4[i_s], make_float4(fix, fiy, fiz, 0.f));
-    __syncwarp();
-}
-
-// The network parameters of every species into the shared-memory layout of
-// FusedNet (zero-padded to the width bound; slots mapped to G columns).
-template <int KRT, int KAT, bool EXACT>
-__device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &net, const float *__restrict__ params,
-                                                const float *__restrict__ shift, const float *__restrict__ scale,
-                                                float *s_par, int tid) {
-    const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
-    for (int t = 0; t < B.n_species; ++t) {
-        const float *src = params + (size_t)t * net.n_params;
-        float *dst = s_par + t * net.stride;
-        const int H1 = net.H[1], hb = net.hb;
-        for (int idx = tid; idx < kSlots * (hb + 1); idx += kPThreads) {  // W1P: (pair, o, slot parity)
-            const int pair = idx / (2 * (hb + 1)), rem = idx % (2 * (hb + 1)), o = rem >> 1;
-            const int col = slot_col<KRT, KAT>(2 * pair + (rem & 1), Kr, Ka);
-            dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
-        }
-        for (int o = tid; o < hb; o += kPThreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
-#pragma unroll
-        for (int l = 2; l < kMaxLayers; ++l) {
-            if (l >= net.L) break;
-            const int Hi = net.H[l - 1], Ho = net.H[l];
-            for (int idx = tid; idx < hb * (hb + 1); idx += kPThreads) {
-                const int o = idx / (hb + 1), k = idx % (hb + 1);
-                dst[net.offW[l] + idx] = (o < Ho && k < Hi) ? src[net.srcOff[l] + o * Hi + k] : 0.f;
-            }
-            for (int o = tid; o < hb; o += kPThreads)
-                dst[net.offB[l] + o] = o < Ho ? src[net.srcOff[l] + Ho * Hi + o] : 0.f;
-        }
-        const int Hl = net.Hlast;
-        for (int k = tid; k < hb; k += kPThreads) dst[net.offWL + k] = k < Hl ? src[net.srcOffL + k] : 0.f;
-        if (tid == 0) dst[net.offBL] = src[net.srcOffL + Hl];
-        for (int slot = tid; slot < kSlots; slot += kPThreads) {
-            const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
-            dst[net.offShift + slot] = col >= 0 ? shift[t * D + col] : 0.f;
-            dst[net.offScale + slot] = col >= 0 ? scale[t * D + col] : 0.f;
-        }
-    }
-}
-
-template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB>
-__global__ void __launch_bounds__(kPThreads, 2)
-    k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
-                const float4 *__restrict__ pos4,
-                const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,
-                const float *__restrict__ scale, float4 *__restrict__ F4, float *__restrict__ eatom,
-                float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
-                double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
-                unsigned *__restrict__ work, const int *__restrict__ order, int n_items, int *__restrict__ vl_out,
-                int *__restrict__ vl_count) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float s_tw[kMaxSpecies];
-    __shared__ float s_vir[kPWarps][9];
-    __shared__ double s_e[kPWarps];
-    __shared__ int s_next, s_item;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = caps.tile;
-    // one layout for every cell: sized for the largest image-offset table
-    // (g_one.n_off is that maximum in a batch)
-    const PLayout L = make_playout(g_one.n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0,
-                                   net.stride);
-    int *off_start = reinterpret_cast<int *>(smem + L.off_start);
-    int *off_count = reinterpret_cast<int *>(smem + L.off_count);
-    int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);
-    float4 *off_shift = reinterpret_cast<float4 *>(smem + L.off_shift);
-    float4 *s_pos = reinterpret_cast<float4 *>(smem + L.s_pos);
-    int *s_idx = reinterpret_cast<int *>(smem + L.s_idx);
-    float *s_par = reinterpret_cast<float *>(smem + L.params);
-    unsigned char *wb = smem + L.warp_base + L.warp_bytes * warp;
-    WarpLists W;
-    W.e_d = reinterpret_cast<float4 *>(wb + L.e_d);
-    W.e_c = reinterpret_cast<float2 *>(wb + L.e_c);
-    W.e_j = reinterpret_cast<int *>(wb + L.e_j);
-    W.e_fx = reinterpret_cast<float *>(wb + L.e_fx);
-    W.e_fy = reinterpret_cast<float *>(wb + L.e_fy);
-    W.e_fz = reinterpret_cast<float *>(wb + L.e_fz);
-    W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
-    W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
-    W.coef = reinterpret_cast<float *>(wb + L.coef);
-
-#pragma unroll
-    for (int t = 0; t < kMaxSpecies; ++t)
-        if (tid == t) s_tw[t] = B.type_weight[t];
-
-    // ---- network parameters of every species into the shared-memory layout
-    if constexpr (MODE == kFused) load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid);
-
-    unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
-    // Work items are cells: one per CTA (work == NULL), or, in the persistent
-    // form, taken from a global counter in the order given by `order` (heaviest
-    // cells first), so that CTAs stay resident and the tail stays short.
-    for (int item_pass = 0;; ++item_pass) {
-    int cell;
-    if (work) {
-        __syncthreads();  // the previous cell's shared-memory use is over
-        if (tid == 0) s_item = (int)atomicAdd(work, 1u);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= n_items) break;
-        cell = order ? order[item] : item;
-    } else {
-        if (item_pass) break;
-        cell = blockIdx.x;
-    }
-    // the cell grid of this cell's structure: the kernel parameter, or in a batch
-    // the grid of the structure that owns the cell (read in place, not copied)
-    int sidx = 0;
-    if constexpr (BATCH) {
-        int lo = 0, hi = n_struct - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sinfo[mid].cell0 <= cell) lo = mid; else hi = mid - 1;
-        }
-        sidx = lo;
-    }
-    const Grid &g = BATCH ? sinfo[sidx].g : g_one;
-    const int cell0 = BATCH ? sinfo[sidx].cell0 : 0;
-    const int n_off = g.n_off;
-    if (tid == 0) s_next = 0;
-
-    // ---- neighbour-cell table: start, count and image shift of every offset
-    const int lcell = cell - cell0;         // cell inside its structure's grid
-    const int cx = lcell % g.nc[0], cy = (lcell / g.nc[0]) % g.nc[1], cz = lcell / (g.nc[0] * g.nc[1]);
-    const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
-    for (int o = tid; o < n_off; o += kPThreads) {
-        const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
-        const int ux = cx + ox, uy = cy + oy, uz = cz + oz;
-        const int vx = ux - floor_div(ux, g.nc[0]) * g.nc[0];
-        const int vy = uy - floor_div(uy, g.nc[1]) * g.nc[1];
-        const int vz = uz - floor_div(uz, g.nc[2]) * g.nc[2];
-        const int nc = cell0 + (vz * g.nc[1] + vy) * g.nc[0] + vx;
-        const int s0 = cell_start[nc];
-        off_start[o] = s0;
-        off_count[o] = cell_start[nc + 1] - s0;
-        off_shift[o] = make_float4(ox * g.hf[0], oy * g.hf[1], oz * g.hf[2],
-                                   __int_as_float((ox | oy | oz) != 0 ? 1 : 0));
-    }
-    __syncthreads();
-    if (warp == 0) {
-        int carry = 0;
-        for (int base = 0; base < n_off; base += 32) {
-            const int o = base + lane;
-            const int v = o < n_off ? off_count[o] : 0;
-            int x = v;
-#pragma unroll
-            for (int s = 1; s < 32; s <<= 1) {
-                const int y = __shfl_up_sync(kFull, x, s);
-                if (lane >= s) x += y;
-            }
-            if (o < n_off) off_prefix[o] = carry + x - v;
-            carry += __shfl_sync(kFull, x, 31);
-        }
-        if (lane == 0) off_prefix[n_off] = carry;
-    }
-    __syncthreads();
-
-    const int total = off_prefix[n_off];
-    const int c0 = cell_start[cell];
-    const int cnt = cell_start[cell + 1] - c0;
-    const int n_chunks = (total + tile - 1) / tile;
-    auto stage = [&](int chunk) {
-        const int base = chunk * tile;
-        const int len = min(tile, total - base);
-        for (int t = tid; t < len; t += kPThreads) {
-            const int q = base + t;
-            int lo = 0, hi = n_off - 1;  // largest o with off_prefix[o] <= q
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (off_prefix[mid] <= q) lo = mid; else hi = mid - 1;
-            }
-            const int j = off_start[lo] + (q - off_prefix[lo]);
-            const float4 p = pos4[j];
-            const float4 sh = off_shift[lo];
-            s_pos[t] = make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w);
-            if constexpr (MODE == kBuildList)
-                s_idx[t] = j | (lo << caps.vl_jbits);  // the Verlet-list entry: index and image offset
-            else
-                s_idx[t] = j | (__float_as_int(sh.w) ? kShiftBit : 0);
-        }
-    };
-    // list-build mode: the entry of the atom itself (zero image offset) is excluded
-    const int self_code = (g.m[0] + wx * (g.m[1] + wy * g.m[2])) << caps.vl_jbits;
-    const float rc2list = caps.rc_list * caps.rc_list;
-
-    float vir[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) vir[k] = 0.f;
-    double e_acc = 0.0;
-
-    auto finish_list = [&](int &nnb, int &nang) {
-        if (nnb > caps.nb) {  // entries past the capacity were dropped
-            if (lane == 0) atomicOr(err, kErrNbCap);
-            nnb = caps.nb;
-        }
-        __syncwarp();
-        complete_list(B, s_tw, caps, W, lane, nnb, nang, err);
-        if (nang > caps.ang) {
-            if (lane == 0) atomicOr(err, kErrAngCap);
-            nang = caps.ang;
-        }
-        st_nb += nnb;
-        st_ang += nang;
-        st_pairs += (unsigned long long)(nang * (nang - 1) / 2);
-        __syncwarp();
-    };
-
-    if (n_chunks <= 1) {
-        if (total > 0) stage(0);
-        __syncthreads();
-        for (;;) {
-            int a = 0;
-            if (lane == 0) a = atomicAdd(&s_next, 1);
-            a = __shfl_sync(kFull, a, 0);
-            if (a >= cnt) break;
-            const int i_s = c0 + a;
-            const float4 ui = pos4[i_s];
-            int nnb = 0, nang = 0;
-            if constexpr (MODE == kBuildList) {
-                scan_tile_build(s_pos, s_idx, total, ui, i_s | self_code, rc2list,
-                                vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
-                store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
-            } else {
-                scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
-                finish_list(nnb, nang);
-                process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
-                                                        eatom, G_out, dEdG_in, e_acc, vir);
-            }
-        }
-    } else {
-        const int n_rounds = (cnt + kPWarps - 1) / kPWarps;
-        for (int round = 0; round < n_rounds; ++round) {
-            const int a = round * kPWarps + warp;
-            const bool active = a < cnt;
-            const int i_s = c0 + a;
-            const float4 ui = active ? pos4[i_s] : make_float4(0.f, 0.f, 0.f, 0.f);
-            int nnb = 0, nang = 0;
-            for (int chunk = 0; chunk < n_chunks; ++chunk) {
-                __syncthreads();
-                stage(chunk);
-                __syncthreads();
-                if (active) {
-                    const int len = min(tile, total - chunk * tile);
-                    if constexpr (MODE == kBuildList)
-                        scan_tile_build(s_pos, s_idx, len, ui, i_s | self_code, rc2list,
-                                        vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
-                    else
-                        scan_tile(s_pos, s_idx, len, ui, i_s, B, caps, W, lane, nnb);
-                }
-            }
-            if (active) {
-                if constexpr (MODE == kBuildList) {
-                    store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
-                } else {
-                    finish_list(nnb, nang);
-                    process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
-                                                            eatom, G_out, dEdG_in, e_acc, vir);
-                }
-            }
-        }
-    }
-
-    // ---- cell partials: energy (FP64), virial (FP32 lanes -> FP64)
-    if constexpr (MODE == kFused || MODE == kForces) {
-    #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float v = warp_sum(vir[k]);
-            if (lane == 0) s_vir[warp][k] = v;
-        }
-        if (lane == 0) s_e[warp] = e_acc;
-        __syncthreads();
-        if (tid < 9) {
-            float s = 0.f;
-    #pragma unroll
-            for (int w = 0; w < kPWarps; ++w) s += s_vir[w][tid];
-            vir_part[(size_t)cell * 9 + tid] = (double)s;
-        }
-        if (MODE == kFused && warp == 0) {  // FP64 tree over the warps' energies
-            double v = lane < kPWarps ? s_e[lane] : 0.0;
-    #pragma unroll
-            for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0) e_part[cell] = v;
-        }
-    }
-    }  // work items
-    if (MODE != kForces && lane == 0 && st_nb) {  // statistics
-        atomicAdd(&stats[0], st_nb);
-        atomicAdd(&stats[1], st_ang);
-        atomicAdd(&stats[2], st_pairs);
-    }
-}
 
 template <int KRT, int KAT, bool EXACT, int MODE>
 cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
@@ -1077,146 +46,6 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
                                               c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,
                                               work ? c.batch_order : nullptr, g.ncell, nullptr, nullptr);
     c.last_grid = grid;
-    return cudaGetLastError();
-}
-
-// The fused potential over the Verlet list (MD steps between list builds).
-// Persistent CTAs (the network parameters are staged once per CTA); each warp
-// takes the next sorted atom from a global counter, forms its neighbour list
-// from its Verlet-list row (scan_list) and then runs the same descriptor,
-// network and chain rule as k_potential. Energy and virial partials per CTA.
-template <int KRT, int KAT, bool EXACT, int HB>
-__global__ void __launch_bounds__(kPThreads, 2)
-    k_potential_list(Basis B, FusedNet net, Grid g, Caps caps, int n, const float4 *__restrict__ pos4,
-                     const int *__restrict__ vl, const int *__restrict__ vl_count, const float *__restrict__ params,
-                     const float *__restrict__ shift, const float *__restrict__ scale, float4 *__restrict__ F4,
-                     float *__restrict__ eatom, double *__restrict__ e_part, double *__restrict__ vir_part,
-                     unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
-                     unsigned *__restrict__ work) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float s_tw[kMaxSpecies];
-    __shared__ float s_vir[kPWarps][9];
-    __shared__ double s_e[kPWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const PLayout L = make_playout(g.n_off, 0, caps.nb, caps.ang, B.n_species, net.stride);
-    float4 *off_shift = reinterpret_cast<float4 *>(smem + L.off_shift);
-    float *s_par = reinterpret_cast<float *>(smem + L.params);
-    unsigned char *wb = smem + L.warp_base + L.warp_bytes * warp;
-    WarpLists W;
-    W.e_d = reinterpret_cast<float4 *>(wb + L.e_d);
-    W.e_c = reinterpret_cast<float2 *>(wb + L.e_c);
-    W.e_j = reinterpret_cast<int *>(wb + L.e_j);
-    W.e_fx = reinterpret_cast<float *>(wb + L.e_fx);
-    W.e_fy = reinterpret_cast<float *>(wb + L.e_fy);
-    W.e_fz = reinterpret_cast<float *>(wb + L.e_fz);
-    W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
-    W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
-    W.coef = reinterpret_cast<float *>(wb + L.coef);
-#pragma unroll
-    for (int t = 0; t < kMaxSpecies; ++t)
-        if (tid == t) s_tw[t] = B.type_weight[t];
-    load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid);
-    const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
-    for (int o = tid; o < g.n_off; o += kPThreads) {  // image offset of every list code
-        const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
-        off_shift[o] = make_float4(ox * g.hf[0], oy * g.hf[1], oz * g.hf[2], 0.f);
-    }
-    __syncthreads();
-
-    float vir[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) vir[k] = 0.f;
-    double e_acc = 0.0;
-    unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
-    for (;;) {
-        int a = 0;
-        if (lane == 0) a = (int)atomicAdd(work, 1u);
-        a = __shfl_sync(kFull, a, 0);
-        if (a >= n) break;
-        const int i_s = a;
-        const float4 ui = pos4[i_s];
-        int nnb = 0, nang = 0;
-        scan_list(vl + (size_t)i_s * caps.vl_cap, vl_count[i_s], pos4, off_shift, ui, caps.vl_jbits, B, caps, W,
-                  lane, nnb);
-        if (nnb > caps.nb) {
-            if (lane == 0) atomicOr(err, kErrNbCap);
-            nnb = caps.nb;
-        }
-        __syncwarp();
-        complete_list(B, s_tw, caps, W, lane, nnb, nang, err);
-        if (nang > caps.ang) {
-            if (lane == 0) atomicOr(err, kErrAngCap);
-            nang = caps.ang;
-        }
-        st_nb += nnb;
-        st_ang += nang;
-        st_pairs += (unsigned long long)(nang * (nang - 1) / 2);
-        __syncwarp();
-        process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
-                                                  nullptr, nullptr, e_acc, vir);
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const float v = warp_sum(vir[k]);
-        if (lane == 0) s_vir[warp][k] = v;
-    }
-    if (lane == 0) s_e[warp] = e_acc;
-    if (lane == 0 && st_nb) {
-        atomicAdd(&stats[0], st_nb);
-        atomicAdd(&stats[1], st_ang);
-        atomicAdd(&stats[2], st_pairs);
-    }
-    __syncthreads();
-    if (tid < 9) {
-        float sv = 0.f;
-#pragma unroll
-        for (int w = 0; w < kPWarps; ++w) sv += s_vir[w][tid];
-        vir_part[(size_t)blockIdx.x * 9 + tid] = (double)sv;
-    }
-    if (warp == 0) {
-        double v = lane < kPWarps ? s_e[lane] : 0.0;
-#pragma unroll
-        for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if (lane == 0) e_part[blockIdx.x] = v;
-    }
-}
-
-template <int KRT, int KAT, bool EXACT>
-cudaError_t launch_build(Context &c, const Grid &g) {
-    const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, 0, 0).total;
-    auto kern = k_potential<KRT, KAT, EXACT, kBuildList, false, 32>;
-    cudaError_t e = allow_max_smem(kern);
-    if (e != cudaSuccess) return e;
-    const FusedNet net{};
-    kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, nullptr, 0, c.caps, c.d_pos4, c.d_cell_start,
-                                                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr, nullptr, c.d_stats, c.d_err, nullptr, nullptr, g.ncell,
-                                                 c.d_vl, c.d_vl_count);
-    return cudaGetLastError();
-}
-
-size_t potential_list_smem(const Context &c, const Grid &g, const FusedNet &net) {
-    return make_playout(g.n_off, 0, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
-}
-
-template <int KRT, int KAT, bool EXACT>
-cudaError_t launch_list(Context &c, const Grid &g, int n) {
-    const FusedNet net = make_fused_net(c.net);
-    const size_t smem = potential_list_smem(c, g, net);
-    auto kern = net.hb == 16 ? k_potential_list<KRT, KAT, EXACT, 16> : k_potential_list<KRT, KAT, EXACT, 32>;
-    cudaError_t e = allow_max_smem(kern);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem)) != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(std::min(std::max(1, per_sm), 4) * c.n_sm, (n + kPWarps - 1) / kPWarps));
-    if ((e = cudaMemsetAsync(c.d_work, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
-    kern<<<grid, kPThreads, smem, c.stream>>>(c.basis, net, g, c.caps, n, c.d_pos4, c.d_vl, c.d_vl_count, c.d_params,
-                                              c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_vl_epart, c.d_vl_vpart,
-                                              c.d_stats, c.d_err, c.d_work);
-    c.last_epart = c.d_vl_epart;
-    c.last_vpart = c.d_vl_vpart;
-    c.last_eparts = grid;
-    c.last_vparts = grid;
     return cudaGetLastError();
 }
 
@@ -1260,31 +89,6 @@ cudaError_t launch_fp_forward(Context &c, const Grid &g, int n) {
     cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
     if (e != cudaSuccess) return e;
     return dispatch<kDescriptor>(c, g);
-}
-
-int potential_list_max_ctas(const Context &c) { return 4 * std::max(1, c.n_sm); }
-
-cudaError_t launch_vl_build(Context &c, const Grid &g, int n) {
-    (void)n;
-    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
-    if (Kr == 17 && Ka == 9) return launch_build<17, 9, true>(c, g);
-    if (Kr == 21 && Ka == 7) return launch_build<21, 7, true>(c, g);
-    if (Kr <= 20 && Ka <= 12) return launch_build<20, 12, false>(c, g);
-    if (Kr <= 24 && Ka <= 8) return launch_build<24, 8, false>(c, g);
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_potential_list(Context &c, const Grid &g, int n) {
-    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
-    if (e != cudaSuccess) return e;
-    const int Kr = c.basis.Kr, Ka = c.basis.Ka;
-    if (Kr == 17 && Ka == 9) return launch_list<17, 9, true>(c, g, n);
-    if (Kr == 21 && Ka == 7) return launch_list<21, 7, true>(c, g, n);
-    if (Kr <= 20 && Ka <= 12) return launch_list<20, 12, false>(c, g, n);
-    if (Kr <= 24 && Ka <= 8) return launch_list<24, 8, false>(c, g, n);
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fp_backward(Context &c, const Grid &g, int n) {
