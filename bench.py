@@ -66,7 +66,7 @@ TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha25
 
 def captured_traffic(workload_name, precision):
     import hashlib
-    src = os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", "potential.cu")
+    src = os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", "potential_kernels.cuh")
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     c = TRAFFIC_CAPTURE
@@ -386,8 +386,8 @@ def main():
     ap.add_argument("--workload", default="water_12288")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--skin", type=float, default=1.0,
-                    help="Verlet-list skin in A for the MD step (0: cell list every step)")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="Verlet-list skin in A for the MD step (0, the default: cell list every step)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
