@@ -404,7 +404,8 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2107_11311_gb300.aenet import AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING, AenetGPU
+    from paper_2107_11311_gb300.aenet import (AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING,
+                                              AENET_MD_TIMING_POTENTIAL, AenetGPU)
 
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
@@ -426,7 +427,10 @@ def main():
     clocks.start()  # running before the warm-up, so the timed window is sampled
     with torch.cuda.stream(stream):
         gpu.md_nve(pos, vel, types, st.box, DT_PS, 1)  # initial forces + graph capture
-        flags = AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING
+        # timed steps record events only around the potential (each event node
+        # adds ~2 us to a step); the full stage breakdown comes from extra steps
+        # after the timed ones
+        flags = AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING_POTENTIAL
         for _ in range(args.warmup):
             flush.zero_()
             gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
@@ -450,16 +454,28 @@ def main():
             gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
             ends[k].record(stream)
             ms, kernels_per_step, fused = gpu.md_stage_times()  # synchronises: per-step stage times
-            stage_sum = ms if stage_sum is None else {s: stage_sum[s] + ms[s] for s in ms}
+            stage_sum = ms if stage_sum is None else {s: (None if ms[s] is None else stage_sum[s] + ms[s])
+                                                      for s in ms}
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         clk = clocks.stop()
         gpu.check()
         builds = gpu.md_list_builds() - builds0
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        # untimed: the full stage breakdown (every stage bracketed by events)
+        n_diag = 10
+        diag = None
+        for _ in range(n_diag):
+            flush.zero_()
+            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1,
+                       flags=AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING)
+            ms_full, _, _ = gpu.md_stage_times()
+            diag = ms_full if diag is None else {s: diag[s] + ms_full[s] for s in ms_full}
+        gpu.check()
     t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
     value = world * n * args.steps / t_dev
-    stage_avg = {s: stage_sum[s] / args.steps for s in stage_sum}
+    stage_avg = {s: (None if v is None else v / args.steps) for s, v in stage_sum.items()}
+    stage_full = {s: round(v / n_diag, 5) for s, v in diag.items()}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -524,7 +540,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "neighbour_entries": stats[0], "angular_pairs": stats[2],
                    "skin_A": args.skin, "list_builds": builds if args.skin > 0 else None},
-        "stage_ms": {s: round(v, 5) for s, v in stage_avg.items()},
+        "stage_ms": {s: round(v, 5) for s, v in stage_avg.items() if v is not None},
+        "stage_ms_all_events": stage_full,
         # kernel nodes of the step graph, plus the 4 kernels of each list rebuild
         # (the body of the graph's conditional node) that ran in the timed steps
         "gpu_launches": kernels_per_step * args.steps + (4 * builds if args.skin > 0 else 0),

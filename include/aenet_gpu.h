@@ -226,8 +226,12 @@ int aenet_descriptors(aenet_ctx *ctx, int n_atoms, const double *pos, const int3
  * of being recomputed for frame 0. */
 #define AENET_MD_CONTINUE 2
 /* AENET_MD_TIMING: record CUDA events between the stages of every captured MD
- * step; read them with aenet_md_stage_times(). */
+ * step; read them with aenet_md_stage_times(). Each event adds about 2 us of
+ * device time to a step. AENET_MD_TIMING_POTENTIAL records only the events
+ * around the potential (the fused kernel, or each split kernel), so that the
+ * step is timed nearly as it runs untimed; the other stages then read NaN. */
 #define AENET_MD_TIMING 4
+#define AENET_MD_TIMING_POTENTIAL 8
 int aenet_md_nve(aenet_ctx *ctx, int n_atoms, double *pos, double *vel, const int32_t *types,
                  const double *box, double dt_ps, int n_steps, double *e_pot, double *e_kin,
                  int flags);

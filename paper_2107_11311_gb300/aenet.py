@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
-AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING = 1, 2, 4
+AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING, AENET_MD_TIMING_POTENTIAL = 1, 2, 4, 8
 AENET_OPT_KEEP_ACTIVATIONS = 1
 AENET_BATCH_AUTOTUNE = 1
 STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
@@ -316,13 +316,15 @@ class AenetGPU:
         return tuple(int(x) for x in out)
 
     def md_stage_times(self):
-        """Per-stage device milliseconds of the last AENET_MD_TIMING step, the
-        number of kernel launches per MD step and whether the fused kernel ran."""
+        """Per-stage device milliseconds of the last timed MD step (None for the
+        stages AENET_MD_TIMING_POTENTIAL does not record), the number of kernel
+        launches per MD step and whether the fused kernel ran."""
         ms = np.zeros(len(STAGES), dtype=np.float32)
         k = C.c_int(0)
         f = C.c_int(0)
         self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), C.byref(k), C.byref(f)))
-        return dict(zip(STAGES, map(float, ms))), int(k.value), bool(f.value & 1)
+        vals = [None if np.isnan(v) else float(v) for v in ms]
+        return dict(zip(STAGES, vals)), int(k.value), bool(f.value & 1)
 
 
 def _energy_function():

@@ -256,7 +256,9 @@ struct Context {
         bool timing = false;
         unsigned gen = 0;
         double skin = 0.0;
+        unsigned ev_mask = 0;
     } md_key;
+    unsigned ev_mask = 0;              // stage events recorded while an MD step is captured
 
     // stage timing of the captured MD step (events recorded inside the graph)
     static constexpr int kStages = 6;  // kick+drift+bin, sort, descriptor, network, forces, kick+reductions

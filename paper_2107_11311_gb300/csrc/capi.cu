@@ -177,20 +177,22 @@ int check_smem(Context &c, const Grid &g) {
     return AENET_OK;
 }
 
-// Timing event inside a captured graph (an event-record node) or eagerly.
-cudaError_t mark(Context &c, cudaEvent_t ev) {
-    if (!ev) return cudaSuccess;
-    return cudaEventRecordWithFlags(ev, c.stream, cudaEventRecordExternal);
+// Stage event k of the MD step (an event-record node inside the captured graph)
+// when c.ev_mask selects it. Each node costs the step ~2 us of device time, so
+// the light timing mode records only the events around the potential.
+cudaError_t mark(Context &c, int k) {
+    if (!((c.ev_mask >> k) & 1u)) return cudaSuccess;
+    return cudaEventRecordWithFlags(c.ev[k], c.stream, cudaEventRecordExternal);
 }
 
 // Descriptor, networks and forces after the cell list (fused kernel or the
-// three split kernels). evs (optional): 3 events after descriptor, network,
-// forces. *n_eparts = number of energy partials written.
-int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent_t *evs) {
+// three split kernels), with stage events 3, 4 (after descriptor, network) and
+// 5 (after forces) when selected. *n_eparts = number of energy partials written.
+int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts) {
     if (fused_supported(c)) {
         // descriptor, network and forces in one kernel: their stage events coincide
-        if (evs) CK(mark(c, evs[0]), "event");
-        if (evs) CK(mark(c, evs[1]), "event");
+        CK(mark(c, 3), "event");
+        CK(mark(c, 4), "event");
         CK(launch_fused_potential(c, g, n), "potential kernel");
         *n_eparts = g.ncell;
         c.last_epart = c.d_e_part;
@@ -199,7 +201,7 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent
         c.last_vparts = g.ncell;
     } else {
         CK(launch_fp_forward(c, g, n), "descriptor kernel");
-        if (evs) CK(mark(c, evs[0]), "event");
+        CK(mark(c, 3), "event");
         if (c.precision == AENET_FP32) {
             CK(launch_ann(c, n), "network kernel");
             *n_eparts = ann_blocks(n);
@@ -207,7 +209,7 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent
             CK(launch_ann_bf16(c, n), "BF16 network kernel");
             *n_eparts = bf16_eparts(c, n);
         }
-        if (evs) CK(mark(c, evs[1]), "event");
+        CK(mark(c, 4), "event");
         CK(launch_fp_backward(c, g, n), "force kernel");
         c.last_epart = c.d_e_part;
         c.last_eparts = *n_eparts;
@@ -216,7 +218,7 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts, cudaEvent
     }
     c.maps_n = n;          // the cell maps now describe this evaluation
     c.vl_valid = false;    // and no Verlet list matches them
-    if (evs) CK(mark(c, evs[2]), "event");
+    CK(mark(c, 5), "event");
     return AENET_OK;
 }
 
@@ -228,7 +230,7 @@ int enqueue_compute(Context &c, const Grid &g, int n, const double *pos, const i
     if (rc) return rc;
     CK(launch_cells(c, g, n, pos, types), "cell list");
     int n_eparts = 0;
-    if ((rc = enqueue_potential(c, g, n, &n_eparts, nullptr))) return rc;
+    if ((rc = enqueue_potential(c, g, n, &n_eparts))) return rc;
     CK(launch_finalize(c, g, n, n_eparts, forces, e_atom), "reductions");
     if (n_eparts_out) *n_eparts_out = n_eparts;
     return AENET_OK;
@@ -580,7 +582,7 @@ int batch_enqueue(Context &c, const BatchLayout &L, const StructInfo *sinfo, con
     c.batch_n = (int)L.info.size();
     cudaError_t e = launch_cells_batch(c, L.n, L.gall.ncell, dpos, dtypes);
     int n_eparts = 0;
-    if (e == cudaSuccess) rc = enqueue_potential(c, L.gall, L.n, &n_eparts, nullptr);
+    if (e == cudaSuccess) rc = enqueue_potential(c, L.gall, L.n, &n_eparts);
     if (e == cudaSuccess && !rc) e = launch_batch_reduce(c, energies, virials);
     if (e == cudaSuccess && !rc) e = launch_finalize_forces(c, L.n, dF);
     c.batch_sinfo = nullptr;
@@ -888,19 +890,18 @@ extern "C" int aenet_descriptors(aenet_ctx *h, int n, const double *pos, const i
 // the new positions, closing kick with the FP64 reductions (and the record of
 // (E_pot, E_kin) when rec != NULL). With timing, events bracket the 6 stages.
 static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
-                           const int32_t *types, double *rec, bool timing) {
-    cudaEvent_t *ev = timing ? c.ev : nullptr;
+                           const int32_t *types, double *rec) {
     int rc = check_smem(c, g);
     if (rc) return rc;
-    if (ev) CK(mark(c, ev[0]), "event");
+    CK(mark(c, 0), "event");
     CK(launch_md_kick_drift_bin(c, g, n, dt, pos, vel, types), "kick + drift + binning");
-    if (ev) CK(mark(c, ev[1]), "event");
+    CK(mark(c, 1), "event");
     CK(launch_sort(c, g, n), "cell sort");
-    if (ev) CK(mark(c, ev[2]), "event");
+    CK(mark(c, 2), "event");
     int n_eparts = 0;
-    if ((rc = enqueue_potential(c, g, n, &n_eparts, ev ? ev + 3 : nullptr))) return rc;
+    if ((rc = enqueue_potential(c, g, n, &n_eparts))) return rc;
     CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr), "kick + reductions");
-    if (ev) CK(mark(c, ev[6]), "event");
+    CK(mark(c, 6), "event");
     return AENET_OK;
 }
 
@@ -910,8 +911,7 @@ static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *
 // sort, list build; captured on the auxiliary stream), the potential over the
 // list, and the closing kick with the reductions. Events bracket the stages.
 static int enqueue_md_step_verlet(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
-                                  const int32_t *types, double *rec, bool timing) {
-    cudaEvent_t *ev = timing ? c.ev : nullptr;
+                                  const int32_t *types, double *rec) {
     int rc = check_smem(c, g);
     if (rc) return rc;
     cudaStreamCaptureStatus status;
@@ -920,9 +920,9 @@ static int enqueue_md_step_verlet(Context &c, const Grid &g, int n, double dt, d
     if (status != cudaStreamCaptureStatusActive || !graph) return fail(&c, AENET_E_STATE, "stream is not capturing");
     cudaGraphConditionalHandle cond;
     CK(cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault), "conditional handle");
-    if (ev) CK(mark(c, ev[0]), "event");
+    CK(mark(c, 0), "event");
     CK(launch_md_vl_kick_drift(c, n, dt, pos, vel, types, cond), "kick + drift");
-    if (ev) CK(mark(c, ev[1]), "event");
+    CK(mark(c, 1), "event");
     // the conditional node after everything captured so far
     const cudaGraphNode_t *deps = nullptr;
     size_t n_deps = 0;
@@ -950,14 +950,14 @@ static int enqueue_md_step_verlet(Context &c, const Grid &g, int n, double dt, d
     cudaError_t ee = cudaStreamEndCapture(c.aux_stream, &body_out);
     if (be != cudaSuccess) return cuda_fail(&c, be, "list rebuild");
     if (ee != cudaSuccess) return cuda_fail(&c, ee, "body capture");
-    if (ev) CK(mark(c, ev[2]), "event");
-    if (ev) CK(mark(c, ev[3]), "event");
-    if (ev) CK(mark(c, ev[4]), "event");
+    CK(mark(c, 2), "event");
+    CK(mark(c, 3), "event");
+    CK(mark(c, 4), "event");
     CK(launch_potential_list(c, g, n), "potential kernel (Verlet list)");
-    if (ev) CK(mark(c, ev[5]), "event");
+    CK(mark(c, 5), "event");
     CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr, true),
        "kick + reductions");
-    if (ev) CK(mark(c, ev[6]), "event");
+    CK(mark(c, 6), "event");
     return AENET_OK;
 }
 
@@ -1019,7 +1019,12 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
     } restore{c, keep_act};
     // continuing needs the cell maps and forces of an evaluation of these n atoms
     const bool cont = (flags & AENET_MD_CONTINUE) != 0 && c.maps_n == n;
-    const bool timing = (flags & AENET_MD_TIMING) != 0;
+    // stage events: all 7 (AENET_MD_TIMING), or only those around the potential
+    // (AENET_MD_TIMING_POTENTIAL; around each split kernel outside the fused form)
+    const unsigned ev_mask = (flags & AENET_MD_TIMING) ? 0x7Fu
+                             : (flags & AENET_MD_TIMING_POTENTIAL) ? (fused_supported(c) ? 0x30u : 0x3Cu)
+                                                                   : 0u;
+    const bool timing = ev_mask != 0;
     const bool verlet = c.skin > 0.0 && fused_supported(c);
     const bool pos_dev = is_device_ptr(pos), vel_dev = is_device_ptr(vel), typ_dev = is_device_ptr(types);
     const bool rec_dev = (!e_pot || is_device_ptr(e_pot)) && (!e_kin || is_device_ptr(e_kin));
@@ -1079,14 +1084,16 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
                           c.md_key.box[2] == box[2] && c.md_key.dt == dt && c.md_key.rec == rec &&
                           c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
                           c.md_key.caps.ang == c.caps.ang && c.md_key.caps.tile == c.caps.tile &&
-                          c.md_key.timing == timing && c.md_key.gen == c.buf_gen && c.md_key.skin == c.skin &&
+                          c.md_key.ev_mask == ev_mask && c.md_key.gen == c.buf_gen && c.md_key.skin == c.skin &&
                           c.md_key.caps.vl_cap == c.caps.vl_cap;
         if (!same) {
             destroy_graph(c);
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            int src = verlet ? enqueue_md_step_verlet(c, g, n, dt, dpos, dvel, dtypes, rec, timing)
-                             : enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec, timing);
+            c.ev_mask = ev_mask;
+            int src = verlet ? enqueue_md_step_verlet(c, g, n, dt, dpos, dvel, dtypes, rec)
+                             : enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec);
+            c.ev_mask = 0u;
             cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
             if (src) {
                 if (graph) cudaGraphDestroy(graph);
@@ -1121,6 +1128,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
             c.md_key.stream = c.stream;
             c.md_key.caps = c.caps;
             c.md_key.timing = timing;
+            c.md_key.ev_mask = ev_mask;
             c.md_key.gen = c.buf_gen;
             c.md_key.skin = c.skin;
         }
@@ -1158,7 +1166,13 @@ extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_st
     Context &c = h->c;
     if (!c.md_exec || !c.md_key.timing) return fail(&c, AENET_E_STATE, "no MD step was run with AENET_MD_TIMING");
     CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
-    for (int k = 0; k < Context::kStages; ++k) CK(cudaEventElapsedTime(&ms[k], c.ev[k], c.ev[k + 1]), "elapsed");
+    for (int k = 0; k < Context::kStages; ++k) {
+        const unsigned both = (1u << k) | (1u << (k + 1));
+        if ((c.md_key.ev_mask & both) == both)
+            CK(cudaEventElapsedTime(&ms[k], c.ev[k], c.ev[k + 1]), "elapsed");
+        else
+            ms[k] = nanf("");  // stage not recorded in the light timing mode
+    }
     if (kernels_per_step) *kernels_per_step = c.md_kernels;
     if (path_flags) *path_flags = fused_supported(c) ? AENET_PATH_FUSED : 0;
     return AENET_OK;

@@ -293,3 +293,22 @@ def test_md_water_12288_1000_steps(gpu_mod):
     assert drift <= 2.0 * ref + 5e-3
     r0 = O.compute(m, st.pos, st.types, st.box)
     assert abs(ep[0].item() - r0["energy"]) / st.n <= E_TOL
+
+
+def test_md_stage_timing_modes(gpu_mod):
+    """AENET_MD_TIMING brackets every stage of the captured step with events;
+    AENET_MD_TIMING_POTENTIAL only the potential (the other stages read None)."""
+    st = inputs.water_192()
+    m = inputs.make_model("water")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    p, v = torch.tensor(st.pos, device="cuda"), torch.tensor(v0, device="cuda")
+    t = torch.tensor(st.types, device="cuda")
+    g.md_nve(p, v, t, st.box, 5e-4, 1, flags=gpu_mod.AENET_MD_TIMING)
+    full, kernels, fused = g.md_stage_times()
+    assert fused and kernels >= 4
+    assert all(x is not None and x >= 0.0 for x in full.values()) and full["forces"] > 0.0
+    g.md_nve(p, v, t, st.box, 5e-4, 1, flags=gpu_mod.AENET_MD_CONTINUE | gpu_mod.AENET_MD_TIMING_POTENTIAL)
+    light, _, _ = g.md_stage_times()
+    assert light["forces"] is not None and light["forces"] > 0.0
+    assert all(light[s] is None for s in ("kick_drift_bin", "cell_sort", "kick_reductions"))
