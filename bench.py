@@ -60,17 +60,18 @@ def network_flops(widths, n_atoms):
 # DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
 # profiles/k_potential_water_12288.md; reported only while the kernel source is the
 # one the counters were taken on (first 16 hex digits of its SHA-256).
-TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha256_16": "8e87fcc066be1018",
-                   "bytes": 494848}
+TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha256_16": "1b42398bdfe4d33c",
+                   "bytes": 518656}
 
 
-def captured_traffic(workload_name, precision):
+def captured_traffic(workload_name, precision, skin=0.0):
     import hashlib
     src = os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", "potential_kernels.cuh")
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     c = TRAFFIC_CAPTURE
-    if workload_name == c["workload"] and precision == c["precision"] and sha == c["source_sha256_16"]:
+    if (workload_name == c["workload"] and precision == c["precision"] and sha == c["source_sha256_16"]
+            and skin == 0.0):
         return c["bytes"]
     return None
 
@@ -548,7 +549,7 @@ def main():
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": captured_traffic(args.workload, args.precision) if fused else None,
+                     "traffic": captured_traffic(args.workload, args.precision, args.skin) if fused else None,
                      "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
                                    f"(SM clock max from MEASURED_PEAKS.json, {peak_kind})"},
         "clocks": clk,
