@@ -88,7 +88,18 @@ def max_over_ranks(value, world):
     return float(t.item())
 
 
-def workload(name):
+def model_overrides(args):
+    """(hidden widths, basis orders) given on the command line, or None."""
+    hidden = tuple(int(x) for x in args.hidden.split("-")) if getattr(args, "hidden", None) else None
+    orders = tuple(int(x) for x in args.orders.split(",")) if getattr(args, "orders", None) else None
+    return hidden, orders
+
+
+def workload(name, hidden=None, orders=None):
+    """Structure, model and initial velocities of a named workload. water_<N>
+    (N a multiple of 3) is N/3 molecules at 1.0 g/cm^3 (structure seed 10);
+    hidden / orders override the network widths / basis orders (model-size
+    sweeps)."""
     from paper_2107_11311_gb300 import inputs
     if name == "water_12288":
         st, fam, vseed = inputs.water_12288(), "water", 12
@@ -98,10 +109,13 @@ def workload(name):
         st, fam, vseed = inputs.water_331776(), "water", 42
     elif name == "amorphous_27000":
         st, fam, vseed = inputs.amorphous_27000(), "amorphous", 22
+    elif name.startswith("water_") and name[6:].isdigit() and int(name[6:]) % 3 == 0:
+        st, fam, vseed = inputs.water(int(name[6:]) // 3, None, 10), "water", 12
     else:
         raise SystemExit(f"unknown workload {name}")
-    hidden = (32, 32) if name == "water_331776" else None
-    m = inputs.make_model(fam, hidden=hidden)
+    if hidden is None and name == "water_331776":
+        hidden = (32, 32)
+    m = inputs.make_model(fam, hidden=hidden, orders=orders)
     masses = m.masses[st.types] if fam == "water" else np.ones(st.n)
     if fam != "water":
         m.masses = np.ones(m.n_species)
@@ -199,7 +213,7 @@ def cpu_baseline(args, budget_s=12.0):
     """The FP64 oracle on the host cores, on a bounded sample of the workload:
     E+F of the first frame evaluated for a contiguous block of centre atoms."""
     from oracle import oracle
-    st, m, _ = workload(args.workload)
+    st, m, _ = workload(args.workload, *model_overrides(args))
     cores = os.cpu_count() or 1
     n_cent = min(st.n, 2048)
     mask = np.zeros(st.n, dtype=np.uint8)
@@ -223,7 +237,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from oracle import oracle
-    st, m, _ = workload(args.workload)
+    st, m, _ = workload(args.workload, *model_overrides(args))
     cores = os.cpu_count() or 1
     n_cent = min(st.n, 1024)
     mask = np.zeros(st.n, dtype=np.uint8)
@@ -387,6 +401,8 @@ def main():
     ap.add_argument("--workload", default="water_12288")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hidden", default=None, help="hidden widths, e.g. 25-25 (model-size sweeps)")
+    ap.add_argument("--orders", default=None, help="basis orders N_r,N_a, e.g. 5,3 (model-size sweeps)")
     ap.add_argument("--skin", type=float, default=0.0,
                     help="Verlet-list skin in A for the MD step (0, the default: cell list every step)")
     args = ap.parse_args()
@@ -412,7 +428,7 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    st, m, v0 = workload(args.workload)
+    st, m, v0 = workload(args.workload, *model_overrides(args))
     n = st.n
 
     stream = torch.cuda.Stream(device=dev)

@@ -249,11 +249,15 @@ def input_scaling(family: str, n_species: int, D: int):
     return shift, scale
 
 
-def make_model(family: str, hidden=None, seed: int = 1, identity_scaling: bool = False) -> Model:
+def make_model(family: str, hidden=None, seed: int = 1, identity_scaling: bool = False, orders=None) -> Model:
     """Model of a basis family with seeded N(0, 1/fan_in) weights.
 
     water:     rad 6.0 A / order 16, ang 4.0 A / order 8, D = 52, 52-15-15-1
     amorphous: rad 8.0 A / order 20, ang 6.5 A / order 6, D = 56, 56-30-30-1
+
+    ``orders`` = (N_r, N_a) replaces the basis orders (model-size sweeps); the
+    input standardisation is then the identity, since stored statistics exist
+    only for the families' own bases.
     """
     if family == "water":
         basis, tw, masses = WATER_BASIS, WATER_TYPE_WEIGHTS, np.array([MASS_O, MASS_H])
@@ -263,6 +267,9 @@ def make_model(family: str, hidden=None, seed: int = 1, identity_scaling: bool =
         hidden = (30, 30) if hidden is None else tuple(hidden)
     else:
         raise ValueError(family)
+    if orders is not None:
+        basis = dict(basis, order_rad=int(orders[0]), order_ang=int(orders[1]))
+        identity_scaling = True
     D = descriptor_dim(basis["order_rad"], basis["order_ang"])
     widths = (D,) + hidden + (1,)
     ns = len(tw)
