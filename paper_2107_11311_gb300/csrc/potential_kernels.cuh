@@ -136,7 +136,7 @@ inline FusedNet make_fused_net(const Net &net) {
 
 struct PLayout {
     size_t off_start, off_count, off_prefix, off_shift, s_pos, s_idx, params, warp_base, warp_bytes, total;
-    size_t e_d, e_c, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
+    size_t e_d, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
 };
 
 __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, int acap, int n_species, int stride) {
@@ -160,8 +160,6 @@ __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, in
     size_t q = 0;
     L.e_d = q;
     q = align16(q + sizeof(float4) * cap);
-    L.e_c = q;
-    q = align16(q + sizeof(float2) * cap);
     L.e_j = q;
     q = align16(q + sizeof(int) * cap);
     L.e_fx = q;
@@ -199,7 +197,6 @@ __device__ inline bool slot_is_angular(int slot) {
 
 struct WarpLists {
     float4 *e_d, *a_u, *a_x;  // e_d: (dx, dy, dz, r)
-    float2 *e_c;              // (f_c, f_c') of the radial cutoff (0 beyond it)
     int *e_j;                 // sorted neighbour index | species << 28
     float *e_fx, *e_fy, *e_fz, *coef;
 };
@@ -241,12 +238,23 @@ __device__ __forceinline__ void scan_tile(const float4 *s_pos, const int *s_idx,
     }
 }
 
-// Phase 2 of the list build, dense over the nnb entries: r, the radial cutoff
-// f_c and f_c', and the angular sub-list (unit vector, 1/r, angular f_c, f_c',
-// species weight, index of the main entry).
+// Cosine cutoff of the radial term and its derivative (Eq. cos-cutoff), for
+// r <= R_c: f_c = (cos(pi r / R_c) + 1) / 2, f_c' = -(pi / 2R_c) sin(pi r / R_c).
+// Recomputed where needed rather than stored per entry: the per-warp lists then
+// fit two CTAs per SM for networks up to 32 wide.
+__device__ __forceinline__ void radial_cutoff(float r, float inv_rc, float &fc, float &dfc) {
+    float sn, cs;
+    sincospif(r * inv_rc, &sn, &cs);
+    fc = 0.5f * (cs + 1.0f);
+    dfc = -0.5f * 3.14159265358979f * inv_rc * sn;
+}
+
+// Phase 2 of the list build, dense over the nnb entries: r, and the angular
+// sub-list (unit vector, 1/r, angular f_c, f_c', species weight, index of the
+// main entry).
 __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw, const Caps &caps,
                                               const WarpLists &W, int lane, int nnb, int &nang, unsigned *err) {
-    const float inv_rcr = 1.0f / B.rc_rad, inv_rca = 1.0f / B.rc_ang;
+    const float inv_rca = 1.0f / B.rc_ang;
     const unsigned lt_mask = (1u << lane) - 1u;
     nang = 0;
     for (int base = 0; base < nnb; base += 32) {
@@ -261,15 +269,7 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
                 atomicOr(err, kErrOverlap);
                 r = 1e-6f;
             }
-            float fc = 0.f, dfc = 0.f;
-            if (r <= B.rc_rad) {
-                float sn, cs;
-                sincospif(r * inv_rcr, &sn, &cs);
-                fc = 0.5f * (cs + 1.0f);
-                dfc = -0.5f * 3.14159265358979f * inv_rcr * sn;
-            }
             W.e_d[k].w = r;
-            W.e_c[k] = make_float2(fc, dfc);
             ina = r <= B.rc_ang;
         }
         const unsigned ma = __ballot_sync(kFull, ina);
@@ -445,7 +445,8 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     for (int k = lane; k < nnb; k += 32) {
         const float r = W.e_d[k].w;
         if (r <= B.rc_rad) {
-            const float fc = W.e_c[k].x;
+            float fc, dfc;
+            radial_cutoff(r, inv_rcr, fc, dfc);
             const float x = 2.0f * r * inv_rcr - 1.0f;
             const float sfc = s_tw[W.e_j[k] >> 28] * fc;
             float tm1 = 1.0f, t = x;
@@ -647,8 +648,9 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         const float4 e = W.e_d[k];
         float fx = 0.f, fy = 0.f, fz = 0.f;
         if (e.w <= B.rc_rad) {
-            const float2 c = W.e_c[k];
-            const float s = s_tw[W.e_j[k] >> 28], fc = c.x, dfc = c.y;
+            float fc, dfc;
+            radial_cutoff(e.w, inv_rcr, fc, dfc);
+            const float s = s_tw[W.e_j[k] >> 28];
             const float x = 2.0f * e.w * inv_rcr - 1.0f;
             // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c',  T_q' = q U_{q-1}
             float dEdr = (cr[0] + s * crw[0]) * dfc;
@@ -832,7 +834,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
     unsigned char *wb = smem + L.warp_base + L.warp_bytes * warp;
     WarpLists W;
     W.e_d = reinterpret_cast<float4 *>(wb + L.e_d);
-    W.e_c = reinterpret_cast<float2 *>(wb + L.e_c);
     W.e_j = reinterpret_cast<int *>(wb + L.e_j);
     W.e_fx = reinterpret_cast<float *>(wb + L.e_fx);
     W.e_fy = reinterpret_cast<float *>(wb + L.e_fy);
@@ -1076,7 +1077,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
     unsigned char *wb = smem + L.warp_base + L.warp_bytes * warp;
     WarpLists W;
     W.e_d = reinterpret_cast<float4 *>(wb + L.e_d);
-    W.e_c = reinterpret_cast<float2 *>(wb + L.e_c);
     W.e_j = reinterpret_cast<int *>(wb + L.e_j);
     W.e_fx = reinterpret_cast<float *>(wb + L.e_fx);
     W.e_fy = reinterpret_cast<float *>(wb + L.e_fy);
