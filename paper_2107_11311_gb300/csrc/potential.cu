@@ -55,6 +55,9 @@ cudaError_t dispatch(Context &c, const Grid &g) {
     const int Kr = c.basis.Kr, Ka = c.basis.Ka;
     if (Kr == 17 && Ka == 9) return launch_mode<17, 9, true, MODE>(c, g, net);
     if (Kr == 21 && Ka == 7) return launch_mode<21, 7, true, MODE>(c, g, net);
+    // small bases (e.g. D = 20) get their own bound, so that the fixed-trip
+    // order loops do not run the masked orders of the (20, 12) form
+    if (Kr <= 8 && Ka <= 6) return launch_mode<8, 6, false, MODE>(c, g, net);
     if (Kr <= 20 && Ka <= 12) return launch_mode<20, 12, false, MODE>(c, g, net);
     if (Kr <= 24 && Ka <= 8) return launch_mode<24, 8, false, MODE>(c, g, net);
     return cudaErrorInvalidValue;

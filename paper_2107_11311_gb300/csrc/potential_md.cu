@@ -58,6 +58,7 @@ cudaError_t launch_vl_build(Context &c, const Grid &g, int n) {
     const int Kr = c.basis.Kr, Ka = c.basis.Ka;
     if (Kr == 17 && Ka == 9) return launch_build<17, 9, true>(c, g);
     if (Kr == 21 && Ka == 7) return launch_build<21, 7, true>(c, g);
+    if (Kr <= 8 && Ka <= 6) return launch_build<8, 6, false>(c, g);
     if (Kr <= 20 && Ka <= 12) return launch_build<20, 12, false>(c, g);
     if (Kr <= 24 && Ka <= 8) return launch_build<24, 8, false>(c, g);
     return cudaErrorInvalidValue;
@@ -71,6 +72,7 @@ cudaError_t launch_potential_list(Context &c, const Grid &g, int n) {
     const int Kr = c.basis.Kr, Ka = c.basis.Ka;
     if (Kr == 17 && Ka == 9) return launch_list<17, 9, true>(c, g, n);
     if (Kr == 21 && Ka == 7) return launch_list<21, 7, true>(c, g, n);
+    if (Kr <= 8 && Ka <= 6) return launch_list<8, 6, false>(c, g, n);
     if (Kr <= 20 && Ka <= 12) return launch_list<20, 12, false>(c, g, n);
     if (Kr <= 24 && Ka <= 8) return launch_list<24, 8, false>(c, g, n);
     return cudaErrorInvalidValue;

@@ -78,6 +78,22 @@ def test_energy_force_virial_parity(gpu_mod, case):
     _check_efw(ref, got, st.n, case)
 
 
+@pytest.mark.parametrize("orders,hidden", [((5, 3), (25, 25)), ((12, 10), (5, 5)), ((20, 4), (32, 32))])
+def test_other_basis_sizes_and_widths(gpu_mod, orders, hidden):
+    """Bases and networks other than the two families' own (the kernel forms for
+    small bases, for the (20, 12) bound and for 32-wide layers), on water
+    without input standardisation."""
+    st = inputs.water_192()
+    m = inputs.make_model("water", hidden=hidden, orders=orders)
+    g = gpu_mod.AenetGPU(m, "fp32")
+    got = g.compute(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, got, st.n, f"orders {orders}, hidden {hidden}")
+    G = g.descriptors(st.pos, st.types, st.box)
+    refG = O.compute(m, st.pos, st.types, st.box, want_G=True, want_forces=False)["G"]
+    assert not (np.abs(G - refG) > descriptor_tol(refG, m)).any()
+
+
 def test_device_and_host_pointers_agree(gpu_mod):
     st = inputs.water_192()
     m = inputs.make_model("water")
