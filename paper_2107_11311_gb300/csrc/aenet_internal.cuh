@@ -219,6 +219,7 @@ struct Context {
     int *d_order = nullptr;            // [cap_order] that order for aenet_compute_batch
     int cap_order = 0;
     int last_grid = 0;                 // CTAs of the last potential launch
+    int pot_parts = 0;                 // energy / virial partial rows of the last potential launch
 
     // prepared batch (aenet_batch_prepare): its own layout buffers, the tuned
     // launch and the captured evaluation
@@ -322,6 +323,11 @@ cudaError_t launch_species_group(Context &c, int n);
 cudaError_t launch_grad_weights(Context &c, int n);
 std::vector<int2> grad_pairs(const Net &net);
 int grad_max_params();
+
+// Work items per cell of a single-structure potential launch (persistent CTAs
+// take cell parts from a counter); partial buffers hold kMaxSplit rows per cell.
+constexpr int kMaxSplit = 4;
+int potential_split(const Context &c, const Grid &g);
 
 // Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
 bool fused_supported(const Context &c);

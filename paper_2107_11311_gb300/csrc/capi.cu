@@ -134,7 +134,7 @@ int ensure(Context &c, int n, const Grid &g) {
     if (g.ncell > c.cap_cells) {
         CK(grow(c.d_cell_count, 0, (size_t)g.ncell), "cudaMalloc");
         CK(grow(c.d_cell_start, 0, (size_t)g.ncell + 1), "cudaMalloc");
-        CK(grow(c.d_vir_part, 0, (size_t)g.ncell * 9), "cudaMalloc");
+        CK(grow(c.d_vir_part, 0, (size_t)g.ncell * kMaxSplit * 9), "cudaMalloc");  // a row per cell part
         c.cap_cells = g.ncell;
         ++c.buf_gen;
     }
@@ -143,7 +143,8 @@ int ensure(Context &c, int n, const Grid &g) {
         c.cap_act = std::max(n, 1);
         ++c.buf_gen;
     }
-    const int need_e = std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell), bf16_eparts(c, std::max(n, 1))) + 1;
+    const int need_e =
+        std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell * kMaxSplit), bf16_eparts(c, std::max(n, 1))) + 1;
     if (need_e > c.cap_blocks || !c.d_e_part) {
         CK(grow(c.d_e_part, 0, (size_t)need_e), "cudaMalloc");
         c.cap_blocks = need_e;
@@ -194,11 +195,11 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts) {
         CK(mark(c, 3), "event");
         CK(mark(c, 4), "event");
         CK(launch_fused_potential(c, g, n), "potential kernel");
-        *n_eparts = g.ncell;
+        *n_eparts = c.pot_parts;
         c.last_epart = c.d_e_part;
-        c.last_eparts = g.ncell;
+        c.last_eparts = c.pot_parts;
         c.last_vpart = c.d_vir_part;
-        c.last_vparts = g.ncell;
+        c.last_vparts = c.pot_parts;
     } else {
         CK(launch_fp_forward(c, g, n), "descriptor kernel");
         CK(mark(c, 3), "event");
@@ -214,7 +215,7 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts) {
         c.last_epart = c.d_e_part;
         c.last_eparts = *n_eparts;
         c.last_vpart = c.d_vir_part;
-        c.last_vparts = g.ncell;
+        c.last_vparts = c.pot_parts;
     }
     c.maps_n = n;          // the cell maps now describe this evaluation
     c.vl_valid = false;    // and no Verlet list matches them

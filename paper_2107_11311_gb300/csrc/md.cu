@@ -329,7 +329,7 @@ KickParams kick_params(const Context &c, double dt) {
 
 cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom) {
     k_reduce<<<(10 + kRedThreads / 32 - 1) / (kRedThreads / 32), kRedThreads, 0, c.stream>>>(
-        n_eparts, c.d_e_part, g.ncell, c.d_vir_part, c.d_result);
+        n_eparts, c.d_e_part, c.last_vparts, c.d_vir_part, c.d_result);
     if ((forces || e_atom) && n > 0)
         k_unsort_outputs<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_perm, c.d_F4, c.d_eatom, forces, e_atom);
     return cudaGetLastError();

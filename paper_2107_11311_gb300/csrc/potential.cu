@@ -28,15 +28,18 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
     float *rows = MODE == kFused ? (c.keep_act ? c.d_act : nullptr) : c.d_G;  // activation records / G rows
+    // one structure: cells split into parts (persistent CTAs); batches: whole cells
+    const int split = c.batch_sinfo ? 1 : potential_split(c, g);
+    const int n_items = g.ncell * split;
     int grid = g.ncell;
     unsigned *work = nullptr;
-    if (c.persist && c.batch_sinfo && c.d_work && g.ncell > 0) {
+    if (((c.persist && c.batch_sinfo) || split > 1) && c.d_work && g.ncell > 0) {
         // persistent form: as many CTAs as stay resident (or the tuned count)
         int per_sm = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem)) != cudaSuccess)
             return e;
         const int resident = std::max(1, per_sm) * c.n_sm;
-        grid = std::min(g.ncell, c.persist_ctas > 0 ? std::min(c.persist_ctas, resident) : resident);
+        grid = std::min(n_items, c.persist_ctas > 0 ? std::min(c.persist_ctas, resident) : resident);
         work = c.d_work;
         if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
     }
@@ -44,8 +47,10 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
                                               c.d_cell_start, c.d_params,
                                               c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
                                               c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,
-                                              work ? c.batch_order : nullptr, g.ncell, nullptr, nullptr);
+                                              (work && c.batch_sinfo) ? c.batch_order : nullptr, n_items, nullptr,
+                                              nullptr, split);
     c.last_grid = grid;
+    c.pot_parts = n_items;
     return cudaGetLastError();
 }
 
@@ -64,6 +69,22 @@ cudaError_t dispatch(Context &c, const Grid &g) {
 }
 
 }  // namespace
+
+// Parts per cell of a single-structure evaluation. Only a system with fewer
+// cells than one wave of resident CTAs (2 per SM) is split, into enough parts to
+// fill that wave (at most kMaxSplit, and no part with fewer than 8 atoms -- one
+// per warp -- on average): each part restages the cell's neighbourhood, which
+// costs more than the tail it removes once there are more cells than CTA slots
+// (measured: water 12,288 with 512 cells, 3 parts, 2% slower; 1,536 atoms with
+// 64 cells, 3 parts, 23% faster).
+int potential_split(const Context &c, const Grid &g) {
+    const int wave = 2 * std::max(1, c.n_sm);
+    if (g.ncell <= 0 || g.ncell >= wave) return 1;
+    const int want = (wave + g.ncell - 1) / g.ncell;
+    const double per_cell = c.cap_atoms > 0 ? (double)c.cap_atoms / g.ncell : 8.0;
+    int split = std::min(std::min(want, kMaxSplit), std::max(1, (int)(per_cell / 8.0)));
+    return std::max(1, split);
+}
 
 bool fused_supported(const Context &c) {
     if (c.precision != AENET_FP32) return false;
@@ -188,7 +209,7 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
     kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
                                            nullptr,
                                            nullptr, Gs, nullptr, nullptr, nullptr, stats, err, nullptr, nullptr,
-                                           g.ncell, nullptr, nullptr);
+                                           g.ncell, nullptr, nullptr, 1);
     return cudaGetLastError();
 }
 

@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
                 double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
                 unsigned *__restrict__ work, const int *__restrict__ order, int n_items, int *__restrict__ vl_out,
-                int *__restrict__ vl_count) {
+                int *__restrict__ vl_count, int split) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
     __shared__ float s_vir[kPWarps][9];
@@ -851,17 +851,25 @@ __global__ void __launch_bounds__(kPThreads, 2)
 
     unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
     // Work items are cells: one per CTA (work == NULL), or, in the persistent
-    // form, taken from a global counter in the order given by `order` (heaviest
-    // cells first), so that CTAs stay resident and the tail stays short.
+    // form, taken from a global counter -- in a batch in the order given by
+    // `order` (heaviest cells first); for one structure as `split` parts of each
+    // cell (consecutive ranges of its atoms, each part staging the whole
+    // neighbourhood), so that the last wave of a few hundred cells does not
+    // leave most SMs idle.
     for (int item_pass = 0;; ++item_pass) {
-    int cell;
+    int cell, part = 0;
     if (work) {
-        __syncthreads();  // the previous cell's shared-memory use is over
+        __syncthreads();  // the previous item's shared-memory use is over
         if (tid == 0) s_item = (int)atomicAdd(work, 1u);
         __syncthreads();
         const int item = s_item;
         if (item >= n_items) break;
-        cell = order ? order[item] : item;
+        if (order) {
+            cell = order[item];
+        } else {
+            cell = item / split;
+            part = item - cell * split;
+        }
     } else {
         if (item_pass) break;
         cell = blockIdx.x;
@@ -919,8 +927,11 @@ __global__ void __launch_bounds__(kPThreads, 2)
     __syncthreads();
 
     const int total = off_prefix[n_off];
-    const int c0 = cell_start[cell];
-    const int cnt = cell_start[cell + 1] - c0;
+    const int cell_first = cell_start[cell], cell_cnt = cell_start[cell + 1] - cell_first;
+    const int a_lo = part * cell_cnt / split, a_hi = (part + 1) * cell_cnt / split;
+    const int c0 = cell_first + a_lo;  // this item's atoms: c0 .. c0 + cnt - 1
+    const int cnt = a_hi - a_lo;
+    const int slot = cell * split + part;  // row of this item's energy / virial partials
     const int n_chunks = (total + tile - 1) / tile;
     auto stage = [&](int chunk) {
         const int base = chunk * tile;
@@ -1036,13 +1047,13 @@ __global__ void __launch_bounds__(kPThreads, 2)
             float s = 0.f;
     #pragma unroll
             for (int w = 0; w < kPWarps; ++w) s += s_vir[w][tid];
-            vir_part[(size_t)cell * 9 + tid] = (double)s;
+            vir_part[(size_t)slot * 9 + tid] = (double)s;
         }
         if (MODE == kFused && warp == 0) {  // FP64 tree over the warps' energies
             double v = lane < kPWarps ? s_e[lane] : 0.0;
     #pragma unroll
             for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0) e_part[cell] = v;
+            if (lane == 0) e_part[slot] = v;
         }
     }
     }  // work items
