@@ -60,8 +60,8 @@ def network_flops(widths, n_atoms):
 # DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
 # profiles/k_potential_water_12288.md; reported only while the kernel source is the
 # one the counters were taken on (first 16 hex digits of its SHA-256).
-TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha256_16": "1b42398bdfe4d33c",
-                   "bytes": 518656}
+TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha256_16": "c46af5179266da81",
+                   "bytes": 524032}
 
 
 def captured_traffic(workload_name, precision, skin=0.0):
@@ -86,6 +86,14 @@ def max_over_ranks(value, world):
     t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def md_config(args, st, m, world=1):
+    """The workload description shared by both arms' JSON lines."""
+    return {"workload": args.workload, "atoms": st.n, "box_A": float(st.box[0]), "dt_fs": DT_PS * 1e3,
+            "precision": args.precision, "basis": f"rad {m.order_rad}/{m.rc_rad} A, ang {m.order_ang}/{m.rc_ang} A",
+            "ann": "-".join(map(str, m.widths)), "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU", "skin_A": args.skin}
 
 
 def model_overrides(args):
@@ -253,7 +261,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "atoms": st.n, "sample_centres": n_cent},
+            "config": dict(md_config(args, st, m), sample_centres=n_cent),
             "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: E+F of {n_cent} centre atoms of {args.workload}"},
             "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -551,12 +559,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
         "data": "synthetic",
-        "config": {"workload": args.workload, "atoms": n, "box_A": float(st.box[0]), "dt_fs": DT_PS * 1e3,
-                   "precision": args.precision, "basis": f"rad {m.order_rad}/{m.rc_rad} A, ang {m.order_ang}/{m.rc_ang} A",
-                   "ann": "-".join(map(str, m.widths)), "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "neighbour_entries": stats[0], "angular_pairs": stats[2],
-                   "skin_A": args.skin, "list_builds": builds if args.skin > 0 else None},
+        "config": dict(md_config(args, st, m, world), neighbour_entries=stats[0], angular_pairs=stats[2],
+                       list_builds=builds if args.skin > 0 else None),
         "stage_ms": {s: round(v, 5) for s, v in stage_avg.items() if v is not None},
         "stage_ms_all_events": stage_full,
         # kernel nodes of the step graph, plus the 4 kernels of each list rebuild
