@@ -142,7 +142,7 @@ struct Context {
     float4 *d_F4 = nullptr;        // [n] force accumulators, sorted order
     double *d_vir_part = nullptr;  // [cells * 9]
     double *d_e_part = nullptr;    // [blocks]
-    double *d_ke_part = nullptr;   // [blocks]
+    double *d_ke_part = nullptr;   // [MD CTAs * 11] per-CTA energy, virial and kinetic-energy sums
     double *d_result = nullptr;    // [10]: energy, virial[9]
     unsigned *d_err = nullptr;     // device error word
     unsigned long long *d_stats = nullptr;  // [4] radial entries, angular entries, angular pairs
@@ -214,7 +214,7 @@ struct Context {
     int n_sm = 0;                      // SMs of the device
     bool persist = false;              // CTAs take cells from a global counter (batches only)
     int persist_ctas = 0;              // CTAs of the persistent launch (0 = all resident)
-    unsigned *d_work = nullptr;        // [1] the counter (zeroed before each launch)
+    unsigned *d_work = nullptr;        // [2] item counter, exit counter (each launch leaves both 0)
     const int *batch_order = nullptr;  // cell order of the batch being enqueued, heaviest first
     int *d_order = nullptr;            // [cap_order] that order for aenet_compute_batch
     int cap_order = 0;
@@ -327,7 +327,7 @@ int grad_max_params();
 // Work items per cell of a single-structure potential launch (persistent CTAs
 // take cell parts from a counter); partial buffers hold kMaxSplit rows per cell.
 constexpr int kMaxSplit = 4;
-int potential_split(const Context &c, const Grid &g);
+int potential_split(const Context &c, const Grid &g, int *split_from);
 
 // Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
 bool fused_supported(const Context &c);

@@ -124,7 +124,7 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_dEdG, 0, N * D), "cudaMalloc");
         CK(grow(c.d_eatom, 0, N), "cudaMalloc");
         CK(grow(c.d_F4, 0, N), "cudaMalloc");
-        CK(grow(c.d_ke_part, 0, (N + 255) / 256 + 1), "cudaMalloc");
+        CK(grow(c.d_ke_part, 0, 11 * ((N + 255) / 256 + 1)), "cudaMalloc");  // an 11-entry row per MD CTA
         CK(grow(c.d_sp_rank, 0, N), "cudaMalloc");
         CK(grow(c.d_sp_list, 0, N), "cudaMalloc");
         CK(grow(c.d_tiles, 0, (size_t)bf16_max_tiles(c, n) + 1), "cudaMalloc");
@@ -375,7 +375,8 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
     if ((e = cudaMalloc(&c.d_n_tiles, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_result, sizeof(double) * 11)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_mass, sizeof(double) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&c.d_work, sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&c.d_work, 2 * sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
+    if ((e = cudaMemset(c.d_work, 0, 2 * sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMemset");
     if ((e = cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, c.device)) != cudaSuccess)
         return setup_fail(e, "cudaDeviceGetAttribute");
     double masses[kMaxSpecies] = {0};

@@ -125,14 +125,17 @@ __global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double 
     slot[i] = atomicAdd(&cell_count[cell], 1);
 }
 
-// v += dt/2 F/m c with F of the current evaluation; kinetic energy per CTA; the
-// last CTA reduces energy, virial and kinetic energy into result[0..10] and
-// appends (E_pot, E_kin) to the records.
+// v += dt/2 F/m c with F of the current evaluation. Every CTA also sums a fixed
+// slice of the potential's energy and virial partial rows and its atoms'
+// kinetic energy into an 11-entry row of cta_part; the last CTA reduces those
+// rows into result[0..10] (energy, virial, kinetic energy) and appends
+// (E_pot, E_kin) to the records. The partition is by CTA index, so the FP64 sums
+// do not depend on scheduling.
 __global__ void __launch_bounds__(kMdThreads)
     k_md_kick_finish(int n, KickParams kp, double *__restrict__ vel, const int32_t *__restrict__ types,
                      const float4 *__restrict__ F4, const int *__restrict__ cell_start, const int *__restrict__ cell_of,
                      const int *__restrict__ slot, int n_e, const double *__restrict__ e_part, int n_v,
-                     const double *__restrict__ vir_part, double *__restrict__ ke_part, unsigned *__restrict__ done,
+                     const double *__restrict__ vir_part, double *__restrict__ cta_part, unsigned *__restrict__ done,
                      double *__restrict__ result, int *__restrict__ step, double *__restrict__ rec_pot,
                      double *__restrict__ rec_kin, unsigned *__restrict__ vl_flag,
                      unsigned long long *__restrict__ vl_builds) {
@@ -155,12 +158,24 @@ __global__ void __launch_bounds__(kMdThreads)
     }
     ke = warp_sum_d(ke);
     if (lane == 0) s_w[warp] = ke;
+    // this CTA's slice of the energy (q = 0) and virial (q = 1..9) partial rows
+    double *row = cta_part + (size_t)blockIdx.x * 11;
+    for (int q = warp; q < 10; q += kMdThreads / 32) {
+        const int rows = q == 0 ? n_e : n_v;
+        const int per = (rows + gridDim.x - 1) / gridDim.x;
+        const int r0 = min(rows, (int)blockIdx.x * per), r1 = min(rows, r0 + per);
+        double a = 0.0;
+        for (int r = r0 + lane; r < r1; r += 32)
+            a += q == 0 ? __ldcg(e_part + r) : __ldcg(vir_part + (size_t)r * 9 + (q - 1));
+        a = warp_sum_d(a);
+        if (lane == 0) row[q] = a;
+    }
     __syncthreads();
     if (warp == 0) {
         double v = lane < kMdThreads / 32 ? s_w[lane] : 0.0;
         v = warp_sum_d(v);
         if (lane == 0) {
-            ke_part[blockIdx.x] = v;
+            row[10] = v;
             __threadfence();
             s_last = atomicAdd(done, 1u) == gridDim.x - 1;
         }
@@ -168,12 +183,9 @@ __global__ void __launch_bounds__(kMdThreads)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last CTA: 11 quantities, one warp each (8 warps, so warps 0-2 take two)
+    // last CTA: the 11 columns over the CTAs' rows, one warp each
     for (int q = warp; q < 11; q += kMdThreads / 32) {
-        double v;
-        if (q == 0) v = warp_reduce_strided(e_part, n_e, 1, lane);
-        else if (q < 10) v = warp_reduce_strided(vir_part + (q - 1), n_v, 9, lane);
-        else v = warp_reduce_strided(ke_part, gridDim.x, 1, lane);
+        const double v = warp_reduce_strided(cta_part + q, gridDim.x, 11, lane);
         if (lane == 0) result[q] = v;
     }
     __syncthreads();

@@ -28,9 +28,10 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
     float *rows = MODE == kFused ? (c.keep_act ? c.d_act : nullptr) : c.d_G;  // activation records / G rows
-    // one structure: cells split into parts (persistent CTAs); batches: whole cells
-    const int split = c.batch_sinfo ? 1 : potential_split(c, g);
-    const int n_items = g.ncell * split;
+    // one structure: (some) cells split into parts (persistent CTAs); batches: whole cells
+    int split_from = 0;
+    const int split = c.batch_sinfo ? 1 : potential_split(c, g, &split_from);
+    const int n_items = split_from + (g.ncell - split_from) * split;
     int grid = g.ncell;
     unsigned *work = nullptr;
     if (((c.persist && c.batch_sinfo) || split > 1) && c.d_work && g.ncell > 0) {
@@ -40,15 +41,14 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
             return e;
         const int resident = std::max(1, per_sm) * c.n_sm;
         grid = std::min(n_items, c.persist_ctas > 0 ? std::min(c.persist_ctas, resident) : resident);
-        work = c.d_work;
-        if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
+        work = c.d_work;  // left at zero by the previous persistent launch
     }
     kern<<<grid, kPThreads, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
                                               c.d_cell_start, c.d_params,
                                               c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
                                               c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,
                                               (work && c.batch_sinfo) ? c.batch_order : nullptr, n_items, nullptr,
-                                              nullptr, split);
+                                              nullptr, split, split_from);
     c.last_grid = grid;
     c.pot_parts = n_items;
     return cudaGetLastError();
@@ -70,20 +70,32 @@ cudaError_t dispatch(Context &c, const Grid &g) {
 
 }  // namespace
 
-// Parts per cell of a single-structure evaluation. Only a system with fewer
-// cells than one wave of resident CTAs (2 per SM) is split, into enough parts to
-// fill that wave (at most kMaxSplit, and no part with fewer than 8 atoms -- one
-// per warp -- on average): each part restages the cell's neighbourhood, which
-// costs more than the tail it removes once there are more cells than CTA slots
-// (measured: water 12,288 with 512 cells, 3 parts, 2% slower; 1,536 atoms with
-// 64 cells, 3 parts, 23% faster).
-int potential_split(const Context &c, const Grid &g) {
+// How a single-structure evaluation divides cells into work items for the
+// persistent CTAs. Cells split_from .. ncell-1 are split into `split` parts
+// (consecutive ranges of their atoms; each part restages the cell's
+// neighbourhood), the others stay whole:
+//  * fewer cells than one wave of resident CTAs (2 per SM): every cell, into
+//    enough parts to fill the wave (at most kMaxSplit, no part with fewer than 8
+//    atoms -- one per warp -- on average): 1,536 atoms in 64 cells run 23% faster;
+//  * up to kTailWaves waves: the last wave's worth of cells into 2 parts, so that
+//    the tail is made of half-size items;
+//  * more cells: none (the tail is a small share of the launch).
+constexpr int kTailWaves = 8;
+int potential_split(const Context &c, const Grid &g, int *split_from) {
     const int wave = 2 * std::max(1, c.n_sm);
-    if (g.ncell <= 0 || g.ncell >= wave) return 1;
-    const int want = (wave + g.ncell - 1) / g.ncell;
+    *split_from = 0;
+    if (g.ncell <= 0) return 1;
     const double per_cell = c.cap_atoms > 0 ? (double)c.cap_atoms / g.ncell : 8.0;
-    int split = std::min(std::min(want, kMaxSplit), std::max(1, (int)(per_cell / 8.0)));
-    return std::max(1, split);
+    const int most = std::max(1, (int)(per_cell / 8.0));
+    if (g.ncell < wave) {
+        const int want = (wave + g.ncell - 1) / g.ncell;
+        return std::max(1, std::min(std::min(want, kMaxSplit), most));
+    }
+    if (g.ncell <= kTailWaves * wave && most >= 2) {
+        *split_from = g.ncell - wave;
+        return 2;
+    }
+    return 1;
 }
 
 bool fused_supported(const Context &c) {
@@ -209,7 +221,7 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
     kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
                                            nullptr,
                                            nullptr, Gs, nullptr, nullptr, nullptr, stats, err, nullptr, nullptr,
-                                           g.ncell, nullptr, nullptr, 1);
+                                           g.ncell, nullptr, nullptr, 1, 0);
     return cudaGetLastError();
 }
 

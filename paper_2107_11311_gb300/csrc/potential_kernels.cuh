@@ -358,6 +358,17 @@ __device__ __forceinline__ void scan_list(const int *__restrict__ row, int cnt, 
     }
 }
 
+// Work counters of the persistent forms: work[0] hands out items, work[1]
+// counts CTAs that have left the item loop; the last one puts both back to 0,
+// so the next launch finds them cleared without a memset in between.
+__device__ __forceinline__ void release_work_counter(unsigned *work) {
+    __threadfence();
+    if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {
+        atomicExch(&work[0], 0u);
+        atomicExch(&work[1], 0u);
+    }
+}
+
 // Step it of the rotation schedule over one block pair of angular entries:
 // lane l pairs its entry with column cc of block B. Inside a diagonal block
 // (A = B, n_A entries) step it uses the shift t = it + 1 and pairs l with
@@ -811,7 +822,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
                 double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
                 unsigned *__restrict__ work, const int *__restrict__ order, int n_items, int *__restrict__ vl_out,
-                int *__restrict__ vl_count, int split) {
+                int *__restrict__ vl_count, int split, int split_from) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
     __shared__ float s_vir[kPWarps][9];
@@ -852,27 +863,31 @@ __global__ void __launch_bounds__(kPThreads, 2)
     unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
     // Work items are cells: one per CTA (work == NULL), or, in the persistent
     // form, taken from a global counter -- in a batch in the order given by
-    // `order` (heaviest cells first); for one structure as `split` parts of each
-    // cell (consecutive ranges of its atoms, each part staging the whole
-    // neighbourhood), so that the last wave of a few hundred cells does not
-    // leave most SMs idle.
+    // `order` (heaviest cells first); for one structure cells 0 .. split_from-1
+    // whole and every later cell as `split` parts (consecutive ranges of its
+    // atoms, each part staging the whole neighbourhood), so that the last wave
+    // is made of small items and does not leave most SMs idle.
     for (int item_pass = 0;; ++item_pass) {
-    int cell, part = 0;
+    int cell, part = 0, nparts = 1, item;
     if (work) {
         __syncthreads();  // the previous item's shared-memory use is over
         if (tid == 0) s_item = (int)atomicAdd(work, 1u);
         __syncthreads();
-        const int item = s_item;
+        item = s_item;
         if (item >= n_items) break;
         if (order) {
             cell = order[item];
+        } else if (item < split_from) {
+            cell = item;
         } else {
-            cell = item / split;
-            part = item - cell * split;
+            const int k = item - split_from;
+            cell = split_from + k / split;
+            part = k - (cell - split_from) * split;
+            nparts = split;
         }
     } else {
         if (item_pass) break;
-        cell = blockIdx.x;
+        cell = item = blockIdx.x;
     }
     // the cell grid of this cell's structure: the kernel parameter, or in a batch
     // the grid of the structure that owns the cell (read in place, not copied)
@@ -928,10 +943,10 @@ __global__ void __launch_bounds__(kPThreads, 2)
 
     const int total = off_prefix[n_off];
     const int cell_first = cell_start[cell], cell_cnt = cell_start[cell + 1] - cell_first;
-    const int a_lo = part * cell_cnt / split, a_hi = (part + 1) * cell_cnt / split;
+    const int a_lo = part * cell_cnt / nparts, a_hi = (part + 1) * cell_cnt / nparts;
     const int c0 = cell_first + a_lo;  // this item's atoms: c0 .. c0 + cnt - 1
     const int cnt = a_hi - a_lo;
-    const int slot = cell * split + part;  // row of this item's energy / virial partials
+    const int slot = order ? cell : item;  // row of this item's energy / virial partials (per cell in a batch)
     const int n_chunks = (total + tile - 1) / tile;
     auto stage = [&](int chunk) {
         const int base = chunk * tile;
@@ -1057,6 +1072,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
         }
     }
     }  // work items
+    if (work && tid == 0) release_work_counter(work);  // every thread has left the loop
     if (MODE != kForces && lane == 0 && st_nb) {  // statistics
         atomicAdd(&stats[0], st_nb);
         atomicAdd(&stats[1], st_ang);
@@ -1138,6 +1154,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
         process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
                                                   nullptr, nullptr, e_acc, vir);
     }
+    __syncthreads();  // every warp has left the loop
+    if (tid == 0) release_work_counter(work);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const float v = warp_sum(vir[k]);

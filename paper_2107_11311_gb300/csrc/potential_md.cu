@@ -20,7 +20,7 @@ cudaError_t launch_build(Context &c, const Grid &g) {
     kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, nullptr, 0, c.caps, c.d_pos4, c.d_cell_start,
                                                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                  nullptr, nullptr, c.d_stats, c.d_err, nullptr, nullptr, g.ncell,
-                                                 c.d_vl, c.d_vl_count, 1);
+                                                 c.d_vl, c.d_vl_count, 1, 0);
     return cudaGetLastError();
 }
 
@@ -38,7 +38,6 @@ cudaError_t launch_list(Context &c, const Grid &g, int n) {
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(std::min(std::max(1, per_sm), 4) * c.n_sm, (n + kPWarps - 1) / kPWarps));
-    if ((e = cudaMemsetAsync(c.d_work, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
     kern<<<grid, kPThreads, smem, c.stream>>>(c.basis, net, g, c.caps, n, c.d_pos4, c.d_vl, c.d_vl_count, c.d_params,
                                               c.d_shift, c.d_scale, c.d_F4, c.d_eatom, c.d_vl_epart, c.d_vl_vpart,
                                               c.d_stats, c.d_err, c.d_work);
