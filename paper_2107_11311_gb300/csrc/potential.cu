@@ -13,17 +13,35 @@ namespace {
 
 using namespace detail;
 
+// Shared memory of one CTA that still lets two CTAs share an SM (228 KB per SM,
+// 1 KB of it reserved per CTA).
+constexpr size_t kTwoCtaSmem = 113 * 1024;
+
 template <int KRT, int KAT, bool EXACT, int MODE>
 cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
-    const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang,
-                                     MODE == kFused ? c.basis.n_species : 0, net.stride)
-                            .total;
+    const int n_sp = MODE == kFused ? c.basis.n_species : 0;
+    size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, n_sp, net.stride).total;
     // the network's hidden-width bound is a template argument of the fused form only
     auto kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 32> : k_potential<KRT, KAT, EXACT, MODE, false, 32>;
+    int nw = kPWarps;
     if constexpr (MODE == kFused) {
-        if (net.hb == 16)
+        if (net.hb == 16) {
             kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 16>
                                  : k_potential<KRT, KAT, EXACT, MODE, false, 16>;
+        } else if (smem > kTwoCtaSmem) {
+            // one CTA per SM anyway (wide networks of several species): give it
+            // 12 warps instead of 8 if their lists fit
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            const size_t smem12 = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, n_sp, net.stride, 12).total;
+            if (smem12 + 1024 <= (size_t)optin) {
+                nw = 12;
+                smem = smem12;
+                kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 32, 12>
+                                     : k_potential<KRT, KAT, EXACT, MODE, false, 32, 12>;
+            }
+        }
     }
     cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
@@ -37,13 +55,13 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     if (((c.persist && c.batch_sinfo) || split > 1) && c.d_work && g.ncell > 0) {
         // persistent form: as many CTAs as stay resident (or the tuned count)
         int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nw * 32, smem)) != cudaSuccess)
             return e;
         const int resident = std::max(1, per_sm) * c.n_sm;
         grid = std::min(n_items, c.persist_ctas > 0 ? std::min(c.persist_ctas, resident) : resident);
         work = c.d_work;  // left at zero by the previous persistent launch
     }
-    kern<<<grid, kPThreads, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
+    kern<<<grid, nw * 32, smem, c.stream>>>(c.basis, net, g, c.batch_sinfo, c.batch_n, c.caps, c.d_pos4,
                                               c.d_cell_start, c.d_params,
                                               c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
                                               c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,

@@ -139,7 +139,8 @@ struct PLayout {
     size_t e_d, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
 };
 
-__host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, int acap, int n_species, int stride) {
+__host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, int acap, int n_species, int stride,
+                                                int nw = kPWarps) {
     PLayout L{};
     size_t p = 0;
     L.off_start = p;
@@ -175,7 +176,7 @@ __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, in
     L.coef = q;
     q = align16(q + sizeof(float) * kSlots);
     L.warp_bytes = q;
-    L.total = p + q * kPWarps;
+    L.total = p + q * nw;
     return L;
 }
 
@@ -779,33 +780,33 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
 template <int KRT, int KAT, bool EXACT>
 __device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &net, const float *__restrict__ params,
                                                 const float *__restrict__ shift, const float *__restrict__ scale,
-                                                float *s_par, int tid) {
+                                                float *s_par, int tid, int nthreads) {
     const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
     for (int t = 0; t < B.n_species; ++t) {
         const float *src = params + (size_t)t * net.n_params;
         float *dst = s_par + t * net.stride;
         const int H1 = net.H[1], hb = net.hb;
-        for (int idx = tid; idx < kSlots * (hb + 1); idx += kPThreads) {  // W1P: (pair, o, slot parity)
+        for (int idx = tid; idx < kSlots * (hb + 1); idx += nthreads) {  // W1P: (pair, o, slot parity)
             const int pair = idx / (2 * (hb + 1)), rem = idx % (2 * (hb + 1)), o = rem >> 1;
             const int col = slot_col<KRT, KAT>(2 * pair + (rem & 1), Kr, Ka);
             dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
         }
-        for (int o = tid; o < hb; o += kPThreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
+        for (int o = tid; o < hb; o += nthreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
 #pragma unroll
         for (int l = 2; l < kMaxLayers; ++l) {
             if (l >= net.L) break;
             const int Hi = net.H[l - 1], Ho = net.H[l];
-            for (int idx = tid; idx < hb * (hb + 1); idx += kPThreads) {
+            for (int idx = tid; idx < hb * (hb + 1); idx += nthreads) {
                 const int o = idx / (hb + 1), k = idx % (hb + 1);
                 dst[net.offW[l] + idx] = (o < Ho && k < Hi) ? src[net.srcOff[l] + o * Hi + k] : 0.f;
             }
-            for (int o = tid; o < hb; o += kPThreads)
+            for (int o = tid; o < hb; o += nthreads)
                 dst[net.offB[l] + o] = o < Ho ? src[net.srcOff[l] + Ho * Hi + o] : 0.f;
         }
         const int Hl = net.Hlast;
-        for (int k = tid; k < hb; k += kPThreads) dst[net.offWL + k] = k < Hl ? src[net.srcOffL + k] : 0.f;
+        for (int k = tid; k < hb; k += nthreads) dst[net.offWL + k] = k < Hl ? src[net.srcOffL + k] : 0.f;
         if (tid == 0) dst[net.offBL] = src[net.srcOffL + Hl];
-        for (int slot = tid; slot < kSlots; slot += kPThreads) {
+        for (int slot = tid; slot < kSlots; slot += nthreads) {
             const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
             dst[net.offShift + slot] = col >= 0 ? shift[t * D + col] : 0.f;
             dst[net.offScale + slot] = col >= 0 ? scale[t * D + col] : 0.f;
@@ -813,8 +814,8 @@ __device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &
     }
 }
 
-template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB>
-__global__ void __launch_bounds__(kPThreads, 2)
+template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB, int NW = kPWarps>
+__global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
                 const float4 *__restrict__ pos4,
                 const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,
@@ -825,8 +826,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
                 int *__restrict__ vl_count, int split, int split_from) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
-    __shared__ float s_vir[kPWarps][9];
-    __shared__ double s_e[kPWarps];
+    __shared__ float s_vir[NW][9];
+    __shared__ double s_e[NW];
     __shared__ int s_next, s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -834,7 +835,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     // one layout for every cell: sized for the largest image-offset table
     // (g_one.n_off is that maximum in a batch)
     const PLayout L = make_playout(g_one.n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0,
-                                   net.stride);
+                                   net.stride, NW);
     int *off_start = reinterpret_cast<int *>(smem + L.off_start);
     int *off_count = reinterpret_cast<int *>(smem + L.off_count);
     int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);
@@ -858,7 +859,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
         if (tid == t) s_tw[t] = B.type_weight[t];
 
     // ---- network parameters of every species into the shared-memory layout
-    if constexpr (MODE == kFused) load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid);
+    if constexpr (MODE == kFused) load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid, NW * 32);
 
     unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
     // Work items are cells: one per CTA (work == NULL), or, in the persistent
@@ -909,7 +910,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int lcell = cell - cell0;         // cell inside its structure's grid
     const int cx = lcell % g.nc[0], cy = (lcell / g.nc[0]) % g.nc[1], cz = lcell / (g.nc[0] * g.nc[1]);
     const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
-    for (int o = tid; o < n_off; o += kPThreads) {
+    for (int o = tid; o < n_off; o += NW * 32) {
         const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
         const int ux = cx + ox, uy = cy + oy, uz = cz + oz;
         const int vx = ux - floor_div(ux, g.nc[0]) * g.nc[0];
@@ -951,7 +952,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     auto stage = [&](int chunk) {
         const int base = chunk * tile;
         const int len = min(tile, total - base);
-        for (int t = tid; t < len; t += kPThreads) {
+        for (int t = tid; t < len; t += NW * 32) {
             const int q = base + t;
             int lo = 0, hi = n_off - 1;  // largest o with off_prefix[o] <= q
             while (lo < hi) {
@@ -1017,9 +1018,9 @@ __global__ void __launch_bounds__(kPThreads, 2)
             }
         }
     } else {
-        const int n_rounds = (cnt + kPWarps - 1) / kPWarps;
+        const int n_rounds = (cnt + NW - 1) / NW;
         for (int round = 0; round < n_rounds; ++round) {
-            const int a = round * kPWarps + warp;
+            const int a = round * NW + warp;
             const bool active = a < cnt;
             const int i_s = c0 + a;
             const float4 ui = active ? pos4[i_s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1061,14 +1062,13 @@ __global__ void __launch_bounds__(kPThreads, 2)
         if (tid < 9) {
             float s = 0.f;
     #pragma unroll
-            for (int w = 0; w < kPWarps; ++w) s += s_vir[w][tid];
+            for (int w = 0; w < NW; ++w) s += s_vir[w][tid];
             vir_part[(size_t)slot * 9 + tid] = (double)s;
         }
-        if (MODE == kFused && warp == 0) {  // FP64 tree over the warps' energies
-            double v = lane < kPWarps ? s_e[lane] : 0.0;
-    #pragma unroll
-            for (int o = kPWarps / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0) e_part[slot] = v;
+        if (MODE == kFused && tid == 0) {  // FP64 sum over the warps' energies, fixed order
+            double v = 0.0;
+            for (int w = 0; w < NW; ++w) v += s_e[w];
+            e_part[slot] = v;
         }
     }
     }  // work items
@@ -1114,7 +1114,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
         if (tid == t) s_tw[t] = B.type_weight[t];
-    load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid);
+    load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid, kPThreads);
     const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
     for (int o = tid; o < g.n_off; o += kPThreads) {  // image offset of every list code
         const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
