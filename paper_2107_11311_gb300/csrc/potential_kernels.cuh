@@ -243,9 +243,12 @@ __device__ __forceinline__ void scan_tile(const float4 *s_pos, const int *s_idx,
 // r <= R_c: f_c = (cos(pi r / R_c) + 1) / 2, f_c' = -(pi / 2R_c) sin(pi r / R_c).
 // Recomputed where needed rather than stored per entry: the per-warp lists then
 // fit two CTAs per SM for networks up to 32 wide.
+// The argument pi r / R_c lies in [0, pi], where the hardware sine and cosine
+// (__sincosf) are accurate to ~2^-21 absolute, below the FP32 rounding of the
+// sums they enter.
 __device__ __forceinline__ void radial_cutoff(float r, float inv_rc, float &fc, float &dfc) {
     float sn, cs;
-    sincospif(r * inv_rc, &sn, &cs);
+    __sincosf(3.14159265358979f * (r * inv_rc), &sn, &cs);
     fc = 0.5f * (cs + 1.0f);
     dfc = -0.5f * 3.14159265358979f * inv_rc * sn;
 }
@@ -279,7 +282,7 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
             if (aslot < caps.ang) {
                 const float inv = 1.0f / r;
                 float sn, cs;
-                sincospif(r * inv_rca, &sn, &cs);
+                __sincosf(3.14159265358979f * (r * inv_rca), &sn, &cs);  // argument in [0, pi]
                 W.a_u[aslot] = make_float4(e.x * inv, e.y * inv, e.z * inv, 0.5f * (cs + 1.0f));
                 W.a_x[aslot] = make_float4(inv, -0.5f * 3.14159265358979f * inv_rca * sn, s_tw[W.e_j[k] >> 28],
                                            __int_as_float(k));
