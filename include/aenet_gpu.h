@@ -129,6 +129,18 @@ int aenet_compute(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t 
  */
 int aenet_set_skin(aenet_ctx *ctx, double skin);
 
+/*
+ * Thermostat for aenet_md_nve (the MD cycle of Fig. 1 takes a temperature;
+ * the paper names no thermostat, so this is the Berendsen weak coupling):
+ * at the start of every step the velocities are scaled by
+ *     lambda = sqrt(1 + (dt / tau) (T0 / T - 1)),  T = 2 E_kin / ((3N - 3) k_B),
+ * E_kin being the kinetic energy of the frame the step starts from (the one
+ * recorded in e_kin). T0 in K (>= 0), tau in ps; tau <= 0 (the default) turns
+ * it off (NVE). The factor is computed on the device by the closing reduction
+ * of each step, so steps stay asynchronous. Errors: AENET_E_ARG.
+ */
+int aenet_set_thermostat(aenet_ctx *ctx, double T0, double tau);
+
 /* Number of Verlet-list builds so far on this context (synchronises). */
 int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
 

@@ -699,10 +699,16 @@ int orc_forces_subset(const orc_model *m, int n, const double *pos, const int *t
  * v += dt/2 F/m c, with c = 9648.533212 (A/ps)^2 per eV/amu.
  * pos, vel updated in place; e_pot, e_kin [n_steps + 1] (frame 0 first).
  */
-int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *types,
-               const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
-               int n_threads, double *e_pot, double *e_kin) {
+/* Velocity Verlet; with tau > 0 the Berendsen weak-coupling thermostat: at the
+ * start of every step the velocities are scaled by
+ *     lambda = sqrt(1 + (dt / tau) (T0 / T - 1)),   T = 2 E_kin / ((3N - 3) k_B),
+ * E_kin being the kinetic energy recorded for the frame the step starts from
+ * (the paper's MD cycle takes T as an input, Fig. 1; it names no thermostat). */
+static int md_run(const orc_model *m, int n, double *pos, double *vel, const int *types,
+                  const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
+                  int n_threads, double *e_pot, double *e_kin, double T0, double tau) {
     const double c = 9648.533212;
+    const double kB = 8.617333262e-5;
     if (check_model(m) || n <= 0 || !pos || !vel || !mass_of_type || n_steps < 0) return ORC_E_ARG;
     double *F = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     if (!F) return ORC_E_NOMEM;
@@ -717,6 +723,13 @@ int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *t
         if (e_pot) e_pot[s] = E;
         if (e_kin) e_kin[s] = K;
         if (s == n_steps) break;
+        if (tau > 0.0) {
+            const int dof = 3 * n - 3 > 0 ? 3 * n - 3 : 1;
+            const double T = 2.0 * K / (dof * kB);
+            const double l2 = T > 0.0 ? 1.0 + (dt / tau) * (T0 / T - 1.0) : 1.0;
+            const double lambda = l2 > 0.0 ? sqrt(l2) : 0.0;
+            for (int q = 0; q < 3 * n; ++q) vel[q] *= lambda;
+        }
         for (int i = 0; i < n; ++i) {
             double k = 0.5 * dt * c / mass_of_type[types[i]];
             for (int a = 0; a < 3; ++a) {
@@ -733,6 +746,18 @@ int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *t
     }
     free(F);
     return err;
+}
+
+int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *types,
+               const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
+               int n_threads, double *e_pot, double *e_kin) {
+    return md_run(m, n, pos, vel, types, mass_of_type, box, dt, n_steps, mode, n_threads, e_pot, e_kin, 0.0, 0.0);
+}
+
+int orc_md_nvt(const orc_model *m, int n, double *pos, double *vel, const int *types,
+               const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
+               int n_threads, double *e_pot, double *e_kin, double T0, double tau) {
+    return md_run(m, n, pos, vel, types, mass_of_type, box, dt, n_steps, mode, n_threads, e_pot, e_kin, T0, tau);
 }
 
 /* Test hooks: the basis pieces on their own. */

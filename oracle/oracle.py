@@ -55,6 +55,8 @@ def lib():
                                            C.c_int, P, P, P]
         _lib.orc_md_nve.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, P, C.c_double,
                                     C.c_int, C.c_int, C.c_int, P, P]
+        _lib.orc_md_nvt.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, P, C.c_double,
+                                    C.c_int, C.c_int, C.c_int, P, P, C.c_double, C.c_double]
         _lib.orc_neighbour_lists.argtypes = [C.c_int, C.c_int, P, P, C.c_double, P, P, P, P]
         _lib.orc_chebyshev.argtypes = [C.c_int, C.c_double, P, P]
         _lib.orc_chebyshev.restype = None
@@ -159,8 +161,10 @@ def forces_subset(model, pos, types, box, targets, mode=CELLS, n_threads=0):
     return F, Ea
 
 
-def md_nve(model, pos, vel, types, box, dt, n_steps, mode=CELLS, n_threads=0):
-    """Velocity-Verlet NVE; returns (pos, vel, e_pot[n+1], e_kin[n+1])."""
+def md_nve(model, pos, vel, types, box, dt, n_steps, mode=CELLS, n_threads=0, thermostat=None):
+    """Velocity-Verlet NVE; returns (pos, vel, e_pot[n+1], e_kin[n+1]). With
+    thermostat = (T0 in K, tau in ps): the Berendsen thermostat (velocities
+    scaled at the start of every step, see aenet_oracle.c)."""
     pk = _Packed(model)
     pos = _f64(pos).copy()
     vel = _f64(vel).copy()
@@ -169,9 +173,14 @@ def md_nve(model, pos, vel, types, box, dt, n_steps, mode=CELLS, n_threads=0):
     mass = _f64(model.masses)
     ep = np.zeros(n_steps + 1)
     ek = np.zeros(n_steps + 1)
-    rc = lib().orc_md_nve(C.byref(pk.s), pos.shape[0], _ptr(pos), _ptr(vel), _ptr(types), _ptr(mass),
-                          _ptr(box), float(dt), int(n_steps), mode, n_threads, _ptr(ep), _ptr(ek))
-    _check(rc, "orc_md_nve")
+    if thermostat is None:
+        rc = lib().orc_md_nve(C.byref(pk.s), pos.shape[0], _ptr(pos), _ptr(vel), _ptr(types), _ptr(mass),
+                              _ptr(box), float(dt), int(n_steps), mode, n_threads, _ptr(ep), _ptr(ek))
+    else:
+        rc = lib().orc_md_nvt(C.byref(pk.s), pos.shape[0], _ptr(pos), _ptr(vel), _ptr(types), _ptr(mass),
+                              _ptr(box), float(dt), int(n_steps), mode, n_threads, _ptr(ep), _ptr(ek),
+                              float(thermostat[0]), float(thermostat[1]))
+    _check(rc, "orc_md_nvt" if thermostat is not None else "orc_md_nve")
     return pos, vel, ep, ek
 
 

@@ -67,6 +67,7 @@ def load(build_if_missing: bool = True):
     lib.aenet_batch_prepare.argtypes = [P, I, P, P, P, P, P, P, P, I]
     lib.aenet_batch_run.argtypes = [P]
     lib.aenet_set_skin.argtypes = [P, D]
+    lib.aenet_set_thermostat.argtypes = [P, D, D]
     lib.aenet_md_list_builds.argtypes = [P, P]
     lib.aenet_batch_tuning.argtypes = [P, P, P, P, P, P]
     lib.aenet_set_option.argtypes = [P, I, I]
@@ -282,6 +283,11 @@ class AenetGPU:
     def set_skin(self, skin):
         """Verlet-list skin (A) for md_nve; 0 rebuilds the cell list every step."""
         self._check(self.lib.aenet_set_skin(self.h, float(skin)))
+
+    def set_thermostat(self, T0, tau):
+        """Berendsen thermostat for md_nve: target T0 (K), coupling time tau (ps);
+        tau <= 0 turns it off (NVE)."""
+        self._check(self.lib.aenet_set_thermostat(self.h, float(T0), float(tau)))
 
     def md_list_builds(self):
         """Verlet-list builds so far on this context."""

@@ -206,6 +206,12 @@ struct Context {
     const double *last_epart = nullptr, *last_vpart = nullptr;
     int last_eparts = 0, last_vparts = 0;
 
+    // Berendsen thermostat of the MD path (tau <= 0: NVE). d_lambda holds the
+    // velocity scale of the next step, written by the closing kick.
+    double thermo_T0 = 0.0, thermo_tau = 0.0, thermo_dt = 0.0;
+    double *d_lambda = nullptr;
+    bool lambda_valid = false;         // d_lambda was computed with the current settings
+
     // Generation of the work buffers: bumped whenever one is reallocated, so a
     // captured graph (which holds their addresses) knows it must be re-captured.
     unsigned buf_gen = 0;
@@ -258,6 +264,7 @@ struct Context {
         unsigned gen = 0;
         double skin = 0.0;
         unsigned ev_mask = 0;
+        double thermo_T0 = 0.0, thermo_tau = 0.0;
     } md_key;
     unsigned ev_mask = 0;              // stage events recorded while an MD step is captured
 

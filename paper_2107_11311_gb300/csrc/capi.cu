@@ -1078,8 +1078,16 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
         }
         if (rc) return rc;
     }
-    if (want_rec)  // kinetic energy and record of frame 0 (a kick with dt = 0)
-        CK(launch_md_kick_finish(c, n, 0.0, dvel, dtypes, rec, rec + c.cap_rec), "frame 0");
+    // thermostat: the coupling factor of each step comes from the closing
+    // reductions of the step before (frame 0: the kick with dt = 0 below)
+    c.thermo_dt = dt;
+    const bool thermo = c.thermo_tau > 0.0;
+    if (thermo && !c.d_lambda) {
+        CK(cudaMalloc(&c.d_lambda, sizeof(double)), "cudaMalloc");
+        ++c.buf_gen;
+    }
+    if (want_rec || (thermo && (!cont || !c.lambda_valid)))  // kinetic energy and record of frame 0
+        CK(launch_md_kick_finish(c, n, 0.0, dvel, dtypes, rec, rec ? rec + c.cap_rec : nullptr), "frame 0");
     if (n_steps > 0) {
         const bool same = c.md_exec && c.md_key.n == n && c.md_key.pos == dpos && c.md_key.vel == dvel &&
                           c.md_key.types == dtypes && c.md_key.box[0] == box[0] && c.md_key.box[1] == box[1] &&
@@ -1087,7 +1095,8 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
                           c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
                           c.md_key.caps.ang == c.caps.ang && c.md_key.caps.tile == c.caps.tile &&
                           c.md_key.ev_mask == ev_mask && c.md_key.gen == c.buf_gen && c.md_key.skin == c.skin &&
-                          c.md_key.caps.vl_cap == c.caps.vl_cap;
+                          c.md_key.caps.vl_cap == c.caps.vl_cap && c.md_key.thermo_T0 == c.thermo_T0 &&
+                          c.md_key.thermo_tau == c.thermo_tau;
         if (!same) {
             destroy_graph(c);
             cudaGraph_t graph = nullptr;
@@ -1133,6 +1142,8 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
             c.md_key.ev_mask = ev_mask;
             c.md_key.gen = c.buf_gen;
             c.md_key.skin = c.skin;
+            c.md_key.thermo_T0 = c.thermo_T0;
+            c.md_key.thermo_tau = c.thermo_tau;
         }
         // the first step after any other evaluation (or a new list shape) builds the list
         if (verlet && (!cont || !c.vl_valid))
@@ -1140,6 +1151,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
         for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(c.md_exec, c.stream), "graph launch");
         c.maps_n = n;
         c.vl_valid = verlet;
+        c.lambda_valid = thermo;
     }
     if (want_rec) {
         if (e_pot) CK(cudaMemcpyAsync(e_pot, rec, sizeof(double) * (n_steps + 1), cudaMemcpyDefault, c.stream), "e_pot");
@@ -1245,7 +1257,7 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
                     c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres, c.d_act,
                     c.d_wpart, c.d_wpairs, c.d_dEdW, c.d_work, c.d_order, c.d_psinfo, c.d_porder,
                     c.d_vl, c.d_vl_count, c.d_vl_origin, c.d_vl_ref, c.d_vl_flag, c.d_vl_builds,
-                    c.d_vl_epart, c.d_vl_vpart};
+                    c.d_vl_epart, c.d_vl_vpart, c.d_lambda};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k <= Context::kStages; ++k)
@@ -1253,6 +1265,20 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
     if (c.aux_stream) cudaStreamDestroy(c.aux_stream);
     delete h;
+}
+
+extern "C" int aenet_set_thermostat(aenet_ctx *h, double T0, double tau) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (!isfinite(T0) || !isfinite(tau) || T0 < 0.0) return fail(&c, AENET_E_ARG, "T0 must be >= 0, tau finite");
+    if (tau <= 0.0) T0 = tau = 0.0;
+    if (T0 != c.thermo_T0 || tau != c.thermo_tau) {
+        c.thermo_T0 = T0;
+        c.thermo_tau = tau;
+        c.lambda_valid = false;
+        destroy_graph(c);
+    }
+    return AENET_OK;
 }
 
 extern "C" int aenet_set_skin(aenet_ctx *h, double skin) {

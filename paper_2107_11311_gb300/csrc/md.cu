@@ -25,6 +25,14 @@ struct KickParams {
     double hm[kMaxSpecies];
 };
 
+// Berendsen weak coupling: velocities are scaled by lambda at the start of each
+// step, lambda = sqrt(1 + dt/tau (T0/T - 1)) with T = 2 E_kin / ((3N - 3) k_B)
+// of the frame the step starts from. lambda == nullptr: NVE.
+struct Thermostat {
+    double *lambda;
+    double T0, dt_over_tau, inv_dof_kb;
+};
+
 __device__ inline double select_species(const double (&v)[kMaxSpecies], int t) {
     double r = v[0];
 #pragma unroll
@@ -97,9 +105,11 @@ __global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double 
                                     double *__restrict__ vel, const int32_t *__restrict__ types,
                                     const float4 *__restrict__ F4, const int *__restrict__ cell_start, Grid g,
                                     float4 *__restrict__ tmp4, int *__restrict__ cell_of, int *__restrict__ slot,
-                                    int *__restrict__ cell_count, unsigned *__restrict__ err) {
+                                    int *__restrict__ cell_count, unsigned *__restrict__ err,
+                                    const double *__restrict__ lambda) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double scale = lambda ? *lambda : 1.0;  // thermostat (1 for NVE)
     int t = types[i];
     if (t < 0 || t >= n_species) {
         atomicOr(err, kErrType);
@@ -111,7 +121,7 @@ __global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double 
     const float fa[3] = {f.x, f.y, f.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double v = fma(k, (double)fa[a], vel[3 * i + a]);
+        const double v = fma(k, (double)fa[a], scale * vel[3 * i + a]);
         vel[3 * i + a] = v;
         x[a] = fma(dt, v, pos[3 * i + a]);
         pos[3 * i + a] = x[a];
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(kMdThreads)
                      const double *__restrict__ vir_part, double *__restrict__ cta_part, unsigned *__restrict__ done,
                      double *__restrict__ result, int *__restrict__ step, double *__restrict__ rec_pot,
                      double *__restrict__ rec_kin, unsigned *__restrict__ vl_flag,
-                     unsigned long long *__restrict__ vl_builds) {
+                     unsigned long long *__restrict__ vl_builds, Thermostat th) {
     __shared__ double s_w[kMdThreads / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -201,6 +211,11 @@ __global__ void __launch_bounds__(kMdThreads)
             rec_kin[s] = result[10];
             *step = s + 1;
         }
+        if (th.lambda) {  // Berendsen factor of the next step, from this frame's temperature
+            const double T = 2.0 * result[10] * th.inv_dof_kb;
+            const double l2 = T > 0.0 ? 1.0 + th.dt_over_tau * (th.T0 / T - 1.0) : 1.0;
+            *th.lambda = l2 > 0.0 ? sqrt(l2) : 0.0;
+        }
     }
 }
 
@@ -218,7 +233,7 @@ __global__ void k_md_vl_kick_drift(int n, int n_species, KickParams kp, double d
                                    const int *__restrict__ slot, const double *__restrict__ origin,
                                    const double *__restrict__ ref, float4 *__restrict__ pos4,
                                    unsigned *__restrict__ flag, cudaGraphConditionalHandle cond,
-                                   unsigned *__restrict__ err) {
+                                   unsigned *__restrict__ err, const double *__restrict__ lambda) {
     __shared__ bool s_last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool moved = false;
@@ -234,9 +249,10 @@ __global__ void k_md_vl_kick_drift(int n, int n_species, KickParams kp, double d
         const float fa[3] = {f.x, f.y, f.z};
         double x[3], d2 = 0.0;
         float u[3];
+        const double scale = lambda ? *lambda : 1.0;  // thermostat (1 for NVE)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double v = fma(k, (double)fa[a], vel[3 * i + a]);
+            const double v = fma(k, (double)fa[a], scale * vel[3 * i + a]);
             vel[3 * i + a] = v;
             x[a] = fma(dt, v, pos[3 * i + a]);
             pos[3 * i + a] = x[a];
@@ -327,6 +343,19 @@ __global__ void k_batch_reduce(int n_struct, const StructInfo *__restrict__ sinf
     }
 }
 
+bool thermostat_on(const Context &c) { return c.thermo_tau > 0.0 && c.d_lambda; }
+
+Thermostat thermostat(const Context &c, int n) {
+    Thermostat th{};
+    if (!thermostat_on(c)) return th;
+    const int dof = 3 * n - 3 > 0 ? 3 * n - 3 : 1;
+    th.lambda = c.d_lambda;
+    th.T0 = c.thermo_T0;
+    th.dt_over_tau = c.thermo_dt / c.thermo_tau;
+    th.inv_dof_kb = 1.0 / (dof * 8.617333262e-5);
+    return th;
+}
+
 KickParams kick_params(const Context &c, double dt) {
     KickParams kp{};
     for (int t = 0; t < kMaxSpecies; ++t) {
@@ -373,7 +402,7 @@ cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt
     if (e != cudaSuccess || n <= 0) return e;
     k_md_kick_drift_bin<<<(n + kMdThreads - 1) / kMdThreads, kMdThreads, 0, c.stream>>>(
         n, c.basis.n_species, kick_params(c, dt), dt, pos, vel, types, c.d_F4, c.d_cell_start, g, c.d_tmp4,
-        c.d_cell_of, c.d_slot, c.d_cell_count, c.d_err);
+        c.d_cell_of, c.d_slot, c.d_cell_count, c.d_err, thermostat_on(c) ? c.d_lambda : nullptr);
     return cudaGetLastError();
 }
 
@@ -383,7 +412,7 @@ cudaError_t launch_md_kick_finish(Context &c, int n, double dt, double *vel, con
     k_md_kick_finish<<<blocks, kMdThreads, 0, c.stream>>>(
         n, kick_params(c, dt), vel, types, c.d_F4, c.d_cell_start, c.d_cell_of, c.d_slot, c.last_eparts,
         c.last_epart, c.last_vparts, c.last_vpart, c.d_ke_part, c.d_done, c.d_result, c.d_step, rec_pot, rec_kin,
-        clear_vl ? c.d_vl_flag : nullptr, c.d_vl_builds);
+        clear_vl ? c.d_vl_flag : nullptr, c.d_vl_builds, thermostat(c, n));
     return cudaGetLastError();
 }
 
@@ -393,7 +422,8 @@ cudaError_t launch_md_vl_kick_drift(Context &c, int n, double dt, double *pos, d
     const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
     k_md_vl_kick_drift<<<blocks, kMdThreads, 0, c.stream>>>(
         n, c.basis.n_species, kick_params(c, dt), dt, h * h, pos, vel, types, c.d_F4, c.d_cell_start, c.d_cell_of,
-        c.d_slot, c.d_vl_origin, c.d_vl_ref, c.d_pos4, c.d_vl_flag, cond, c.d_err);
+        c.d_slot, c.d_vl_origin, c.d_vl_ref, c.d_pos4, c.d_vl_flag, cond, c.d_err,
+        thermostat_on(c) ? c.d_lambda : nullptr);
     return cudaGetLastError();
 }
 

@@ -405,3 +405,29 @@ def test_masses_are_the_papers():
     gold = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
     assert inputs.MASS_H == gold["mass_H_amu"]["value"]
     assert inputs.MASS_O == gold["mass_O_amu"]["value"]
+
+
+def test_berendsen_thermostat_closed_forms():
+    """The thermostat (velocities scaled by sqrt(1 + dt/tau (T0/T - 1)) at the
+    start of every step): a coupling time far beyond the run reproduces NVE
+    exactly; with tau = dt and no forces (two atoms farther apart than every
+    cutoff) one step sets the kinetic energy to (3N - 3) k_B T0 / 2 exactly."""
+    m = inputs.make_model("water")
+    st = inputs.water(8, 6.6, seed=3)
+    v = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=5)
+    a = O.md_nve(m, st.pos, v, st.types, st.box, 5e-4, 5)
+    b = O.md_nve(m, st.pos, v, st.types, st.box, 5e-4, 5, thermostat=(1000.0, 1e30))
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    pos = np.array([[10.0, 10.0, 10.0], [60.0, 60.0, 60.0]])
+    types = np.array([0, 1], dtype=np.int32)
+    vel = np.array([[1.0, -2.0, 0.5], [-0.3, 0.7, 1.1]])
+    box = np.full(3, 100.0)
+    T0, dt = 450.0, 5e-4
+    _, v1, ep, ek = O.md_nve(m, pos, vel, types, box, dt, 2, thermostat=(T0, dt))
+    kB = 8.617333262e-5
+    assert ek[1] == pytest.approx(1.5 * kB * T0, rel=1e-12)
+    assert ek[2] == pytest.approx(1.5 * kB * T0, rel=1e-12)
+    assert ep[0] == ep[1] == ep[2]
+    # the scaling is uniform: the velocity directions are kept
+    np.testing.assert_allclose(v1 / np.linalg.norm(v1), vel / np.linalg.norm(vel), rtol=1e-12)
