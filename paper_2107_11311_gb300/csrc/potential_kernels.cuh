@@ -265,13 +265,18 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
         const int k = base + lane;
         bool ina = false;
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        float r = 0.f;
+        float r = 0.f, inv = 0.f;
         if (k < nnb) {
             e = W.e_d[k];
-            r = sqrtf(e.w);
-            if (r < 1e-6f) {
+            // r and 1/r from one reciprocal square root (a few ulp, far below the
+            // cutoff-function and descriptor error budget)
+            if (e.w < 1e-12f) {  // r < 1e-6 A
                 atomicOr(err, kErrOverlap);
                 r = 1e-6f;
+                inv = 1e6f;
+            } else {
+                inv = rsqrtf(e.w);
+                r = e.w * inv;
             }
             W.e_d[k].w = r;
             ina = r <= B.rc_ang;
@@ -280,7 +285,6 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
         if (ina) {
             const int aslot = nang + __popc(ma & lt_mask);
             if (aslot < caps.ang) {
-                const float inv = 1.0f / r;
                 float sn, cs;
                 __sincosf(3.14159265358979f * (r * inv_rca), &sn, &cs);  // argument in [0, pi]
                 W.a_u[aslot] = make_float4(e.x * inv, e.y * inv, e.z * inv, 0.5f * (cs + 1.0f));
@@ -684,7 +688,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
                     u = un;
                 }
             }
-            const float gr = __fdiv_rn(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
+            const float gr = __fdividef(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
             fx = -gr * e.x;
             fy = -gr * e.y;
             fz = -gr * e.z;
