@@ -405,6 +405,32 @@ __device__ __forceinline__ int rotation_source(bool diag, int it, int nA, int la
     return (lane - it) & 31;
 }
 
+// S(x) = sum_q a_q T_q(x) and S'(x) = sum_q a_q T_q'(x), a_q = a0[q] + w a1[q],
+// by Clenshaw's recurrence b_q = a_q + 2x b_{q+1} - b_{q+2} (S = a_0 + x b_1 -
+// b_2) and its derivative b'_q = 2 b_{q+1} + 2x b'_{q+1} - b'_{q+2} (S' = b_1 +
+// x b'_1 - b'_2): five operations per order instead of the six or seven of the
+// forward T and U recurrences.
+template <int KT>
+__device__ __forceinline__ void clenshaw_d(float x, float w, const float (&a0)[KT], const float (&a1)[KT], int K,
+                                           float &S, float &dS) {
+    float b1 = 0.f, b2 = 0.f, d1 = 0.f, d2 = 0.f;
+    const float x2 = 2.0f * x;
+#pragma unroll
+    for (int q = KT - 1; q >= 1; --q) {
+        if (q < K) {
+            const float a = fmaf(w, a1[q], a0[q]);
+            const float b = fmaf(x2, b1, a - b2);
+            const float d = fmaf(x2, d1, fmaf(2.0f, b1, -d2));
+            b2 = b1;
+            b1 = b;
+            d2 = d1;
+            d1 = d;
+        }
+    }
+    S = fmaf(x, b1, fmaf(w, a1[0], a0[0]) - b2);
+    dS = fmaf(x, d1, b1 - d2);
+}
+
 // Chain rule through one angular term T(cos th) f_c(r_j) f_c(r_k) weighted by
 // b_q = ca_q + (s_j s_k) caw_q: adds dE/dd_j to (jx, jy, jz) and returns dE/dd_k
 // in (gx, gy, gz); nothing when v is false (uk, xk then hold any valid entry).
@@ -415,23 +441,8 @@ __device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj
                                               float &jx, float &jy, float &jz, float &gx, float &gy, float &gz) {
     const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
     const float w = xj.z * xk.z;
-    float S = fmaf(w, caw[0], ca[0]);
-    float dS = 0.f;
-    float tm1 = 1.0f, tt = c, um1 = 0.0f, u = 1.0f;
-#pragma unroll
-    for (int q = 1; q < KAT; ++q) {
-        if (q < Ka) {
-            const float b = fmaf(w, caw[q], ca[q]);
-            S = fmaf(b, tt, S);
-            dS = fmaf(b * (float)q, u, dS);
-            const float tn = fmaf(2.0f * c, tt, -tm1);
-            tm1 = tt;
-            tt = tn;
-            const float un = fmaf(2.0f * c, u, -um1);
-            um1 = u;
-            u = un;
-        }
-    }
+    float S, dS;  // sum_q b_q T_q(c) and sum_q b_q T_q'(c), b_q = ca_q + w caw_q
+    clenshaw_d<KAT>(c, w, ca, caw, Ka, S, dS);
     const float fj = uj.w, fk = uk.w;
     const float Af = v ? dS * fj * fk : 0.f;
     const float Aj = Af * xj.x, Ak = Af * xk.x;
@@ -671,23 +682,11 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
             radial_cutoff(e.w, inv_rcr, fc, dfc);
             const float s = s_tw[W.e_j[k] >> 28];
             const float x = 2.0f * e.w * inv_rcr - 1.0f;
-            // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c',  T_q' = q U_{q-1}
-            float dEdr = (cr[0] + s * crw[0]) * dfc;
-            float tm1 = 1.0f, tt = x, um1 = 0.0f, u = 1.0f;
-            const float k2fc = k2 * fc;
-#pragma unroll
-            for (int q = 1; q < KRT; ++q) {
-                if (q < Kr) {
-                    const float coef = fmaf(s, crw[q], cr[q]);
-                    dEdr = fmaf(coef, fmaf((float)q * u, k2fc, tt * dfc), dEdr);
-                    const float tn = fmaf(2.0f * x, tt, -tm1);
-                    tm1 = tt;
-                    tt = tn;
-                    const float un = fmaf(2.0f * x, u, -um1);
-                    um1 = u;
-                    u = un;
-                }
-            }
+            // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c', summed over q with
+            // the coefficients cr_q + s crw_q
+            float S, dS;
+            clenshaw_d<KRT>(x, s, cr, crw, Kr, S, dS);
+            const float dEdr = fmaf(dS, k2 * fc, S * dfc);
             const float gr = __fdividef(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
             fx = -gr * e.x;
             fy = -gr * e.y;
