@@ -45,7 +45,8 @@ DT_PS = 5e-4
 # arithmetic each unit needs (recurrences for T_a and U_a, coefficient
 # combination, chain rule, force scatter and virial); derivation in the design doc.
 def force_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
-    return (13 * (Kr - 1) + 38) * n_entries + (11 * (Ka - 1) + 52) * n_ang_pairs
+    """Chain rule with Clenshaw's recurrence for S and S' (9 flops per order)."""
+    return (9 * (Kr - 1) + 42) * n_entries + (9 * (Ka - 1) + 57) * n_ang_pairs
 
 
 def descriptor_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
