@@ -840,8 +840,10 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     const int tile = caps.tile;
     // one layout for every cell: sized for the largest image-offset table
     // (g_one.n_off is that maximum in a batch)
-    const PLayout L = make_playout(g_one.n_off, tile, caps.nb, caps.ang, MODE == kFused ? B.n_species : 0,
-                                   net.stride, NW);
+    // (the list-build form keeps no per-warp lists: its CTAs are small)
+    constexpr bool kLists = MODE != kBuildList;
+    const PLayout L = make_playout(g_one.n_off, tile, kLists ? caps.nb : 0, kLists ? caps.ang : 0,
+                                   MODE == kFused ? B.n_species : 0, net.stride, NW);
     int *off_start = reinterpret_cast<int *>(smem + L.off_start);
     int *off_count = reinterpret_cast<int *>(smem + L.off_count);
     int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);

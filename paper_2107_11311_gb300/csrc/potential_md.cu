@@ -12,7 +12,7 @@ using namespace detail;
 
 template <int KRT, int KAT, bool EXACT>
 cudaError_t launch_build(Context &c, const Grid &g) {
-    const size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, 0, 0).total;
+    const size_t smem = make_playout(g.n_off, c.caps.tile, 0, 0, 0, 0).total;  // no per-warp lists
     auto kern = k_potential<KRT, KAT, EXACT, kBuildList, false, 32>;
     cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
