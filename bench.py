@@ -58,11 +58,11 @@ def network_flops(widths, n_atoms):
     return 4 * sum(widths[l] * widths[l - 1] for l in range(1, len(widths))) * n_atoms
 
 
-# DRAM bytes per launch of the dominant kernel, from the ncu capture summarised in
-# profiles/k_potential_water_12288.md; reported only while the kernel source is the
+# DRAM bytes per launch of the dominant kernel, from the ncu captures summarised in
+# profiles/k_potential_<workload>.md; reported only while the kernel source is the
 # one the counters were taken on (first 16 hex digits of its SHA-256).
-TRAFFIC_CAPTURE = {"workload": "water_12288", "precision": "fp32", "source_sha256_16": "c46af5179266da81",
-                   "bytes": 524032}
+TRAFFIC_SOURCE_SHA256_16 = "a502f65dbc8664b2"
+TRAFFIC_CAPTURE = {("water_12288", "fp32"): 521984, ("amorphous_27000", "fp32"): 1075200}
 
 
 def captured_traffic(workload_name, precision, skin=0.0):
@@ -70,11 +70,9 @@ def captured_traffic(workload_name, precision, skin=0.0):
     src = os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", "potential_kernels.cuh")
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    c = TRAFFIC_CAPTURE
-    if (workload_name == c["workload"] and precision == c["precision"] and sha == c["source_sha256_16"]
-            and skin == 0.0):
-        return c["bytes"]
-    return None
+    if sha != TRAFFIC_SOURCE_SHA256_16 or skin != 0.0:
+        return None
+    return TRAFFIC_CAPTURE.get((workload_name, precision))
 
 
 def max_over_ranks(value, world):
