@@ -125,6 +125,36 @@ def test_full_size_water_12288(gpu_mod):
     _check_efw(ref, got, st.n, "water_12288")
 
 
+def test_water_20736_split_tail(gpu_mod):
+    """A 20,736-atom water box (729 cells, 2.4 waves of persistent CTAs with the
+    last wave's cells split in halves): every output against the oracle, and two
+    MD steps against the oracle's own integration."""
+    st = inputs.water(6912, None, 10)
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    got = g.compute(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, got, st.n, "water_20736")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=5)
+    xo, vo, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 2)
+    pos, vel = st.pos.copy(), v0.copy()
+    ep, ek = np.zeros(3), np.zeros(3)
+    g.md_nve(pos, vel, st.types, st.box, 5e-4, 2, e_pot=ep, e_kin=ek)
+    assert np.abs(ep - epo).max() / st.n <= E_TOL
+    np.testing.assert_allclose(ek, eko, rtol=1e-5)
+    np.testing.assert_allclose(pos, xo, atol=1e-5)
+
+
+def test_water_98304_many_waves(gpu_mod):
+    """98,304 atoms (4,096 cells, 13 waves of persistent CTAs): every output
+    against the oracle."""
+    st = inputs.water(32768, None, 10)
+    m = inputs.make_model("water")
+    got = gpu_mod.AenetGPU(m, "fp32").compute(st.pos, st.types, st.box)
+    ref = O.compute(m, st.pos, st.types, st.box)
+    _check_efw(ref, got, st.n, "water_98304")
+
+
 def test_full_size_amorphous_27000(gpu_mod):
     st = inputs.amorphous_27000()
     m = inputs.make_model("amorphous")
