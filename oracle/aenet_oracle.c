@@ -24,6 +24,11 @@
  *   - dE/dW, dE/db (back-propagation, Sec. II.C) summed over atoms;
  *   - velocity-Verlet NVE integration in metal units.
  *
+ * Periodic boxes: orthorhombic (edges L_x, L_y, L_z), or the restricted
+ * triclinic cell of the MD codes the paper plugs into (LAMMPS): lattice vectors
+ * a = (L_x, 0, 0), b = (xy, L_y, 0), c = (xz, yz, L_z). A tilted cell is handled
+ * by brute force over lattice images only: x_j + n_a a + n_b b + n_c c.
+ *
  * Derivative identities used (not printed in the paper, derived here):
  *   dT_n/dx = n U_{n-1}(x), U_0 = 1, U_1 = 2x, U_{n+1} = 2x U_n - U_{n-1};
  *   df_c/dr = -(pi / (2 R_c)) sin(pi r / R_c) for r <= R_c, else 0;
@@ -109,6 +114,49 @@ static double wrap1(double x, double L) {
     if (w >= L) w -= L;
     if (w < 0.0) w = 0.0;
     return w;
+}
+
+/* A periodic box: edges L (the diagonal of the cell matrix) and the tilt
+ * factors xy, xz, yz of the restricted triclinic form; tilted = any tilt != 0. */
+typedef struct {
+    double L[3];
+    double xy, xz, yz;
+    int tilted;
+} orc_box;
+
+static orc_box box_of(const double *box, const double *tilt) {
+    orc_box B;
+    for (int a = 0; a < 3; ++a) B.L[a] = box[a];
+    B.xy = tilt ? tilt[0] : 0.0;
+    B.xz = tilt ? tilt[1] : 0.0;
+    B.yz = tilt ? tilt[2] : 0.0;
+    B.tilted = B.xy != 0.0 || B.xz != 0.0 || B.yz != 0.0;
+    return B;
+}
+
+/* Fractional coordinates s of x = H s, H upper triangular with columns a, b, c
+ * (back substitution). */
+static void to_fractional(const orc_box *B, const double *x, double *s) {
+    s[2] = x[2] / B->L[2];
+    s[1] = (x[1] - B->yz * s[2]) / B->L[1];
+    s[0] = (x[0] - B->xy * s[1] - B->xz * s[2]) / B->L[0];
+}
+
+static void from_fractional(const orc_box *B, const double *s, double *x) {
+    x[0] = B->L[0] * s[0] + B->xy * s[1] + B->xz * s[2];
+    x[1] = B->L[1] * s[1] + B->yz * s[2];
+    x[2] = B->L[2] * s[2];
+}
+
+/* Distance between the two lattice planes bounding the cell along each lattice
+ * direction: volume / area of the face spanned by the other two vectors. */
+static void plane_widths(const orc_box *B, double *w) {
+    const double V = B->L[0] * B->L[1] * B->L[2];
+    const double bc[3] = {B->L[1] * B->L[2], -B->xy * B->L[2], B->xy * B->yz - B->L[1] * B->xz}; /* b x c */
+    const double ca[3] = {0.0, B->L[2] * B->L[0], -B->yz * B->L[0]};                           /* c x a */
+    w[0] = V / sqrt(bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+    w[1] = V / sqrt(ca[0] * ca[0] + ca[1] * ca[1] + ca[2] * ca[2]);
+    w[2] = B->L[2]; /* a x b = (0, 0, L_x L_y) */
 }
 
 typedef struct {
@@ -219,6 +267,44 @@ static int neighbours_brute(int i, int n, const double *wpos, const double *box,
     return ORC_OK;
 }
 
+/* Brute force in a tilted cell: every atom j and every lattice image
+ * n = (n_a, n_b, n_c) with |x_j + n_a a + n_b b + n_c c - x_i| <= rc, except
+ * (j = i, n = 0). A displacement with fractional coordinates f has length at
+ * least |f_a| times the plane width along a, so |f_a| <= rc / width_a bounds
+ * the images (widened by one on each side; the distance test decides). */
+static int neighbours_brute_tri(int i, int n, const double *wpos, const orc_box *B, double rc, nb_buf *out) {
+    out->n = 0;
+    const double rc2 = rc * rc;
+    double w[3];
+    plane_widths(B, w);
+    const double A[3][3] = {{B->L[0], 0.0, 0.0}, {B->xy, B->L[1], 0.0}, {B->xz, B->yz, B->L[2]}}; /* a, b, c */
+    for (int j = 0; j < n; ++j) {
+        double del[3], f[3];
+        int lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) del[a] = wpos[3 * j + a] - wpos[3 * i + a];
+        to_fractional(B, del, f);
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (int)ceil(-rc / w[a] - f[a]) - 1;
+            hi[a] = (int)floor(rc / w[a] - f[a]) + 1;
+        }
+        int img[3];
+        for (img[0] = lo[0]; img[0] <= hi[0]; ++img[0])
+            for (img[1] = lo[1]; img[1] <= hi[1]; ++img[1])
+                for (img[2] = lo[2]; img[2] <= hi[2]; ++img[2]) {
+                    if (j == i && img[0] == 0 && img[1] == 0 && img[2] == 0) continue;
+                    double d[3], r2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = del[a] + img[0] * A[0][a] + img[1] * A[1][a] + img[2] * A[2][a];
+                        r2 += d[a] * d[a];
+                    }
+                    if (r2 > rc2) continue;
+                    int e = nb_push(out, j, img, d, sqrt(r2));
+                    if (e) return e;
+                }
+    }
+    return ORC_OK;
+}
+
 /* Cell list: cells of edge h >= rc (or one cell per axis), scanned over cell
  * offsets -m..m with m = ceil(rc / h); the image index of the neighbour cell
  * follows from floor division of the unwrapped cell index. */
@@ -265,6 +351,20 @@ static double *wrapped_copy(int n, const double *pos, const double *box) {
     if (!w) return NULL;
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < 3; ++a) w[3 * i + a] = wrap1(pos[3 * i + a], box[a]);
+    return w;
+}
+
+/* Positions wrapped into the cell: each fractional coordinate into [0, 1). */
+static double *wrapped_copy_box(int n, const double *pos, const orc_box *B) {
+    if (!B->tilted) return wrapped_copy(n, pos, B->L);
+    double *w = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    if (!w) return NULL;
+    for (int i = 0; i < n; ++i) {
+        double s[3];
+        to_fractional(B, pos + 3 * i, s);
+        for (int a = 0; a < 3; ++a) s[a] = wrap1(s[a], 1.0);
+        from_fractional(B, s, w + 3 * i);
+    }
     return w;
 }
 
@@ -517,24 +617,27 @@ static int check_model(const orc_model *m) {
 
 /*
  * Energy, forces, virial (and optionally per-atom energies, G, dE/dG, dE/dW)
- * of one periodic orthorhombic structure.
+ * of one periodic structure (orthorhombic, or a tilted restricted triclinic cell).
  *   mode        0 = brute-force neighbours, 1 = cell list
  *   center_mask NULL = every atom is a centre; else only atoms with mask != 0
  *               contribute E_i (and their force / virial terms)
  *   outputs     any may be NULL; forces [n*3], virial [9] row-major,
  *               e_atom [n], G and dEdG [n*D], dEdW [n_species*n_params]
  */
-int orc_compute(const orc_model *m, int n, const double *pos, const int *types, const double *box,
-                int mode, int n_threads, const unsigned char *center_mask, double *energy, double *e_atom,
-                double *forces, double *virial, double *G_out, double *dEdG_out, double *dEdW) {
-    if (check_model(m) || n < 0 || (n > 0 && (!pos || !types)) || !box) return ORC_E_ARG;
+static int compute_box(const orc_model *m, int n, const double *pos, const int *types, const orc_box *B,
+                       int mode, int n_threads, const unsigned char *center_mask, double *energy, double *e_atom,
+                       double *forces, double *virial, double *G_out, double *dEdG_out, double *dEdW) {
+    if (check_model(m) || n < 0 || (n > 0 && (!pos || !types))) return ORC_E_ARG;
     for (int a = 0; a < 3; ++a)
-        if (!(box[a] > 0.0)) return ORC_E_ARG;
+        if (!(B->L[a] > 0.0)) return ORC_E_ARG;
+    if (!isfinite(B->xy) || !isfinite(B->xz) || !isfinite(B->yz)) return ORC_E_ARG;
     for (int i = 0; i < n; ++i)
         if (types[i] < 0 || types[i] >= m->n_species) return ORC_E_ARG;
+    if (B->tilted) mode = 0; /* tilted cells: brute force only */
+    const double *box = B->L;
     const int D = orc_D(m), NP = orc_nparams(m);
     const double rc = m->rc_rad > m->rc_ang ? m->rc_rad : m->rc_ang;
-    double *w = wrapped_copy(n, pos, box);
+    double *w = wrapped_copy_box(n, pos, B);
     if (!w) return ORC_E_NOMEM;
     orc_cells cells = {0};
     if (mode == 1 && cells_build(&cells, n, w, box, rc)) {
@@ -570,7 +673,8 @@ int orc_compute(const orc_model *m, int n, const double *pos, const int *types, 
                 if (e_atom) e_atom[i] = 0.0;
                 continue;
             }
-            int e = (mode == 1) ? neighbours_cells(i, w, box, rc, &cells, &wk.nb)
+            int e = (mode == 1)  ? neighbours_cells(i, w, box, rc, &cells, &wk.nb)
+                    : B->tilted ? neighbours_brute_tri(i, n, w, B, rc, &wk.nb)
                                 : neighbours_brute(i, n, w, box, rc, &wk.nb);
             if (e) {
                 lerr = e;
@@ -647,6 +751,26 @@ int orc_compute(const orc_model *m, int n, const double *pos, const int *types, 
     return err;
 }
 
+int orc_compute(const orc_model *m, int n, const double *pos, const int *types, const double *box,
+                int mode, int n_threads, const unsigned char *center_mask, double *energy, double *e_atom,
+                double *forces, double *virial, double *G_out, double *dEdG_out, double *dEdW) {
+    if (!box) return ORC_E_ARG;
+    const orc_box B = box_of(box, NULL);
+    return compute_box(m, n, pos, types, &B, mode, n_threads, center_mask, energy, e_atom, forces, virial, G_out,
+                       dEdG_out, dEdW);
+}
+
+/* The same in a restricted triclinic cell: box = (L_x, L_y, L_z), tilt =
+ * (xy, xz, yz); a tilted cell is evaluated by brute force whatever the mode. */
+int orc_compute_tri(const orc_model *m, int n, const double *pos, const int *types, const double *box,
+                    const double *tilt, int mode, int n_threads, double *energy, double *e_atom, double *forces,
+                    double *virial, double *G_out) {
+    if (!box || !tilt) return ORC_E_ARG;
+    const orc_box B = box_of(box, tilt);
+    return compute_box(m, n, pos, types, &B, mode, n_threads, NULL, energy, e_atom, forces, virial, G_out, NULL,
+                       NULL);
+}
+
 /* Forces on a few target atoms only: every atom within the largest cutoff of a
  * target (any image) is a centre; the rest are skipped. */
 int orc_forces_subset(const orc_model *m, int n, const double *pos, const int *types, const double *box,
@@ -705,7 +829,7 @@ int orc_forces_subset(const orc_model *m, int n, const double *pos, const int *t
  * E_kin being the kinetic energy recorded for the frame the step starts from
  * (the paper's MD cycle takes T as an input, Fig. 1; it names no thermostat). */
 static int md_run(const orc_model *m, int n, double *pos, double *vel, const int *types,
-                  const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
+                  const double *mass_of_type, const orc_box *box, double dt, int n_steps, int mode,
                   int n_threads, double *e_pot, double *e_kin, double T0, double tau) {
     const double c = 9648.533212;
     const double kB = 8.617333262e-5;
@@ -713,7 +837,7 @@ static int md_run(const orc_model *m, int n, double *pos, double *vel, const int
     double *F = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     if (!F) return ORC_E_NOMEM;
     double E = 0.0;
-    int err = orc_compute(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
+    int err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
     for (int s = 0; s <= n_steps && !err; ++s) {
         double K = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -737,7 +861,7 @@ static int md_run(const orc_model *m, int n, double *pos, double *vel, const int
                 pos[3 * i + a] += dt * vel[3 * i + a];
             }
         }
-        err = orc_compute(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
+        err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
         if (err) break;
         for (int i = 0; i < n; ++i) {
             double k = 0.5 * dt * c / mass_of_type[types[i]];
@@ -751,13 +875,27 @@ static int md_run(const orc_model *m, int n, double *pos, double *vel, const int
 int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *types,
                const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
                int n_threads, double *e_pot, double *e_kin) {
-    return md_run(m, n, pos, vel, types, mass_of_type, box, dt, n_steps, mode, n_threads, e_pot, e_kin, 0.0, 0.0);
+    if (!box) return ORC_E_ARG;
+    const orc_box B = box_of(box, NULL);
+    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, mode, n_threads, e_pot, e_kin, 0.0, 0.0);
 }
 
 int orc_md_nvt(const orc_model *m, int n, double *pos, double *vel, const int *types,
                const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
                int n_threads, double *e_pot, double *e_kin, double T0, double tau) {
-    return md_run(m, n, pos, vel, types, mass_of_type, box, dt, n_steps, mode, n_threads, e_pot, e_kin, T0, tau);
+    if (!box) return ORC_E_ARG;
+    const orc_box B = box_of(box, NULL);
+    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, mode, n_threads, e_pot, e_kin, T0, tau);
+}
+
+/* Velocity Verlet (tau > 0: with the Berendsen thermostat) in a restricted
+ * triclinic cell: box = (L_x, L_y, L_z), tilt = (xy, xz, yz). */
+int orc_md_tri(const orc_model *m, int n, double *pos, double *vel, const int *types, const double *mass_of_type,
+               const double *box, const double *tilt, double dt, int n_steps, int n_threads, double *e_pot,
+               double *e_kin, double T0, double tau) {
+    if (!box || !tilt) return ORC_E_ARG;
+    const orc_box B = box_of(box, tilt);
+    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, 0, n_threads, e_pot, e_kin, T0, tau);
 }
 
 /* Test hooks: the basis pieces on their own. */

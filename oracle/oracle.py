@@ -57,6 +57,10 @@ def lib():
                                     C.c_int, C.c_int, C.c_int, P, P]
         _lib.orc_md_nvt.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, P, C.c_double,
                                     C.c_int, C.c_int, C.c_int, P, P, C.c_double, C.c_double]
+        _lib.orc_compute_tri.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, C.c_int, C.c_int,
+                                         P, P, P, P, P]
+        _lib.orc_md_tri.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, P, P, C.c_double, C.c_int,
+                                    C.c_int, P, P, C.c_double, C.c_double]
         _lib.orc_neighbour_lists.argtypes = [C.c_int, C.c_int, P, P, C.c_double, P, P, P, P]
         _lib.orc_chebyshev.argtypes = [C.c_int, C.c_double, P, P]
         _lib.orc_chebyshev.restype = None
@@ -144,6 +148,50 @@ def compute(model, pos, types, box, mode=CELLS, n_threads=0, center_mask=None,
     if want_dEdW:
         out["dEdW"] = dW
     return out
+
+
+def compute_tri(model, pos, types, box, tilt, n_threads=0, want_G=False):
+    """Energy, forces, virial, per-atom energies (and optionally G) of one
+    structure in the restricted triclinic cell a = (L_x, 0, 0), b = (xy, L_y, 0),
+    c = (xz, yz, L_z): box = (L_x, L_y, L_z), tilt = (xy, xz, yz). Brute-force
+    lattice images (zero tilt takes the orthorhombic brute-force path)."""
+    pk = _Packed(model)
+    pos = _f64(pos)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    box = _f64(box)
+    tilt = _f64(tilt)
+    n = pos.shape[0]
+    e = np.zeros(1)
+    ea = np.zeros(n)
+    F = np.zeros((n, 3))
+    W = np.zeros((3, 3))
+    G = np.zeros((n, model.widths[0])) if want_G else None
+    rc = lib().orc_compute_tri(C.byref(pk.s), n, _ptr(pos), _ptr(types), _ptr(box), _ptr(tilt), BRUTE,
+                               n_threads, _ptr(e), _ptr(ea), _ptr(F), _ptr(W), _ptr(G))
+    _check(rc, "orc_compute_tri")
+    out = dict(energy=float(e[0]), e_atom=ea, forces=F, virial=W)
+    if want_G:
+        out["G"] = G
+    return out
+
+
+def md_tri(model, pos, vel, types, box, tilt, dt, n_steps, n_threads=0, thermostat=None):
+    """Velocity Verlet (optionally Berendsen) in a restricted triclinic cell;
+    returns (pos, vel, e_pot[n+1], e_kin[n+1])."""
+    pk = _Packed(model)
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    box = _f64(box)
+    tilt = _f64(tilt)
+    mass = _f64(model.masses)
+    ep = np.zeros(n_steps + 1)
+    ek = np.zeros(n_steps + 1)
+    T0, tau = (0.0, 0.0) if thermostat is None else (float(thermostat[0]), float(thermostat[1]))
+    rc = lib().orc_md_tri(C.byref(pk.s), pos.shape[0], _ptr(pos), _ptr(vel), _ptr(types), _ptr(mass),
+                          _ptr(box), _ptr(tilt), float(dt), int(n_steps), n_threads, _ptr(ep), _ptr(ek), T0, tau)
+    _check(rc, "orc_md_tri")
+    return pos, vel, ep, ek
 
 
 def forces_subset(model, pos, types, box, targets, mode=CELLS, n_threads=0):

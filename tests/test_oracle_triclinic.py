@@ -1,0 +1,136 @@
+"""Pins of the oracle's restricted triclinic cell (a = (L_x, 0, 0),
+b = (xy, L_y, 0), c = (xz, yz, L_z), the box form of the MD codes the paper
+plugs into): checks that hold for any correct periodic evaluation, none of
+which reuses the tilted code path on both sides.
+
+* integer tilts (multiples of the edges) describe the same lattice as the
+  orthorhombic box: equal to the orthorhombic cell-list oracle;
+* a supercell doubled along a, b or c of a tilted cell has twice the energy and
+  virial and the same per-atom energies and forces on every copy;
+* forces are minus the finite-difference gradient of the energy;
+* the virial is minus the derivative of the energy under a homogeneous strain
+  of positions and cell (upper-triangular strains keep the restricted form).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2107_11311_gb300 import inputs
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+
+def _cell_matrix(box, tilt):
+    """Columns a, b, c."""
+    lx, ly, lz = box
+    xy, xz, yz = tilt
+    return np.array([[lx, xy, xz], [0.0, ly, yz], [0.0, 0.0, lz]])
+
+
+def _tilted(st, tilt):
+    """The structure's fractional coordinates placed in the tilted cell."""
+    H = _cell_matrix(st.box, tilt)
+    frac = st.pos / np.asarray(st.box)
+    return frac @ H.T
+
+
+def _water():
+    return inputs.water_192(), inputs.make_model("water")
+
+
+def _amorphous():
+    st = inputs.amorphous(96, seed=5)
+    return st, inputs.make_model("amorphous")
+
+
+@pytest.mark.parametrize("family", ["water", "amorphous"])
+@pytest.mark.parametrize("k", [(1, 0, 0), (0, 1, -1), (2, -1, 1)])
+def test_integer_tilts_are_the_orthorhombic_lattice(family, k):
+    st, m = _water() if family == "water" else _amorphous()
+    L = np.asarray(st.box)
+    tilt = (k[0] * L[0], k[1] * L[0], k[2] * L[1])  # b + k0 a, c + k1 a + k2 b
+    ref = O.compute(m, st.pos, st.types, st.box, mode=O.CELLS)
+    got = O.compute_tri(m, st.pos, st.types, st.box, tilt)
+    assert abs(got["energy"] - ref["energy"]) < 1e-9 * st.n
+    np.testing.assert_allclose(got["forces"], ref["forces"], atol=1e-9)
+    np.testing.assert_allclose(got["e_atom"], ref["e_atom"], atol=1e-10)
+    np.testing.assert_allclose(got["virial"], ref["virial"], atol=1e-8)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_supercell_of_a_tilted_cell(axis):
+    st, m = _amorphous()
+    tilt = (0.31 * st.box[0], -0.22 * st.box[0], 0.17 * st.box[1])
+    pos = _tilted(st, tilt)
+    one = O.compute_tri(m, pos, st.types, st.box, tilt)
+    H = _cell_matrix(st.box, tilt)
+    H2 = H.copy()
+    H2[:, axis] *= 2.0  # the lattice vector along `axis` doubled
+    pos2 = np.vstack([pos, pos + H[:, axis]])
+    types2 = np.concatenate([st.types, st.types])
+    box2 = (H2[0, 0], H2[1, 1], H2[2, 2])
+    tilt2 = (H2[0, 1], H2[0, 2], H2[1, 2])
+    two = O.compute_tri(m, pos2, types2, box2, tilt2)
+    assert abs(two["energy"] - 2.0 * one["energy"]) < 1e-9 * st.n
+    np.testing.assert_allclose(two["virial"], 2.0 * one["virial"], atol=1e-8)
+    for half in (slice(0, st.n), slice(st.n, 2 * st.n)):
+        np.testing.assert_allclose(two["forces"][half], one["forces"], atol=1e-9)
+        np.testing.assert_allclose(two["e_atom"][half], one["e_atom"], atol=1e-10)
+
+
+def test_tilted_cell_is_not_the_orthorhombic_one():
+    """A non-integer tilt changes the lattice, hence the energy (the test above
+    would pass for an oracle that ignored the tilt only if this one failed)."""
+    st, m = _amorphous()
+    tilt = (0.31 * st.box[0], 0.0, 0.0)
+    a = O.compute_tri(m, st.pos, st.types, st.box, tilt)
+    b = O.compute(m, st.pos, st.types, st.box)
+    assert abs(a["energy"] - b["energy"]) > 1e-3
+
+
+def test_forces_are_the_energy_gradient_in_a_tilted_cell():
+    st, m = _water()
+    tilt = (0.4 * st.box[0], 0.25 * st.box[0], -0.3 * st.box[1])
+    pos = _tilted(st, tilt)
+    F = O.compute_tri(m, pos, st.types, st.box, tilt)["forces"]
+    h = 1e-5
+    rng = np.random.default_rng(3)
+    for i in rng.choice(st.n, 6, replace=False):
+        for a in range(3):
+            p = pos.copy()
+            p[i, a] += h
+            ep = O.compute_tri(m, p, st.types, st.box, tilt)["energy"]
+            p[i, a] -= 2 * h
+            em = O.compute_tri(m, p, st.types, st.box, tilt)["energy"]
+            fd = -(ep - em) / (2 * h)
+            assert abs(fd - F[i, a]) < 1e-6 * max(1.0, abs(F[i, a])), (i, a, fd, F[i, a])
+
+
+@pytest.mark.parametrize("ab", [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)])
+def test_virial_is_the_strain_derivative_in_a_tilted_cell(ab):
+    st, m = _amorphous()
+    tilt = (0.31 * st.box[0], -0.22 * st.box[0], 0.17 * st.box[1])
+    pos = _tilted(st, tilt)
+    H = _cell_matrix(st.box, tilt)
+    W = O.compute_tri(m, pos, st.types, st.box, tilt)["virial"]
+    np.testing.assert_allclose(W, W.T, atol=1e-8 * max(1.0, np.abs(W).max()))
+    a, b = ab
+    h = 1e-6
+
+    def energy(eps):
+        S = np.eye(3)
+        S[a, b] += eps
+        H2 = S @ H  # stays upper triangular for a <= b
+        return O.compute_tri(m, pos @ S.T, st.types, (H2[0, 0], H2[1, 1], H2[2, 2]),
+                             (H2[0, 1], H2[0, 2], H2[1, 2]))["energy"]
+
+    dE = (energy(h) - energy(-h)) / (2 * h)
+    # x -> (I + eps E_ab) x moves every displacement d by eps d_b along a:
+    # dE/deps = sum d_b dE/dd_a = -W_ba with W_ab = -sum d_a dE/dd_b
+    assert abs(-dE - W[b, a]) < 1e-5 * max(1.0, np.abs(W).max()), (ab, -dE, W[b, a])
+
+
+def test_tilt_must_be_finite():
+    st, m = _water()
+    with pytest.raises(O.OracleError):
+        O.compute_tri(m, st.pos, st.types, st.box, (np.nan, 0.0, 0.0))
