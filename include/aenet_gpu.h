@@ -141,6 +141,23 @@ int aenet_set_skin(aenet_ctx *ctx, double skin);
  */
 int aenet_set_thermostat(aenet_ctx *ctx, double T0, double tau);
 
+/*
+ * Tilted (restricted triclinic) periodic cell for the single-structure calls
+ * of this context (aenet_compute, aenet_descriptors, aenet_md_nve): their box
+ * [3] = (L_x, L_y, L_z) then gives the lattice vectors
+ *     a = (L_x, 0, 0),  b = (xy, L_y, 0),  c = (xz, yz, L_z),
+ * the box form of the MD codes the paper's potential is used from (LAMMPS,
+ * Sec. IV.B). Positions are wrapped by their fractional coordinates; the cell
+ * grid has at least one cutoff between opposite cell faces along each lattice
+ * direction. All zero (the default) is the orthorhombic box. Any finite tilt is
+ * accepted (a very oblique cell needs a wide image window: more than 4096 image
+ * cells per atom is AENET_E_ARG at the next call). Batched calls and
+ * aenet_descriptors_noalloc stay orthorhombic. A change invalidates the MD
+ * graph and list: the next aenet_md_nve starts from frame 0.
+ * Errors: AENET_E_ARG (non-finite tilt).
+ */
+int aenet_set_box_tilt(aenet_ctx *ctx, double xy, double xz, double yz);
+
 /* Number of Verlet-list builds so far on this context (synchronises). */
 int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
 

@@ -67,6 +67,7 @@ def load(build_if_missing: bool = True):
     lib.aenet_batch_prepare.argtypes = [P, I, P, P, P, P, P, P, P, I]
     lib.aenet_batch_run.argtypes = [P]
     lib.aenet_set_skin.argtypes = [P, D]
+    lib.aenet_set_box_tilt.argtypes = [P, D, D, D]
     lib.aenet_set_thermostat.argtypes = [P, D, D]
     lib.aenet_md_list_builds.argtypes = [P, P]
     lib.aenet_batch_tuning.argtypes = [P, P, P, P, P, P]
@@ -283,6 +284,12 @@ class AenetGPU:
     def set_skin(self, skin):
         """Verlet-list skin (A) for md_nve; 0 rebuilds the cell list every step."""
         self._check(self.lib.aenet_set_skin(self.h, float(skin)))
+
+    def set_box_tilt(self, xy, xz, yz):
+        """Tilt factors of the restricted triclinic cell a = (L_x, 0, 0),
+        b = (xy, L_y, 0), c = (xz, yz, L_z) used by later single-structure calls
+        (box = (L_x, L_y, L_z)); zeros restore the orthorhombic box."""
+        self._check(self.lib.aenet_set_box_tilt(self.h, float(xy), float(xz), float(yz)))
 
     def set_thermostat(self, T0, tau):
         """Berendsen thermostat for md_nve: target T0 (K), coupling time tau (ps);

@@ -47,16 +47,25 @@ struct Net {
 // Cell grid of one orthorhombic box: nc cells per axis of edge h >= rc_max (or
 // a single cell when the box is shorter than the cutoff); neighbour cells are
 // scanned over offsets -m..m per axis, each offset one periodic image.
+// Cell grid of one periodic box. The box is the restricted triclinic cell of
+// LAMMPS, lattice vectors a = (L_x, 0, 0), b = (xy, L_y, 0), c = (xz, yz, L_z)
+// (orthorhombic when the tilts are zero): nc[k] cells along lattice vector k,
+// so a cell's edge vectors are A = a / nc[0], B = b / nc[1], C = c / nc[2], and
+// image-cell offset (ox, oy, oz) is the shift ox A + oy B + oz C.
 struct Grid {
     int nc[3];
     int m[3];
     int ncell;
     int n_off;                     // prod(2 m + 1)
-    double box[3];
-    double h[3];
+    double box[3];                 // L_x, L_y, L_z
+    double h[3];                   // diagonal of A, B, C: L_k / nc[k]
     double inv_box[3];             // reciprocals: no FP64 division on the device
     double inv_h[3];
     float hf[3];
+    int tri;                       // any tilt != 0
+    double tilt[3];                // xy, xz, yz
+    double ht[3];                  // off-diagonal of the cell edges: B_x = xy / nc[1], C_x = xz / nc[2], C_y = yz / nc[2]
+    float htf[3];
 };
 
 // Wrap one position into [0, box) and bin it: returns the cell and the FP32
@@ -65,6 +74,45 @@ struct Grid {
 // long latency on this part.
 __device__ inline int bin_position(double x0, double x1, double x2, const Grid &g, float *u, bool &finite,
                                    double *ud = nullptr) {
+    if (g.tri) {
+        // tilted cell: fractional coordinates by back substitution (x = H s, H
+        // upper triangular), each wrapped into [0, 1) and binned; the position
+        // relative to the cell's centre (c0 + 1/2) A + (c1 + 1/2) B + (c2 + 1/2) C
+        // in Cartesian (the centre, not a corner: an oblique cell's long
+        // diagonal would double the FP32 coordinates' magnitude and rounding)
+        double x[3] = {x0, x1, x2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (!isfinite(x[a])) {
+                finite = false;
+                x[a] = 0.0;
+            }
+        double s[3];
+        s[2] = x[2] * g.inv_box[2];
+        s[1] = fma(-g.tilt[2], s[2], x[1]) * g.inv_box[1];
+        s[0] = fma(-g.tilt[1], s[2], fma(-g.tilt[0], s[1], x[0])) * g.inv_box[0];
+        int ci[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double w = s[a] - floor(s[a]);
+            if (w >= 1.0) w -= 1.0;
+            if (w < 0.0) w = 0.0;
+            s[a] = w;
+            int c = (int)(w * g.nc[a]);
+            ci[a] = c >= g.nc[a] ? g.nc[a] - 1 : c;
+        }
+        const double xw[3] = {fma(g.tilt[1], s[2], fma(g.tilt[0], s[1], g.box[0] * s[0])),
+                              fma(g.tilt[2], s[2], g.box[1] * s[1]), g.box[2] * s[2]};
+        const double k0 = ci[0] + 0.5, k1 = ci[1] + 0.5, k2 = ci[2] + 0.5;
+        const double ua[3] = {xw[0] - fma(k2, g.ht[1], fma(k1, g.ht[0], k0 * g.h[0])),
+                              xw[1] - fma(k2, g.ht[2], k1 * g.h[1]), xw[2] - k2 * g.h[2]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            u[a] = (float)ua[a];
+            if (ud) ud[a] = ua[a];
+        }
+        return (ci[2] * g.nc[1] + ci[1]) * g.nc[0] + ci[0];
+    }
     const double xs[3] = {x0, x1, x2};
     int ci[3];
 #pragma unroll
@@ -189,6 +237,9 @@ struct Context {
     // built by k_potential's list mode, rebuilt inside the captured step (a graph
     // conditional node) whenever an atom moved more than skin/2 since the build.
     double skin = 0.0;
+    // tilt factors xy, xz, yz of the restricted triclinic cell of single-structure
+    // calls (zero: orthorhombic)
+    double tilt[3] = {0.0, 0.0, 0.0};
     int cap_vl_atoms = 0;
     long long cap_vl_entries = 0;
     int *d_vl = nullptr;               // [atoms * vl_cap] sorted order

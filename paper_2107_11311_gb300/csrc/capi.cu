@@ -63,15 +63,33 @@ cudaError_t grow(T *&p, size_t have, size_t need) {
     return cudaMalloc(&p, sizeof(T) * (need > 0 ? need : 1));
 }
 
-// Cell grid of a box: cells of edge >= rc_cut (default: the largest cutoff) and
-// the (2m+1)^3 image-cell window that covers rc_cut.
-int make_grid(Context &c, const double *box, Grid &g, double rc_cut = 0.0) {
+// Cell grid of a box: cells at least rc_cut (default: the largest cutoff) thick
+// along each lattice direction, and the (2m+1)^3 image-cell window that covers
+// rc_cut. tilt (xy, xz, yz) or NULL: the restricted triclinic cell. A
+// displacement of length <= rc has a fractional component along lattice
+// vector k of at most rc / w_k (w_k the distance between the cell's faces
+// across k), so cell indices differ by at most m_k = ceil(rc nc_k / w_k).
+int make_grid(Context &c, const double *box, Grid &g, double rc_cut = 0.0, const double *tilt = nullptr) {
     const double rc = rc_cut > 0.0 ? rc_cut : c.basis.rc_max;
     g.ncell = 1;
     g.n_off = 1;
     for (int a = 0; a < 3; ++a) {
         if (!(box[a] > 0.0) || !isfinite(box[a])) return fail(&c, AENET_E_ARG, "box[%d] must be finite and > 0", a);
-        int nc = (int)floor(box[a] / rc);
+        g.tilt[a] = tilt ? tilt[a] : 0.0;
+        if (!isfinite(g.tilt[a])) return fail(&c, AENET_E_ARG, "box tilt %d must be finite", a);
+    }
+    g.tri = g.tilt[0] != 0.0 || g.tilt[1] != 0.0 || g.tilt[2] != 0.0;
+    double w[3] = {box[0], box[1], box[2]};
+    if (g.tri) {  // face distances: volume / |b x c|, volume / |c x a|, L_z
+        const double xy = g.tilt[0], xz = g.tilt[1], yz = g.tilt[2];
+        const double V = box[0] * box[1] * box[2];
+        w[0] = V / sqrt(box[1] * box[2] * box[1] * box[2] + xy * box[2] * xy * box[2] +
+                        (xy * yz - box[1] * xz) * (xy * yz - box[1] * xz));
+        w[1] = V / (box[0] * sqrt(box[2] * box[2] + yz * yz));
+        w[2] = box[2];
+    }
+    for (int a = 0; a < 3; ++a) {
+        int nc = (int)floor(w[a] / rc);
         if (nc < 1) nc = 1;
         if (nc > 1024) nc = 1024;
         g.nc[a] = nc;
@@ -80,10 +98,14 @@ int make_grid(Context &c, const double *box, Grid &g, double rc_cut = 0.0) {
         g.hf[a] = (float)g.h[a];
         g.inv_box[a] = 1.0 / g.box[a];
         g.inv_h[a] = 1.0 / g.h[a];
-        g.m[a] = (int)ceil(rc / g.h[a]);
+        g.m[a] = g.tri ? (int)ceil(rc * nc / w[a]) : (int)ceil(rc / g.h[a]);
         g.ncell *= nc;
         g.n_off *= 2 * g.m[a] + 1;
     }
+    g.ht[0] = g.tilt[0] / g.nc[1];
+    g.ht[1] = g.tilt[1] / g.nc[2];
+    g.ht[2] = g.tilt[2] / g.nc[2];
+    for (int a = 0; a < 3; ++a) g.htf[a] = (float)g.ht[a];
     if (g.n_off > 4096)
         return fail(&c, AENET_E_ARG, "box too small for the cutoff: %d image cells per atom (limit 4096)", g.n_off);
     return AENET_OK;
@@ -427,7 +449,7 @@ static int compute_impl(Context &c, int n, const double *pos, const int32_t *typ
     if (!box) return fail(&c, AENET_E_ARG, "box is NULL");
     if (n > 0 && (!pos || !types)) return fail(&c, AENET_E_ARG, "pos/types NULL");
     Grid g;
-    int rc = make_grid(c, box, g);
+    int rc = make_grid(c, box, g, 0.0, c.tilt);
     if (rc) return rc;
     if ((rc = validate_types_host(c, n, types))) return rc;
     if ((rc = ensure(c, n, g)) || (rc = ensure_stage(c, n))) return rc;
@@ -1034,7 +1056,7 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
         return fail(&c, AENET_E_ARG, "AENET_MD_ASYNC needs device pointers");
     Grid g;
     // with a Verlet list the cells must cover the list cutoff rc_max + skin
-    int rc = make_grid(c, box, g, verlet ? c.basis.rc_max + c.skin : 0.0);
+    int rc = make_grid(c, box, g, verlet ? c.basis.rc_max + c.skin : 0.0, c.tilt);
     if (rc) return rc;
     if ((rc = validate_types_host(c, n, types))) return rc;
     if ((rc = ensure(c, n, g)) || (rc = ensure_stage(c, n))) return rc;
@@ -1289,6 +1311,21 @@ extern "C" int aenet_set_skin(aenet_ctx *h, double skin) {
         c.skin = skin;
         c.vl_valid = false;
         c.caps.vl_cap = 0;
+        destroy_graph(c);
+    }
+    return AENET_OK;
+}
+
+extern "C" int aenet_set_box_tilt(aenet_ctx *h, double xy, double xz, double yz) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (!isfinite(xy) || !isfinite(xz) || !isfinite(yz)) return fail(&c, AENET_E_ARG, "tilt factors must be finite");
+    if (xy != c.tilt[0] || xz != c.tilt[1] || yz != c.tilt[2]) {
+        c.tilt[0] = xy;
+        c.tilt[1] = xz;
+        c.tilt[2] = yz;
+        c.vl_valid = false;
+        c.maps_n = -1;  // forces and cell maps of the old cell: the next MD call starts from frame 0
         destroy_graph(c);
     }
     return AENET_OK;

@@ -928,8 +928,9 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         const int s0 = cell_start[nc];
         off_start[o] = s0;
         off_count[o] = cell_start[nc + 1] - s0;
-        off_shift[o] = make_float4(ox * g.hf[0], oy * g.hf[1], oz * g.hf[2],
-                                   __int_as_float((ox | oy | oz) != 0 ? 1 : 0));
+        // image shift ox A + oy B + oz C (the tilt terms are zero in an orthorhombic box)
+        off_shift[o] = make_float4(ox * g.hf[0] + oy * g.htf[0] + oz * g.htf[1], oy * g.hf[1] + oz * g.htf[2],
+                                   oz * g.hf[2], __int_as_float((ox | oy | oz) != 0 ? 1 : 0));
     }
     __syncthreads();
     if (warp == 0) {
@@ -1126,7 +1127,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
     const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
     for (int o = tid; o < g.n_off; o += kPThreads) {  // image offset of every list code
         const int ox = o % wx - g.m[0], oy = (o / wx) % wy - g.m[1], oz = o / (wx * wy) - g.m[2];
-        off_shift[o] = make_float4(ox * g.hf[0], oy * g.hf[1], oz * g.hf[2], 0.f);
+        off_shift[o] = make_float4(ox * g.hf[0] + oy * g.htf[0] + oz * g.htf[1], oy * g.hf[1] + oz * g.htf[2],
+                                   oz * g.hf[2], 0.f);
     }
     __syncthreads();
 
