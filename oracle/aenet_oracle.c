@@ -828,16 +828,32 @@ int orc_forces_subset(const orc_model *m, int n, const double *pos, const int *t
  *     lambda = sqrt(1 + (dt / tau) (T0 / T - 1)),   T = 2 E_kin / ((3N - 3) k_B),
  * E_kin being the kinetic energy recorded for the frame the step starts from
  * (the paper's MD cycle takes T as an input, Fig. 1; it names no thermostat). */
+/* Berendsen barostat (isotropic; not in the paper, which runs its potential
+ * inside LAMMPS): after every `every`-th step of a run, with the pressure of
+ * that frame
+ *     P = (2 E_kin + tr W) / (3 V)   (W the virial above, V = L_x L_y L_z),
+ * positions and cell (edges and tilts) are scaled by
+ *     mu = (1 - (every dt / tau) (P0 - P) / B)^(1/3),
+ * B the bulk modulus, and the forces re-evaluated; the record of that frame is
+ * the scaled state. Pressures in bar: 1 eV/A^3 = 1.602176634e6 bar. */
+typedef struct {
+    double P0, tau, modulus; /* bar, ps, bar */
+    int every;
+} orc_baro;
+
+#define ORC_EV_A3_BAR 1.602176634e6
+
 static int md_run(const orc_model *m, int n, double *pos, double *vel, const int *types,
-                  const double *mass_of_type, const orc_box *box, double dt, int n_steps, int mode,
-                  int n_threads, double *e_pot, double *e_kin, double T0, double tau) {
+                  const double *mass_of_type, orc_box *box, double dt, int n_steps, int mode,
+                  int n_threads, double *e_pot, double *e_kin, double T0, double tau, const orc_baro *baro) {
     const double c = 9648.533212;
     const double kB = 8.617333262e-5;
     if (check_model(m) || n <= 0 || !pos || !vel || !mass_of_type || n_steps < 0) return ORC_E_ARG;
+    if (baro && (baro->every < 1 || !(baro->tau > 0.0) || !(baro->modulus > 0.0))) return ORC_E_ARG;
     double *F = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     if (!F) return ORC_E_NOMEM;
-    double E = 0.0;
-    int err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
+    double E = 0.0, W[9];
+    int err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, W, NULL, NULL, NULL);
     for (int s = 0; s <= n_steps && !err; ++s) {
         double K = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -861,11 +877,32 @@ static int md_run(const orc_model *m, int n, double *pos, double *vel, const int
                 pos[3 * i + a] += dt * vel[3 * i + a];
             }
         }
-        err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, NULL, NULL, NULL, NULL);
+        err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, W, NULL, NULL, NULL);
         if (err) break;
         for (int i = 0; i < n; ++i) {
             double k = 0.5 * dt * c / mass_of_type[types[i]];
             for (int a = 0; a < 3; ++a) vel[3 * i + a] += k * F[3 * i + a];
+        }
+        if (baro && (s + 1) % baro->every == 0) {
+            double K1 = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double mi = mass_of_type[types[i]];
+                for (int a = 0; a < 3; ++a) K1 += 0.5 * mi * vel[3 * i + a] * vel[3 * i + a] / c;
+            }
+            const double V = box->L[0] * box->L[1] * box->L[2];
+            const double P = (2.0 * K1 + W[0] + W[4] + W[8]) / (3.0 * V) * ORC_EV_A3_BAR;
+            const double arg = 1.0 - (baro->every * dt / baro->tau) * (baro->P0 - P) / baro->modulus;
+            if (!(arg > 0.0)) {
+                err = ORC_E_ARG;
+                break;
+            }
+            const double mu = cbrt(arg);
+            for (int q = 0; q < 3 * n; ++q) pos[q] *= mu;
+            for (int a = 0; a < 3; ++a) box->L[a] *= mu;
+            box->xy *= mu;
+            box->xz *= mu;
+            box->yz *= mu;
+            err = compute_box(m, n, pos, types, box, mode, n_threads, NULL, &E, NULL, F, W, NULL, NULL, NULL);
         }
     }
     free(F);
@@ -876,16 +913,18 @@ int orc_md_nve(const orc_model *m, int n, double *pos, double *vel, const int *t
                const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
                int n_threads, double *e_pot, double *e_kin) {
     if (!box) return ORC_E_ARG;
-    const orc_box B = box_of(box, NULL);
-    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, mode, n_threads, e_pot, e_kin, 0.0, 0.0);
+    orc_box B = box_of(box, NULL);
+    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, mode, n_threads, e_pot, e_kin, 0.0, 0.0,
+                  NULL);
 }
 
 int orc_md_nvt(const orc_model *m, int n, double *pos, double *vel, const int *types,
                const double *mass_of_type, const double *box, double dt, int n_steps, int mode,
                int n_threads, double *e_pot, double *e_kin, double T0, double tau) {
     if (!box) return ORC_E_ARG;
-    const orc_box B = box_of(box, NULL);
-    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, mode, n_threads, e_pot, e_kin, T0, tau);
+    orc_box B = box_of(box, NULL);
+    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, mode, n_threads, e_pot, e_kin, T0, tau,
+                  NULL);
 }
 
 /* Velocity Verlet (tau > 0: with the Berendsen thermostat) in a restricted
@@ -894,8 +933,27 @@ int orc_md_tri(const orc_model *m, int n, double *pos, double *vel, const int *t
                const double *box, const double *tilt, double dt, int n_steps, int n_threads, double *e_pot,
                double *e_kin, double T0, double tau) {
     if (!box || !tilt) return ORC_E_ARG;
-    const orc_box B = box_of(box, tilt);
-    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, 0, n_threads, e_pot, e_kin, T0, tau);
+    orc_box B = box_of(box, tilt);
+    return md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, 0, n_threads, e_pot, e_kin, T0, tau, NULL);
+}
+
+/* Velocity Verlet with the Berendsen barostat (and, tau_T > 0, the Berendsen
+ * thermostat) in an orthorhombic or restricted triclinic cell; box [3] and
+ * tilt [3] are updated in place to the final cell. */
+int orc_md_npt(const orc_model *m, int n, double *pos, double *vel, const int *types, const double *mass_of_type,
+               double *box, double *tilt, double dt, int n_steps, int n_threads, double *e_pot, double *e_kin,
+               double T0, double tau_T, double P0, double tau_P, double modulus, int every) {
+    if (!box || !tilt) return ORC_E_ARG;
+    orc_box B = box_of(box, tilt);
+    const orc_baro baro = {P0, tau_P, modulus, every};
+    /* the cell list needs a fixed orthorhombic cell: brute force throughout */
+    int err = md_run(m, n, pos, vel, types, mass_of_type, &B, dt, n_steps, 0, n_threads, e_pot, e_kin, T0, tau_T,
+                     &baro);
+    for (int a = 0; a < 3; ++a) box[a] = B.L[a];
+    tilt[0] = B.xy;
+    tilt[1] = B.xz;
+    tilt[2] = B.yz;
+    return err;
 }
 
 /* Test hooks: the basis pieces on their own. */

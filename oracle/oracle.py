@@ -61,6 +61,9 @@ def lib():
                                          P, P, P, P, P]
         _lib.orc_md_tri.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, P, P, C.c_double, C.c_int,
                                     C.c_int, P, P, C.c_double, C.c_double]
+        _lib.orc_md_npt.argtypes = [C.POINTER(_Model), C.c_int, P, P, P, P, P, P, C.c_double, C.c_int,
+                                    C.c_int, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_int]
         _lib.orc_neighbour_lists.argtypes = [C.c_int, C.c_int, P, P, C.c_double, P, P, P, P]
         _lib.orc_chebyshev.argtypes = [C.c_int, C.c_double, P, P]
         _lib.orc_chebyshev.restype = None
@@ -192,6 +195,29 @@ def md_tri(model, pos, vel, types, box, tilt, dt, n_steps, n_threads=0, thermost
                           _ptr(box), _ptr(tilt), float(dt), int(n_steps), n_threads, _ptr(ep), _ptr(ek), T0, tau)
     _check(rc, "orc_md_tri")
     return pos, vel, ep, ek
+
+
+def md_npt(model, pos, vel, types, box, tilt, dt, n_steps, barostat, thermostat=None, n_threads=0):
+    """Velocity Verlet with the Berendsen barostat (see aenet_oracle.c):
+    barostat = (P0 in bar, tau_P in ps, bulk modulus in bar, every K steps);
+    optional thermostat = (T0 in K, tau_T in ps). Returns (pos, vel, e_pot,
+    e_kin, box, tilt) with the final cell."""
+    pk = _Packed(model)
+    pos = _f64(pos).copy()
+    vel = _f64(vel).copy()
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    box = _f64(box).copy()
+    tilt = _f64(tilt).copy()
+    mass = _f64(model.masses)
+    ep = np.zeros(n_steps + 1)
+    ek = np.zeros(n_steps + 1)
+    T0, tau = (0.0, 0.0) if thermostat is None else (float(thermostat[0]), float(thermostat[1]))
+    P0, tau_p, modulus, every = barostat
+    rc = lib().orc_md_npt(C.byref(pk.s), pos.shape[0], _ptr(pos), _ptr(vel), _ptr(types), _ptr(mass),
+                          _ptr(box), _ptr(tilt), float(dt), int(n_steps), n_threads, _ptr(ep), _ptr(ek), T0, tau,
+                          float(P0), float(tau_p), float(modulus), int(every))
+    _check(rc, "orc_md_npt")
+    return pos, vel, ep, ek, box, tilt
 
 
 def forces_subset(model, pos, types, box, targets, mode=CELLS, n_threads=0):

@@ -10,6 +10,12 @@ which reuses the tilted code path on both sides.
 * forces are minus the finite-difference gradient of the energy;
 * the virial is minus the derivative of the energy under a homogeneous strain
   of positions and cell (upper-triangular strains keep the restricted form).
+
+And of the Berendsen barostat of the oracle's MD loop (the cell scaled by
+mu = (1 - (K dt / tau) (P0 - P) / B)^(1/3) after every K-th step): an infinite
+bulk modulus is the fixed-cell run bit for bit; an ideal gas (no forces) is
+driven to the ideal-gas volume 2 E_kin / (3 P0) with edges and tilts scaled
+alike; a target above / below the pressure compresses / expands the cell.
 """
 import numpy as np
 import pytest
@@ -134,3 +140,73 @@ def test_tilt_must_be_finite():
     st, m = _water()
     with pytest.raises(O.OracleError):
         O.compute_tri(m, st.pos, st.types, st.box, (np.nan, 0.0, 0.0))
+
+
+# ---------------------------------------------------------------- barostat
+
+EV_A3_BAR = 1.602176634e6
+
+
+def test_barostat_with_infinite_modulus_is_nve():
+    """mu = 1 exactly: the same trajectory as without the barostat, bit for bit
+    (one thread: the same summation order), and the cell unchanged."""
+    st, m = _water()
+    tilt = (0.2 * st.box[0], 0.0, -0.1 * st.box[1])
+    pos = _tilted(st, tilt)
+    v = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=5)
+    a = O.md_tri(m, pos, v, st.types, st.box, tilt, 5e-4, 6, n_threads=1)
+    b = O.md_npt(m, pos, v, st.types, st.box, tilt, 5e-4, 6, (1.0, 0.1, 1e300, 2), n_threads=1)
+    for x, y in zip(a, b[:4]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(b[4], st.box)
+    np.testing.assert_array_equal(b[5], tilt)
+
+
+def _free_gas(n=64, seed=1):
+    """Atoms of a zero-weight network (no forces, zero virial): an ideal gas."""
+    m = inputs.make_model("amorphous")
+    m.params = np.zeros_like(m.params)
+    m.masses = np.ones(m.n_species)
+    rng = np.random.default_rng(seed)
+    box = np.full(3, 20.0)
+    pos = rng.uniform(0.0, 20.0, (n, 3))
+    types = rng.integers(0, m.n_species, n).astype(np.int32)
+    vel = rng.normal(0.0, 5.0, (n, 3))
+    return m, pos, vel, types, box
+
+
+def test_barostat_drives_an_ideal_gas_to_the_target_pressure():
+    """Without forces the pressure is 2 E_kin / (3 V) and E_kin is constant, so
+    repeated couplings take the volume to the ideal-gas value 2 E_kin / (3 P0)."""
+    m, pos, vel, types, box = _free_gas()
+    P0 = 50.0  # bar
+    tilt = (3.0, -2.0, 1.5)
+    _, _, ep, ek, box1, tilt1 = O.md_npt(m, pos, vel, types, box, tilt, 1e-3, 400, (P0, 0.01, 1.0e2, 1))
+    assert np.all(ep == 0.0)
+    assert np.ptp(ek) < 1e-12 * ek[0]
+    V_star = 2.0 * ek[0] / (3.0 * P0 / EV_A3_BAR)
+    V1 = np.prod(box1)
+    assert abs(V1 / V_star - 1.0) < 1e-6, (V1, V_star)
+    # isotropic: edges and tilts scaled by the same factor
+    mu = box1[0] / box[0]
+    np.testing.assert_allclose(box1, mu * box, rtol=1e-12)
+    np.testing.assert_allclose(tilt1, mu * np.asarray(tilt), rtol=1e-12)
+
+
+def test_barostat_direction():
+    """A target above the current pressure (about -3.3e5 bar for this random-
+    weight water box) compresses the cell; below it, expands it."""
+    st, m = _water()
+    v = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=5)
+    tilt = (0.0, 0.0, 0.0)
+    up = O.md_npt(m, st.pos, v, st.types, st.box, tilt, 5e-4, 4, (1e5, 0.05, 2.2e4, 2))
+    down = O.md_npt(m, st.pos, v, st.types, st.box, tilt, 5e-4, 4, (-1e6, 0.05, 2.2e4, 2))
+    assert np.all(up[4] < st.box) and np.all(down[4] > st.box)
+
+
+def test_barostat_rejects_bad_parameters():
+    st, m = _water()
+    v = np.zeros_like(st.pos)
+    for bad in ((1.0, 0.0, 1e4, 1), (1.0, 0.1, 0.0, 1), (1.0, 0.1, 1e4, 0)):
+        with pytest.raises(O.OracleError):
+            O.md_npt(m, st.pos, v, st.types, st.box, (0.0, 0.0, 0.0), 5e-4, 2, bad)
