@@ -158,6 +158,30 @@ int aenet_set_thermostat(aenet_ctx *ctx, double T0, double tau);
  */
 int aenet_set_box_tilt(aenet_ctx *ctx, double xy, double xz, double yz);
 
+/*
+ * Berendsen barostat for aenet_md_nve (the MD cycle of Fig. 1 takes T and p as
+ * inputs; the paper names no barostat, so this is the isotropic weak coupling
+ * of LAMMPS's press/berendsen): after every `every`-th step of a call, with the
+ * pressure of that frame
+ *     P = (2 E_kin + tr W) / (3 V),   V = L_x L_y L_z,  W the virial,
+ * positions and the cell (edges and the tilts of aenet_set_box_tilt) are
+ * scaled by
+ *     mu = (1 - (every dt / tau) (P0 - P) / modulus)^(1/3),
+ * and that frame is evaluated again: its e_pot / e_kin records are those of the
+ * scaled state. P0 and modulus (the bulk modulus) in bar, tau in ps, every >= 1
+ * steps; tau <= 0 turns it off (the default). Each coupling synchronises and
+ * the next run of steps is captured again (a new cell), so AENET_MD_ASYNC is
+ * refused while it is on. The cell after a call: aenet_md_box. A volume factor
+ * <= 0 (a coupling too strong for the pressure) stops the call with
+ * AENET_E_ARG. Errors: AENET_E_ARG.
+ */
+int aenet_set_barostat(aenet_ctx *ctx, double P0, double tau, double modulus, int every);
+
+/* The cell the last aenet_md_nve call ended in: box [3] edges, tilt [3] (or
+ * NULL) the tilt factors, also the context's tilt for later calls. Errors:
+ * AENET_E_ARG, AENET_E_STATE (no MD call yet). */
+int aenet_md_box(aenet_ctx *ctx, double *box, double *tilt);
+
 /* Number of Verlet-list builds so far on this context (synchronises). */
 int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
 
@@ -246,7 +270,9 @@ int aenet_descriptors(aenet_ctx *ctx, int n_atoms, const double *pos, const int3
  *            and e_kin must be device pointers (or NULL) and device errors are
  *            reported by the next synchronising call or aenet_check();
  *            AENET_MD_CONTINUE: see below.
- * Every step after the first is one replay of a captured CUDA graph.
+ * Every step after the first is one replay of a captured CUDA graph. With the
+ * barostat on (aenet_set_barostat) the cell changes during the call: read the
+ * final one with aenet_md_box.
  */
 #define AENET_MD_ASYNC 1
 /* AENET_MD_CONTINUE: pos and vel are exactly as the previous aenet_md_nve call

@@ -68,6 +68,8 @@ def load(build_if_missing: bool = True):
     lib.aenet_batch_run.argtypes = [P]
     lib.aenet_set_skin.argtypes = [P, D]
     lib.aenet_set_box_tilt.argtypes = [P, D, D, D]
+    lib.aenet_set_barostat.argtypes = [P, D, D, D, I]
+    lib.aenet_md_box.argtypes = [P, P, P]
     lib.aenet_set_thermostat.argtypes = [P, D, D]
     lib.aenet_md_list_builds.argtypes = [P, P]
     lib.aenet_batch_tuning.argtypes = [P, P, P, P, P, P]
@@ -290,6 +292,18 @@ class AenetGPU:
         b = (xy, L_y, 0), c = (xz, yz, L_z) used by later single-structure calls
         (box = (L_x, L_y, L_z)); zeros restore the orthorhombic box."""
         self._check(self.lib.aenet_set_box_tilt(self.h, float(xy), float(xz), float(yz)))
+
+    def set_barostat(self, P0, tau, modulus, every=1):
+        """Berendsen barostat for md_nve: target P0 (bar), coupling time tau (ps),
+        bulk modulus (bar), coupling after every `every` steps; tau <= 0 turns it
+        off."""
+        self._check(self.lib.aenet_set_barostat(self.h, float(P0), float(tau), float(modulus), int(every)))
+
+    def md_box(self):
+        """(edges [3], tilts [3]) of the cell the last md_nve call ended in."""
+        box, tilt = np.zeros(3), np.zeros(3)
+        self._check(self.lib.aenet_md_box(self.h, _ptr(box), _ptr(tilt)))
+        return box, tilt
 
     def set_thermostat(self, T0, tau):
         """Berendsen thermostat for md_nve: target T0 (K), coupling time tau (ps);

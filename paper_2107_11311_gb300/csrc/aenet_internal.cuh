@@ -263,6 +263,14 @@ struct Context {
     double *d_lambda = nullptr;
     bool lambda_valid = false;         // d_lambda was computed with the current settings
 
+    // Berendsen barostat of the MD path (baro_every 0: off): after every
+    // baro_every-th step of a call, positions and cell scaled by
+    // mu = (1 - (baro_every dt / baro_tau) (baro_P0 - P) / baro_modulus)^(1/3).
+    double baro_P0 = 0.0, baro_tau = 0.0, baro_modulus = 0.0;  // bar, ps, bar
+    int baro_every = 0;
+    double md_box[3] = {0.0, 0.0, 0.0};  // edges of the cell after the last MD call
+    bool md_box_valid = false;
+
     // Generation of the work buffers: bumped whenever one is reallocated, so a
     // captured graph (which holds their addresses) knows it must be re-captured.
     unsigned buf_gen = 0;
@@ -410,6 +418,8 @@ cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt
 // clear_vl, the last CTA also counts a list build and clears the rebuild flag.
 cudaError_t launch_md_kick_finish(Context &c, int n, double dt, double *vel, const int32_t *types,
                                   double *rec_pot, double *rec_kin, bool clear_vl = false);
+// x *= mu for count doubles (the barostat's isotropic scaling of positions).
+cudaError_t launch_scale(Context &c, double *x, long long count, double mu);
 
 // Verlet form of the opening half-kick and drift (no binning): refresh the FP32
 // coordinates relative to the origins of the last list build, raise the rebuild

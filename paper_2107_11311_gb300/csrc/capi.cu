@@ -1024,9 +1024,9 @@ static int ensure_verlet(Context &c, int n, const Grid &g) {
     return AENET_OK;
 }
 
-extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const int32_t *types,
-                            const double *box, double dt, int n_steps, double *e_pot, double *e_kin, int flags) {
-    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+// n_steps MD steps in one fixed cell (edges box, tilts c.tilt).
+static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const int32_t *types, const double *box,
+                         double dt, int n_steps, double *e_pot, double *e_kin, int flags) {
     Context &c = h->c;
     cudaGetLastError();
     if (c.mass.empty()) return fail(&c, AENET_E_ARG, "model has no masses");
@@ -1185,6 +1185,106 @@ extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const
     if (!vel_dev) CK(cudaMemcpyAsync(vel, dvel, 3 * sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "vel out");
     if (async) return AENET_OK;
     return read_error_word(c);
+}
+
+// Berendsen coupling after a step: the pressure of the frame the step ended on
+// (energy, virial and kinetic energy of its closing reduction, d_result),
+//     P = (2 E_kin + tr W) / (3 V),  V = L_x L_y L_z,
+// then positions, edges and tilts scaled by
+//     mu = (1 - (every dt / tau) (P0 - P) / B)^(1/3).
+// The cell maps, forces and list of the old cell are invalidated, so the next
+// steps start from a fresh evaluation in the scaled cell.
+static int barostat_couple(Context &c, int n, double *pos, double *L, double dt) {
+    constexpr double kEvPerA3InBar = 1.602176634e6;
+    double res[11];
+    CK(cudaMemcpyAsync(res, c.d_result, sizeof(res), cudaMemcpyDeviceToHost, c.stream), "pressure copy");
+    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    const double V = L[0] * L[1] * L[2];
+    const double P = (2.0 * res[10] + res[1] + res[5] + res[9]) / (3.0 * V) * kEvPerA3InBar;
+    const double arg = 1.0 - (c.baro_every * dt / c.baro_tau) * (c.baro_P0 - P) / c.baro_modulus;
+    if (!(arg > 0.0) || !isfinite(arg))
+        return fail(&c, AENET_E_ARG, "barostat: volume factor %g <= 0 (pressure %g bar; lower dt * every / tau)", arg, P);
+    const double mu = cbrt(arg);
+    const bool pos_dev = is_device_ptr(pos);
+    double *dpos = pos_dev ? pos : c.d_pos;  // the device copy holds the final positions either way
+    CK(launch_scale(c, dpos, 3LL * n, mu), "scale positions");
+    if (!pos_dev) {
+        CK(cudaMemcpyAsync(pos, dpos, 3 * sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream), "pos out");
+        CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    }
+    for (int a = 0; a < 3; ++a) {
+        L[a] *= mu;
+        c.tilt[a] *= mu;
+    }
+    c.vl_valid = false;
+    c.maps_n = -1;
+    destroy_graph(c);
+    return AENET_OK;
+}
+
+extern "C" int aenet_md_nve(aenet_ctx *h, int n, double *pos, double *vel, const int32_t *types,
+                            const double *box, double dt, int n_steps, double *e_pot, double *e_kin, int flags) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (!box) return fail(&c, AENET_E_ARG, "bad MD arguments");
+    double L[3] = {box[0], box[1], box[2]};
+    int rc = AENET_OK;
+    if (c.baro_every <= 0) {
+        rc = md_fixed_cell(h, n, pos, vel, types, L, dt, n_steps, e_pot, e_kin, flags);
+    } else {
+        // runs of baro_every steps between couplings; the records of a coupling
+        // step hold the scaled state (its frame is evaluated again)
+        if (flags & AENET_MD_ASYNC)
+            return fail(&c, AENET_E_ARG, "the barostat reads the pressure at every coupling: no AENET_MD_ASYNC");
+        int s0 = 0;
+        do {
+            const int k = std::min(c.baro_every, n_steps - s0);
+            rc = md_fixed_cell(h, n, pos, vel, types, L, dt, k, e_pot ? e_pot + s0 : nullptr,
+                               e_kin ? e_kin + s0 : nullptr, s0 == 0 ? flags : (flags & ~AENET_MD_CONTINUE));
+            if (rc) break;
+            s0 += k;
+            if (k == c.baro_every) {
+                if ((rc = barostat_couple(c, n, pos, L, dt))) break;
+                if (s0 == n_steps)  // the scaled last frame: its forces, energy and records
+                    rc = md_fixed_cell(h, n, pos, vel, types, L, dt, 0, e_pot ? e_pot + s0 : nullptr,
+                                       e_kin ? e_kin + s0 : nullptr, flags & ~AENET_MD_CONTINUE);
+                if (rc) break;
+            }
+        } while (s0 < n_steps);
+    }
+    if (rc == AENET_OK) {
+        for (int a = 0; a < 3; ++a) c.md_box[a] = L[a];
+        c.md_box_valid = true;
+    }
+    return rc;
+}
+
+extern "C" int aenet_set_barostat(aenet_ctx *h, double P0, double tau, double modulus, int every) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    if (!isfinite(P0) || !isfinite(tau) || !isfinite(modulus))
+        return fail(&c, AENET_E_ARG, "barostat parameters must be finite");
+    if (tau <= 0.0) {
+        c.baro_every = 0;
+        return AENET_OK;
+    }
+    if (!(modulus > 0.0) || every < 1) return fail(&c, AENET_E_ARG, "barostat: modulus > 0 and every >= 1 required");
+    c.baro_P0 = P0;
+    c.baro_tau = tau;
+    c.baro_modulus = modulus;
+    c.baro_every = every;
+    return AENET_OK;
+}
+
+extern "C" int aenet_md_box(aenet_ctx *h, double *box, double *tilt) {
+    if (!h || !box) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
+    Context &c = h->c;
+    if (!c.md_box_valid) return fail(&c, AENET_E_STATE, "no MD call has run on this context");
+    for (int a = 0; a < 3; ++a) {
+        box[a] = c.md_box[a];
+        if (tilt) tilt[a] = c.tilt[a];
+    }
+    return AENET_OK;
 }
 
 extern "C" int aenet_neighbor_stats(aenet_ctx *h, int64_t *out) {

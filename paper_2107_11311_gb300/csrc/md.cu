@@ -406,6 +406,18 @@ cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt
     return cudaGetLastError();
 }
 
+__global__ void k_scale(double *__restrict__ x, long long count, double mu) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x)
+        x[k] *= mu;
+}
+
+cudaError_t launch_scale(Context &c, double *x, long long count, double mu) {
+    if (count <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((count + 255) / 256, 4LL * std::max(1, c.n_sm));
+    k_scale<<<(int)blocks, 256, 0, c.stream>>>(x, count, mu);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_md_kick_finish(Context &c, int n, double dt, double *vel, const int32_t *types,
                                   double *rec_pot, double *rec_kin, bool clear_vl) {
     const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
