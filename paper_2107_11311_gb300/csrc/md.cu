@@ -366,6 +366,12 @@ KickParams kick_params(const Context &c, double dt) {
     return kp;
 }
 
+// Isotropic scaling of positions by the barostat.
+__global__ void k_scale(double *__restrict__ x, long long count, double mu) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x)
+        x[k] *= mu;
+}
+
 }  // namespace
 
 cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom) {
@@ -404,11 +410,6 @@ cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt
         n, c.basis.n_species, kick_params(c, dt), dt, pos, vel, types, c.d_F4, c.d_cell_start, g, c.d_tmp4,
         c.d_cell_of, c.d_slot, c.d_cell_count, c.d_err, thermostat_on(c) ? c.d_lambda : nullptr);
     return cudaGetLastError();
-}
-
-__global__ void k_scale(double *__restrict__ x, long long count, double mu) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x)
-        x[k] *= mu;
 }
 
 cudaError_t launch_scale(Context &c, double *x, long long count, double mu) {

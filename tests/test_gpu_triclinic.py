@@ -154,3 +154,17 @@ def test_set_box_tilt_rejects_non_finite(gpu_mod):
         with pytest.raises(gpu_mod.AenetError) as ei:
             g.set_box_tilt(*bad)
         assert ei.value.code == -1
+
+
+def test_tilted_cell_edge_cases(gpu_mod):
+    """No atoms in a tilted cell; a cell so small and oblique that its image
+    window passes the 4,096-cell limit is refused before any launch."""
+    m = inputs.make_model("water")
+    g = gpu_mod.AenetGPU(m, "fp32")
+    g.set_box_tilt(2.0, -1.0, 1.5)
+    out = g.compute(np.zeros((0, 3)), np.zeros(0, dtype=np.int32), (10.0, 10.0, 10.0))
+    assert out["energy"] == 0.0
+    g.set_box_tilt(0.99, 0.99, 0.99)  # face distances ~0.7 A for a 6 A cutoff: 19 x 19 x 13 image cells
+    with pytest.raises(gpu_mod.AenetError) as ei:
+        g.compute(np.array([[0.1, 0.2, 0.3], [0.5, 0.5, 0.5]]), np.array([0, 1], dtype=np.int32), (1.0, 1.0, 1.0))
+    assert ei.value.code == -1
