@@ -42,8 +42,12 @@ DT_PS = 5e-4
 
 # FP32 operations per unit of the two fingerprint kernels (FMA = 2 flops):
 # per radial neighbour entry and per unordered angular pair, counted from the
-# arithmetic each unit needs (recurrences for T_a and U_a, coefficient
-# combination, chain rule, force scatter and virial); derivation in the design doc.
+# arithmetic each unit needs. Forward: the Chebyshev recurrence T_a and two
+# accumulations (plain and species-weighted) per order, plus the distance,
+# cutoff and weight. Backward: per order the coefficient and the Clenshaw
+# steps for S = sum a_q T_q and S' = sum a_q T_q', plus the cutoff derivative,
+# the radial or angle chain rule to the displacement vectors, the force
+# scatter and the virial outer product.
 def force_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
     """Chain rule with Clenshaw's recurrence for S and S' (9 flops per order)."""
     return (9 * (Kr - 1) + 42) * n_entries + (9 * (Ka - 1) + 57) * n_ang_pairs

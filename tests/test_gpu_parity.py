@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded inputs, plus the edge cases and error paths of the boundary.
 
-Tolerances (FP32 form, spec bound): energy |dE|/N <= 0.5 meV/atom and
+Tolerances (FP32 form, the accuracy bound the method is held to): energy |dE|/N <= 0.5 meV/atom and
 force RMS error <= 1 meV/A; virial within 1e-4 relative to its largest
 component. Descriptor columns: every coefficient is an FP32 sum of terms with
 |T_a| <= 1, so its rounding error is bounded by a small multiple of the FP32
