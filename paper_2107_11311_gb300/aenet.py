@@ -275,8 +275,10 @@ class AenetGPU:
         return G
 
     def md_nve(self, pos, vel, types, box, dt, n_steps, e_pot=None, e_kin=None, flags=0):
-        """Velocity-Verlet NVE in place on ``pos`` and ``vel`` (float64 arrays or
-        tensors; numpy arrays must already be float64 and contiguous)."""
+        """Velocity Verlet in place on ``pos`` and ``vel`` (float64 arrays or
+        tensors; numpy arrays must already be float64 and contiguous): NVE, or
+        with set_thermostat / set_barostat the Berendsen NVT / NPT couplings
+        (the cell a barostat run ends in: md_box())."""
         types = _as(types, np.int32)
         n = int(pos.shape[0])
         box = self._box(box)
