@@ -177,12 +177,14 @@ int aenet_set_box_tilt(aenet_ctx *ctx, double xy, double xz, double yz);
  */
 int aenet_set_barostat(aenet_ctx *ctx, double P0, double tau, double modulus, int every);
 
-/* The cell the last aenet_md_nve call ended in: box [3] edges, tilt [3] (or
- * NULL) the tilt factors, also the context's tilt for later calls. Errors:
- * AENET_E_ARG, AENET_E_STATE (no MD call yet). */
+/* The cell the last aenet_md_nve call ended in (a query of the MD state with
+ * no counterpart in the paper): box [3] HOST, the edges; tilt [3] HOST or NULL,
+ * the tilt factors, which are also the context's tilt for later calls.
+ * Errors: AENET_E_ARG (NULL box), AENET_E_STATE (no MD call yet). */
 int aenet_md_box(aenet_ctx *ctx, double *box, double *tilt);
 
-/* Number of Verlet-list builds so far on this context (synchronises). */
+/* Number of Verlet-list builds so far on this context (a measurement with no
+ * counterpart in the paper): *builds HOST. Synchronises. Errors: AENET_E_ARG. */
 int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
 
 /*
