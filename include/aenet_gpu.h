@@ -96,18 +96,20 @@ int aenet_setup(aenet_ctx **out, const aenet_model_desc *model, int precision, v
 int aenet_set_stream(aenet_ctx *ctx, void *stream);
 
 /*
- * Energy, forces and virial of one periodic orthorhombic structure
- * (the potential of Sec. II evaluated as the interface of Sec. III returns it).
+ * Energy, forces and virial of one periodic structure (the potential of
+ * Sec. II evaluated as the interface of Sec. III returns it), in an
+ * orthorhombic box or in the tilted cell of aenet_set_box_tilt.
  *   n_atoms  >= 0
- *   pos      [n_atoms * 3] double, host or device; any real coordinates (wrapped
- *            internally into [0, box))
+ *   pos      [n_atoms * 3] double, host or device; any real coordinates
+ *            (wrapped internally into the cell by their fractional coordinates)
  *   types    [n_atoms] int32, host or device; 0-based species index in setup
  *            order (the species-order rule of the LAMMPS interface)
  *   box      [3] double, HOST; box edge lengths (A), each > 0
  *   energy   [1] double, host or device, or NULL: E = sum_i E_i (FP64 sum)
  *   forces   [n_atoms * 3] double, host or device, or NULL: F = -dE/dr
  *   virial   [9] double, host or device, or NULL: W_ab = -sum_d d_a dE/dd_b
- *            over all displacement vectors d = x_j + nL - x_i (row-major)
+ *            over all displacement vectors d = x_j + (lattice image) - x_i
+ *            (row-major)
  *   e_atom   [n_atoms] double, host or device, or NULL: E_i
  * Synchronises the stream before returning.
  */
@@ -251,9 +253,10 @@ int aenet_batch_run(aenet_ctx *ctx);
 int aenet_batch_tuning(aenet_ctx *ctx, int *persistent, int *tile, int *ctas, int *kernels, float *ms);
 
 /*
- * Descriptor only (rows a1-a5 of the path): G [n_atoms * D] float32, host or
- * device, row i = atom i in input order, layout [radial, angular, radial_w,
- * angular_w] before standardisation. Synchronises.
+ * Descriptor only (rows a1-a5 of the path; Sec. II.B): G [n_atoms * D]
+ * float32, host or device, row i = atom i in input order, layout [radial,
+ * angular, radial_w, angular_w] before standardisation. Other arguments and
+ * errors as aenet_compute. Synchronises.
  */
 int aenet_descriptors(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t *types,
                       const double *box, float *G);
