@@ -110,3 +110,42 @@ def test_prepared_batch_errors(gpu_mod):
     with pytest.raises(gpu_mod.AenetError) as ei:  # host buffers are refused
         g.batch_prepare(off, boxes, pos, types)
     assert ei.value.code == -1
+
+
+def test_full_batch_512_in_the_benchmark_launch(gpu_mod):
+    """The benchmark's batch_512 workload at full size, prepared and replayed as
+    the benchmark times it (tuned launch, one graph per model family): a seeded
+    sample of structures per family (with the largest and the smallest) against
+    the oracle, and on every structure finite energies and a net force that
+    vanishes up to FP32 rounding."""
+    wat, amo = inputs.batch_structures()
+    rng = np.random.default_rng(7)
+    for family, structs in (("water", wat), ("amorphous", amo)):
+        m = inputs.make_model(family)
+        off, boxes, d = _device_batch(structs)
+        g = gpu_mod.AenetGPU(m, "fp32")
+        g.batch_prepare(off, boxes, d["pos"], d["types"], d["energies"], d["forces"], d["virials"])
+        g.batch_run()
+        torch.cuda.synchronize()
+        g.check()
+        E = d["energies"].cpu().numpy()
+        F = d["forces"].cpu().numpy()
+        assert np.isfinite(E).all() and np.isfinite(F).all()
+        for s, st in enumerate(structs):
+            net = F[off[s]:off[s + 1]].sum(axis=0)
+            assert np.abs(net).max() <= 5e-3 * np.sqrt(st.n), (family, s, net)
+        sizes = np.array([st.n for st in structs])
+        pick = {int(np.argmax(sizes)), int(np.argmin(sizes))} | set(int(i) for i in rng.choice(len(structs), 6,
+                                                                                                 replace=False))
+        pos = d["pos"].cpu().numpy()
+        _check_against_oracle(m, [structs[i] for i in sorted(pick)],
+                              np.concatenate([[0], np.cumsum([structs[i].n for i in sorted(pick)])]),
+                              np.concatenate([pos[off[i]:off[i + 1]] for i in sorted(pick)]),
+                              {k: _take(v, off, sorted(pick), k) for k, v in d.items()})
+
+
+def _take(t, off, picks, key):
+    """The rows of the picked structures (per-structure or per-atom tensors)."""
+    if key in ("energies", "virials"):
+        return t[picks]
+    return torch.cat([t[off[i]:off[i + 1]] for i in picks])
