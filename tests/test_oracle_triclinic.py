@@ -210,3 +210,38 @@ def test_barostat_rejects_bad_parameters():
     for bad in ((1.0, 0.0, 1e4, 1), (1.0, 0.1, 0.0, 1), (1.0, 0.1, 1e4, 0)):
         with pytest.raises(O.OracleError):
             O.md_npt(m, st.pos, v, st.types, st.box, (0.0, 0.0, 0.0), 5e-4, 2, bad)
+
+
+# ------------------------------------------------- image-window rule of the grid
+
+def test_image_window_rule_covers_the_cutoff():
+    """The cell grid of a tilted cell (nc_k cells along lattice vector k, at
+    least one cutoff between opposite cell faces) scans m_k = ceil(rc nc_k / w_k)
+    neighbour cells each way, w_k the distance between the faces of the whole
+    cell across k (volume over the area of the face spanned by the other two
+    vectors). Check on random oblique cells: two points within rc never lie in
+    cells whose indices differ by more than m_k along any k."""
+    rng = np.random.default_rng(17)
+    rc = 6.0
+    reached = 0
+    for _ in range(200):
+        L = rng.uniform(4.0, 30.0, 3)
+        tilt = rng.uniform(-0.5, 0.5, 3) * np.array([L[0], L[0], L[1]])
+        H = _cell_matrix(L, tilt)
+        V = np.prod(L)
+        w = np.array([V / np.linalg.norm(np.cross(H[:, 1], H[:, 2])),
+                      V / np.linalg.norm(np.cross(H[:, 2], H[:, 0])),
+                      V / np.linalg.norm(np.cross(H[:, 0], H[:, 1]))])
+        nc = np.maximum(1, np.floor(w / rc)).astype(int)
+        m = np.ceil(rc * nc / w).astype(int)
+        Hinv = np.linalg.inv(H)
+        p = rng.uniform(0.0, 1.0, (400, 3)) @ H.T
+        d = rng.normal(size=(400, 3))
+        d *= (rc * rng.uniform(0.0, 1.0, (400, 1)) ** (1 / 3)) / np.linalg.norm(d, axis=1, keepdims=True)
+        q = p + d
+        cp = np.floor((p @ Hinv.T) * nc).astype(int)
+        cq = np.floor((q @ Hinv.T) * nc).astype(int)  # unwrapped cell index of the image
+        assert (np.abs(cq - cp) <= m).all()
+        reached += int((np.abs(cq - cp) == m).any())
+    # the window is used to its edge (a window one cell narrower would miss pairs)
+    assert reached > 100
