@@ -144,7 +144,9 @@ def test_tilt_must_be_finite():
 
 # ---------------------------------------------------------------- barostat
 
-EV_A3_BAR = 1.602176634e6
+# 1 eV/A^3 in bar, from the SI elementary charge (1 eV = 1.602176634e-19 J, exact):
+# e / (1e-30 m^3) Pa, and 1 bar = 1e5 Pa
+EV_A3_BAR = 1.602176634e-19 / 1e-30 / 1e5
 
 
 def test_barostat_with_infinite_modulus_is_nve():
