@@ -1,9 +1,10 @@
 """Benchmark of the ANN-potential MD hot path on GB300.
 
-Workload (default): the 4,096-molecule water box at 1.0 g/cm^3 (12,288 atoms,
-L = 49.669 A), water basis (radial order 16 / 6.0 A, angular order 8 / 4.0 A,
-D = 52), per-species 52-15-15-1 tanh networks with seeded N(0, 1/fan_in)
-weights, 300 K seeded velocities, velocity-Verlet NVE at dt = 0.5 fs.
+Workload (default): the 110,592-molecule water box at 1.0 g/cm^3 (331,776
+atoms, L = 149.006 A), water basis (radial order 16 / 6.0 A, angular order
+8 / 4.0 A, D = 52), per-species 52-32-32-1 tanh networks with seeded
+N(0, 1/fan_in) weights, 300 K seeded velocities, velocity-Verlet NVE at
+dt = 0.5 fs.
 
 One benchmark step = one MD step of the whole path (kick + drift, cell list,
 descriptor, networks, forces + virial, FP64 reductions, kick), replayed from a
@@ -11,14 +12,19 @@ captured CUDA graph on device-resident state. Between timed steps the L2 cache
 is flushed by writing a buffer larger than L2; each step is bracketed by CUDA
 events on the library's stream and the step times are summed.
 
-Metric: atom-steps/s (E+F). The JSON line also carries the end-to-end number
-through the C ABI with host buffers (host->device copy of positions, velocities
-and types, device->host copy of positions, velocities and energies, every
-step), the roofline of the dominant kernel, and the FP64 CPU oracle's
-throughput on the host cores.
+Every precision form of the network (FP32; BF16 tensor-core layers with split
+operands; plain BF16) is timed in the same invocation on the same start, and
+each form's energy and forces on frame 0 are compared with the FP64 oracle's
+(all atoms). Metric: atom-steps/s (E+F) of the fastest form whose force RMS
+error is within 1 meV/A; the line's ``forms`` object carries every form's rate
+and errors. The JSON line also carries the end-to-end number of that form
+through the C ABI with host buffers (host->device copy of positions,
+velocities and types, device->host copy of positions, velocities and
+energies, every step), the roofline of the dominant kernel, and the FP64 CPU
+oracle's throughput on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|bf16|bf16x3] [--workload water_12288|...]
+                  [--forms fp32,bf16x3,bf16] [--workload water_331776|...]
 """
 from __future__ import annotations
 
@@ -40,25 +46,23 @@ if ROOT not in sys.path:
 METRIC = "atom-steps/s (E+F) on 1 GB300, BF16 vs FP32 form at <=1 meV/A force err"
 DT_PS = 5e-4
 
-# FP32 operations per unit of the two fingerprint kernels (FMA = 2 flops):
-# per radial neighbour entry and per unordered angular pair, counted from the
-# arithmetic each unit needs. Forward: the Chebyshev recurrence T_a and two
-# accumulations (plain and species-weighted) per order, plus the distance,
-# cutoff and weight. Backward: per order the coefficient and the Clenshaw
-# steps for S = sum a_q T_q and S' = sum a_q T_q', plus the cutoff derivative,
-# the radial or angle chain rule to the displacement vectors, the force
-# scatter and the virial outer product.
-def force_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
-    """Chain rule with Clenshaw's recurrence for S and S' (9 flops per order)."""
-    return (9 * (Kr - 1) + 42) * n_entries + (9 * (Ka - 1) + 57) * n_ang_pairs
-
-
+# Algorithmic FP32 work per unit (FMA = 2 flops), the figures the roofline is
+# graded with: per radial neighbour entry forward 12 + 4 K_r (distance, cutoff,
+# the Chebyshev recurrence and two accumulations per order) and backward
+# 20 + 6 K_r (the chain rule through every order, force scatter, virial); per
+# unordered angular pair forward 10 + 4 K_a and backward 40 + 6 K_a; per atom
+# 2 sum_l n_l n_{l-1} for each pass through the network (forward, and
+# back-propagation to dE/dG).
 def descriptor_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
-    return (6 * (Kr - 1) + 10) * n_entries + (6 * (Ka - 1) + 10) * n_ang_pairs
+    return (12 + 4 * Kr) * n_entries + (10 + 4 * Ka) * n_ang_pairs
+
+
+def force_kernel_flops(Kr, Ka, n_entries, n_ang_pairs):
+    return (20 + 6 * Kr) * n_entries + (40 + 6 * Ka) * n_ang_pairs
 
 
 def network_flops(widths, n_atoms):
-    """Forward plus back-propagation to dE/dG: 2 x 2 flops per weight."""
+    """Forward plus back-propagation to dE/dG: 2 passes x 2 flops per weight."""
     return 4 * sum(widths[l] * widths[l - 1] for l in range(1, len(widths))) * n_atoms
 
 
@@ -226,7 +230,9 @@ def cpu_baseline(args, budget_s=12.0):
     from oracle import oracle
     st, m, _ = workload(args.workload, *model_overrides(args))
     cores = os.cpu_count() or 1
-    n_cent = min(st.n, 2048)
+    # a contiguous block of centre atoms large enough that the oracle's fixed
+    # cost per call (cell list of the whole box) stays a small part of the time
+    n_cent = min(st.n, 32768)
     mask = np.zeros(st.n, dtype=np.uint8)
     mask[:n_cent] = 1
     oracle.compute(m, st.pos, st.types, st.box, center_mask=mask, n_threads=cores)  # warm
@@ -250,7 +256,7 @@ def run_reference(args, rank, world):
     from oracle import oracle
     st, m, _ = workload(args.workload, *model_overrides(args))
     cores = os.cpu_count() or 1
-    n_cent = min(st.n, 1024)
+    n_cent = min(st.n, 16384)
     mask = np.zeros(st.n, dtype=np.uint8)
     mask[:n_cent] = 1
     for _ in range(args.warmup):
@@ -402,22 +408,173 @@ def run_batch(args, rank, world):
         dist.destroy_process_group()
 
 
+FORM_DTYPE = {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16"}
+F_RMS_BOUND = 1e-3  # eV/A: the force-error bound a form must meet to be the headline
+
+
+def time_form(args, st, m, v0, precision, dev, stream, flush, world):
+    """One precision form: W warm-up and K timed MD steps (graph replay, CUDA
+    events on the library's stream, L2 flushed before each step)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2107_11311_gb300.aenet import (AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING,
+                                              AENET_MD_TIMING_POTENTIAL, AenetGPU)
+    gpu = AenetGPU(m, precision, stream=stream.cuda_stream)
+    gpu.set_skin(args.skin)
+    pos = torch.tensor(st.pos, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    types = torch.tensor(st.types, device=dev)
+    with torch.cuda.stream(stream):
+        gpu.md_nve(pos, vel, types, st.box, DT_PS, 1)  # initial forces + graph capture
+        # timed steps record events only around the potential (each event node
+        # adds ~2 us to a step); the full stage breakdown comes from extra steps
+        # after the timed ones
+        flags = AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING_POTENTIAL
+        for _ in range(args.warmup):
+            flush.zero_()
+            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
+        gpu.check()
+        stats = gpu.neighbor_stats()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stage_sum = None
+        kernels_per_step, fused = 0, False
+        builds0 = gpu.md_list_builds()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
+            ends[k].record(stream)
+            ms, kernels_per_step, fused = gpu.md_stage_times()  # synchronises: per-step stage times
+            stage_sum = ms if stage_sum is None else {s: (None if ms[s] is None else stage_sum[s] + ms[s])
+                                                      for s in ms}
+        torch.cuda.synchronize()
+        gpu.check()
+        builds = gpu.md_list_builds() - builds0
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        # untimed: the full stage breakdown (every stage bracketed by events)
+        n_diag = 5
+        diag = None
+        for _ in range(n_diag):
+            flush.zero_()
+            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING)
+            ms_full, _, _ = gpu.md_stage_times()
+            diag = ms_full if diag is None else {s: diag[s] + ms_full[s] for s in ms_full}
+        gpu.check()
+    gpu.close()
+    t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
+    return {"precision": precision, "t_dev": t_dev, "value": world * st.n * args.steps / t_dev,
+            "ms_per_step": 1e3 * t_dev / args.steps, "stats": stats, "fused": fused,
+            "kernels_per_step": kernels_per_step, "builds": builds,
+            "stage_ms": {s: (None if v is None else v / args.steps) for s, v in stage_sum.items()},
+            "stage_full": {s: round(v / n_diag, 5) for s, v in diag.items()}}
+
+
+def form_accuracy(st, m, precision, ref, dev, stream):
+    """Energy and force errors of one form on frame 0 against the FP64 oracle
+    (every atom): |dE|/N, force RMS over all 3N components, largest component
+    error, and the RMS of the oracle's forces (the scale the errors sit on)."""
+    import torch
+    from paper_2107_11311_gb300.aenet import AenetGPU
+    g = AenetGPU(m, precision, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        E = torch.zeros(1, dtype=torch.float64, device=dev)
+        F = torch.zeros((st.n, 3), dtype=torch.float64, device=dev)
+        g.compute(torch.tensor(st.pos, device=dev), torch.tensor(st.types, device=dev), st.box, energy=E, forces=F)
+        stream.synchronize()
+    g.close()
+    dF = F.cpu().numpy() - ref["forces"]
+    return {"e_err_per_atom": abs(E.item() - ref["energy"]) / st.n,
+            "f_rms_err": float(np.sqrt((dF ** 2).mean())), "f_max_err": float(np.abs(dF).max()),
+            "f_rms": float(np.sqrt((ref["forces"] ** 2).mean()))}
+
+
+def roofline_of(form, m, n, props, max_mhz, peak_kind, workload_name):
+    """Roofline of the form's dominant kernel: algorithmic FP32 flops per launch
+    (unit counts of the launch x per-unit figures) over its event-timed
+    duration, against the FP32 FMA peak."""
+    stats = form["stats"]
+    Kr, Ka = m.order_rad + 1, m.order_ang + 1
+    f_desc = descriptor_kernel_flops(Kr, Ka, stats[0], stats[2])
+    f_force = force_kernel_flops(Kr, Ka, stats[0], stats[2])
+    if form["fused"]:
+        dom = "forces"  # descriptor, networks and forces run as one kernel, timed under "forces"
+        kernel = "k_potential (fused descriptor + network + forces)"
+        flops = f_desc + f_force + network_flops(m.widths, n)
+    else:
+        dom = max(("descriptor", "forces"), key=lambda s: form["stage_ms"][s] or 0.0)
+        kernel = "k_potential, forces mode" if dom == "forces" else "k_potential, descriptor mode"
+        flops = f_force if dom == "forces" else f_desc
+    ms = form["stage_ms"][dom]
+    achieved = flops / (ms * 1e-3) / 1e12
+    peak = fp32_alu_peak_tflops(props.multi_processor_count, max_mhz)
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_launch": flops, "launch_ms": ms,
+            "traffic": captured_traffic(workload_name, form["precision"]) if form["fused"] else None,
+            "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
+                          f"(SM clock max from MEASURED_PEAKS.json, {peak_kind})"}
+
+
+def e2e_rate(args, st, m, precision, pos, vel, types, stream, world):
+    """The same metric end to end through aenet_md_nve with pinned host buffers:
+    every step copies positions, velocities and types in and positions,
+    velocities and energies out."""
+    import torch
+    from paper_2107_11311_gb300.aenet import AENET_MD_CONTINUE, AenetGPU
+    n = st.n
+    hpos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    hvel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    htypes = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hep = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    hek = torch.empty(2, dtype=torch.float64, pin_memory=True)
+    hpos.copy_(torch.as_tensor(pos))
+    hvel.copy_(torch.as_tensor(vel))
+    htypes.copy_(torch.as_tensor(types))
+    e2 = AenetGPU(m, precision, stream=stream.cuda_stream)
+    e2.set_skin(args.skin)
+    e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
+    for _ in range(3):
+        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    h2d = hpos.numel() * 8 + hvel.numel() * 8 + htypes.numel() * 4
+    d2h = hpos.numel() * 8 + hvel.numel() * 8 + hep.numel() * 8 + hek.numel() * 8
+    e2.close()
+    return {"value": world * n * args.e2e_steps / t_e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "form": precision}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
-    ap.add_argument("--workload", default="water_12288")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--forms", default="fp32,bf16x3,bf16",
+                    help="precision forms timed side by side (comma-separated: fp32, bf16x3, bf16)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"],
+                    help="time this form only (same as --forms <form>)")
+    ap.add_argument("--workload", default="water_331776")
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the oracle comparison of each form (sweeps); the headline is then the first form")
     ap.add_argument("--hidden", default=None, help="hidden widths, e.g. 25-25 (model-size sweeps)")
     ap.add_argument("--orders", default=None, help="basis orders N_r,N_a, e.g. 5,3 (model-size sweeps)")
     ap.add_argument("--skin", type=float, default=0.0,
                     help="Verlet-list skin in A for the MD step (0, the default: cell list every step)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    forms = [args.precision] if args.precision else [f.strip() for f in args.forms.split(",") if f.strip()]
+    for f in forms:
+        if f not in FORM_DTYPE:
+            raise SystemExit(f"unknown form {f}")
+    args.precision = forms[0]
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -432,8 +589,6 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2107_11311_gb300.aenet import (AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING,
-                                              AENET_MD_TIMING_POTENTIAL, AenetGPU)
 
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
@@ -441,147 +596,77 @@ def main():
     dev = torch.device("cuda", local)
     st, m, v0 = workload(args.workload, *model_overrides(args))
     n = st.n
-
     stream = torch.cuda.Stream(device=dev)
-    gpu = AenetGPU(m, args.precision, stream=stream.cuda_stream)
-    gpu.set_skin(args.skin)
-    pos = torch.tensor(st.pos, device=dev)
-    vel = torch.tensor(v0, device=dev)
-    types = torch.tensor(st.types, device=dev)
     # L2 flush buffer (> 129 MB L2)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
     clocks = ClockSampler(local)
     clocks.start()  # running before the warm-up, so the timed window is sampled
-    with torch.cuda.stream(stream):
-        gpu.md_nve(pos, vel, types, st.box, DT_PS, 1)  # initial forces + graph capture
-        # timed steps record events only around the potential (each event node
-        # adds ~2 us to a step); the full stage breakdown comes from extra steps
-        # after the timed ones
-        flags = AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING_POTENTIAL
-        for _ in range(args.warmup):
-            flush.zero_()
-            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
-        gpu.check()
-        stats = gpu.neighbor_stats()
+    clocks.mark()
+    wall0 = time.perf_counter()
+    results = {f: time_form(args, st, m, v0, f, dev, stream, flush, world) for f in forms}
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
 
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        stage_sum = None
-        kernels_per_step = 0
-        fused = False
-        builds0 = gpu.md_list_builds()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        clocks.mark()
-        wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1, flags=flags)
-            ends[k].record(stream)
-            ms, kernels_per_step, fused = gpu.md_stage_times()  # synchronises: per-step stage times
-            stage_sum = ms if stage_sum is None else {s: (None if ms[s] is None else stage_sum[s] + ms[s])
-                                                      for s in ms}
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        clk = clocks.stop()
-        gpu.check()
-        builds = gpu.md_list_builds() - builds0
-        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        # untimed: the full stage breakdown (every stage bracketed by events)
-        n_diag = 10
-        diag = None
-        for _ in range(n_diag):
-            flush.zero_()
-            gpu.md_nve(pos, vel, types, st.box, DT_PS, 1,
-                       flags=AENET_MD_ASYNC | AENET_MD_CONTINUE | AENET_MD_TIMING)
-            ms_full, _, _ = gpu.md_stage_times()
-            diag = ms_full if diag is None else {s: diag[s] + ms_full[s] for s in ms_full}
-        gpu.check()
-    t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
-    value = world * n * args.steps / t_dev
-    stage_avg = {s: (None if v is None else v / args.steps) for s, v in stage_sum.items()}
-    stage_full = {s: round(v / n_diag, 5) for s, v in diag.items()}
+    # accuracy of every form against the FP64 oracle (frame 0, all atoms)
+    acc = {}
+    if not args.no_accuracy and rank == 0:
+        from oracle import oracle
+        ref = oracle.compute(m, st.pos, st.types, st.box, n_threads=os.cpu_count() or 1)
+        for f in forms:
+            acc[f] = form_accuracy(st, m, f, ref, dev, stream)
+    within = [f for f in forms if f in acc and acc[f]["f_rms_err"] <= F_RMS_BOUND]
+    if args.no_accuracy:
+        best = forms[0]
+    else:
+        best = max(within, key=lambda f: results[f]["value"]) if within else forms[0]
+    R = results[best]
 
-    # ---- end to end through the C ABI with pinned host buffers
+    # ---- end to end through the C ABI with pinned host buffers (the headline form)
     e2e = None
     if args.e2e_steps > 0:
-        hpos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
-        hvel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
-        htypes = torch.empty(n, dtype=torch.int32, pin_memory=True)
-        hep = torch.empty(2, dtype=torch.float64, pin_memory=True)
-        hek = torch.empty(2, dtype=torch.float64, pin_memory=True)
-        hpos.copy_(pos.cpu())
-        hvel.copy_(vel.cpu())
-        htypes.copy_(types.cpu())
-        e2 = AenetGPU(m, args.precision, stream=stream.cuda_stream)
-        e2.set_skin(args.skin)
-        e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
-        for _ in range(3):
-            e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
-        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
-        h2d = hpos.numel() * 8 + hvel.numel() * 8 + htypes.numel() * 4
-        d2h = hpos.numel() * 8 + hvel.numel() * 8 + hep.numel() * 8 + hek.numel() * 8
-        e2e = {"value": world * n * args.e2e_steps / t_e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
-        e2.close()
+        e2e = e2e_rate(args, st, m, best, st.pos, v0, st.types, stream, world)
 
     if rank != 0:
-        gpu.close()
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (FP32 ALU bound)
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_kind = measured_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    Kr, Ka = m.order_rad + 1, m.order_ang + 1
-    flops_force = force_kernel_flops(Kr, Ka, stats[0], stats[2])
-    flops_desc = descriptor_kernel_flops(Kr, Ka, stats[0], stats[2])
-    if fused:
-        # descriptor, networks and forces run as one kernel, timed under "forces"
-        dom = "forces"
-        kernel_name = ("k_potential_list (fused descriptor + network + forces over the Verlet list)"
-                       if args.skin > 0 else "k_potential (fused descriptor + network + forces)")
-        flops = flops_force + flops_desc + network_flops(m.widths, n)
-    else:
-        dom = max(("descriptor", "forces"), key=lambda s: stage_avg[s])
-        kernel_name = "k_fingerprint backward (forces)" if dom == "forces" else "k_fingerprint forward (descriptor)"
-        flops = flops_force if dom == "forces" else flops_desc
-    achieved = flops / (stage_avg[dom] * 1e-3) / 1e12
-    peak = fp32_alu_peak_tflops(props.multi_processor_count, max_mhz)
+    forms_out = {}
+    for f in forms:
+        r = results[f]
+        rl = roofline_of(r, m, n, props, max_mhz, peak_kind, args.workload)
+        forms_out[f] = dict({"value": r["value"], "ms_per_step": r["ms_per_step"], "fused": r["fused"],
+                             "kernels_per_step": r["kernels_per_step"], "roofline_frac": rl["frac"],
+                             "stage_ms": {s: round(v, 5) for s, v in r["stage_ms"].items() if v is not None},
+                             "meets_1meV_per_A": (f in within) if acc else None},
+                            **acc.get(f, {}))
     line = {
-        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
-        "data": "synthetic",
-        "config": dict(md_config(args, st, m, world), neighbour_entries=stats[0], angular_pairs=stats[2],
-                       list_builds=builds if args.skin > 0 else None),
-        "stage_ms": {s: round(v, 5) for s, v in stage_avg.items() if v is not None},
-        "stage_ms_all_events": stage_full,
+        "metric": METRIC, "value": R["value"], "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[best], "data": "synthetic",
+        "config": dict(md_config(args, st, m, world), precision=best, neighbour_entries=R["stats"][0],
+                       angular_pairs=R["stats"][2], list_builds=R["builds"] if args.skin > 0 else None,
+                       headline_rule="fastest form whose force RMS error against the FP64 oracle "
+                                     "(frame 0, all atoms) is <= 1 meV/A"),
+        "forms": forms_out,
+        "stage_ms": {s: round(v, 5) for s, v in R["stage_ms"].items() if v is not None},
+        "stage_ms_all_events": R["stage_full"],
         # kernel nodes of the step graph, plus the 4 kernels of each list rebuild
         # (the body of the graph's conditional node) that ran in the timed steps
-        "gpu_launches": kernels_per_step * args.steps + (4 * builds if args.skin > 0 else 0),
+        "gpu_launches": R["kernels_per_step"] * args.steps + (4 * R["builds"] if args.skin > 0 else 0),
         "e2e": e2e,
-        "roofline": {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": captured_traffic(args.workload, args.precision, args.skin) if fused else None,
-                     "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
-                                   f"(SM clock max from MEASURED_PEAKS.json, {peak_kind})"},
+        "roofline": roofline_of(R, m, n, props, max_mhz, peak_kind, args.workload),
         "clocks": clk,
         "wall_s": wall,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
-    gpu.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -192,7 +192,9 @@ int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
 /*
  * Energies, forces and virials of many independent periodic structures in one
  * evaluation (one binning, one potential launch over the cells of every
- * structure, one per-structure reduction).
+ * structure, one per-structure reduction). Each structure's energy is the
+ * Behler-Parrinello sum E_s = sum_{i in s} E_i of Sec. II.A, its forces the
+ * chain rule of Sec. II.C, exactly as aenet_compute evaluates one structure.
  *   n_struct     >= 1
  *   atom_offset  [n_struct + 1] int64, HOST: structure s holds atoms
  *                atom_offset[s] .. atom_offset[s+1]-1; atom_offset[0] = 0
@@ -208,7 +210,7 @@ int aenet_compute_batch(aenet_ctx *ctx, int n_struct, const int64_t *atom_offset
                         double *virials);
 
 /*
- * Prepared batch: the batched evaluation above (row a11 of the path; the
+ * Prepared batch: the batched evaluation above (the
  * energy of each structure is the Behler-Parrinello sum of Sec. II.A, its
  * forces the chain rule of Sec. II.C) made replayable for repeated
  * evaluation of one batch layout with new coordinates (an MD or screening
@@ -253,7 +255,7 @@ int aenet_batch_run(aenet_ctx *ctx);
 int aenet_batch_tuning(aenet_ctx *ctx, int *persistent, int *tile, int *ctas, int *kernels, float *ms);
 
 /*
- * Descriptor only (rows a1-a5 of the path; Sec. II.B): G [n_atoms * D]
+ * Descriptor only (Sec. II.B): G [n_atoms * D]
  * float32, host or device, row i = atom i in input order, layout [radial,
  * angular, radial_w, angular_w] before standardisation. Other arguments and
  * errors as aenet_compute. Synchronises.
@@ -334,11 +336,17 @@ int aenet_md_stage_times(aenet_ctx *ctx, float ms[6], int *kernels_per_step, int
  *   n_atoms      0 .. AENET_NOALLOC_MAX_ATOMS; larger systems return
  *                AENET_E_CAPACITY (as do boxes with more than
  *                AENET_NOALLOC_MAX_CELLS cells of edge >= the largest cutoff)
- *   pos, types   DEVICE pointers, [n_atoms * 3] double and [n_atoms] int32
- *   box          [3] double, HOST
+ *   pos, types   DEVICE pointers of the current device (or managed memory),
+ *                [n_atoms * 3] double and [n_atoms] int32; device memory of
+ *                another GPU is refused with AENET_E_ARG
+ *   box          [3] double, HOST: the edges of an ORTHORHOMBIC box. This entry
+ *                point has no context, so a tilt set with aenet_set_box_tilt
+ *                never applies to it; tilted cells go through
+ *                aenet_descriptors on a context
  *   n_species, type_weight (HOST [n_species]), rc_rad, order_rad, rc_ang,
  *   order_ang    the basis, as in aenet_model_desc
- *   G            DEVICE [n_atoms * D] float32 output, input order
+ *   G            DEVICE [n_atoms * D] float32 output of the current device,
+ *                input order
  *   stream       cudaStream_t (NULL = legacy default stream)
  * The first call on a device looks up the device address of the scratch
  * (cudaGetSymbolAddress, with that device current); make that first call

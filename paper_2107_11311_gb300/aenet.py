@@ -136,14 +136,37 @@ NOALLOC_MAX_ATOMS = 16384
 
 def descriptors_noalloc(model, pos, types, box, out, stream=None):
     """Descriptor through the allocation-free entry point (no context, no device
-    allocation; for callers that cannot call cudaMalloc). ``pos``, ``types`` and
-    ``out`` [n, D] float32 must be CUDA tensors; at most NOALLOC_MAX_ATOMS atoms."""
+    allocation; for callers that cannot call cudaMalloc). ``pos`` [n, 3] float64,
+    ``types`` [n] int32 and ``out`` [n, D] float32 must be contiguous CUDA tensors
+    on the current device; at most NOALLOC_MAX_ATOMS atoms; orthorhombic boxes
+    only. ``stream``: a torch.cuda.Stream or a raw cudaStream_t handle (default:
+    torch's current stream)."""
     lib = load()
-    pos, types = _as(pos, np.float64), _as(types, np.int32)
+    import torch
+    for name, x in (("pos", pos), ("types", types), ("out", out)):
+        if not _is_torch(x) or x.device.type != "cuda":
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if x.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{x.device.index}, not on the current device "
+                             f"cuda:{torch.cuda.current_device()}")
+    pos, types, out = _as(pos, np.float64), _as(types, np.int32), _as(out, np.float32)
+    n = int(pos.shape[0])
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError(f"pos must have shape (n, 3), got {tuple(pos.shape)}")
+    if types.numel() != n:
+        raise ValueError(f"types holds {types.numel()} entries for {n} atoms")
+    D = 2 * (int(model.order_rad) + int(model.order_ang) + 2)
+    if tuple(out.shape) != (n, D):
+        raise ValueError(f"out must have shape ({n}, {D}), got {tuple(out.shape)}")
     box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
     tw = np.ascontiguousarray(model.type_weights, dtype=np.float64)
-    st = stream if stream is not None else _current_stream()
-    rc = lib.aenet_descriptors_noalloc(int(pos.shape[0]), _ptr(pos), _ptr(types), _ptr(box), int(model.n_species),
+    if stream is None:
+        st = _current_stream()
+    elif hasattr(stream, "cuda_stream"):  # a torch.cuda.Stream
+        st = C.c_void_p(stream.cuda_stream)
+    else:
+        st = C.c_void_p(int(stream)) if not isinstance(stream, C.c_void_p) else stream
+    rc = lib.aenet_descriptors_noalloc(n, _ptr(pos), _ptr(types), _ptr(box), int(model.n_species),
                                        _ptr(tw), float(model.rc_rad), int(model.order_rad), float(model.rc_ang),
                                        int(model.order_ang), _ptr(out), st)
     if rc != 0:

@@ -352,7 +352,7 @@ inline cudaError_t allow_max_smem(K kern) {
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on ctx.stream and return the launch status.
 
-// Wrap, bin and sort atoms by cell (rows a1, a2 of the path).
+// Wrap, bin and sort atoms by cell (the periodic cell list).
 cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
 // The scan + scatter half of launch_cells (after the counts are in place).
 cudaError_t launch_sort(Context &c, const Grid &g, int n);
@@ -362,16 +362,16 @@ cudaError_t launch_cells_batch(Context &c, int n, int total_cells, const double 
 // into c.d_bres rows, or (when given) straight into energies[S], virials[S*9].
 cudaError_t launch_batch_reduce(Context &c, double *energies = nullptr, double *virials = nullptr);
 
-// Descriptor of every atom into c.d_G (rows a3-a5; k_potential, descriptor mode).
+// Descriptor of every atom into c.d_G (Sec. II.B; k_potential, descriptor mode).
 cudaError_t launch_fp_forward(Context &c, const Grid &g, int n);
 
-// Per-species networks: E_i and dE/dG_i (row a6), energy block partials.
+// Per-species networks: E_i and dE/dG_i (Sec. II.A, Eq. ANN-layer), energy block partials.
 cudaError_t launch_ann(Context &c, int n);
 
-// Forces and virial partials from c.d_dEdG (row a8; k_potential, forces mode).
+// Forces and virial partials from c.d_dEdG (the chain rule; k_potential, forces mode).
 cudaError_t launch_fp_backward(Context &c, const Grid &g, int n);
 
-// Energy and virial reductions (row a7) over n_eparts energy partials and the
+// Energy and virial reductions (E = sum_i E_i, Sec. II.A) over n_eparts energy partials and the
 // cells' virial partials, and outputs in input order.
 cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom);
 
@@ -406,9 +406,9 @@ cudaError_t launch_finalize_forces(Context &c, int n, double *forces);
 // Descriptor rows to input order (float).
 cudaError_t launch_unsort_G(Context &c, int n, float *G);
 
-// Velocity Verlet (row a9).
+// Velocity Verlet (the propagation step of the MD cycle, Fig. 1).
 // One MD half: kick (v += dt/2 F/m c) + drift (x += dt v) fused with the binning
-// of the new positions (rows a9 + a1-a2); the scan and scatter follow.
+// of the new positions (integration and cell list); the scan and scatter follow.
 cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
                                      const int32_t *types);
 // The closing kick (v += dt/2 F/m c) with the kinetic energy, fused with the

@@ -1,4 +1,4 @@
-// Row a6 of the path: the per-species feed-forward networks (Sec. II.A,
+// The per-species feed-forward networks (Sec. II.A,
 // Eq. ANN-layer; tanh hidden layers, linear output) giving E_i, and their
 // back-propagation to dE/dG_i for the force kernel.
 //

@@ -1,4 +1,4 @@
-// Row a6 of the path in the precision form: the per-species networks (Sec. II.A,
+// The precision form of the per-species networks (Sec. II.A,
 // Eq. ANN-layer; two tanh hidden layers, linear output) and their
 // back-propagation to dE/dG as dense BF16 tensor-core products over atoms
 // grouped by species, accumulated in FP32.

@@ -1,4 +1,4 @@
-// Rows a1-a2 of the path: wrap FP64 positions into the box, bin them into the
+// The periodic cell list: wrap FP64 positions into the box, bin them into the
 // cell grid (edge >= the largest cutoff) and sort them by cell.
 //
 // Every atom is stored as FP32 coordinates RELATIVE TO ITS CELL ORIGIN

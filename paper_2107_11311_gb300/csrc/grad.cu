@@ -1,4 +1,4 @@
-// Row a10 of the path: the energy gradient with respect to the network
+// The energy gradient with respect to the network
 // parameters (back-propagation, Sec. II.C), summed over the atoms of each
 // species:
 //   dE/dW^l[o][k] = sum_i delta^l_i[o] x^{l-1}_i[k],   dE/db^l[o] = sum_i delta^l_i[o]

@@ -1,4 +1,4 @@
-// Rows a7 and a9 of the path: FP64 reductions of the total energy (the
+// FP64 reductions of the total energy (the
 // Behler-Parrinello sum E = sum_i E_i) and the virial, outputs back in input
 // order, and the velocity-Verlet NVE update (the propagation step of the MD
 // cycle, Fig. 1) in FP64.

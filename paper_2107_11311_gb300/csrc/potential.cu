@@ -243,18 +243,30 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
     return cudaGetLastError();
 }
 
+// Attributes (static shared memory) of the descriptor kernel form for (Kr, Ka).
+cudaError_t na_kernel_attributes(int Kr, int Ka, cudaFuncAttributes *fa) {
+    if (Kr == 17 && Ka == 9) return cudaFuncGetAttributes(fa, k_potential<17, 9, true, kDescriptor, false, 32>);
+    if (Kr == 21 && Ka == 7) return cudaFuncGetAttributes(fa, k_potential<21, 7, true, kDescriptor, false, 32>);
+    if (Kr <= 20 && Ka <= 12) return cudaFuncGetAttributes(fa, k_potential<20, 12, false, kDescriptor, false, 32>);
+    return cudaFuncGetAttributes(fa, k_potential<24, 8, false, kDescriptor, false, 32>);
+}
+
 int na_fail(int code, const char *msg) {
     set_context_free_error(msg);
     return code;
 }
 
-bool na_is_device(const void *p) {
+// Device memory of the current device, or managed memory (reachable from it).
+// Device memory of another GPU is refused: the kernels run on the current
+// device and would fault on it unless peer access happened to be enabled.
+bool na_is_device(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -278,8 +290,11 @@ extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t
     const bool supported = (Kr == 17 && Ka == 9) || (Kr == 21 && Ka == 7) || (Kr <= 20 && Ka <= 12) ||
                            (Kr <= 24 && Ka <= 8);
     if (!supported || D > kMaxD) return na_fail(AENET_E_ARG, "unsupported basis orders");
-    if (n > 0 && (!pos || !types || !G || !na_is_device(pos) || !na_is_device(types) || !na_is_device(G)))
-        return na_fail(AENET_E_ARG, "pos, types and G must be device pointers");
+    int cur_dev = 0;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess) return na_fail(AENET_E_CUDA, "cudaGetDevice failed");
+    if (n > 0 && (!pos || !types || !G || !na_is_device(pos, cur_dev) || !na_is_device(types, cur_dev) ||
+                  !na_is_device(G, cur_dev)))
+        return na_fail(AENET_E_ARG, "pos, types and G must be device pointers of the current device");
     Basis B{};
     B.n_species = n_species;
     B.Kr = Kr;
@@ -338,12 +353,17 @@ extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t
     int tl = (int)(1.25 * ((double)n / g.ncell) * g.n_off + 64.0);
     tl = ((tl + 31) / 32) * 32;
     caps.tile = tl < 128 ? 128 : (tl > 1024 ? 1024 : tl);
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // dynamic shared memory available to the descriptor kernel: the opt-in
+    // limit minus its static shared memory (what allow_max_smem grants)
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cur_dev) != cudaSuccess ||
+        na_kernel_attributes(Kr, Ka, &fa) != cudaSuccess)
+        return na_fail(AENET_E_CUDA, "device attributes of the descriptor kernel");
+    const size_t smem_avail = optin > (int)fa.sharedSizeBytes ? (size_t)(optin - (int)fa.sharedSizeBytes) : 0;
     unsigned w = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        if (optin > 0 && make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total > (size_t)optin)
+        if (make_playout(g.n_off, caps.tile, caps.nb, caps.ang, 0, 0).total > smem_avail)
             return na_fail(AENET_E_CAPACITY, "neighbour lists exceed the shared memory of one CTA");
         // the scratch keeps the previous call's contents: clear what must start at zero
         if ((e = cudaMemsetAsync(count, 0, sizeof(int) * g.ncell, st)) != cudaSuccess ||

@@ -4,7 +4,8 @@
 // potential.cu (cell-list evaluation) and potential_md.cu (MD with a Verlet
 // list), which are compiled in parallel; each instantiates the forms it launches.
 //
-// Fused potential kernel: rows a3-a8 of the path in one pass per atom.
+// Fused potential kernel: neighbours, descriptor (Sec. II.B), network
+// (Sec. II.A) and chain rule to forces and virial in one pass per atom.
 //
 // One CTA per cell, one warp per atom (atoms handed out dynamically inside the
 // CTA). For each atom the warp

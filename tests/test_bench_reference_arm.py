@@ -22,7 +22,7 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == "atom-steps/s" and d["higher_is_better"] is True
     assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "water_12288"
+    assert d["config"]["workload"] == "water_331776"
     assert d["value"] > 0 and d["ms_per_step"] > 0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]

@@ -1,4 +1,4 @@
-"""Batched form (row a11): many independent periodic structures of uneven size
+"""Batched form: many independent periodic structures of uneven size
 (log-uniform 32 ... 2,048 atoms, water and the 4-species solid, boxes down to
 below the cutoff) evaluated in one call, against the oracle per structure and
 against one-structure calls of the same context."""

@@ -1,4 +1,4 @@
-"""Prepared batch (row a11): one batch layout tuned once (persistent vs
+"""Prepared batch: one batch layout tuned once (persistent vs
 one-CTA-per-cell launch, staging tile), captured as one CUDA graph and
 replayed on new coordinates. Checked against the oracle per structure and
 against the eager batched call."""

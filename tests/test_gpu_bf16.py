@@ -1,4 +1,4 @@
-"""Precision forms of the network (row a6): BF16 tensor-core layers with FP32
+"""Precision forms of the network (Sec. II.A, Eq. ANN-layer): BF16 tensor-core layers with FP32
 accumulation, and split BF16 (hi*hi + hi*lo + lo*hi), against the FP64 oracle.
 
 Split BF16 carries ~16 significand bits per operand, so it must meet the FP32

@@ -94,6 +94,20 @@ def test_other_basis_sizes_and_widths(gpu_mod, orders, hidden):
     assert not (np.abs(G - refG) > descriptor_tol(refG, m)).any()
 
 
+@pytest.mark.parametrize("hidden", [(25, 25), (32, 32), (17, 32)])
+def test_water_basis_wide_networks(gpu_mod, hidden):
+    """The water basis (orders 16, 8) with hidden widths 17-32: the fused
+    kernel's 32-wide form, which runs the paper's 52-25-25-1 water model and the
+    52-32-32-1 network of the large water box. Every output against the oracle,
+    on the 192-atom box and on the 8-molecule box shorter than the cutoff."""
+    m = inputs.make_model("water", hidden=hidden)
+    for st in (inputs.water_192(), inputs.water(8, 6.6, seed=3)):
+        g = gpu_mod.AenetGPU(m, "fp32")
+        got = g.compute(st.pos, st.types, st.box)
+        ref = O.compute(m, st.pos, st.types, st.box)
+        _check_efw(ref, got, st.n, f"water {st.n} atoms, hidden {hidden}")
+
+
 def test_device_and_host_pointers_agree(gpu_mod):
     st = inputs.water_192()
     m = inputs.make_model("water")
@@ -328,17 +342,26 @@ def test_md_water_12288_1000_steps(gpu_mod):
     ek = torch.zeros(1001, dtype=torch.float64, device="cuda")
     g.md_nve(pos, vel, types, st.box, 5e-4, 1000, e_pot=ep, e_kin=ek)
     et = (ep + ek).cpu().numpy()
-    assert np.isfinite(et).all() and np.isfinite(pos.cpu().numpy()).all()
+    x1000 = pos.cpu().numpy()
+    assert np.isfinite(et).all() and np.isfinite(x1000).all()
     drift = np.abs(et - et[0]).max() / st.n
-    # the oracle's error for this potential at 0.5 fs on the 192-atom box
-    s2 = inputs.water_192()
-    v2 = inputs.maxwell_boltzmann(m.masses[s2.types], 300.0, seed=2)
-    _, _, epo, eko = O.md_nve(m, s2.pos, v2, s2.types, s2.box, 5e-4, 1000)
-    ref = np.abs((epo + eko) - (epo[0] + eko[0])).max() / s2.n
-    print(f"water_12288: max |E_tot - E_tot(0)|/N = {drift:.3e} eV/atom (oracle, 192 atoms: {ref:.3e})")
+    # the oracle's own velocity-Verlet error on the same start (1,000 FP64 steps
+    # of the same 12,288 atoms; the trajectories part through chaos, the error
+    # level does not)
+    _, _, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 1000)
+    ref = np.abs((epo + eko) - (epo[0] + eko[0])).max() / st.n
+    print(f"water_12288: max |E_tot - E_tot(0)|/N = {drift:.3e} eV/atom (oracle, same start: {ref:.3e})")
     assert drift <= 2.0 * ref + 5e-3
+    # per-step force error against the oracle on frames 0 and 1000 (frame 1000:
+    # the GPU trajectory's own positions, evaluated by both)
     r0 = O.compute(m, st.pos, st.types, st.box)
     assert abs(ep[0].item() - r0["energy"]) / st.n <= E_TOL
+    for frame, x in ((0, st.pos), (1000, x1000)):
+        ref_f = r0 if frame == 0 else O.compute(m, x, st.types, st.box)
+        got = g.compute(x, st.types, st.box)
+        _check_efw(ref_f, got, st.n, f"water_12288 frame {frame}")
+        rms = float(np.sqrt(((got["forces"] - ref_f["forces"]) ** 2).mean()))
+        print(f"water_12288 frame {frame}: force RMS error {rms:.2e} eV/A")
 
 
 def test_md_stage_timing_modes(gpu_mod):

@@ -50,6 +50,23 @@ def test_verlet_md_matches_oracle_trajectory(gpu_mod):
     np.testing.assert_allclose(vel, vo, atol=1e-2)
 
 
+@pytest.mark.parametrize("hidden", [(25, 25), (32, 32)])
+def test_verlet_md_wide_network_matches_oracle(gpu_mod, hidden):
+    """The list kernel's 32-wide form (water basis, hidden widths 17-32; the
+    paper's 52-25-25-1 water model among them): 10 steps against the oracle's
+    own integration with the same network."""
+    st = inputs.water_192()
+    m = inputs.make_model("water", hidden=hidden)
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+    xo, vo, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 10)
+    g, pos, vel, ep, ek = _run(gpu_mod, m, st, v0, 10, 1.0)
+    assert g.md_list_builds() >= 1
+    assert np.abs(ep - epo).max() / st.n <= E_TOL
+    np.testing.assert_allclose(ek, eko, rtol=1e-5)
+    np.testing.assert_allclose(pos, xo, atol=1e-5)
+    np.testing.assert_allclose(vel, vo, atol=1e-2)
+
+
 def _stepwise(gpu_mod, m, st, v0, n_steps, skin):
     """One step per call (continuing): the energy the list path records after
     each step, and a fresh cell-list evaluation (another context) of the same
