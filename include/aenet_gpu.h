@@ -368,6 +368,15 @@ int aenet_descriptors_noalloc(int n_atoms, const double *pos, const int32_t *typ
  * aenet_grad_weights can follow; costs (D + 2 sum H_l) floats per atom.
  */
 #define AENET_OPT_KEEP_ACTIVATIONS 1
+/*
+ * AENET_OPT_FUSED_NETWORK (value 0/1, default 1), BF16 forms only: with 1 the
+ * per-species networks run on the tensor cores inside the fused potential
+ * kernel (one geometry pass; the water and solid bases, two hidden layers of
+ * at most 32); with 0 they run as the three-kernel path (descriptor kernel,
+ * tensor-core network kernel over species-grouped tiles, force kernel). Both
+ * compute the same products; the option exists to compare the two.
+ */
+#define AENET_OPT_FUSED_NETWORK 2
 int aenet_set_option(aenet_ctx *ctx, int option, int value);
 
 /*

@@ -26,6 +26,7 @@ constexpr unsigned kErrAngCap = 2u;     // angular list overflow
 constexpr unsigned kErrOverlap = 4u;    // |d| < 1e-6 A
 constexpr unsigned kErrNonfinite = 8u;  // non-finite coordinate
 constexpr unsigned kErrType = 16u;      // species index out of range
+constexpr unsigned kErrTimeout = 32u;   // a bounded in-kernel wait ran out
 
 // Descriptor basis and species constants, passed by value to the kernels.
 struct Basis {
@@ -160,6 +161,7 @@ struct Context {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int precision = AENET_FP32;
+    bool fuse_network = true;      // BF16 forms: tensor-core network inside the fused kernel
     Basis basis{};
     Net net{};
     std::vector<double> mass;      // [n_species], empty if none
@@ -398,6 +400,13 @@ int potential_split(const Context &c, const Grid &g, int *split_from);
 // Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
 bool fused_supported(const Context &c);
 cudaError_t launch_fused_potential(Context &c, const Grid &g, int n);
+// Fused kernel with the networks on the tensor cores (BF16 forms; two hidden
+// layers <= 32 wide; the water (16, 8) and solid (20, 6) bases), unless the
+// context asked for the three-kernel path (AENET_OPT_FUSED_NETWORK 0).
+bool tc_fused_supported(const Context &c);
+cudaError_t launch_fused_tc(Context &c, const Grid &g, int n);
+// Either fused form: descriptor, networks and forces in one kernel.
+inline bool fused_path(const Context &c) { return fused_supported(c) || tc_fused_supported(c); }
 int ann_blocks(int n);
 
 // Forces to input order (FP64) only.

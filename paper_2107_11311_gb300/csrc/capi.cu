@@ -212,11 +212,14 @@ cudaError_t mark(Context &c, int k) {
 // three split kernels), with stage events 3, 4 (after descriptor, network) and
 // 5 (after forces) when selected. *n_eparts = number of energy partials written.
 int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts) {
-    if (fused_supported(c)) {
+    if (fused_path(c)) {
         // descriptor, network and forces in one kernel: their stage events coincide
         CK(mark(c, 3), "event");
         CK(mark(c, 4), "event");
-        CK(launch_fused_potential(c, g, n), "potential kernel");
+        if (fused_supported(c))
+            CK(launch_fused_potential(c, g, n), "potential kernel");
+        else
+            CK(launch_fused_tc(c, g, n), "potential kernel (tensor-core network)");
         *n_eparts = c.pot_parts;
         c.last_epart = c.d_e_part;
         c.last_eparts = c.pot_parts;
@@ -269,6 +272,7 @@ int read_error_word(Context &c) {
     if (w & kErrOverlap) return fail(&c, AENET_E_OVERLAP, "two image-atoms closer than 1e-6 A");
     if (w & (kErrNbCap | kErrAngCap))
         return fail(&c, AENET_E_CAPACITY, "neighbour list overflow (capacity %d / %d)", c.caps.nb, c.caps.ang);
+    if (w & kErrTimeout) return fail(&c, AENET_E_TIMEOUT, "a bounded wait inside the potential kernel gave up");
     return AENET_OK;
 }
 
@@ -1046,7 +1050,7 @@ static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const in
     // stage events: all 7 (AENET_MD_TIMING), or only those around the potential
     // (AENET_MD_TIMING_POTENTIAL; around each split kernel outside the fused form)
     const unsigned ev_mask = (flags & AENET_MD_TIMING) ? 0x7Fu
-                             : (flags & AENET_MD_TIMING_POTENTIAL) ? (fused_supported(c) ? 0x30u : 0x3Cu)
+                             : (flags & AENET_MD_TIMING_POTENTIAL) ? (fused_path(c) ? 0x30u : 0x3Cu)
                                                                    : 0u;
     const bool timing = ev_mask != 0;
     const bool verlet = c.skin > 0.0 && fused_supported(c);
@@ -1310,7 +1314,7 @@ extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_st
             ms[k] = nanf("");  // stage not recorded in the light timing mode
     }
     if (kernels_per_step) *kernels_per_step = c.md_kernels;
-    if (path_flags) *path_flags = fused_supported(c) ? AENET_PATH_FUSED : 0;
+    if (path_flags) *path_flags = fused_path(c) ? AENET_PATH_FUSED : 0;
     return AENET_OK;
 }
 
@@ -1320,6 +1324,13 @@ extern "C" int aenet_set_option(aenet_ctx *h, int option, int value) {
     if (option == AENET_OPT_KEEP_ACTIVATIONS) {
         c.keep_act = value != 0;
         c.act_valid = false;
+        return AENET_OK;
+    }
+    if (option == AENET_OPT_FUSED_NETWORK) {
+        if (c.fuse_network != (value != 0)) {
+            c.fuse_network = value != 0;
+            destroy_graph(c);  // the captured MD step holds the other path's kernels
+        }
         return AENET_OK;
     }
     return fail(&c, AENET_E_ARG, "unknown option %d", option);

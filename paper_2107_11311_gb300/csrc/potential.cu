@@ -17,13 +17,34 @@ using namespace detail;
 // 1 KB of it reserved per CTA).
 constexpr size_t kTwoCtaSmem = 113 * 1024;
 
+// The tensor-core form's network: packed BF16 weights and FP32 biases of the
+// context (prepare_bf16_weights), hidden widths and the activation record.
+TcNet make_tc_net(const Context &c, const FusedNet &net) {
+    TcNet tn;
+    tn.pk = make_packed(c.net.widths[1], c.net.widths[2]);
+    tn.wpk = reinterpret_cast<const uint32_t *>(c.d_wbf);
+    tn.bias = reinterpret_cast<const float *>(reinterpret_cast<const uint32_t *>(c.d_wbf) + c.wbf_elems);
+    tn.H1 = c.net.widths[1];
+    tn.H2 = c.net.widths[2];
+    tn.rec_len = net.rec_len;
+    return tn;
+}
+
 template <int KRT, int KAT, bool EXACT, int MODE>
 cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
-    const int n_sp = MODE == kFused ? c.basis.n_species : 0;
-    size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, n_sp, net.stride).total;
-    // the network's hidden-width bound is a template argument of the fused form only
+    constexpr bool tc = is_tc_mode(MODE);
+    const int n_sp = (MODE == kFused || tc) ? c.basis.n_species : 0;
+    size_t smem = make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, n_sp, tc ? kTcParStride : net.stride,
+                               kPWarps, tc)
+                      .total;
+    // the network's hidden-width bound is a template argument of the fused forms only
     auto kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 32> : k_potential<KRT, KAT, EXACT, MODE, false, 32>;
     int nw = kPWarps;
+    if constexpr (tc) {
+        if (net.hb == 16)
+            kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 16>
+                                 : k_potential<KRT, KAT, EXACT, MODE, false, 16>;
+    }
     if constexpr (MODE == kFused) {
         if (net.hb == 16) {
             kern = c.batch_sinfo ? k_potential<KRT, KAT, EXACT, MODE, true, 16>
@@ -45,7 +66,9 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
     }
     cudaError_t e = allow_max_smem(kern);
     if (e != cudaSuccess) return e;
-    float *rows = MODE == kFused ? (c.keep_act ? c.d_act : nullptr) : c.d_G;  // activation records / G rows
+    // activation records (fused forms) / G rows
+    float *rows = (MODE == kFused || tc) ? (c.keep_act ? c.d_act : nullptr) : c.d_G;
+    const TcNet tn = tc ? make_tc_net(c, net) : TcNet{};
     // one structure: (some) cells split into parts (persistent CTAs); batches: whole cells
     int split_from = 0;
     const int split = c.batch_sinfo ? 1 : potential_split(c, g, &split_from);
@@ -66,7 +89,7 @@ cudaError_t launch_mode(Context &c, const Grid &g, const FusedNet &net) {
                                               c.d_shift, c.d_scale, c.d_F4, c.d_eatom, rows, c.d_dEdG,
                                               c.d_e_part, c.d_vir_part, c.d_stats, c.d_err, work,
                                               (work && c.batch_sinfo) ? c.batch_order : nullptr, n_items, nullptr,
-                                              nullptr, split, split_from);
+                                              nullptr, split, split_from, tn);
     c.last_grid = grid;
     c.pot_parts = n_items;
     return cudaGetLastError();
@@ -76,6 +99,11 @@ template <int MODE>
 cudaError_t dispatch(Context &c, const Grid &g) {
     const FusedNet net = make_fused_net(c.net);
     const int Kr = c.basis.Kr, Ka = c.basis.Ka;
+    if constexpr (is_tc_mode(MODE)) {  // the bases whose slots are the G columns
+        if (Kr == 17 && Ka == 9) return launch_mode<17, 9, true, MODE>(c, g, net);
+        if (Kr == 21 && Ka == 7) return launch_mode<21, 7, true, MODE>(c, g, net);
+        return cudaErrorInvalidValue;
+    }
     if (Kr == 17 && Ka == 9) return launch_mode<17, 9, true, MODE>(c, g, net);
     if (Kr == 21 && Ka == 7) return launch_mode<21, 7, true, MODE>(c, g, net);
     // small bases (e.g. D = 20) get their own bound, so that the fixed-trip
@@ -123,8 +151,17 @@ bool fused_supported(const Context &c) {
     return true;
 }
 
+bool tc_fused_supported(const Context &c) {
+    if (c.precision == AENET_FP32 || !c.fuse_network || !bf16_supported(c.net) || !c.d_wbf) return false;
+    return (c.basis.Kr == 17 && c.basis.Ka == 9) || (c.basis.Kr == 21 && c.basis.Ka == 7);
+}
+
 size_t potential_smem_bytes(const Context &c, const Grid &g) {
     const FusedNet net = make_fused_net(c.net);
+    if (tc_fused_supported(c))
+        return make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, kTcParStride, kPWarps,
+                            true)
+            .total;
     return make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, fused_supported(c) ? c.basis.n_species : 0,
                         net.stride)
         .total;
@@ -136,6 +173,14 @@ cudaError_t launch_fused_potential(Context &c, const Grid &g, int n) {
     e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
     if (e != cudaSuccess) return e;
     return dispatch<kFused>(c, g);
+}
+
+cudaError_t launch_fused_tc(Context &c, const Grid &g, int n) {
+    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
+    if (e != cudaSuccess) return e;
+    return c.precision == AENET_BF16X3 ? dispatch<kFusedTCx3>(c, g) : dispatch<kFusedTC>(c, g);
 }
 
 cudaError_t launch_fp_forward(Context &c, const Grid &g, int n) {
@@ -239,7 +284,7 @@ cudaError_t na_launch_fp(const Basis &B, const Grid &g, const Caps &caps, cudaSt
     kern<<<g.ncell, kPThreads, smem, st>>>(B, net, g, nullptr, 0, caps, pos4, cell_start, nullptr, nullptr, nullptr,
                                            nullptr,
                                            nullptr, Gs, nullptr, nullptr, nullptr, stats, err, nullptr, nullptr,
-                                           g.ncell, nullptr, nullptr, 1, 0);
+                                           g.ncell, nullptr, nullptr, 1, 0, TcNet{});
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@
 #include <algorithm>
 
 #include "aenet_internal.cuh"
+#include "bf16_mma.cuh"
 #include "fp_common.cuh"
 
 namespace aenet {
@@ -53,7 +54,32 @@ enum Mode : int {
     kFused = 0,       // descriptor -> FP32 network -> forces, energy and virial
     kDescriptor = 1,  // descriptor only: G rows (sorted order)
     kForces = 2,      // forces and virial from given dE/dG rows (sorted order)
-    kBuildList = 3    // Verlet list: every image-atom within rc_max + skin (no potential)
+    kBuildList = 3,   // Verlet list: every image-atom within rc_max + skin (no potential)
+    kFusedTC = 4,     // descriptor -> BF16 tensor-core network -> forces (one geometry pass)
+    kFusedTCx3 = 5    // the same with split-BF16 operands (hi*hi + hi*lo + lo*hi)
+};
+
+__host__ __device__ constexpr bool is_tc_mode(int mode) { return mode == kFusedTC || mode == kFusedTCx3; }
+
+// Atoms of one sub-item of the tensor-core form: a work item's atoms are taken
+// in sub-items of at most this many, each in two halves of at most 16 (one
+// 16-row tensor-core tile per species and half).
+constexpr int kTcMaxAtoms = 32;
+// Parameter block of one species in the tensor-core form: the standardisation
+// shift [64] and scale [64] in slot order (the network itself is read from L2).
+constexpr int kTcParStride = 2 * kSlots;
+// Bounded wait of a warp for its half's network (then kErrTimeout is raised).
+constexpr int kTcSpin = 1 << 22;
+
+// Network of the tensor-core form: BF16 weights packed in mma B-fragment order
+// (hi and lo parts per species, hidden widths padded to pk.H1p = pk.H2p), FP32
+// biases b1 [H1p], b2 [H2p], output weights w3 [H2p] and b3 per species.
+struct TcNet {
+    const uint32_t *wpk = nullptr;  // [species][2][pk.words]
+    const float *bias = nullptr;    // [species][H1p + 2 H2p + 1]
+    PackedNet pk{};
+    int H1 = 0, H2 = 0;
+    int rec_len = 0;                // activation record length when records are kept
 };
 
 // Per-species parameter block in shared memory (floats), every hidden layer
@@ -138,10 +164,11 @@ inline FusedNet make_fused_net(const Net &net) {
 struct PLayout {
     size_t off_start, off_count, off_prefix, off_shift, s_pos, s_idx, params, warp_base, warp_bytes, total;
     size_t e_d, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
+    size_t tc_g, tc_cl, tc_nnb;                         // tensor-core form: rows, compact lists, counts
 };
 
 __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, int acap, int n_species, int stride,
-                                                int nw = kPWarps) {
+                                                int nw = kPWarps, bool tc = false) {
     PLayout L{};
     size_t p = 0;
     L.off_start = p;
@@ -158,6 +185,15 @@ __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, in
     p = align16(p + sizeof(int) * tile);
     L.params = p;
     p = align16(p + sizeof(float) * (size_t)n_species * stride);
+    L.tc_g = L.tc_cl = L.tc_nnb = p;
+    if (tc) {
+        L.tc_g = p;  // [kTcMaxAtoms][64] float: standardised g, then dE/dG, in slot order
+        p = align16(p + sizeof(float) * kTcMaxAtoms * kSlots);
+        L.tc_cl = p;  // [kTcMaxAtoms][cap] int: staging index of every list entry
+        p = align16(p + sizeof(int) * (size_t)kTcMaxAtoms * cap);
+        L.tc_nnb = p;  // [kTcMaxAtoms] int: list lengths
+        p = align16(p + sizeof(int) * kTcMaxAtoms);
+    }
     L.warp_base = p;
     size_t q = 0;
     L.e_d = q;
@@ -207,10 +243,13 @@ struct WarpLists {
 // lie within the largest cutoff of atom i, as (d, r^2) and index | species << 28.
 // Only a ballot compaction runs per 32 candidates; everything per neighbour is
 // deferred to the dense phase 2 (complete_list), so that the ~85% of lanes
-// whose candidate is out of range do not idle through it.
+// whose candidate is out of range do not idle through it. With CL the staging
+// index of every kept entry (qbase + its index in the staged chunk) is also
+// written to cl[], so that the list can be rebuilt later without a new scan.
+template <bool CL = false>
 __device__ __forceinline__ void scan_tile(const float4 *s_pos, const int *s_idx, int len, float4 ui, int i_s,
                                           const Basis &B, const Caps &caps, const WarpLists &W, int lane,
-                                          int &nnb) {
+                                          int &nnb, int *cl = nullptr, int qbase = 0) {
     const float rc2max = B.rc_max * B.rc_max;
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int base = 0; base < len; base += 32) {
@@ -234,6 +273,7 @@ __device__ __forceinline__ void scan_tile(const float4 *s_pos, const int *s_idx,
             if (slot < caps.nb) {
                 W.e_d[slot] = make_float4(dx, dy, dz, r2);
                 W.e_j[slot] = (jid & ~kShiftBit) | (typ << 28);
+                if constexpr (CL) cl[slot] = qbase + q;
             }
         }
         nnb += __popc(m);
@@ -456,20 +496,18 @@ __device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj
     gz = Ak * (uj.z - c * uk.z) + Bk * uk.z;
 }
 
-template <int KRT, int KAT, bool EXACT, int MODE, int HB>
-__device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
-                                             const float *s_par, const float *s_tw, const WarpLists &W, int lane,
-                                             const float4 *__restrict__ pos4, float4 *__restrict__ F4,
-                                             float *__restrict__ eatom, float *__restrict__ G_out,
-                                             const float *__restrict__ dEdG_in, double &e_acc, float (&vir)[9]) {
+// Descriptor of atom i (Sec. II.B: Eq. radial and Eq. angular with the cosine
+// cutoff, and their species-weighted copy) from its neighbour lists, reduced
+// across the warp: lane l returns the coefficients of slots 2l and 2l + 1.
+// Angular slots carry the factor 2 of the paper's ordered-pair sum.
+template <int KRT, int KAT, bool EXACT>
+__device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &B, const float *s_tw,
+                                                const WarpLists &W, int lane, float &G0, float &G1) {
     constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
     const float inv_rcr = 1.0f / B.rc_rad;
-
     const int s0 = 2 * lane, s1 = 2 * lane + 1;
-    if constexpr (MODE != kForces) {
-    // ---- descriptor
     float acc[64];
 #pragma unroll
     for (int k = 0; k < 64; ++k) acc[k] = 0.f;
@@ -544,8 +582,153 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         }
     }
     transpose_reduce64(acc, lane);
-    const float G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
-    const float G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
+    G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
+    G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
+}
+
+// Chain rule of atom i's energy through every radial term and angular pair to
+// forces (one FP32 vector atomic per neighbour entry) and the virial, given
+// dE/dG of the atom in slot order (coef[64], shared memory; angular slots
+// without the ordered-sum factor 2, which is applied here).
+template <int KRT, int KAT, bool EXACT>
+__device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, const Basis &B, const float *s_tw,
+                                                const WarpLists &W, const float *coef, int lane,
+                                                float4 *__restrict__ F4, float (&vir)[9]) {
+    constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
+    const int Kr = EXACT ? KRT : B.Kr;
+    const int Ka = EXACT ? KAT : B.Ka;
+    const float inv_rcr = 1.0f / B.rc_rad;
+    float cr[KRT], crw[KRT], ca[KAT], caw[KAT];
+#pragma unroll
+    for (int q = 0; q < KRT; ++q) {
+        cr[q] = coef[q];
+        crw[q] = coef[SLOT_RADW + q];
+    }
+#pragma unroll
+    for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
+        ca[q] = 2.0f * coef[SLOT_ANG + q];
+        caw[q] = 2.0f * coef[SLOT_ANGW + q];
+    }
+    const float k2 = 2.0f * inv_rcr;
+    for (int k = lane; k < nnb; k += 32) {
+        const float4 e = W.e_d[k];
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        if (e.w <= B.rc_rad) {
+            float fc, dfc;
+            radial_cutoff(e.w, inv_rcr, fc, dfc);
+            const float s = s_tw[W.e_j[k] >> 28];
+            const float x = 2.0f * e.w * inv_rcr - 1.0f;
+            // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c', summed over q with
+            // the coefficients cr_q + s crw_q
+            float S, dS;
+            clenshaw_d<KRT>(x, s, cr, crw, Kr, S, dS);
+            const float dEdr = fmaf(dS, k2 * fc, S * dfc);
+            const float gr = __fdividef(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
+            fx = -gr * e.x;
+            fy = -gr * e.y;
+            fz = -gr * e.z;
+        }
+        W.e_fx[k] = fx;
+        W.e_fy[k] = fy;
+        W.e_fz[k] = fz;
+    }
+    __syncwarp();
+    // Angular chain rule by the rotation schedule: the angular entries form
+    // blocks of 32 (lane l owns entries 32b + l). Inside a diagonal block, step t
+    // pairs lane l with entry (l + t) mod n_A (t = 1..n_A/2; at t = n_A/2 only the
+    // lower half of lanes, so each unordered pair is visited once); between
+    // blocks A < B, step t pairs lane l with column (l + t) mod 32 of B. The lane
+    // keeps dE/dd_j of its own entry in registers and hands dE/dd_k to the owner
+    // of k with one rotation shuffle; every entry is written only by its owner,
+    // so no atomics are needed. Coefficients carry the factor 2 of the ordered sum.
+    {
+        const int nbk = (nang + 31) >> 5;
+        for (int A = 0; A < nbk; ++A) {
+            const int nA = min(32, nang - 32 * A);
+            const bool vj = lane < nA;
+            const int self = 32 * A + (vj ? lane : 0);
+            const float4 uj = W.a_u[self];
+            const float4 xj = W.a_x[self];
+            for (int Bk = A; Bk < nbk; ++Bk) {
+                const int nB = min(32, nang - 32 * Bk);
+                const bool diag = Bk == A;
+                const int nt = diag ? nA / 2 : 32;
+                float jx = 0.f, jy = 0.f, jz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+                for (int it = 0; it < nt; it += 2) {  // two independent steps per iteration (ILP)
+                    int ccA, ccB;
+                    bool vA, vB;
+                    rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
+                    rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
+                    const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
+                    float gAx, gAy, gAz, gBx, gBy, gBz;
+                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kA], W.a_x[kA], vA, ca, caw, Ka, jx, jy, jz, gAx, gAy,
+                                              gAz);
+                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kB], W.a_x[kB], vB, ca, caw, Ka, jx, jy, jz, gBx, gBy,
+                                              gBz);
+                    // dE/dd_k goes to the lane that owns k: it sits t lanes to the left
+                    const int srcA = rotation_source(diag, it, nA, lane);
+                    const int srcB = rotation_source(diag, it + 1, nA, lane);
+                    kx += __shfl_sync(kFull, gAx, srcA);
+                    ky += __shfl_sync(kFull, gAy, srcA);
+                    kz += __shfl_sync(kFull, gAz, srcA);
+                    kx += __shfl_sync(kFull, gBx, srcB);
+                    ky += __shfl_sync(kFull, gBy, srcB);
+                    kz += __shfl_sync(kFull, gBz, srcB);
+                }
+                // force on neighbour = -dE_i/dd; each entry is touched by its owner lane only
+                if (vj) {
+                    const int sl = __float_as_int(xj.w);
+                    W.e_fx[sl] -= jx;
+                    W.e_fy[sl] -= jy;
+                    W.e_fz[sl] -= jz;
+                }
+                if (lane < nB) {
+                    const int sl = __float_as_int(W.a_x[32 * Bk + lane].w);
+                    W.e_fx[sl] -= kx;
+                    W.e_fy[sl] -= ky;
+                    W.e_fz[sl] -= kz;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    float fix = 0.f, fiy = 0.f, fiz = 0.f;
+    for (int k = lane; k < nnb; k += 32) {
+        const float fx = W.e_fx[k], fy = W.e_fy[k], fz = W.e_fz[k];
+        const float4 e = W.e_d[k];
+        atomicAdd(&F4[W.e_j[k] & 0x0fffffff], make_float4(fx, fy, fz, 0.f));
+        fix -= fx;
+        fiy -= fy;
+        fiz -= fz;
+        vir[0] = fmaf(e.x, fx, vir[0]);
+        vir[1] = fmaf(e.x, fy, vir[1]);
+        vir[2] = fmaf(e.x, fz, vir[2]);
+        vir[3] = fmaf(e.y, fx, vir[3]);
+        vir[4] = fmaf(e.y, fy, vir[4]);
+        vir[5] = fmaf(e.y, fz, vir[5]);
+        vir[6] = fmaf(e.z, fx, vir[6]);
+        vir[7] = fmaf(e.z, fy, vir[7]);
+        vir[8] = fmaf(e.z, fz, vir[8]);
+    }
+    fix = warp_sum(fix);
+    fiy = warp_sum(fiy);
+    fiz = warp_sum(fiz);
+    if (lane == 0) atomicAdd(&F4[i_s], make_float4(fix, fiy, fiz, 0.f));
+    __syncwarp();
+}
+
+template <int KRT, int KAT, bool EXACT, int MODE, int HB>
+__device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
+                                             const float *s_par, const float *s_tw, const WarpLists &W, int lane,
+                                             const float4 *__restrict__ pos4, float4 *__restrict__ F4,
+                                             float *__restrict__ eatom, float *__restrict__ G_out,
+                                             const float *__restrict__ dEdG_in, double &e_acc, float (&vir)[9]) {
+    const int Kr = EXACT ? KRT : B.Kr;
+    const int Ka = EXACT ? KAT : B.Ka;
+    const int s0 = 2 * lane, s1 = 2 * lane + 1;
+    if constexpr (MODE != kForces) {
+    float G0, G1;
+    atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, W, lane, G0, G1);
     if constexpr (MODE == kDescriptor) {
         const int D = 2 * (Kr + Ka);
         const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
@@ -662,124 +845,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     }
     __syncwarp();
 
-    // ---- chain rule to forces
-    float cr[KRT], crw[KRT], ca[KAT], caw[KAT];
-#pragma unroll
-    for (int q = 0; q < KRT; ++q) {
-        cr[q] = W.coef[q];
-        crw[q] = W.coef[SLOT_RADW + q];
-    }
-#pragma unroll
-    for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
-        ca[q] = 2.0f * W.coef[SLOT_ANG + q];
-        caw[q] = 2.0f * W.coef[SLOT_ANGW + q];
-    }
-    const float k2 = 2.0f * inv_rcr;
-    for (int k = lane; k < nnb; k += 32) {
-        const float4 e = W.e_d[k];
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        if (e.w <= B.rc_rad) {
-            float fc, dfc;
-            radial_cutoff(e.w, inv_rcr, fc, dfc);
-            const float s = s_tw[W.e_j[k] >> 28];
-            const float x = 2.0f * e.w * inv_rcr - 1.0f;
-            // d/dr [T_q(x) f_c(r)] = T_q'(x) (2/Rc) f_c + T_q f_c', summed over q with
-            // the coefficients cr_q + s crw_q
-            float S, dS;
-            clenshaw_d<KRT>(x, s, cr, crw, Kr, S, dS);
-            const float dEdr = fmaf(dS, k2 * fc, S * dfc);
-            const float gr = __fdividef(dEdr, e.w);  // dE_i/dd = gr * d; force on j = -dE_i/dd
-            fx = -gr * e.x;
-            fy = -gr * e.y;
-            fz = -gr * e.z;
-        }
-        W.e_fx[k] = fx;
-        W.e_fy[k] = fy;
-        W.e_fz[k] = fz;
-    }
-    __syncwarp();
-    // Angular chain rule by the rotation schedule: the angular entries form
-    // blocks of 32 (lane l owns entries 32b + l). Inside a diagonal block, step t
-    // pairs lane l with entry (l + t) mod n_A (t = 1..n_A/2; at t = n_A/2 only the
-    // lower half of lanes, so each unordered pair is visited once); between
-    // blocks A < B, step t pairs lane l with column (l + t) mod 32 of B. The lane
-    // keeps dE/dd_j of its own entry in registers and hands dE/dd_k to the owner
-    // of k with one rotation shuffle; every entry is written only by its owner,
-    // so no atomics are needed. Coefficients carry the factor 2 of the ordered sum.
-    {
-        const int nbk = (nang + 31) >> 5;
-        for (int A = 0; A < nbk; ++A) {
-            const int nA = min(32, nang - 32 * A);
-            const bool vj = lane < nA;
-            const int self = 32 * A + (vj ? lane : 0);
-            const float4 uj = W.a_u[self];
-            const float4 xj = W.a_x[self];
-            for (int Bk = A; Bk < nbk; ++Bk) {
-                const int nB = min(32, nang - 32 * Bk);
-                const bool diag = Bk == A;
-                const int nt = diag ? nA / 2 : 32;
-                float jx = 0.f, jy = 0.f, jz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
-                for (int it = 0; it < nt; it += 2) {  // two independent steps per iteration (ILP)
-                    int ccA, ccB;
-                    bool vA, vB;
-                    rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
-                    rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
-                    const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
-                    float gAx, gAy, gAz, gBx, gBy, gBz;
-                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kA], W.a_x[kA], vA, ca, caw, Ka, jx, jy, jz, gAx, gAy,
-                                              gAz);
-                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kB], W.a_x[kB], vB, ca, caw, Ka, jx, jy, jz, gBx, gBy,
-                                              gBz);
-                    // dE/dd_k goes to the lane that owns k: it sits t lanes to the left
-                    const int srcA = rotation_source(diag, it, nA, lane);
-                    const int srcB = rotation_source(diag, it + 1, nA, lane);
-                    kx += __shfl_sync(kFull, gAx, srcA);
-                    ky += __shfl_sync(kFull, gAy, srcA);
-                    kz += __shfl_sync(kFull, gAz, srcA);
-                    kx += __shfl_sync(kFull, gBx, srcB);
-                    ky += __shfl_sync(kFull, gBy, srcB);
-                    kz += __shfl_sync(kFull, gBz, srcB);
-                }
-                // force on neighbour = -dE_i/dd; each entry is touched by its owner lane only
-                if (vj) {
-                    const int sl = __float_as_int(xj.w);
-                    W.e_fx[sl] -= jx;
-                    W.e_fy[sl] -= jy;
-                    W.e_fz[sl] -= jz;
-                }
-                if (lane < nB) {
-                    const int sl = __float_as_int(W.a_x[32 * Bk + lane].w);
-                    W.e_fx[sl] -= kx;
-                    W.e_fy[sl] -= ky;
-                    W.e_fz[sl] -= kz;
-                }
-            }
-        }
-    }
-    __syncwarp();
-    float fix = 0.f, fiy = 0.f, fiz = 0.f;
-    for (int k = lane; k < nnb; k += 32) {
-        const float fx = W.e_fx[k], fy = W.e_fy[k], fz = W.e_fz[k];
-        const float4 e = W.e_d[k];
-        atomicAdd(&F4[W.e_j[k] & 0x0fffffff], make_float4(fx, fy, fz, 0.f));
-        fix -= fx;
-        fiy -= fy;
-        fiz -= fz;
-        vir[0] = fmaf(e.x, fx, vir[0]);
-        vir[1] = fmaf(e.x, fy, vir[1]);
-        vir[2] = fmaf(e.x, fz, vir[2]);
-        vir[3] = fmaf(e.y, fx, vir[3]);
-        vir[4] = fmaf(e.y, fy, vir[4]);
-        vir[5] = fmaf(e.y, fz, vir[5]);
-        vir[6] = fmaf(e.z, fx, vir[6]);
-        vir[7] = fmaf(e.z, fy, vir[7]);
-        vir[8] = fmaf(e.z, fz, vir[8]);
-    }
-    fix = warp_sum(fix);
-    fiy = warp_sum(fiy);
-    fiz = warp_sum(fiz);
-    if (lane == 0) atomicAdd(&F4[i_s], make_float4(fix, fiy, fiz, 0.f));
-    __syncwarp();
+    atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, W, W.coef, lane, F4, vir);
 }
 
 // The network parameters of every species into the shared-memory layout of
@@ -821,6 +887,199 @@ __device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &
     }
 }
 
+// Standardisation of every species in slot order for the tensor-core form:
+// shift at [t][slot], scale at [t][64 + slot] (scale 0 on unused slots).
+template <int KRT, int KAT, bool EXACT>
+__device__ __forceinline__ void load_tc_params(const Basis &B, const float *__restrict__ shift,
+                                               const float *__restrict__ scale, float *s_par, int tid, int nthreads) {
+    const int Kr = EXACT ? KRT : B.Kr, Ka = EXACT ? KAT : B.Ka, D = 2 * (Kr + Ka);
+    for (int idx = tid; idx < B.n_species * kSlots; idx += nthreads) {
+        const int t = idx / kSlots, slot = idx - t * kSlots;
+        const int col = slot_col<KRT, KAT>(slot, Kr, Ka);
+        s_par[t * kTcParStride + slot] = col >= 0 ? shift[t * D + col] : 0.f;
+        s_par[t * kTcParStride + kSlots + slot] = col >= 0 ? scale[t * D + col] : 0.f;
+    }
+}
+
+// Position of the r-th set bit of mask (r from 0), or -1.
+__device__ __forceinline__ int nth_bit(unsigned mask, int r) {
+    for (int k = 0; k < r && mask; ++k) mask &= mask - 1u;
+    return mask ? __ffs(mask) - 1 : -1;
+}
+
+// The network of one species (Sec. II.A, Eq. ANN-layer: two tanh hidden layers,
+// linear output) and its back-propagation to dE/dG, on the tensor cores, for up
+// to 16 atoms of that species: rows r = lane/4 and r + 8 of the mma tiles are
+// the atoms a0 and a1 (sub-item indices, -1 for an empty row). Each layer is
+// one small GEMM on mma.m16n8k16 (BF16 x BF16 -> FP32), operands split into
+// hi + lo parts when X3 (hi*hi + hi*lo + lo*hi):
+//   forward   Z1 = g W1^T + b1, X1 = tanh Z1; Z2 = X1 W2^T + b2, X2 = tanh Z2;
+//             E = X2 w3 + b3 (FP32)
+//   backward  delta2 = (1 - X2^2) w3; delta1 = (1 - X1^2) (delta2 W2); dE/dg = delta1 W1
+// Input: the standardised rows g in s_g (slot order; slot = G column for the
+// bases this form serves); output: dE/dG = dE/dg * scale written over the same
+// rows, E_i to eatom and the warp's energy sum, and, when rec_base is given,
+// the activation record (g, x1, delta1, x2, delta2) of every atom for dE/dW.
+template <int HT, bool X3>
+__device__ __forceinline__ void tc_tile_chain(int t, int a0, int a1, int lane, float *s_g, const float *sc,
+                                              const TcNet &tn, int atom0, float *__restrict__ eatom,
+                                              float *__restrict__ rec_base, int D, double &e_acc) {
+    constexpr int NT = HT / 8, KS1 = kKD / 16, KSH = HT / 16, NTD = kKD / 8;
+    const int tq = lane & 3;
+    const uint32_t *wbase = tn.wpk + (size_t)t * 2 * tn.pk.words;
+    const uint2 *Wh = reinterpret_cast<const uint2 *>(wbase);
+    const uint2 *Wl = reinterpret_cast<const uint2 *>(wbase + tn.pk.words);
+    const float *bias = tn.bias + t * (tn.pk.H1p + 2 * tn.pk.H2p + 1);
+    float *rec0 = (rec_base && a0 >= 0) ? rec_base + (size_t)(atom0 + a0) * tn.rec_len : nullptr;
+    float *rec1 = (rec_base && a1 >= 0) ? rec_base + (size_t)(atom0 + a1) * tn.rec_len : nullptr;
+    const int H1 = tn.H1, H2 = tn.H2;
+
+    // layer-1 input: the standardised descriptor rows as A fragments (K = 64)
+    uint32_t A0h[KS1][4], A0l[KS1][4];
+#pragma unroll
+    for (int ks = 0; ks < KS1; ++ks)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = ks * 16 + 2 * tq + 8 * h;
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int a = rr ? a1 : a0;
+                float *rec = rr ? rec1 : rec0;
+                float x0 = 0.f, x1 = 0.f;
+                if (a >= 0) {
+                    const float2 v = *reinterpret_cast<const float2 *>(s_g + a * kSlots + col);
+                    x0 = v.x;
+                    x1 = v.y;
+                }
+                if (rec) {
+                    if (col < D) rec[col] = x0;
+                    if (col + 1 < D) rec[col + 1] = x1;
+                }
+                uint32_t hi, lo = 0u;
+                if (X3) split_bf2(x0, x1, hi, lo); else hi = pack_bf2(x0, x1);
+                A0h[ks][2 * h + rr] = hi;
+                A0l[ks][2 * h + rr] = lo;
+            }
+        }
+    // forward
+    float C1[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const float b0 = bias[nt * 8 + 2 * tq], b1 = bias[nt * 8 + 2 * tq + 1];
+        C1[nt][0] = b0; C1[nt][1] = b1; C1[nt][2] = b0; C1[nt][3] = b1;
+    }
+    gemm<KS1, NT, X3>(C1, A0h, A0l, Wh + tn.pk.off_w1f / 2, Wl + tn.pk.off_w1f / 2, lane);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) C1[nt][e] = (nt * 8 + 2 * tq + (e & 1) < H1) ? tanhf(C1[nt][e]) : 0.f;
+    uint32_t A1h[KSH][4], A1l[KSH][4];
+    to_a<NT, X3>(C1, A1h, A1l);
+    float C2[NT][4];
+    const float *b2 = bias + tn.pk.H1p;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const float b0 = b2[nt * 8 + 2 * tq], b1 = b2[nt * 8 + 2 * tq + 1];
+        C2[nt][0] = b0; C2[nt][1] = b1; C2[nt][2] = b0; C2[nt][3] = b1;
+    }
+    gemm<KSH, NT, X3>(C2, A1h, A1l, Wh + tn.pk.off_w2f / 2, Wl + tn.pk.off_w2f / 2, lane);
+    // output layer in FP32 on the accumulator fragments
+    const float *w3 = bias + tn.pk.H1p + tn.pk.H2p;
+    const float b3 = bias[tn.pk.H1p + 2 * tn.pk.H2p];
+    float e0 = 0.f, e1 = 0.f;
+    float D2[NT][4];  // delta2 = (1 - x2^2) w3; C2 becomes x2
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int col = nt * 8 + 2 * tq + (e & 1);
+            const float x = col < H2 ? tanhf(C2[nt][e]) : 0.f;
+            const float w = w3[col];
+            if (e < 2) e0 = fmaf(w, x, e0); else e1 = fmaf(w, x, e1);
+            D2[nt][e] = (1.0f - x * x) * w;
+            C2[nt][e] = x;
+        }
+    e0 += __shfl_xor_sync(kFull, e0, 1);
+    e0 += __shfl_xor_sync(kFull, e0, 2);
+    e1 += __shfl_xor_sync(kFull, e1, 1);
+    e1 += __shfl_xor_sync(kFull, e1, 2);
+    e0 += b3;
+    e1 += b3;
+    // backward
+    uint32_t A2h[KSH][4], A2l[KSH][4];
+    to_a<NT, X3>(D2, A2h, A2l);
+    float C3[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) C3[nt][0] = C3[nt][1] = C3[nt][2] = C3[nt][3] = 0.f;
+    gemm<KSH, NT, X3>(C3, A2h, A2l, Wh + tn.pk.off_w2b / 2, Wl + tn.pk.off_w2b / 2, lane);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) C3[nt][e] *= (1.0f - C1[nt][e] * C1[nt][e]);
+    if (rec0 || rec1) {  // x1, delta1, x2, delta2 of the record
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int col = nt * 8 + 2 * tq + (e & 1);
+                float *rec = e < 2 ? rec0 : rec1;
+                if (!rec) continue;
+                if (col < H1) {
+                    rec[D + col] = C1[nt][e];
+                    rec[D + H1 + col] = C3[nt][e];
+                }
+                if (col < H2) {
+                    rec[D + 2 * H1 + col] = C2[nt][e];
+                    rec[D + 2 * H1 + H2 + col] = D2[nt][e];
+                }
+            }
+    }
+    uint32_t A3h[KSH][4], A3l[KSH][4];
+    to_a<NT, X3>(C3, A3h, A3l);
+    float C4[NTD][4];
+#pragma unroll
+    for (int nt = 0; nt < NTD; ++nt) C4[nt][0] = C4[nt][1] = C4[nt][2] = C4[nt][3] = 0.f;
+    gemm<KSH, NTD, X3>(C4, A3h, A3l, Wh + tn.pk.off_w1b / 2, Wl + tn.pk.off_w1b / 2, lane);
+    // dE/dG = dE/dg * scale over the rows g was read from (every (row, column)
+    // pair belongs to one lane, which has already read its inputs)
+#pragma unroll
+    for (int nt = 0; nt < NTD; ++nt) {
+        const int col = nt * 8 + 2 * tq;
+        const float2 s2 = *reinterpret_cast<const float2 *>(sc + col);
+        if (a0 >= 0) *reinterpret_cast<float2 *>(s_g + a0 * kSlots + col) = make_float2(C4[nt][0] * s2.x, C4[nt][1] * s2.y);
+        if (a1 >= 0) *reinterpret_cast<float2 *>(s_g + a1 * kSlots + col) = make_float2(C4[nt][2] * s2.x, C4[nt][3] * s2.y);
+    }
+    if (tq == 0) {
+        if (a0 >= 0) {
+            eatom[atom0 + a0] = e0;
+            e_acc += (double)e0;
+        }
+        if (a1 >= 0) {
+            eatom[atom0 + a1] = e1;
+            e_acc += (double)e1;
+        }
+    }
+}
+
+// Networks of one half [lo, hi) (at most 16 atoms) of a sub-item whose first
+// atom is the sorted atom atom0: one tile per species present.
+template <int HT, bool X3>
+__device__ __forceinline__ void tc_half_network(int lo, int hi, int atom0, int n_species, int lane,
+                                                const float4 *__restrict__ pos4, float *s_g, const float *s_par,
+                                                const TcNet &tn, float *__restrict__ eatom,
+                                                float *__restrict__ rec_base, int D, double &e_acc) {
+    const int na = hi - lo;
+    const int tl = lane < na ? __float_as_int(pos4[atom0 + lo + lane].w) : -1;
+    const int g = lane >> 2;
+    for (int t = 0; t < n_species; ++t) {
+        const unsigned mask = __ballot_sync(kFull, tl == t);
+        if (!mask) continue;
+        const int b0 = nth_bit(mask, g), b1 = nth_bit(mask, g + 8);
+        tc_tile_chain<HT, X3>(t, b0 >= 0 ? lo + b0 : -1, b1 >= 0 ? lo + b1 : -1, lane, s_g,
+                              s_par + t * kTcParStride + kSlots, tn, atom0, eatom, rec_base, D, e_acc);
+    }
+}
+
 template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB, int NW = kPWarps>
 __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
@@ -830,12 +1089,14 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                 float *__restrict__ G_out, const float *__restrict__ dEdG_in, double *__restrict__ e_part,
                 double *__restrict__ vir_part, unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
                 unsigned *__restrict__ work, const int *__restrict__ order, int n_items, int *__restrict__ vl_out,
-                int *__restrict__ vl_count, int split, int split_from) {
+                int *__restrict__ vl_count, int split, int split_from, TcNet tc) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
     __shared__ float s_vir[NW][9];
     __shared__ double s_e[NW];
     __shared__ int s_next, s_item;
+    __shared__ int s_tc_done_a[2], s_tc_done_b[2];  // tensor-core form: atoms of a half through phase A; network done
+    constexpr bool kTC = is_tc_mode(MODE);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = caps.tile;
@@ -844,7 +1105,8 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     // (the list-build form keeps no per-warp lists: its CTAs are small)
     constexpr bool kLists = MODE != kBuildList;
     const PLayout L = make_playout(g_one.n_off, tile, kLists ? caps.nb : 0, kLists ? caps.ang : 0,
-                                   MODE == kFused ? B.n_species : 0, net.stride, NW);
+                                   (MODE == kFused || kTC) ? B.n_species : 0, kTC ? kTcParStride : net.stride, NW,
+                                   kTC);
     int *off_start = reinterpret_cast<int *>(smem + L.off_start);
     int *off_count = reinterpret_cast<int *>(smem + L.off_count);
     int *off_prefix = reinterpret_cast<int *>(smem + L.off_prefix);
@@ -862,6 +1124,9 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
     W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
     W.coef = reinterpret_cast<float *>(wb + L.coef);
+    float *s_g = reinterpret_cast<float *>(smem + L.tc_g);
+    int *s_cl = reinterpret_cast<int *>(smem + L.tc_cl);
+    int *s_nnb = reinterpret_cast<int *>(smem + L.tc_nnb);
 
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
@@ -869,6 +1134,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
 
     // ---- network parameters of every species into the shared-memory layout
     if constexpr (MODE == kFused) load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid, NW * 32);
+    if constexpr (kTC) load_tc_params<KRT, KAT, EXACT>(B, shift, scale, s_par, tid, NW * 32);
 
     unsigned long long st_nb = 0, st_ang = 0, st_pairs = 0;
     // Work items are cells: one per CTA (work == NULL), or, in the persistent
@@ -913,7 +1179,11 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     const Grid &g = BATCH ? sinfo[sidx].g : g_one;
     const int cell0 = BATCH ? sinfo[sidx].cell0 : 0;
     const int n_off = g.n_off;
-    if (tid == 0) s_next = 0;
+    if (tid == 0) {
+        s_next = 0;
+        s_tc_done_a[0] = s_tc_done_a[1] = 0;
+        s_tc_done_b[0] = s_tc_done_b[1] = 0;
+    }
 
     // ---- neighbour-cell table: start, count and image shift of every offset
     const int lcell = cell - cell0;         // cell inside its structure's grid
@@ -1005,7 +1275,156 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         __syncwarp();
     };
 
+    if constexpr (kTC) {
+    // ---- tensor-core form. The item's atoms are taken in sub-items of at most
+    // kTcMaxAtoms, each split into two halves. Phase A of an atom (neighbour
+    // list, descriptor, standardisation) leaves its g row and a compact copy of
+    // its list (staging indices) in shared memory; the warp that completes the
+    // last phase A of a half runs that half's networks on the tensor cores,
+    // which turn the g rows into dE/dG rows; phase C of an atom (its list
+    // rebuilt from the compact copy, the chain rule to forces and virial) waits
+    // only for its own half's network. When the neighbourhood fits one staged
+    // chunk the phases are tasks taken in the order A(half 0), A(half 1),
+    // C(half 0), C(half 1), so the networks run while other warps still work;
+    // otherwise phase A runs in rounds over the staged chunks and the networks
+    // between two block barriers.
+    constexpr bool X3 = MODE == kFusedTCx3;
     if (n_chunks <= 1) {
+        if (total > 0) stage(0);
+        __syncthreads();
+    }
+    auto tc_phase_a_finish = [&](int a, int i_s, int nnb, int nang) {
+        float G0, G1;
+        atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, W, lane, G0, G1);
+        const float *P = s_par + __float_as_int(pos4[i_s].w) * kTcParStride;
+        float2 gv;
+        gv.x = (G0 - P[2 * lane]) * P[kSlots + 2 * lane];
+        gv.y = (G1 - P[2 * lane + 1]) * P[kSlots + 2 * lane + 1];
+        *reinterpret_cast<float2 *>(s_g + a * kSlots + 2 * lane) = gv;
+        if (lane == 0) s_nnb[a] = nnb;
+    };
+    auto tc_phase_c = [&](int a, int i_s, bool staged) {
+        const float4 ui = pos4[i_s];
+        const int nnb = s_nnb[a];
+        const int *cl = s_cl + a * caps.nb;
+        for (int k = lane; k < nnb; k += 32) {
+            const int q = cl[k];
+            float4 p;
+            int j;
+            if (staged) {
+                p = s_pos[q];
+                j = s_idx[q] & ~kShiftBit;
+            } else {  // entry q of the concatenated neighbourhood: offset o, atom j
+                int lo = 0, hi = n_off - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off_prefix[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                j = off_start[lo] + (q - off_prefix[lo]);
+                const float4 pj = pos4[j];
+                const float4 sh = off_shift[lo];
+                p = make_float4(pj.x + sh.x, pj.y + sh.y, pj.z + sh.z, pj.w);
+            }
+            const float dx = p.x - ui.x, dy = p.y - ui.y, dz = p.z - ui.z;
+            W.e_d[k] = make_float4(dx, dy, dz, dx * dx + dy * dy + dz * dz);
+            W.e_j[k] = j | (__float_as_int(p.w) << 28);
+        }
+        __syncwarp();
+        int nang = 0;
+        complete_list(B, s_tw, caps, W, lane, nnb, nang, err);
+        nang = min(nang, caps.ang);  // an overflow was reported in phase A
+        __syncwarp();
+        atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, W, s_g + a * kSlots, lane, F4, vir);
+    };
+    for (int sub0 = 0; sub0 < cnt; sub0 += kTcMaxAtoms) {
+        const int m = min(kTcMaxAtoms, cnt - sub0), mh = (m + 1) >> 1;
+        const int atom0 = c0 + sub0;
+        if (n_chunks <= 1) {
+            for (;;) {
+                int task = 0;
+                if (lane == 0) task = atomicAdd(&s_next, 1);
+                task = __shfl_sync(kFull, task, 0);
+                if (task >= 2 * m) break;
+                const int a = task < m ? task : task - m;
+                const int h = a < mh ? 0 : 1;
+                const int i_s = atom0 + a;
+                if (task < m) {
+                    int nnb = 0, nang = 0;
+                    scan_tile<true>(s_pos, s_idx, total, pos4[i_s], i_s, B, caps, W, lane, nnb, s_cl + a * caps.nb, 0);
+                    finish_list(nnb, nang);
+                    tc_phase_a_finish(a, i_s, nnb, nang);
+                    __syncwarp();
+                    __threadfence_block();
+                    int done = 0;
+                    if (lane == 0) done = atomicAdd(&s_tc_done_a[h], 1);
+                    done = __shfl_sync(kFull, done, 0);
+                    if (done == (h ? m - mh : mh) - 1) {  // the half's last phase A: run its networks
+                        __threadfence_block();
+                        tc_half_network<HB, X3>(h ? mh : 0, h ? m : mh, atom0, B.n_species, lane, pos4, s_g, s_par, tc,
+                                                eatom, G_out, B.D, e_acc);
+                        __threadfence_block();
+                        __syncwarp();
+                        if (lane == 0) atomicExch(&s_tc_done_b[h], 1);
+                    }
+                } else {
+                    if (lane == 0) {  // wait for this half's networks (bounded)
+                        int it = 0;
+                        while (atomicAdd(&s_tc_done_b[h], 0) == 0) {
+                            if (++it > kTcSpin) {
+                                atomicOr(err, kErrTimeout);
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
+                    __syncwarp();
+                    __threadfence_block();
+                    tc_phase_c(a, i_s, true);
+                }
+            }
+        } else {
+            const int n_rounds = (m + NW - 1) / NW;
+            for (int round = 0; round < n_rounds; ++round) {
+                const int a = round * NW + warp;
+                const bool active = a < m;
+                const int i_s = atom0 + a;
+                const float4 ui = active ? pos4[i_s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                int nnb = 0, nang = 0;
+                for (int chunk = 0; chunk < n_chunks; ++chunk) {
+                    __syncthreads();
+                    stage(chunk);
+                    __syncthreads();
+                    if (active)
+                        scan_tile<true>(s_pos, s_idx, min(tile, total - chunk * tile), ui, i_s, B, caps, W, lane, nnb,
+                                        s_cl + a * caps.nb, chunk * tile);
+                }
+                if (active) {
+                    finish_list(nnb, nang);
+                    tc_phase_a_finish(a, i_s, nnb, nang);
+                }
+            }
+            __syncthreads();
+            if (warp < 2 && (warp ? m - mh : mh) > 0)
+                tc_half_network<HB, X3>(warp ? mh : 0, warp ? m : mh, atom0, B.n_species, lane, pos4, s_g, s_par, tc,
+                                        eatom, G_out, B.D, e_acc);
+            __syncthreads();
+            for (;;) {
+                int a = 0;
+                if (lane == 0) a = atomicAdd(&s_next, 1);
+                a = __shfl_sync(kFull, a, 0);
+                if (a >= m) break;
+                tc_phase_c(a, atom0 + a, false);
+            }
+        }
+        __syncthreads();  // every task of the sub-item is done
+        if (tid == 0) {
+            s_next = 0;
+            s_tc_done_a[0] = s_tc_done_a[1] = 0;
+            s_tc_done_b[0] = s_tc_done_b[1] = 0;
+        }
+        __syncthreads();
+    }
+    } else if (n_chunks <= 1) {
         if (total > 0) stage(0);
         __syncthreads();
         for (;;) {
@@ -1061,7 +1480,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     }
 
     // ---- cell partials: energy (FP64), virial (FP32 lanes -> FP64)
-    if constexpr (MODE == kFused || MODE == kForces) {
+    if constexpr (MODE == kFused || MODE == kForces || kTC) {
     #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const float v = warp_sum(vir[k]);
@@ -1075,7 +1494,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
             for (int w = 0; w < NW; ++w) s += s_vir[w][tid];
             vir_part[(size_t)slot * 9 + tid] = (double)s;
         }
-        if (MODE == kFused && tid == 0) {  // FP64 sum over the warps' energies, fixed order
+        if ((MODE == kFused || kTC) && tid == 0) {  // FP64 sum over the warps' energies, fixed order
             double v = 0.0;
             for (int w = 0; w < NW; ++w) v += s_e[w];
             e_part[slot] = v;

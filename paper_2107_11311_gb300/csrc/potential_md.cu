@@ -20,7 +20,7 @@ cudaError_t launch_build(Context &c, const Grid &g) {
     kern<<<g.ncell, kPThreads, smem, c.stream>>>(c.basis, net, g, nullptr, 0, c.caps, c.d_pos4, c.d_cell_start,
                                                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                  nullptr, nullptr, c.d_stats, c.d_err, nullptr, nullptr, g.ncell,
-                                                 c.d_vl, c.d_vl_count, 1, 0);
+                                                 c.d_vl, c.d_vl_count, 1, 0, TcNet{});
     return cudaGetLastError();
 }
 
