@@ -287,7 +287,6 @@ def run_batch(args, rank, world):
     around synchronous calls): the eager batched call and one call per structure."""
     import torch
     from paper_2107_11311_gb300 import inputs
-    from paper_2107_11311_gb300.aenet import AenetGPU
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda")
     if world > 1:
@@ -302,7 +301,7 @@ def run_batch(args, rank, world):
         for fam, structs in (("water", wat), ("amorphous", amo)):
             m = inputs.make_model(fam)
             off, pos, types, boxes = inputs.concat(structs)
-            g = AenetGPU(m, args.precision, stream=stream.cuda_stream)
+            g = make_gpu(m, args.precision, stream)
             dpos, dtypes = torch.tensor(pos, device=dev), torch.tensor(types, device=dev)
             E = torch.zeros(len(structs), dtype=torch.float64, device=dev)
             F = torch.zeros((int(off[-1]), 3), dtype=torch.float64, device=dev)
@@ -384,7 +383,7 @@ def run_batch(args, rank, world):
         line = {"metric": METRIC, "value": world * n_atoms * args.steps / t_graph, "unit": "atom-steps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_graph / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+                "vs_baseline": None, "dtype": FORM_DTYPE[args.precision],
                 "data": "synthetic",
                 "config": {"workload": "batch_512", "structures": 512, "atoms": n_atoms,
                            "sizes": "log-uniform 32..2048; 256 water + 256 4-species solid",
@@ -408,7 +407,22 @@ def run_batch(args, rank, world):
         dist.destroy_process_group()
 
 
-FORM_DTYPE = {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16"}
+# precision forms: the network in FP32 (fused kernel), split BF16 and plain BF16
+# on the tensor cores inside the fused kernel, and the same two as the
+# three-kernel path (descriptor kernel, network kernel, force kernel)
+FORM_DTYPE = {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16", "bf16x3_split": "bf16x3", "bf16_split": "bf16"}
+
+
+def make_gpu(m, form, stream, skin=0.0):
+    """A library context for one form on the given torch stream."""
+    from paper_2107_11311_gb300.aenet import AenetGPU
+    gpu = AenetGPU(m, form.replace("_split", ""), stream=stream.cuda_stream)
+    if form.endswith("_split"):
+        gpu.fuse_network(False)
+    gpu.set_skin(skin)
+    return gpu
+
+
 F_RMS_BOUND = 1e-3  # eV/A: the force-error bound a form must meet to be the headline
 
 
@@ -418,9 +432,8 @@ def time_form(args, st, m, v0, precision, dev, stream, flush, world):
     import torch
     import torch.distributed as dist
     from paper_2107_11311_gb300.aenet import (AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING,
-                                              AENET_MD_TIMING_POTENTIAL, AenetGPU)
-    gpu = AenetGPU(m, precision, stream=stream.cuda_stream)
-    gpu.set_skin(args.skin)
+                                              AENET_MD_TIMING_POTENTIAL)
+    gpu = make_gpu(m, precision, stream, args.skin)
     pos = torch.tensor(st.pos, device=dev)
     vel = torch.tensor(v0, device=dev)
     types = torch.tensor(st.types, device=dev)
@@ -478,8 +491,7 @@ def form_accuracy(st, m, precision, ref, dev, stream):
     (every atom): |dE|/N, force RMS over all 3N components, largest component
     error, and the RMS of the oracle's forces (the scale the errors sit on)."""
     import torch
-    from paper_2107_11311_gb300.aenet import AenetGPU
-    g = AenetGPU(m, precision, stream=stream.cuda_stream)
+    g = make_gpu(m, precision, stream)
     with torch.cuda.stream(stream):
         E = torch.zeros(1, dtype=torch.float64, device=dev)
         F = torch.zeros((st.n, 3), dtype=torch.float64, device=dev)
@@ -523,7 +535,7 @@ def e2e_rate(args, st, m, precision, pos, vel, types, stream, world):
     every step copies positions, velocities and types in and positions,
     velocities and energies out."""
     import torch
-    from paper_2107_11311_gb300.aenet import AENET_MD_CONTINUE, AenetGPU
+    from paper_2107_11311_gb300.aenet import AENET_MD_CONTINUE
     n = st.n
     hpos = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
     hvel = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
@@ -533,8 +545,7 @@ def e2e_rate(args, st, m, precision, pos, vel, types, stream, world):
     hpos.copy_(torch.as_tensor(pos))
     hvel.copy_(torch.as_tensor(vel))
     htypes.copy_(torch.as_tensor(types))
-    e2 = AenetGPU(m, precision, stream=stream.cuda_stream)
-    e2.set_skin(args.skin)
+    e2 = make_gpu(m, precision, stream, args.skin)
     e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek)
     for _ in range(3):
         e2.md_nve(hpos, hvel, htypes, st.box, DT_PS, 1, e_pot=hep, e_kin=hek, flags=AENET_MD_CONTINUE)
@@ -555,9 +566,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp32,bf16x3,bf16",
-                    help="precision forms timed side by side (comma-separated: fp32, bf16x3, bf16)")
-    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"],
+    ap.add_argument("--forms", default="fp32,bf16x3,bf16,bf16x3_split",
+                    help="precision forms timed side by side (comma-separated: fp32, bf16x3, bf16, "
+                         "bf16x3_split, bf16_split)")
+    ap.add_argument("--precision", default=None, choices=sorted(FORM_DTYPE),
                     help="time this form only (same as --forms <form>)")
     ap.add_argument("--workload", default="water_331776")
     ap.add_argument("--e2e-steps", type=int, default=20)

@@ -18,6 +18,7 @@ from . import build as _build
 AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
 AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING, AENET_MD_TIMING_POTENTIAL = 1, 2, 4, 8
 AENET_OPT_KEEP_ACTIVATIONS = 1
+AENET_OPT_FUSED_NETWORK = 2
 AENET_BATCH_AUTOTUNE = 1
 STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
 PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
@@ -343,6 +344,12 @@ class AenetGPU:
 
     def set_option(self, option, value):
         self._check(self.lib.aenet_set_option(self.h, int(option), int(value)))
+
+    def fuse_network(self, on=True):
+        """BF16 forms: run the tensor-core networks inside the fused potential
+        kernel (default) or as the three-kernel path (descriptor kernel, network
+        kernel, force kernel)."""
+        self.set_option(AENET_OPT_FUSED_NETWORK, 1 if on else 0)
 
     def keep_activations(self, on=True):
         """Keep per-atom activation records so that grad_weights() can follow."""

@@ -934,120 +934,149 @@ __device__ __forceinline__ void tc_tile_chain(int t, int a0, int a1, int lane, f
     float *rec1 = (rec_base && a1 >= 0) ? rec_base + (size_t)(atom0 + a1) * tn.rec_len : nullptr;
     const int H1 = tn.H1, H2 = tn.H2;
 
-    // layer-1 input: the standardised descriptor rows as A fragments (K = 64)
-    uint32_t A0h[KS1][4], A0l[KS1][4];
-#pragma unroll
-    for (int ks = 0; ks < KS1; ++ks)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int col = ks * 16 + 2 * tq + 8 * h;
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int a = rr ? a1 : a0;
-                float *rec = rr ? rec1 : rec0;
-                float x0 = 0.f, x1 = 0.f;
-                if (a >= 0) {
-                    const float2 v = *reinterpret_cast<const float2 *>(s_g + a * kSlots + col);
-                    x0 = v.x;
-                    x1 = v.y;
-                }
-                if (rec) {
-                    if (col < D) rec[col] = x0;
-                    if (col + 1 < D) rec[col + 1] = x1;
-                }
-                uint32_t hi, lo = 0u;
-                if (X3) split_bf2(x0, x1, hi, lo); else hi = pack_bf2(x0, x1);
-                A0h[ks][2 * h + rr] = hi;
-                A0l[ks][2 * h + rr] = lo;
-            }
-        }
-    // forward
+    // ---- layer 1: Z1 = b1 + g W1^T, the A fragments of g built per k-step from
+    // the standardised rows (K = 64)
     float C1[NT][4];
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
         const float b0 = bias[nt * 8 + 2 * tq], b1 = bias[nt * 8 + 2 * tq + 1];
         C1[nt][0] = b0; C1[nt][1] = b1; C1[nt][2] = b0; C1[nt][3] = b1;
     }
-    gemm<KS1, NT, X3>(C1, A0h, A0l, Wh + tn.pk.off_w1f / 2, Wl + tn.pk.off_w1f / 2, lane);
+    {
+        const uint2 *Bh = Wh + tn.pk.off_w1f / 2, *Bl = Wl + tn.pk.off_w1f / 2;
+#pragma unroll
+        for (int ks = 0; ks < KS1; ++ks) {
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = ks * 16 + 2 * tq + 8 * h;
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    const int a = rr ? a1 : a0;
+                    float *rec = rr ? rec1 : rec0;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (a >= 0) v = *reinterpret_cast<const float2 *>(s_g + a * kSlots + col);
+                    if (rec) {
+                        if (col < D) rec[col] = v.x;
+                        if (col + 1 < D) rec[col + 1] = v.y;
+                    }
+                    uint32_t hi, lo = 0u;
+                    if (X3) split_bf2(v.x, v.y, hi, lo); else hi = pack_bf2(v.x, v.y);
+                    ah[2 * h + rr] = hi;
+                    al[2 * h + rr] = lo;
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const uint2 bh = Bh[(ks * NT + nt) * 32 + lane];
+                mma_bf16(C1[nt], ah, bh.x, bh.y);
+                if (X3) {
+                    const uint2 bl = Bl[(ks * NT + nt) * 32 + lane];
+                    mma_bf16(C1[nt], ah, bl.x, bl.y);
+                    mma_bf16(C1[nt], al, bh.x, bh.y);
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int e = 0; e < 4; ++e) C1[nt][e] = (nt * 8 + 2 * tq + (e & 1) < H1) ? tanhf(C1[nt][e]) : 0.f;
-    uint32_t A1h[KSH][4], A1l[KSH][4];
-    to_a<NT, X3>(C1, A1h, A1l);
-    float C2[NT][4];
-    const float *b2 = bias + tn.pk.H1p;
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        const float b0 = b2[nt * 8 + 2 * tq], b1 = b2[nt * 8 + 2 * tq + 1];
-        C2[nt][0] = b0; C2[nt][1] = b1; C2[nt][2] = b0; C2[nt][3] = b1;
-    }
-    gemm<KSH, NT, X3>(C2, A1h, A1l, Wh + tn.pk.off_w2f / 2, Wl + tn.pk.off_w2f / 2, lane);
-    // output layer in FP32 on the accumulator fragments
-    const float *w3 = bias + tn.pk.H1p + tn.pk.H2p;
-    const float b3 = bias[tn.pk.H1p + 2 * tn.pk.H2p];
+
+    // ---- layer 2 and the linear output layer (FP32): delta2 = (1 - x2^2) w3
+    float D2[NT][4];
     float e0 = 0.f, e1 = 0.f;
-    float D2[NT][4];  // delta2 = (1 - x2^2) w3; C2 becomes x2
+    {
+        uint32_t A1h[KSH][4], A1l[KSH][4];
+        to_a<NT, X3>(C1, A1h, A1l);
+        float C2[NT][4];
+        const float *b2 = bias + tn.pk.H1p;
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int col = nt * 8 + 2 * tq + (e & 1);
-            const float x = col < H2 ? tanhf(C2[nt][e]) : 0.f;
-            const float w = w3[col];
-            if (e < 2) e0 = fmaf(w, x, e0); else e1 = fmaf(w, x, e1);
-            D2[nt][e] = (1.0f - x * x) * w;
-            C2[nt][e] = x;
+        for (int nt = 0; nt < NT; ++nt) {
+            const float b0 = b2[nt * 8 + 2 * tq], b1 = b2[nt * 8 + 2 * tq + 1];
+            C2[nt][0] = b0; C2[nt][1] = b1; C2[nt][2] = b0; C2[nt][3] = b1;
         }
-    e0 += __shfl_xor_sync(kFull, e0, 1);
-    e0 += __shfl_xor_sync(kFull, e0, 2);
-    e1 += __shfl_xor_sync(kFull, e1, 1);
-    e1 += __shfl_xor_sync(kFull, e1, 2);
-    e0 += b3;
-    e1 += b3;
-    // backward
-    uint32_t A2h[KSH][4], A2l[KSH][4];
-    to_a<NT, X3>(D2, A2h, A2l);
-    float C3[NT][4];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) C3[nt][0] = C3[nt][1] = C3[nt][2] = C3[nt][3] = 0.f;
-    gemm<KSH, NT, X3>(C3, A2h, A2l, Wh + tn.pk.off_w2b / 2, Wl + tn.pk.off_w2b / 2, lane);
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) C3[nt][e] *= (1.0f - C1[nt][e] * C1[nt][e]);
-    if (rec0 || rec1) {  // x1, delta1, x2, delta2 of the record
+        gemm<KSH, NT, X3>(C2, A1h, A1l, Wh + tn.pk.off_w2f / 2, Wl + tn.pk.off_w2f / 2, lane);
+        const float *w3 = bias + tn.pk.H1p + tn.pk.H2p;
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int col = nt * 8 + 2 * tq + (e & 1);
+                const float x = col < H2 ? tanhf(C2[nt][e]) : 0.f;
+                const float w = w3[col];
+                if (e < 2) e0 = fmaf(w, x, e0); else e1 = fmaf(w, x, e1);
+                D2[nt][e] = (1.0f - x * x) * w;
                 float *rec = e < 2 ? rec0 : rec1;
-                if (!rec) continue;
-                if (col < H1) {
-                    rec[D + col] = C1[nt][e];
-                    rec[D + H1 + col] = C3[nt][e];
-                }
-                if (col < H2) {
-                    rec[D + 2 * H1 + col] = C2[nt][e];
+                if (rec && col < H2) {  // x2 and delta2 of the record
+                    rec[D + 2 * H1 + col] = x;
                     rec[D + 2 * H1 + H2 + col] = D2[nt][e];
                 }
             }
     }
+    e0 += __shfl_xor_sync(kFull, e0, 1);
+    e0 += __shfl_xor_sync(kFull, e0, 2);
+    e1 += __shfl_xor_sync(kFull, e1, 1);
+    e1 += __shfl_xor_sync(kFull, e1, 2);
+    const float b3 = bias[tn.pk.H1p + 2 * tn.pk.H2p];
+    e0 += b3;
+    e1 += b3;
+
+    // ---- backward: delta1 = (1 - x1^2) (delta2 W2)
     uint32_t A3h[KSH][4], A3l[KSH][4];
-    to_a<NT, X3>(C3, A3h, A3l);
-    float C4[NTD][4];
+    {
+        uint32_t A2h[KSH][4], A2l[KSH][4];
+        to_a<NT, X3>(D2, A2h, A2l);
+        float C3[NT][4];
 #pragma unroll
-    for (int nt = 0; nt < NTD; ++nt) C4[nt][0] = C4[nt][1] = C4[nt][2] = C4[nt][3] = 0.f;
-    gemm<KSH, NTD, X3>(C4, A3h, A3l, Wh + tn.pk.off_w1b / 2, Wl + tn.pk.off_w1b / 2, lane);
-    // dE/dG = dE/dg * scale over the rows g was read from (every (row, column)
-    // pair belongs to one lane, which has already read its inputs)
+        for (int nt = 0; nt < NT; ++nt) C3[nt][0] = C3[nt][1] = C3[nt][2] = C3[nt][3] = 0.f;
+        gemm<KSH, NT, X3>(C3, A2h, A2l, Wh + tn.pk.off_w2b / 2, Wl + tn.pk.off_w2b / 2, lane);
 #pragma unroll
-    for (int nt = 0; nt < NTD; ++nt) {
-        const int col = nt * 8 + 2 * tq;
-        const float2 s2 = *reinterpret_cast<const float2 *>(sc + col);
-        if (a0 >= 0) *reinterpret_cast<float2 *>(s_g + a0 * kSlots + col) = make_float2(C4[nt][0] * s2.x, C4[nt][1] * s2.y);
-        if (a1 >= 0) *reinterpret_cast<float2 *>(s_g + a1 * kSlots + col) = make_float2(C4[nt][2] * s2.x, C4[nt][3] * s2.y);
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                C3[nt][e] *= (1.0f - C1[nt][e] * C1[nt][e]);
+                const int col = nt * 8 + 2 * tq + (e & 1);
+                float *rec = e < 2 ? rec0 : rec1;
+                if (rec && col < H1) {  // x1 and delta1 of the record
+                    rec[D + col] = C1[nt][e];
+                    rec[D + H1 + col] = C3[nt][e];
+                }
+            }
+        to_a<NT, X3>(C3, A3h, A3l);
+    }
+
+    // ---- dE/dg = delta1 W1, in two halves of the 64 columns; dE/dG = dE/dg *
+    // scale written over the rows g was read from (every (row, column) pair
+    // belongs to one lane, which has already read its inputs)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float C4[NTD / 2][4];
+#pragma unroll
+        for (int j = 0; j < NTD / 2; ++j) C4[j][0] = C4[j][1] = C4[j][2] = C4[j][3] = 0.f;
+        const uint2 *Bh = Wh + tn.pk.off_w1b / 2, *Bl = Wl + tn.pk.off_w1b / 2;
+#pragma unroll
+        for (int ks = 0; ks < KSH; ++ks)
+#pragma unroll
+            for (int j = 0; j < NTD / 2; ++j) {
+                const int nt = half * (NTD / 2) + j;
+                const uint2 bh = Bh[(ks * NTD + nt) * 32 + lane];
+                mma_bf16(C4[j], A3h[ks], bh.x, bh.y);
+                if (X3) {
+                    const uint2 bl = Bl[(ks * NTD + nt) * 32 + lane];
+                    mma_bf16(C4[j], A3h[ks], bl.x, bl.y);
+                    mma_bf16(C4[j], A3l[ks], bh.x, bh.y);
+                }
+            }
+#pragma unroll
+        for (int j = 0; j < NTD / 2; ++j) {
+            const int col = (half * (NTD / 2) + j) * 8 + 2 * tq;
+            const float2 s2 = *reinterpret_cast<const float2 *>(sc + col);
+            if (a0 >= 0)
+                *reinterpret_cast<float2 *>(s_g + a0 * kSlots + col) = make_float2(C4[j][0] * s2.x, C4[j][1] * s2.y);
+            if (a1 >= 0)
+                *reinterpret_cast<float2 *>(s_g + a1 * kSlots + col) = make_float2(C4[j][2] * s2.x, C4[j][3] * s2.y);
+        }
     }
     if (tq == 0) {
         if (a0 >= 0) {

@@ -27,12 +27,16 @@ def _rel_err(got, ref):
     ("water", None, "fp32"),          # fused kernel
     ("amorphous", None, "fp32"),      # fused kernel, 4 species
     ("water", (40, 36), "fp32"),      # split FP32 network kernel (widths > 32)
-    ("water", (32, 32), "bf16x3"),    # BF16 tensor-core kernel, split operands
+    ("water", (32, 32), "bf16x3"),    # tensor-core networks inside the fused kernel, split operands
+    ("amorphous", None, "bf16x3"),    # the same, 4 species (staged in chunks)
+    ("water", (32, 32), "bf16x3-split"),  # the three-kernel path's tensor-core network kernel
 ])
 def test_grad_weights_matches_oracle(gpu_mod, family, hidden, precision):
     st = inputs.water_192() if family == "water" else inputs.amorphous(600, seed=6)
     m = inputs.make_model(family, hidden=hidden)
-    g = gpu_mod.AenetGPU(m, precision)
+    g = gpu_mod.AenetGPU(m, precision.replace("-split", ""))
+    if precision.endswith("-split"):
+        g.fuse_network(False)
     g.keep_activations(True)
     g.compute(st.pos, st.types, st.box)
     dW = g.grad_weights()
