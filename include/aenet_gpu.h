@@ -86,7 +86,8 @@ typedef struct {
 
 /*
  * Create a context on the current CUDA device. `stream` is a cudaStream_t
- * (NULL = legacy default stream); all work of the context is ordered on it.
+ * (NULL: the context creates a blocking stream of its own, which the legacy
+ * default stream orders implicitly); all work of the context is ordered on it.
  * precision: an aenet_precision. Returns AENET_OK and *out, or an error and
  * *out = NULL.
  */
@@ -188,6 +189,21 @@ int aenet_md_box(aenet_ctx *ctx, double *box, double *tilt);
 /* Number of Verlet-list builds so far on this context (a measurement with no
  * counterpart in the paper): *builds HOST. Synchronises. Errors: AENET_E_ARG. */
 int aenet_md_list_builds(aenet_ctx *ctx, int64_t *builds);
+
+/*
+ * aenet_compute without synchronisation, for callers that evaluate repeatedly
+ * on device data (an autograd force loop): the same evaluation enqueued on the
+ * context's stream, every array a DEVICE pointer (energy, forces, virial,
+ * e_atom may be NULL), box HOST. Device-side problems (neighbour-list overflow,
+ * overlapping atoms, species out of range) are not read here: they stay in the
+ * device error word until the next synchronising call, aenet_check for
+ * instance, reports them, and the outputs of the failing evaluation are then
+ * invalid. The list capacities are not regrown here: after an
+ * AENET_E_CAPACITY from aenet_check, one aenet_compute (which regrows and
+ * retries) restores them. Host pointers give AENET_E_ARG.
+ */
+int aenet_compute_async(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t *types, const double *box,
+                        double *energy, double *forces, double *virial, double *e_atom);
 
 /*
  * Energies, forces and virials of many independent periodic structures in one
@@ -387,13 +403,20 @@ int aenet_set_option(aenet_ctx *ctx, int option, int value);
  * dEdW: [n_species * n_params] double, host or device, same layout as the
  * model's params. FP64 sums of FP32 products, deterministic. Returns
  * AENET_E_STATE if the last evaluation kept no activation records.
- * Synchronises.
+ * Synchronises when dEdW is host memory; with a device dEdW the work is only
+ * enqueued on the context's stream.
  */
 int aenet_grad_weights(aenet_ctx *ctx, double *dEdW);
 
 /*
- * Replace the network parameters ([n_species * n_params] double, HOST, same
- * layout as at set-up). A captured MD step picks them up on its next replay.
+ * Replace the network parameters ([n_species * n_params] double, same layout as
+ * at set-up; Sec. II.C trains exactly these). HOST params: converted on the host,
+ * copied after a synchronisation of the context's stream. DEVICE params: the
+ * conversion to FP32 and, in the BF16 forms, the packing of the tensor-core
+ * operands run as kernels on the context's stream, after the work already
+ * enqueued there and without any host round trip; the caller keeps params
+ * valid until the stream reaches them. A captured MD step picks up the new
+ * parameters on its next replay.
  */
 int aenet_set_params(aenet_ctx *ctx, const double *params);
 

@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True):
     lib.aenet_setup.argtypes = [C.POINTER(P), C.POINTER(ModelDesc), I, P]
     lib.aenet_set_stream.argtypes = [P, P]
     lib.aenet_compute.argtypes = [P, I, P, P, P, P, P, P, P]
+    lib.aenet_compute_async.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_descriptors.argtypes = [P, I, P, P, P, P]
     lib.aenet_compute_batch.argtypes = [P, I, P, P, P, P, P, P, P]
     lib.aenet_batch_prepare.argtypes = [P, I, P, P, P, P, P, P, P, I]
@@ -221,7 +222,12 @@ class AenetGPU:
             raise AenetError(rc, self.lib.aenet_last_error(self.h).decode())
 
     def set_stream(self, stream):
-        self._check(self.lib.aenet_set_stream(self.h, stream))
+        """Order the context's work on `stream` (a raw cudaStream_t handle);
+        a no-op when it already is the context's stream."""
+        if getattr(self, "_stream", None) == stream:
+            return
+        self._check(self.lib.aenet_set_stream(self.h, C.c_void_p(stream)))
+        self._stream = stream
 
     def check(self):
         self._check(self.lib.aenet_check(self.h))
@@ -247,6 +253,14 @@ class AenetGPU:
         if ret:
             return dict(energy=float(energy[0]), forces=forces, virial=virial, e_atom=e_atom)
         return None
+
+    def compute_async(self, pos, types, box, energy=None, forces=None, virial=None, e_atom=None):
+        """The evaluation enqueued on the context's stream without waiting:
+        every array a CUDA tensor; errors are reported by the next check()."""
+        pos, types = _as(pos, np.float64), _as(types, np.int32)
+        box = self._box(box)
+        self._check(self.lib.aenet_compute_async(self.h, int(pos.shape[0]), _ptr(pos), _ptr(types), _ptr(box),
+                                                 _ptr(energy), _ptr(forces), _ptr(virial), _ptr(e_atom)))
 
     def compute_batch(self, atom_offset, pos, types, boxes, energies=None, forces=None, virials=None):
         """Energies [S], forces [N,3], virials [S,3,3] of S structures in one
@@ -363,8 +377,14 @@ class AenetGPU:
         return out
 
     def set_params(self, params):
-        """Replace the network parameters ([n_species, n_params], host float64)."""
-        p = np.ascontiguousarray(params, dtype=np.float64)
+        """Replace the network parameters ([n_species, n_params] float64): a
+        CUDA tensor is converted and packed on the device, in stream order and
+        without a host round trip; numpy arrays go through the host."""
+        if _is_torch(params) and params.is_cuda:
+            p = _as(params.contiguous(), np.float64)
+            self._params_keep = p  # valid until the stream has read it
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float64)
         self._check(self.lib.aenet_set_params(self.h, _ptr(p)))
 
     def neighbor_stats(self):
@@ -398,19 +418,36 @@ def _energy_function():
 
         @staticmethod
         def forward(ctx, pos, params, gpu, types, box):
+            """On CUDA tensors everything is enqueued on torch's current stream:
+            the parameters are converted and packed on the device, the
+            evaluation and dE/dW follow without a host round trip. The first
+            call for a system size runs the synchronous evaluation (it sizes the
+            neighbour lists); later calls do not wait, so device-side errors are
+            reported by gpu.check(), which callers run now and then."""
             want_w = params.requires_grad
-            gpu.set_params(params.detach().cpu().numpy())
-            gpu.keep_activations(want_w)
             dev = pos.device
+            on_gpu = dev.type == "cuda" and params.is_cuda and types.is_cuda
+            if on_gpu:
+                h = torch.cuda.current_stream(dev).cuda_stream
+                if h:  # torch's legacy default stream (handle 0) already orders the context's blocking stream
+                    gpu.set_stream(h)
+                gpu.set_params(params.detach())
+            else:
+                gpu.set_params(params.detach().cpu().numpy())
+            gpu.keep_activations(want_w)
             E = torch.zeros(1, dtype=torch.float64, device=dev)
             F = torch.zeros_like(pos, dtype=torch.float64)
-            gpu.compute(pos.detach().contiguous(), types, box, energy=E, forces=F)
+            p = pos.detach().contiguous()
+            n = int(p.shape[0])
+            if on_gpu and getattr(gpu, "_async_n", None) == n:
+                gpu.compute_async(p, types, box, energy=E, forces=F)
+            else:
+                gpu.compute(p, types, box, energy=E, forces=F)
+                gpu._async_n = n if on_gpu else None
             dW = None
             if want_w:
                 dW = torch.zeros(params.shape, dtype=torch.float64, device=dev)
                 gpu.grad_weights(out=dW)
-            if dev.type == "cuda":
-                torch.cuda.current_stream(dev).synchronize()
             ctx.save_for_backward(F, dW if dW is not None else torch.zeros(0))
             ctx.want_w = want_w
             return E[0]

@@ -15,8 +15,6 @@
 // lane per fragment).
 #include <cuda_bf16.h>
 
-#include <vector>
-
 #include "aenet_internal.cuh"
 #include "bf16_mma.cuh"
 
@@ -27,37 +25,59 @@ namespace {
 constexpr int kTileRows = 16;
 constexpr int kAnnWarps = 4;  // tiles per CTA
 
-uint16_t f2bf(float x) {
-    __nv_bfloat16 b = __float2bfloat16_rn(x);
-    return *reinterpret_cast<uint16_t *>(&b);
-}
-float bf2f(uint16_t u) {
-    __nv_bfloat16 b;
-    *reinterpret_cast<uint16_t *>(&b) = u;
-    return __bfloat162float(b);
-}
-
-// Pack B[k][n] (K x N, given by a functor) into mma B-fragment order, hi and lo.
-template <class F>
-void pack_b(F B, int K, int N, uint32_t *hi, uint32_t *lo) {
-    for (int ks = 0; ks < K / 16; ++ks)
-        for (int nt = 0; nt < N / 8; ++nt)
-            for (int lane = 0; lane < 32; ++lane) {
-                const int g = lane >> 2, t = lane & 3;
-                const int n = nt * 8 + g;
-                for (int r = 0; r < 2; ++r) {
-                    const int k0 = ks * 16 + 2 * t + 8 * r;
-                    uint16_t h[2], l[2];
-                    for (int e = 0; e < 2; ++e) {
-                        const float v = B(k0 + e, n);
-                        h[e] = f2bf(v);
-                        l[e] = f2bf(v - bf2f(h[e]));
-                    }
-                    const size_t idx = ((size_t)(ks * (N / 8) + nt) * 32 + lane) * 2 + r;
-                    hi[idx] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-                    lo[idx] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
-                }
-            }
+// The network parameters (FP32 [species][n_params]: W1 b1 W2 b2 w3 b3, W row
+// major) packed for the tensor cores, on the device: for every GEMM a block of
+// [k-steps][n-tiles][32 lanes][2 words] in mma B-fragment order (lane g = l/4,
+// t = l%4 holds (k 2t + 8r, 2t + 8r + 1; column g) in word r), hi and lo BF16
+// parts per species; then FP32 biases b1 [H1p], b2 [H2p], w3 [H2p], b3.
+//   w1f = W1^T (K = 64, N = H1p)    w2f = W2^T (K = H1p, N = H2p)
+//   w2b = W2   (K = H2p, N = H1p)   w1b = W1   (K = H1p, N = 64)
+// One thread per word pair (hi, lo) of one species, or per bias entry.
+__global__ void k_pack_bf16(int ns, int n_params, int D, int H1, int H2, PackedNet pk, const float *__restrict__ P,
+                            uint32_t *__restrict__ wpk, float *__restrict__ bias) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int per_sp = pk.words, nbias = pk.H1p + 2 * pk.H2p + 1;
+    if (tid < ns * per_sp) {
+        const int t = tid / per_sp, w = tid - t * per_sp;
+        const float *p = P + (size_t)t * n_params;
+        const float *W1 = p, *W2 = p + H1 * D + H1;
+        int blk, off, N;
+        if (w < pk.off_w2f) { blk = 0; off = pk.off_w1f; N = pk.H1p; }
+        else if (w < pk.off_w2b) { blk = 1; off = pk.off_w2f; N = pk.H2p; }
+        else if (w < pk.off_w1b) { blk = 2; off = pk.off_w2b; N = pk.H1p; }
+        else { blk = 3; off = pk.off_w1b; N = kKD; }
+        const int idx = w - off, r = idx & 1, lane = (idx >> 1) & 31, tile = idx >> 6;
+        const int NTb = N / 8, ks = tile / NTb, nt = tile - ks * NTb;
+        const int n = nt * 8 + (lane >> 2), k0 = ks * 16 + 2 * (lane & 3) + 8 * r;
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = k0 + e;
+            float x = 0.f;
+            if (blk == 0) x = (k < D && n < H1) ? W1[n * D + k] : 0.f;
+            else if (blk == 1) x = (k < H1 && n < H2) ? W2[n * H1 + k] : 0.f;
+            else if (blk == 2) x = (k < H2 && n < H1) ? W2[k * H1 + n] : 0.f;
+            else x = (k < H1 && n < D) ? W1[k * D + n] : 0.f;
+            v[e] = x;
+        }
+        uint32_t hi, lo;
+        split_bf2(v[0], v[1], hi, lo);
+        uint32_t *base = wpk + (size_t)t * 2 * per_sp;
+        base[w] = hi;
+        base[per_sp + w] = lo;
+        return;
+    }
+    const int b = tid - ns * per_sp;
+    if (b >= ns * nbias) return;
+    const int t = b / nbias, i = b - t * nbias;
+    const float *p = P + (size_t)t * n_params;
+    const float *b1 = p + H1 * D, *b2 = b1 + H1 + H2 * H1, *w3 = b2 + H2, *b3 = w3 + H2;
+    float x = 0.f;
+    if (i < pk.H1p) x = i < H1 ? b1[i] : 0.f;
+    else if (i < pk.H1p + pk.H2p) x = i - pk.H1p < H2 ? b2[i - pk.H1p] : 0.f;
+    else if (i < pk.H1p + 2 * pk.H2p) x = i - pk.H1p - pk.H2p < H2 ? w3[i - pk.H1p - pk.H2p] : 0.f;
+    else x = b3[0];
+    bias[b] = x;
 }
 
 struct AnnBf16Args {
@@ -314,40 +334,22 @@ bool bf16_supported(const Net &net) {
 
 cudaError_t prepare_bf16_weights(Context &c) {
     if (!bf16_supported(c.net)) return cudaErrorInvalidValue;
-    const int D = c.net.widths[0], H1 = c.net.widths[1], H2 = c.net.widths[2];
+    const int H1 = c.net.widths[1], H2 = c.net.widths[2];
     const PackedNet pk = make_packed(H1, H2);
     const int ns = c.net.n_species;
-    std::vector<float> P((size_t)ns * c.net.n_params);
-    cudaError_t e = cudaMemcpy(P.data(), c.d_params, sizeof(float) * P.size(), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
-    std::vector<uint32_t> wpk((size_t)ns * 2 * pk.words, 0u);
-    const int nb = pk.H1p + 2 * pk.H2p + 1;
-    std::vector<float> bias((size_t)ns * nb, 0.f);
-    for (int t = 0; t < ns; ++t) {
-        const float *p = P.data() + (size_t)t * c.net.n_params;
-        const float *W1 = p, *b1 = W1 + H1 * D, *W2 = b1 + H1, *b2 = W2 + H2 * H1, *w3 = b2 + H2, *b3 = w3 + H2;
-        uint32_t *hi = wpk.data() + (size_t)t * 2 * pk.words, *lo = hi + pk.words;
-        auto W1f = [&](int k, int n) { return (k < D && n < H1) ? W1[n * D + k] : 0.f; };   // W1^T
-        auto W2f = [&](int k, int n) { return (k < H1 && n < H2) ? W2[n * H1 + k] : 0.f; };  // W2^T
-        auto W2b = [&](int k, int n) { return (k < H2 && n < H1) ? W2[k * H1 + n] : 0.f; };  // W2
-        auto W1b = [&](int k, int n) { return (k < H1 && n < D) ? W1[k * D + n] : 0.f; };    // W1
-        pack_b(W1f, kKD, pk.H1p, hi + pk.off_w1f, lo + pk.off_w1f);
-        pack_b(W2f, pk.H1p, pk.H2p, hi + pk.off_w2f, lo + pk.off_w2f);
-        pack_b(W2b, pk.H2p, pk.H1p, hi + pk.off_w2b, lo + pk.off_w2b);
-        pack_b(W1b, pk.H1p, kKD, hi + pk.off_w1b, lo + pk.off_w1b);
-        float *bt = bias.data() + (size_t)t * nb;
-        for (int k = 0; k < H1; ++k) bt[k] = b1[k];
-        for (int k = 0; k < H2; ++k) bt[pk.H1p + k] = b2[k];
-        for (int k = 0; k < H2; ++k) bt[pk.H1p + pk.H2p + k] = w3[k];
-        bt[pk.H1p + 2 * pk.H2p] = b3[0];
+    const size_t words = (size_t)ns * 2 * pk.words;
+    const size_t nb = (size_t)ns * (pk.H1p + 2 * pk.H2p + 1);
+    cudaError_t e;
+    if (!c.d_wbf) {  // allocated once at set-up, reused by every parameter update
+        if ((e = cudaMalloc(&c.d_wbf, sizeof(uint32_t) * words + sizeof(float) * nb)) != cudaSuccess) return e;
     }
-    const size_t bytes = sizeof(uint32_t) * wpk.size() + sizeof(float) * bias.size();
-    if (!c.d_wbf && (e = cudaMalloc(&c.d_wbf, bytes)) != cudaSuccess) return e;  // reused on a parameter update
-    c.wbf_elems = wpk.size();
-    if ((e = cudaMemcpy(c.d_wbf, wpk.data(), sizeof(uint32_t) * wpk.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    return cudaMemcpy(reinterpret_cast<uint32_t *>(c.d_wbf) + wpk.size(), bias.data(), sizeof(float) * bias.size(),
-                      cudaMemcpyHostToDevice);
+    c.wbf_elems = words;
+    uint32_t *wpk = reinterpret_cast<uint32_t *>(c.d_wbf);
+    float *bias = reinterpret_cast<float *>(wpk + words);
+    const int total = (int)(words / 2 + nb);
+    k_pack_bf16<<<(total + 255) / 256, 256, 0, c.stream>>>(ns, c.net.n_params, c.net.widths[0], H1, H2, pk,
+                                                           c.d_params, wpk, bias);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_species_group(Context &c, int n) {

@@ -521,6 +521,31 @@ extern "C" int aenet_compute(aenet_ctx *h, int n, const double *pos, const int32
     return compute_impl(h->c, n, pos, types, box, energy, forces, virial, e_atom, nullptr);
 }
 
+extern "C" int aenet_compute_async(aenet_ctx *h, int n, const double *pos, const int32_t *types, const double *box,
+                                   double *energy, double *forces, double *virial, double *e_atom) {
+    if (!h) return fail(nullptr, AENET_E_ARG, "ctx is NULL");
+    Context &c = h->c;
+    cudaGetLastError();
+    if (n < 1) return fail(&c, AENET_E_ARG, "n_atoms < 1");
+    if (!box) return fail(&c, AENET_E_ARG, "box is NULL");
+    const void *arrays[] = {pos, types, energy, forces, virial, e_atom};
+    for (int k = 0; k < 6; ++k)
+        if ((k < 2 || arrays[k]) && !is_device_ptr(arrays[k]))
+            return fail(&c, AENET_E_ARG, "aenet_compute_async takes device pointers only (argument %d)", k);
+    Grid g;
+    int rc = make_grid(c, box, g, 0.0, c.tilt);
+    if (rc) return rc;
+    if ((rc = ensure(c, n, g))) return rc;
+    if (c.caps.nb == 0) c.caps = estimate_caps(c, n, g);
+    if ((rc = enqueue_compute(c, g, n, pos, types, forces, e_atom))) return rc;
+    c.act_valid = c.keep_act;
+    c.act_atoms = n;
+    if (energy) CK(cudaMemcpyAsync(energy, c.d_result, sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "energy");
+    if (virial)
+        CK(cudaMemcpyAsync(virial, c.d_result + 1, 9 * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "virial");
+    return AENET_OK;
+}
+
 // ------------------------------------------------------------ batched form
 // Many periodic structures in one evaluation: per-structure cell grids in one
 // global cell index space; one launch of each kernel over all cells.
@@ -1348,19 +1373,35 @@ extern "C" int aenet_grad_weights(aenet_ctx *h, double *dEdW) {
     CK(cudaMemcpyAsync(dEdW, c.d_dEdW, sizeof(double) * c.basis.n_species * c.net.n_params, cudaMemcpyDefault,
                        c.stream),
        "dE/dW copy");
-    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+    if (!is_device_ptr(dEdW)) CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
     return AENET_OK;
 }
+
+namespace aenet {
+namespace {
+// FP64 parameters (device) to the context's FP32 copy.
+__global__ void k_params_to_f32(size_t n, const double *__restrict__ src, float *__restrict__ dst) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = (float)src[k];
+}
+}  // namespace
+}  // namespace aenet
 
 extern "C" int aenet_set_params(aenet_ctx *h, const double *params) {
     if (!h || !params) return fail(h ? &h->c : nullptr, AENET_E_ARG, "NULL argument");
     Context &c = h->c;
     cudaGetLastError();
     const size_t NP = (size_t)c.basis.n_species * c.net.n_params;
-    std::vector<float> P(NP);
-    for (size_t k = 0; k < NP; ++k) P[k] = (float)params[k];
-    CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
-    CK(cudaMemcpy(c.d_params, P.data(), sizeof(float) * NP, cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (is_device_ptr(params)) {
+        // on the context's stream, after the work already enqueued: no host round trip
+        k_params_to_f32<<<(int)std::min<size_t>((NP + 255) / 256, 1024), 256, 0, c.stream>>>(NP, params, c.d_params);
+        CK(cudaGetLastError(), "parameter conversion");
+    } else {
+        std::vector<float> P(NP);
+        for (size_t k = 0; k < NP; ++k) P[k] = (float)params[k];
+        CK(cudaStreamSynchronize(c.stream), "cudaStreamSynchronize");
+        CK(cudaMemcpy(c.d_params, P.data(), sizeof(float) * NP, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
     if (c.precision != AENET_FP32) CK(prepare_bf16_weights(c), "BF16 weights");
     c.act_valid = false;
     return AENET_OK;
