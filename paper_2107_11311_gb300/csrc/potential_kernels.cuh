@@ -901,6 +901,12 @@ __device__ __forceinline__ void load_tc_params(const Basis &B, const float *__re
     }
 }
 
+// tanh x = 1 - 2 / (exp(2x) + 1): the exponential and one division instead of
+// the full-accuracy tanhf. Its absolute error (a few 1e-7) is far below the
+// 2^-16 relative rounding of the split-BF16 operands it feeds; the limits
+// x -> +-inf give exactly +-1.
+__device__ __forceinline__ float tanh_exp(float x) { return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f); }
+
 // Position of the r-th set bit of mask (r from 0), or -1.
 __device__ __forceinline__ int nth_bit(unsigned mask, int r) {
     for (int k = 0; k < r && mask; ++k) mask &= mask - 1u;
@@ -981,7 +987,7 @@ __device__ __forceinline__ void tc_tile_chain(int t, int a0, int a1, int lane, f
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) C1[nt][e] = (nt * 8 + 2 * tq + (e & 1) < H1) ? tanhf(C1[nt][e]) : 0.f;
+        for (int e = 0; e < 4; ++e) C1[nt][e] = (nt * 8 + 2 * tq + (e & 1) < H1) ? tanh_exp(C1[nt][e]) : 0.f;
 
     // ---- layer 2 and the linear output layer (FP32): delta2 = (1 - x2^2) w3
     float D2[NT][4];
@@ -1003,7 +1009,7 @@ __device__ __forceinline__ void tc_tile_chain(int t, int a0, int a1, int lane, f
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int col = nt * 8 + 2 * tq + (e & 1);
-                const float x = col < H2 ? tanhf(C2[nt][e]) : 0.f;
+                const float x = col < H2 ? tanh_exp(C2[nt][e]) : 0.f;
                 const float w = w3[col];
                 if (e < 2) e0 = fmaf(w, x, e0); else e1 = fmaf(w, x, e1);
                 D2[nt][e] = (1.0f - x * x) * w;
@@ -1078,34 +1084,37 @@ __device__ __forceinline__ void tc_tile_chain(int t, int a0, int a1, int lane, f
                 *reinterpret_cast<float2 *>(s_g + a1 * kSlots + col) = make_float2(C4[j][2] * s2.x, C4[j][3] * s2.y);
         }
     }
+    // E_i of the tile's atoms; their FP64 sum joins the warp's energy (lane 0)
+    double et = 0.0;
     if (tq == 0) {
         if (a0 >= 0) {
             eatom[atom0 + a0] = e0;
-            e_acc += (double)e0;
+            et += (double)e0;
         }
         if (a1 >= 0) {
             eatom[atom0 + a1] = e1;
-            e_acc += (double)e1;
+            et += (double)e1;
         }
     }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) et += __shfl_xor_sync(kFull, et, o);
+    if (lane == 0) e_acc += et;
 }
 
-// Networks of one half [lo, hi) (at most 16 atoms) of a sub-item whose first
-// atom is the sorted atom atom0: one tile per species present.
+// Networks of the cnt atoms of one species in a sub-item whose first atom is
+// the sorted atom atom0: order[0 .. cnt) are their sub-item indices, taken in
+// tiles of 16 rows.
 template <int HT, bool X3>
-__device__ __forceinline__ void tc_half_network(int lo, int hi, int atom0, int n_species, int lane,
-                                                const float4 *__restrict__ pos4, float *s_g, const float *s_par,
-                                                const TcNet &tn, float *__restrict__ eatom,
-                                                float *__restrict__ rec_base, int D, double &e_acc) {
-    const int na = hi - lo;
-    const int tl = lane < na ? __float_as_int(pos4[atom0 + lo + lane].w) : -1;
+__device__ __noinline__ void tc_species_network(int t, const int *order, int cnt, int atom0, int lane,
+                                                   float *s_g, const float *s_par, const TcNet &tn,
+                                                   float *__restrict__ eatom, float *__restrict__ rec_base, int D,
+                                                   double &e_acc) {
     const int g = lane >> 2;
-    for (int t = 0; t < n_species; ++t) {
-        const unsigned mask = __ballot_sync(kFull, tl == t);
-        if (!mask) continue;
-        const int b0 = nth_bit(mask, g), b1 = nth_bit(mask, g + 8);
-        tc_tile_chain<HT, X3>(t, b0 >= 0 ? lo + b0 : -1, b1 >= 0 ? lo + b1 : -1, lane, s_g,
-                              s_par + t * kTcParStride + kSlots, tn, atom0, eatom, rec_base, D, e_acc);
+    for (int r0 = 0; r0 < cnt; r0 += 16) {
+        const int a0 = r0 + g < cnt ? order[r0 + g] : -1;
+        const int a1 = r0 + g + 8 < cnt ? order[r0 + g + 8] : -1;
+        tc_tile_chain<HT, X3>(t, a0, a1, lane, s_g, s_par + t * kTcParStride + kSlots, tn, atom0, eatom, rec_base,
+                              D, e_acc);
     }
 }
 
@@ -1124,7 +1133,11 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     __shared__ float s_vir[NW][9];
     __shared__ double s_e[NW];
     __shared__ int s_next, s_item;
-    __shared__ int s_tc_done_a[2], s_tc_done_b[2];  // tensor-core form: atoms of a half through phase A; network done
+    // tensor-core form: per species of the sub-item, atoms through phase A and
+    // network done; the sub-item's atoms in species order, and each species'
+    // first position and count in that order
+    __shared__ int s_tc_done_a[kMaxSpecies], s_tc_done_b[kMaxSpecies];
+    __shared__ int s_tc_order[kTcMaxAtoms], s_tc_first[kMaxSpecies + 1];
     constexpr bool kTC = is_tc_mode(MODE);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1208,11 +1221,8 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     const Grid &g = BATCH ? sinfo[sidx].g : g_one;
     const int cell0 = BATCH ? sinfo[sidx].cell0 : 0;
     const int n_off = g.n_off;
-    if (tid == 0) {
-        s_next = 0;
-        s_tc_done_a[0] = s_tc_done_a[1] = 0;
-        s_tc_done_b[0] = s_tc_done_b[1] = 0;
-    }
+    if (tid == 0) s_next = 0;
+    if (kTC && tid < kMaxSpecies) s_tc_done_a[tid] = s_tc_done_b[tid] = 0;
 
     // ---- neighbour-cell table: start, count and image shift of every offset
     const int lcell = cell - cell0;         // cell inside its structure's grid
@@ -1306,17 +1316,17 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
 
     if constexpr (kTC) {
     // ---- tensor-core form. The item's atoms are taken in sub-items of at most
-    // kTcMaxAtoms, each split into two halves. Phase A of an atom (neighbour
-    // list, descriptor, standardisation) leaves its g row and a compact copy of
-    // its list (staging indices) in shared memory; the warp that completes the
-    // last phase A of a half runs that half's networks on the tensor cores,
-    // which turn the g rows into dE/dG rows; phase C of an atom (its list
-    // rebuilt from the compact copy, the chain rule to forces and virial) waits
-    // only for its own half's network. When the neighbourhood fits one staged
-    // chunk the phases are tasks taken in the order A(half 0), A(half 1),
-    // C(half 0), C(half 1), so the networks run while other warps still work;
-    // otherwise phase A runs in rounds over the staged chunks and the networks
-    // between two block barriers.
+    // kTcMaxAtoms, ordered by species. Phase A of an atom (neighbour list,
+    // descriptor, standardisation) leaves its g row and a compact copy of its
+    // list (staging indices) in shared memory; the warp that completes the last
+    // phase A of a species runs that species' networks on the tensor cores
+    // (16-row tiles), which turn the g rows into dE/dG rows; phase C of an atom
+    // (its list rebuilt from the compact copy, the chain rule to forces and
+    // virial) waits only for its own species' networks. When the neighbourhood
+    // fits one staged chunk the phases are tasks taken in the order A (species
+    // by species), then C in the same order, so a species' networks run while
+    // other warps still work; otherwise phase A runs in rounds over the staged
+    // chunks and the networks between two block barriers.
     constexpr bool X3 = MODE == kFusedTCx3;
     if (n_chunks <= 1) {
         if (total > 0) stage(0);
@@ -1366,17 +1376,33 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, W, s_g + a * kSlots, lane, F4, vir);
     };
     for (int sub0 = 0; sub0 < cnt; sub0 += kTcMaxAtoms) {
-        const int m = min(kTcMaxAtoms, cnt - sub0), mh = (m + 1) >> 1;
+        const int m = min(kTcMaxAtoms, cnt - sub0);
         const int atom0 = c0 + sub0;
+        if (warp == 0) {  // the sub-item's atoms in species order (one lane per atom)
+            const int ts = lane < m ? __float_as_int(pos4[atom0 + lane].w) : -1;
+            int first = 0;
+            for (int t = 0; t < B.n_species; ++t) {
+                const unsigned mk = __ballot_sync(kFull, ts == t);
+                if (ts == t) s_tc_order[first + __popc(mk & ((1u << lane) - 1u))] = lane;
+                if (lane == 0) s_tc_first[t] = first;
+                first += __popc(mk);
+            }
+            if (lane == 0) s_tc_first[B.n_species] = first;
+        }
+        __syncthreads();
+        auto run_network = [&](int t) {
+            tc_species_network<HB, X3>(t, s_tc_order + s_tc_first[t], s_tc_first[t + 1] - s_tc_first[t], atom0, lane,
+                                       s_g, s_par, tc, eatom, G_out, B.D, e_acc);
+        };
         if (n_chunks <= 1) {
             for (;;) {
                 int task = 0;
                 if (lane == 0) task = atomicAdd(&s_next, 1);
                 task = __shfl_sync(kFull, task, 0);
                 if (task >= 2 * m) break;
-                const int a = task < m ? task : task - m;
-                const int h = a < mh ? 0 : 1;
+                const int a = s_tc_order[task < m ? task : task - m];
                 const int i_s = atom0 + a;
+                const int t = __float_as_int(pos4[i_s].w);
                 if (task < m) {
                     int nnb = 0, nang = 0;
                     scan_tile<true>(s_pos, s_idx, total, pos4[i_s], i_s, B, caps, W, lane, nnb, s_cl + a * caps.nb, 0);
@@ -1385,25 +1411,24 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                     __syncwarp();
                     __threadfence_block();
                     int done = 0;
-                    if (lane == 0) done = atomicAdd(&s_tc_done_a[h], 1);
+                    if (lane == 0) done = atomicAdd(&s_tc_done_a[t], 1);
                     done = __shfl_sync(kFull, done, 0);
-                    if (done == (h ? m - mh : mh) - 1) {  // the half's last phase A: run its networks
+                    if (done == s_tc_first[t + 1] - s_tc_first[t] - 1) {  // the species' last phase A: its networks
                         __threadfence_block();
-                        tc_half_network<HB, X3>(h ? mh : 0, h ? m : mh, atom0, B.n_species, lane, pos4, s_g, s_par, tc,
-                                                eatom, G_out, B.D, e_acc);
+                        run_network(t);
                         __threadfence_block();
                         __syncwarp();
-                        if (lane == 0) atomicExch(&s_tc_done_b[h], 1);
+                        if (lane == 0) atomicExch(&s_tc_done_b[t], 1);
                     }
                 } else {
-                    if (lane == 0) {  // wait for this half's networks (bounded)
+                    if (lane == 0) {  // wait for this species' networks (bounded)
                         int it = 0;
-                        while (atomicAdd(&s_tc_done_b[h], 0) == 0) {
+                        while (atomicAdd(&s_tc_done_b[t], 0) == 0) {
                             if (++it > kTcSpin) {
                                 atomicOr(err, kErrTimeout);
                                 break;
                             }
-                            __nanosleep(64);
+                            __nanosleep(128);
                         }
                     }
                     __syncwarp();
@@ -1414,8 +1439,9 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         } else {
             const int n_rounds = (m + NW - 1) / NW;
             for (int round = 0; round < n_rounds; ++round) {
-                const int a = round * NW + warp;
-                const bool active = a < m;
+                const int k = round * NW + warp;
+                const bool active = k < m;
+                const int a = active ? s_tc_order[k] : 0;
                 const int i_s = atom0 + a;
                 const float4 ui = active ? pos4[i_s] : make_float4(0.f, 0.f, 0.f, 0.f);
                 int nnb = 0, nang = 0;
@@ -1433,9 +1459,8 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                 }
             }
             __syncthreads();
-            if (warp < 2 && (warp ? m - mh : mh) > 0)
-                tc_half_network<HB, X3>(warp ? mh : 0, warp ? m : mh, atom0, B.n_species, lane, pos4, s_g, s_par, tc,
-                                        eatom, G_out, B.D, e_acc);
+            for (int t = warp; t < B.n_species; t += NW)
+                if (s_tc_first[t + 1] > s_tc_first[t]) run_network(t);
             __syncthreads();
             for (;;) {
                 int a = 0;
@@ -1446,11 +1471,8 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
             }
         }
         __syncthreads();  // every task of the sub-item is done
-        if (tid == 0) {
-            s_next = 0;
-            s_tc_done_a[0] = s_tc_done_a[1] = 0;
-            s_tc_done_b[0] = s_tc_done_b[1] = 0;
-        }
+        if (tid == 0) s_next = 0;
+        if (tid < kMaxSpecies) s_tc_done_a[tid] = s_tc_done_b[tid] = 0;
         __syncthreads();
     }
     } else if (n_chunks <= 1) {
