@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libaenet_gpu.so")
-SOURCES = ["cells.cu", "potential.cu", "potential_tc.cu", "potential_md.cu", "ann.cu", "ann_bf16.cu", "grad.cu", "md.cu", "capi.cu"]
+SOURCES = ["cells.cu", "potential.cu", "potential_tc.cu", "potential_md.cu", "ann.cu", "ann_bf16.cu", "ann_tcgen05.cu", "grad.cu", "md.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -382,6 +382,10 @@ bool bf16_supported(const Net &net);
 int bf16_max_tiles(const Context &c, int n);
 int bf16_eparts(const Context &c, int n);
 cudaError_t launch_ann_bf16(Context &c, int n);
+// The same networks on tcgen05 (TMEM accumulators), 128-atom species tiles:
+// the network kernel of the three-kernel path. Energy partials: one per CTA.
+int tcgen05_tiles(const Context &c, int n);
+cudaError_t launch_ann_tcgen05(Context &c, int n);
 
 // Length of the per-atom activation record (g, then x_l and delta_l per hidden layer).
 int activation_record_len(const Net &net);

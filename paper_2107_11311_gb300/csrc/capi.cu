@@ -232,8 +232,8 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts) {
             CK(launch_ann(c, n), "network kernel");
             *n_eparts = ann_blocks(n);
         } else {
-            CK(launch_ann_bf16(c, n), "BF16 network kernel");
-            *n_eparts = bf16_eparts(c, n);
+            CK(launch_ann_tcgen05(c, n), "BF16 network kernel");
+            *n_eparts = tcgen05_tiles(c, n);
         }
         CK(mark(c, 4), "event");
         CK(launch_fp_backward(c, g, n), "force kernel");

@@ -1137,7 +1137,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     // network done; the sub-item's atoms in species order, and each species'
     // first position and count in that order
     __shared__ int s_tc_done_a[kMaxSpecies], s_tc_done_b[kMaxSpecies];
-    __shared__ int s_tc_order[kTcMaxAtoms], s_tc_first[kMaxSpecies + 1];
+    __shared__ int s_tc_order[kTcMaxAtoms], s_tc_first[kMaxSpecies], s_tc_count[kMaxSpecies];
     constexpr bool kTC = is_tc_mode(MODE);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1316,16 +1316,17 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
 
     if constexpr (kTC) {
     // ---- tensor-core form. The item's atoms are taken in sub-items of at most
-    // kTcMaxAtoms, ordered by species. Phase A of an atom (neighbour list,
+    // kTcMaxAtoms, grouped by species (largest group first). Phase A of an atom (neighbour list,
     // descriptor, standardisation) leaves its g row and a compact copy of its
     // list (staging indices) in shared memory; the warp that completes the last
     // phase A of a species runs that species' networks on the tensor cores
     // (16-row tiles), which turn the g rows into dE/dG rows; phase C of an atom
     // (its list rebuilt from the compact copy, the chain rule to forces and
     // virial) waits only for its own species' networks. When the neighbourhood
-    // fits one staged chunk the phases are tasks taken in the order A (species
-    // by species), then C in the same order, so a species' networks run while
-    // other warps still work; otherwise phase A runs in rounds over the staged
+    // fits one staged chunk the phases are tasks taken in the order A (group
+    // by group), then C in the same order, so a group's networks run while
+    // other warps still work (the largest group's while the smaller groups'
+    // phase A runs, the last group's while the earlier groups' phase C runs); otherwise phase A runs in rounds over the staged
     // chunks and the networks between two block barriers.
     constexpr bool X3 = MODE == kFusedTCx3;
     if (n_chunks <= 1) {
@@ -1378,21 +1379,39 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     for (int sub0 = 0; sub0 < cnt; sub0 += kTcMaxAtoms) {
         const int m = min(kTcMaxAtoms, cnt - sub0);
         const int atom0 = c0 + sub0;
-        if (warp == 0) {  // the sub-item's atoms in species order (one lane per atom)
+        if (warp == 0) {  // the sub-item's atoms grouped by species, largest group first
             const int ts = lane < m ? __float_as_int(pos4[atom0 + lane].w) : -1;
-            int first = 0;
+            // lane t < n_species: its species' count; rank = place of the group in the order
+            int cnt_t = 0;
+            for (int t = 0; t < B.n_species; ++t) {
+                const int c = __popc(__ballot_sync(kFull, ts == t));
+                if (lane == t) cnt_t = c;
+            }
+            int rank = 0;
+            for (int u = 0; u < B.n_species; ++u) {
+                const int cu = __shfl_sync(kFull, cnt_t, u);
+                if (lane < B.n_species && (cu > cnt_t || (cu == cnt_t && u < lane))) ++rank;
+            }
+            // first position of species t = sum of the counts of the groups ranked before it
+            int first_t = 0;
+            for (int u = 0; u < B.n_species; ++u) {
+                const int cu = __shfl_sync(kFull, cnt_t, u), ru = __shfl_sync(kFull, rank, u);
+                if (lane < B.n_species && ru < rank) first_t += cu;
+            }
+            if (lane < B.n_species) {
+                s_tc_first[lane] = first_t;
+                s_tc_count[lane] = cnt_t;
+            }
+            const int my_first = __shfl_sync(kFull, first_t, ts >= 0 ? ts : 0);
             for (int t = 0; t < B.n_species; ++t) {
                 const unsigned mk = __ballot_sync(kFull, ts == t);
-                if (ts == t) s_tc_order[first + __popc(mk & ((1u << lane) - 1u))] = lane;
-                if (lane == 0) s_tc_first[t] = first;
-                first += __popc(mk);
+                if (ts == t) s_tc_order[my_first + __popc(mk & ((1u << lane) - 1u))] = lane;
             }
-            if (lane == 0) s_tc_first[B.n_species] = first;
         }
         __syncthreads();
         auto run_network = [&](int t) {
-            tc_species_network<HB, X3>(t, s_tc_order + s_tc_first[t], s_tc_first[t + 1] - s_tc_first[t], atom0, lane,
-                                       s_g, s_par, tc, eatom, G_out, B.D, e_acc);
+            tc_species_network<HB, X3>(t, s_tc_order + s_tc_first[t], s_tc_count[t], atom0, lane, s_g, s_par, tc,
+                                       eatom, G_out, B.D, e_acc);
         };
         if (n_chunks <= 1) {
             for (;;) {
@@ -1413,7 +1432,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                     int done = 0;
                     if (lane == 0) done = atomicAdd(&s_tc_done_a[t], 1);
                     done = __shfl_sync(kFull, done, 0);
-                    if (done == s_tc_first[t + 1] - s_tc_first[t] - 1) {  // the species' last phase A: its networks
+                    if (done == s_tc_count[t] - 1) {  // the species' last phase A: its networks
                         __threadfence_block();
                         run_network(t);
                         __threadfence_block();
@@ -1460,7 +1479,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
             }
             __syncthreads();
             for (int t = warp; t < B.n_species; t += NW)
-                if (s_tc_first[t + 1] > s_tc_first[t]) run_network(t);
+                if (s_tc_count[t] > 0) run_network(t);
             __syncthreads();
             for (;;) {
                 int a = 0;
