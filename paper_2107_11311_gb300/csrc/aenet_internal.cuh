@@ -171,7 +171,8 @@ struct Context {
     float *d_params = nullptr;     // [n_species * n_params] FP32
     float *d_shift = nullptr;      // [n_species * D]
     float *d_scale = nullptr;      // [n_species * D]
-    uint16_t *d_wbf = nullptr;     // BF16 tensor-core operand tiles (hi, lo), see ann.cu
+    uint16_t *d_wbf = nullptr;     // BF16 warp-MMA operand fragments (hi, lo) and biases, see ann_bf16.cu
+    unsigned char *d_wtc = nullptr;  // tcgen05 B operands and biases per species, see ann_tcgen05.cu
     size_t wbf_elems = 0;
     double *d_mass = nullptr;      // [n_species]
 
@@ -385,7 +386,10 @@ cudaError_t launch_ann_bf16(Context &c, int n);
 // The same networks on tcgen05 (TMEM accumulators), 128-atom species tiles:
 // the network kernel of the three-kernel path. Energy partials: one per CTA.
 int tcgen05_tiles(const Context &c, int n);
+int tcgen05_eparts(const Context &c, int n);
 cudaError_t launch_ann_tcgen05(Context &c, int n);
+// Its weights, packed into the B-operand layout (c.d_wtc) from c.d_params.
+cudaError_t pack_tcgen05_weights(Context &c);
 
 // Length of the per-atom activation record (g, then x_l and delta_l per hidden layer).
 int activation_record_len(const Net &net);

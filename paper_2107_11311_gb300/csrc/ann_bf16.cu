@@ -349,7 +349,8 @@ cudaError_t prepare_bf16_weights(Context &c) {
     const int total = (int)(words / 2 + nb);
     k_pack_bf16<<<(total + 255) / 256, 256, 0, c.stream>>>(ns, c.net.n_params, c.net.widths[0], H1, H2, pk,
                                                            c.d_params, wpk, bias);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return pack_tcgen05_weights(c);  // the three-kernel path's network kernel
 }
 
 cudaError_t launch_species_group(Context &c, int n) {

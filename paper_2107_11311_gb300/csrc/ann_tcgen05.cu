@@ -23,6 +23,8 @@
 // i.e. two core matrices along K; the next K-step starts 256 B further on.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "aenet_internal.cuh"
 #include "bf16_mma.cuh"
 
@@ -41,7 +43,11 @@ constexpr int kB1 = kA1 + 2 * kURows * 32 * 2;  // W1: 32 x 64 = 4 KB per part
 constexpr int kB2 = kB1 + 2 * 32 * 64 * 2;      // W2: 32 x 32 = 2 KB per part
 constexpr int kB3 = kB2 + 2 * 32 * 32 * 2;      // W2^T: 32 x 32
 constexpr int kB4 = kB3 + 2 * 32 * 32 * 2;      // W1^T: 64 x 32 = 4 KB per part
-constexpr int kUSmem = kB4 + 2 * 64 * 32 * 2;   // 72 KB
+constexpr int kBias = kB4 + 2 * 64 * 32 * 2;    // b1 [32], b2 [32], w3 [32], b3, padding: 512 B
+constexpr int kUSmem = kBias + 512;             // 72.5 KB
+// One species' weights as the kernel holds them (B operands hi and lo, then the
+// biases): packed once per parameter set, brought in by one bulk copy.
+constexpr int kWtcBytes = kUSmem - kB1;
 
 // Byte offset of element (row, k) in an operand of K columns.
 __device__ __forceinline__ int uoff(int row, int k, int K) {
@@ -147,50 +153,88 @@ __device__ __forceinline__ void store_row32(unsigned char *smem, int a_off, int 
 }
 
 struct AnnTcArgs {
-    int n, D, n_species, H1, H2, n_params, rec_len;
-    const float *G;        // [n, D] sorted order
-    const float *params;   // [species][n_params] FP32
+    int n, D, n_species, H1, H2, rec_len, n_tiles;
+    const float *G;              // [n, D] sorted order
+    const unsigned char *wtc;    // [species][kWtcBytes] packed weights (k_pack_tcgen05)
     const float *shift, *scale;
-    const int *list;       // atoms grouped by species
-    const int *sp_off;     // [species] first list entry of each species
+    const int *list;             // atoms grouped by species
+    const int *sp_off;           // [species] first list entry of each species
     float *dEdG, *eatom;
-    float *act;            // optional activation records [n, rec_len]: g, x1, d1, x2, d2
-    double *e_part;        // [grid]
+    float *act;                  // optional activation records [n, rec_len]: g, x1, d1, x2, d2
+    double *e_part;              // [grid]
     unsigned *err;
 };
 
+// The weights of every species into the B-operand layout of k_ann_tcgen05 (hi
+// and lo BF16 parts) and its bias block: one thread per pair of K-adjacent
+// elements of one operand row, or per bias entry.
+__global__ void k_pack_tcgen05(int ns, int n_params, int D, int H1, int H2, const float *__restrict__ P,
+                               unsigned char *__restrict__ out) {
+    constexpr int n1 = 32 * 32, n2 = 32 * 16, n4 = 64 * 16, nb = 128;
+    const int per = n1 + 2 * n2 + n4 + nb;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * per) return;
+    const int t = idx / per;
+    int w = idx - t * per;
+    const float *p = P + (size_t)t * n_params;
+    const float *W1 = p, *b1 = W1 + H1 * D, *W2 = b1 + H1, *b2 = W2 + H2 * H1, *w3 = b2 + H2, *b3 = w3 + H2;
+    unsigned char *o = out + (size_t)t * kWtcBytes - kB1;  // so that o + kBx addresses operand x
+    float v0 = 0.f, v1 = 0.f;
+    int off, part;
+    if (w < n1) {  // W1 [n][k]: n < 32, k < 64
+        const int nn = w >> 5, k = (w & 31) * 2;
+        v0 = (nn < H1 && k < D) ? W1[nn * D + k] : 0.f;
+        v1 = (nn < H1 && k + 1 < D) ? W1[nn * D + k + 1] : 0.f;
+        off = kB1 + uoff(nn, k, 64);
+        part = 32 * 64 * 2;
+    } else if ((w -= n1) < n2) {  // W2 [n][k]: n < 32, k < 32
+        const int nn = w >> 4, k = (w & 15) * 2;
+        v0 = (nn < H2 && k < H1) ? W2[nn * H1 + k] : 0.f;
+        v1 = (nn < H2 && k + 1 < H1) ? W2[nn * H1 + k + 1] : 0.f;
+        off = kB2 + uoff(nn, k, 32);
+        part = 32 * 32 * 2;
+    } else if ((w -= n2) < n2) {  // W2^T [n][k] = W2[k][n]
+        const int nn = w >> 4, k = (w & 15) * 2;
+        v0 = (nn < H1 && k < H2) ? W2[k * H1 + nn] : 0.f;
+        v1 = (nn < H1 && k + 1 < H2) ? W2[(k + 1) * H1 + nn] : 0.f;
+        off = kB3 + uoff(nn, k, 32);
+        part = 32 * 32 * 2;
+    } else if ((w -= n2) < n4) {  // W1^T [c][j] = W1[j][c]: c < 64, j < 32
+        const int c = w >> 4, j = (w & 15) * 2;
+        v0 = (c < D && j < H1) ? W1[j * D + c] : 0.f;
+        v1 = (c < D && j + 1 < H1) ? W1[(j + 1) * D + c] : 0.f;
+        off = kB4 + uoff(c, j, 32);
+        part = 64 * 32 * 2;
+    } else {  // bias block
+        w -= n4;
+        float x = 0.f;
+        if (w < 32) x = w < H1 ? b1[w] : 0.f;
+        else if (w < 64) x = w - 32 < H2 ? b2[w - 32] : 0.f;
+        else if (w < 96) x = w - 64 < H2 ? w3[w - 64] : 0.f;
+        else if (w == 96) x = b3[0];
+        reinterpret_cast<float *>(o + kBias)[w] = x;
+        return;
+    }
+    uint32_t hi, lo;
+    split_bf2(v0, v1, hi, lo);
+    *reinterpret_cast<uint32_t *>(o + off) = hi;
+    *reinterpret_cast<uint32_t *>(o + off + part) = lo;
+}
+
+// Persistent CTAs take tiles (tile k of the species groups in order) with a
+// stride of the grid; a species' weights stay in shared memory until the CTA
+// reaches a tile of another species.
 template <bool X3>
 __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t s_mbar;
+    __shared__ uint64_t s_mbar[2];  // MMA completion, weight copy
     __shared__ uint32_t s_tmem;
-    __shared__ float s_bias[3 * kUHid + 1];  // b1, b2, w3, b3
     __shared__ double s_e[kUThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float *s_bias = reinterpret_cast<const float *>(smem + kBias);  // b1, b2, w3, b3
 
-    // ---- this CTA's tile: species t, rows r0 .. r0 + rows - 1 of its group
-    int t = 0, r0 = 0, cnt_t = 0;
-    {
-        int k = blockIdx.x;
-        for (t = 0; t < a.n_species; ++t) {
-            cnt_t = (t + 1 < a.n_species ? a.sp_off[t + 1] : a.n) - a.sp_off[t];
-            const int tiles = (cnt_t + kURows - 1) / kURows;
-            if (k < tiles) break;
-            k -= tiles;
-        }
-        if (t >= a.n_species) {  // beyond the last tile
-            if (tid == 0) a.e_part[blockIdx.x] = 0.0;
-            return;
-        }
-        r0 = k * kURows;
-    }
-    const int rows = min(kURows, cnt_t - r0);
-    const int D = a.D, H1 = a.H1, H2 = a.H2;
-    const float *P = a.params + (size_t)t * a.n_params;
-    const float *W1 = P, *b1 = W1 + H1 * D, *W2 = b1 + H1, *b2 = W2 + H2 * H1, *w3 = b2 + H2, *b3 = w3 + H2;
-
-    // ---- TMEM (warp 0 allocates) and the MMA-completion barrier
-    const uint32_t mbar = smem_u32(&s_mbar);
+    // ---- TMEM (warp 0 allocates) and the barriers
+    const uint32_t mbar = smem_u32(&s_mbar[0]), mbar_w = smem_u32(&s_mbar[1]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kUCols)
@@ -199,81 +243,21 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_w) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-
-    // ---- operands: weights of species t (B, N x K rows, hi and lo) and biases
-    for (int idx = tid; idx < 32 * 32; idx += kUThreads) {  // W1: n < 32, k pairs < 64
-        const int nn = idx >> 5, k = (idx & 31) * 2;
-        const float v0 = (nn < H1 && k < D) ? W1[nn * D + k] : 0.f, v1 = (nn < H1 && k + 1 < D) ? W1[nn * D + k + 1] : 0.f;
-        uint32_t hi, lo;
-        split_bf2(v0, v1, hi, lo);
-        *reinterpret_cast<uint32_t *>(smem + kB1 + uoff(nn, k, 64)) = hi;
-        *reinterpret_cast<uint32_t *>(smem + kB1 + 32 * 64 * 2 + uoff(nn, k, 64)) = lo;
-    }
-    for (int idx = tid; idx < 32 * 16; idx += kUThreads) {  // W2 [n][k] and W2^T [n][k] = W2[k][n]
-        const int nn = idx >> 4, k = (idx & 15) * 2;
-        const float f0 = (nn < H2 && k < H1) ? W2[nn * H1 + k] : 0.f, f1 = (nn < H2 && k + 1 < H1) ? W2[nn * H1 + k + 1] : 0.f;
-        const float g0 = (nn < H1 && k < H2) ? W2[k * H1 + nn] : 0.f, g1 = (nn < H1 && k + 1 < H2) ? W2[(k + 1) * H1 + nn] : 0.f;
-        uint32_t hi, lo;
-        split_bf2(f0, f1, hi, lo);
-        *reinterpret_cast<uint32_t *>(smem + kB2 + uoff(nn, k, 32)) = hi;
-        *reinterpret_cast<uint32_t *>(smem + kB2 + 32 * 32 * 2 + uoff(nn, k, 32)) = lo;
-        split_bf2(g0, g1, hi, lo);
-        *reinterpret_cast<uint32_t *>(smem + kB3 + uoff(nn, k, 32)) = hi;
-        *reinterpret_cast<uint32_t *>(smem + kB3 + 32 * 32 * 2 + uoff(nn, k, 32)) = lo;
-    }
-    for (int idx = tid; idx < 64 * 16; idx += kUThreads) {  // W1^T [c][j] = W1[j][c]: c < 64, j pairs < 32
-        const int c = idx >> 4, j = (idx & 15) * 2;
-        const float v0 = (c < D && j < H1) ? W1[j * D + c] : 0.f, v1 = (c < D && j + 1 < H1) ? W1[(j + 1) * D + c] : 0.f;
-        uint32_t hi, lo;
-        split_bf2(v0, v1, hi, lo);
-        *reinterpret_cast<uint32_t *>(smem + kB4 + uoff(c, j, 32)) = hi;
-        *reinterpret_cast<uint32_t *>(smem + kB4 + 64 * 32 * 2 + uoff(c, j, 32)) = lo;
-    }
-    if (tid < kUHid) {
-        s_bias[tid] = tid < H1 ? b1[tid] : 0.f;
-        s_bias[kUHid + tid] = tid < H2 ? b2[tid] : 0.f;
-        s_bias[2 * kUHid + tid] = tid < H2 ? w3[tid] : 0.f;
-    }
-    if (tid == 0) s_bias[3 * kUHid] = b3[0];
-
-    // ---- row tid: the standardised descriptor g of its atom (A0, K = 64)
-    const bool valid = tid < rows;
-    const int s = valid ? a.list[a.sp_off[t] + r0 + tid] : -1;
-    float *rec = (a.act && valid) ? a.act + (size_t)s * a.rec_len : nullptr;
-    const float *sh = a.shift + t * D, *sc = a.scale + t * D;
-    float x1[kUHid];  // this row's hidden activations, kept for the backward pass
-    {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            float g[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int k = 8 * c + e;
-                g[e] = (valid && k < D) ? (a.G[(size_t)s * D + k] - sh[k]) * sc[k] : 0.f;
-                if (rec && k < D) rec[k] = g[e];
-            }
-            uint4 hi, lo;
-            uint32_t *h = &hi.x, *l = &lo.x;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                if (X3) split_bf2(g[2 * p], g[2 * p + 1], h[p], l[p]);
-                else h[p] = pack_bf2(g[2 * p], g[2 * p + 1]);
-            }
-            *reinterpret_cast<uint4 *>(smem + kA0 + uoff(tid, 8 * c, 64)) = hi;
-            if (X3) *reinterpret_cast<uint4 *>(smem + kA0 + kURows * 64 * 2 + uoff(tid, 8 * c, 64)) = lo;
-        }
-    }
-    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
     const uint32_t base = smem_u32(smem);
+    const int D = a.D, H1 = a.H1, H2 = a.H2;
     bool ok = true;
-    uint32_t phase = 0;
+    uint32_t phase = 0, phase_w = 0;
+    int cur_t = -1;
+    double e_cta = 0.0;
+
     auto run = [&](uint32_t d_col, int a_off, int a_K, int b_off, int b_rows, int K, int N) {
         if (tid == 0) {
             tc_fence_after();
@@ -286,76 +270,162 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
         tc_fence_after();
     };
 
-    // ---- layer 1: Z1 = g W1^T (TMEM columns 0..31)
-    run(0, kA0, 64, kB1, 32, 64, 32);
-    float v[32];
-    tmem_ld32(lane_addr + 0, v);
-#pragma unroll
-    for (int j = 0; j < kUHid; ++j) x1[j] = j < H1 ? tanhf(v[j] + s_bias[j]) : 0.f;
-    store_row32<X3>(smem, kA1, tid, x1);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-
-    // ---- layer 2: Z2 = X1 W2^T (columns 32..63); output layer and delta2 in FP32
-    run(32, kA1, 32, kB2, 32, 32, 32);
-    tmem_ld32(lane_addr + 32, v);
-    float e = s_bias[3 * kUHid];
-#pragma unroll
-    for (int j = 0; j < kUHid; ++j) {
-        const float x2 = j < H2 ? tanhf(v[j] + s_bias[kUHid + j]) : 0.f;
-        const float w = s_bias[2 * kUHid + j];
-        e = fmaf(w, x2, e);
-        v[j] = (1.0f - x2 * x2) * w;  // delta2
-        if (rec && j < H2) {
-            rec[D + 2 * H1 + j] = x2;
-            rec[D + 2 * H1 + H2 + j] = v[j];
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        // ---- species t and rows r0 .. r0 + rows - 1 of its group
+        int t = 0, r0 = 0, cnt_t = 0;
+        {
+            int k = tile;
+            for (t = 0; t < a.n_species; ++t) {
+                cnt_t = (t + 1 < a.n_species ? a.sp_off[t + 1] : a.n) - a.sp_off[t];
+                const int tiles = (cnt_t + kURows - 1) / kURows;
+                if (k < tiles) break;
+                k -= tiles;
+            }
+            if (t >= a.n_species) break;
+            r0 = k * kURows;
         }
-    }
-    tc_fence_before();
-    __syncthreads();  // every lane has read Z2 and the layer-2 MMAs are complete: A1 is free
-    store_row32<X3>(smem, kA1, tid, v);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-
-    // ---- backward: dX1 = delta2 W2 (columns 64..95), delta1 = (1 - x1^2) dX1
-    run(64, kA1, 32, kB3, 32, 32, 32);
-    tmem_ld32(lane_addr + 64, v);
-#pragma unroll
-    for (int j = 0; j < kUHid; ++j) {
-        v[j] *= (1.0f - x1[j] * x1[j]);
-        if (rec && j < H1) {
-            rec[D + j] = x1[j];
-            rec[D + H1 + j] = v[j];
+        const int rows = min(kURows, cnt_t - r0);
+        // ---- this species' weights (one bulk copy) when the CTA changes species;
+        // the previous tile's MMAs and bias reads are over (barrier below)
+        const bool new_w = t != cur_t;
+        if (new_w) {
+            if (tid == 0) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_w), "r"(kWtcBytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        base + kB1),
+                    "l"(a.wtc + (size_t)t * kWtcBytes), "r"(kWtcBytes), "r"(mbar_w)
+                    : "memory");
+            }
+            cur_t = t;
         }
-    }
-    tc_fence_before();
-    __syncthreads();
-    store_row32<X3>(smem, kA1, tid, v);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
+        // ---- row tid: the standardised descriptor g of its atom (A0, K = 64)
+        const bool valid = tid < rows;
+        const int s = valid ? a.list[a.sp_off[t] + r0 + tid] : -1;
+        float *rec = (a.act && valid) ? a.act + (size_t)s * a.rec_len : nullptr;
+        const float *sh = a.shift + t * D, *sc = a.scale + t * D;
+        const float *grow = valid ? a.G + (size_t)s * D : nullptr;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float g[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) g[e] = 0.f;
+            if (valid) {
+                if ((D & 3) == 0) {  // rows start on 16-byte boundaries
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int k = 8 * c + 4 * q;
+                        if (k < D) {
+                            const float4 v = *reinterpret_cast<const float4 *>(grow + k);
+                            g[4 * q] = v.x;
+                            g[4 * q + 1] = v.y;
+                            g[4 * q + 2] = v.z;
+                            g[4 * q + 3] = v.w;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if (8 * c + e < D) g[e] = grow[8 * c + e];
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int k = 8 * c + e;
+                    g[e] = k < D ? (g[e] - sh[k]) * sc[k] : 0.f;
+                    if (rec && k < D) rec[k] = g[e];
+                }
+            }
+            uint4 hi, lo;
+            uint32_t *h = &hi.x, *l = &lo.x;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (X3) split_bf2(g[2 * p], g[2 * p + 1], h[p], l[p]);
+                else h[p] = pack_bf2(g[2 * p], g[2 * p + 1]);
+            }
+            *reinterpret_cast<uint4 *>(smem + kA0 + uoff(tid, 8 * c, 64)) = hi;
+            if (X3) *reinterpret_cast<uint4 *>(smem + kA0 + kURows * 64 * 2 + uoff(tid, 8 * c, 64)) = lo;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (new_w) {  // the species' weights have landed
+            ok = mbar_wait(mbar_w, phase_w) && ok;
+            phase_w ^= 1u;
+        }
+        float x1[kUHid];
+        float v[32];
+        // ---- layer 1: Z1 = g W1^T (TMEM columns 0..31)
+        run(0, kA0, 64, kB1, 32, 64, 32);
+        tmem_ld32(lane_addr + 0, v);
+#pragma unroll
+        for (int j = 0; j < kUHid; ++j) x1[j] = j < H1 ? tanhf(v[j] + s_bias[j]) : 0.f;
+        store_row32<X3>(smem, kA1, tid, x1);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
 
-    // ---- dE/dg = delta1 W1 (columns 0..63), dE/dG = dE/dg * scale
-    run(0, kA1, 32, kB4, 64, 32, 64);
+        // ---- layer 2: Z2 = X1 W2^T (columns 32..63); output layer and delta2 in FP32
+        run(32, kA1, 32, kB2, 32, 32, 32);
+        tmem_ld32(lane_addr + 32, v);
+        float e = s_bias[3 * kUHid];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        tmem_ld32(lane_addr + 32 * half, v);
-        if (valid) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int k = 32 * half + j;
-                if (k < D) a.dEdG[(size_t)s * D + k] = v[j] * sc[k];
+        for (int j = 0; j < kUHid; ++j) {
+            const float x2 = j < H2 ? tanhf(v[j] + s_bias[kUHid + j]) : 0.f;
+            const float w = s_bias[2 * kUHid + j];
+            e = fmaf(w, x2, e);
+            v[j] = (1.0f - x2 * x2) * w;  // delta2
+            if (rec && j < H2) {
+                rec[D + 2 * H1 + j] = x2;
+                rec[D + 2 * H1 + H2 + j] = v[j];
             }
         }
-    }
-    if (valid) a.eatom[s] = e;
-    // energy partial of the tile (FP64, fixed order)
-    double es = valid ? (double)e : 0.0;
+        store_row32<X3>(smem, kA1, tid, v);  // the layer-2 MMAs are complete: A1 is free
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+
+        // ---- backward: dX1 = delta2 W2 (columns 64..95), delta1 = (1 - x1^2) dX1
+        run(64, kA1, 32, kB3, 32, 32, 32);
+        tmem_ld32(lane_addr + 64, v);
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) es += __shfl_xor_sync(0xffffffffu, es, o);
-    if (lane == 0) s_e[warp] = es;
+        for (int j = 0; j < kUHid; ++j) {
+            v[j] *= (1.0f - x1[j] * x1[j]);
+            if (rec && j < H1) {
+                rec[D + j] = x1[j];
+                rec[D + H1 + j] = v[j];
+            }
+        }
+        store_row32<X3>(smem, kA1, tid, v);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+
+        // ---- dE/dg = delta1 W1 (columns 0..63), dE/dG = dE/dg * scale
+        run(0, kA1, 32, kB4, 64, 32, 64);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            tmem_ld32(lane_addr + 32 * half, v);
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int k = 32 * half + j;
+                    if (k < D) a.dEdG[(size_t)s * D + k] = v[j] * sc[k];
+                }
+            }
+        }
+        if (valid) {
+            a.eatom[s] = e;
+            e_cta += (double)e;
+        }
+        tc_fence_before();
+        __syncthreads();  // TMEM reads and A-operand reads of this tile are over
+    }
+    // energy partial of the CTA (FP64, fixed order)
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) e_cta += __shfl_xor_sync(0xffffffffu, e_cta, o);
+    if (lane == 0) s_e[warp] = e_cta;
     if (!ok && tid == 0) atomicOr(a.err, kErrTimeout);
     tc_fence_before();
     __syncthreads();
@@ -370,6 +440,23 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
 
 int tcgen05_tiles(const Context &c, int n) { return (n + kURows - 1) / kURows + c.basis.n_species; }
 
+// Persistent CTAs of the network kernel: three fit an SM (72.5 KB of shared
+// memory and 128 TMEM columns each).
+static int tcgen05_ctas(const Context &c, int n) { return std::min(tcgen05_tiles(c, n), 3 * std::max(1, c.n_sm)); }
+
+int tcgen05_eparts(const Context &c, int n) { return tcgen05_ctas(c, n); }
+
+cudaError_t pack_tcgen05_weights(Context &c) {
+    const int ns = c.net.n_species;
+    cudaError_t e;
+    if (!c.d_wtc && (e = cudaMalloc(&c.d_wtc, (size_t)ns * kWtcBytes)) != cudaSuccess) return e;
+    const int per = 32 * 32 + 2 * 32 * 16 + 64 * 16 + 128;
+    k_pack_tcgen05<<<(ns * per + 255) / 256, 256, 0, c.stream>>>(ns, c.net.n_params, c.net.widths[0],
+                                                                   c.net.widths[1], c.net.widths[2], c.d_params,
+                                                                   c.d_wtc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ann_tcgen05(Context &c, int n) {
     if (n <= 0) return cudaSuccess;
     cudaError_t e;
@@ -380,10 +467,10 @@ cudaError_t launch_ann_tcgen05(Context &c, int n) {
     a.n_species = c.basis.n_species;
     a.H1 = c.net.widths[1];
     a.H2 = c.net.widths[2];
-    a.n_params = c.net.n_params;
     a.rec_len = activation_record_len(c.net);
+    a.n_tiles = tcgen05_tiles(c, n);
     a.G = c.d_G;
-    a.params = c.d_params;
+    a.wtc = c.d_wtc;
     a.shift = c.d_shift;
     a.scale = c.d_scale;
     a.list = c.d_sp_list;
@@ -396,7 +483,7 @@ cudaError_t launch_ann_tcgen05(Context &c, int n) {
     const bool x3 = c.precision == AENET_BF16X3;
     auto kern = x3 ? k_ann_tcgen05<true> : k_ann_tcgen05<false>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kUSmem)) != cudaSuccess) return e;
-    kern<<<tcgen05_tiles(c, n), kUThreads, kUSmem, c.stream>>>(a);
+    kern<<<tcgen05_ctas(c, n), kUThreads, kUSmem, c.stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -233,7 +233,7 @@ int enqueue_potential(Context &c, const Grid &g, int n, int *n_eparts) {
             *n_eparts = ann_blocks(n);
         } else {
             CK(launch_ann_tcgen05(c, n), "BF16 network kernel");
-            *n_eparts = tcgen05_tiles(c, n);
+            *n_eparts = tcgen05_eparts(c, n);
         }
         CK(mark(c, 4), "event");
         CK(launch_fp_backward(c, g, n), "force kernel");
@@ -1424,7 +1424,7 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
     if (c.batch_exec) cudaGraphExecDestroy(c.batch_exec);
     c.batch_exec = nullptr;
     if (c.stream) cudaStreamSynchronize(c.stream);
-    void *ptrs[] = {c.d_params, c.d_shift, c.d_scale, c.d_wbf, c.d_mass, c.d_pos4, c.d_tmp4, c.d_perm,
+    void *ptrs[] = {c.d_params, c.d_shift, c.d_scale, c.d_wbf, c.d_wtc, c.d_mass, c.d_pos4, c.d_tmp4, c.d_perm,
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,

@@ -86,12 +86,15 @@ struct TcNet {
 // zero-padded to the compile-time width bound hb (16 or 32) so the network
 // loops run a fixed trip count with no masks; padded neurons see zero weights
 // and biases, so they stay at tanh(0) = 0 and contribute nothing:
-//   W1P [32 slot pairs][hb + 1] float2   layer-1 weights of slots (2p, 2p+1)
+//   W1  [hb][kW1Stride]    layer-1 weights, row o = neuron o over the 64 slots
 //   b1  [hb]
-//   for hidden l = 2..L-1: W_l [hb][hb + 1], b_l [hb]
+//   for hidden l = 2..L-1: W_l [hb][hb + 4] (row o = neuron o), b_l [hb]
 //   wL  [hb], bL [1]
 //   shift [64 slots], scale [64 slots] (scale 0 on unused slots)
-// The odd row strides keep the lane-strided reads free of bank conflicts.
+// Row strides of 4 mod 32 floats (68 = 17 x 16 B, 36 = 9 x 16 B, 20 = 5 x 16 B)
+// keep the 128-bit loads of eight lanes reading eight rows free of bank
+// conflicts, and a row read by all lanes at consecutive columns is too.
+constexpr int kW1Stride = kSlots + 4;
 struct FusedNet {
     int L;                          // weight layers
     int hb;                         // hidden-width bound of the layout (16 or 32)
@@ -122,12 +125,12 @@ inline FusedNet make_fused_net(const Net &net) {
     for (int l = 0; l <= net.n_layers; ++l) f.H[l] = net.widths[l];
     int p = 0;
     f.offW[1] = p;
-    p += kSlots * (hb + 1);
+    p += hb * kW1Stride;
     f.offB[1] = p;
     p += hb;
     for (int l = 2; l < f.L; ++l) {
         f.offW[l] = p;
-        p += hb * (hb + 1);
+        p += hb * (hb + 4);
         f.offB[l] = p;
         p += hb;
     }
@@ -750,23 +753,35 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         if (c1 >= 0) rec[c1] = x01;
     }
     // Lanes own neurons: o = lane for hb = 32; for hb = 16 both half-warps hold
-    // neurons 0..15 (o = lane & 15) and split every sum over k into even and odd
-    // terms (half h takes k = 2j + h), joined by one shuffle.
+    // neurons 0..15 (o = lane & 15) and split every sum over its inputs in two
+    // halves (half h takes the h-th half), joined by one shuffle. Inputs reach
+    // every lane through the warp's scratch row (W.coef, 64 floats, later the
+    // dE/dG coefficients) as broadcast 128-bit loads.
     const int o = lane & (HB - 1), h = HB == 16 ? lane >> 4 : 0;
-    const float2 *W1P = reinterpret_cast<const float2 *>(Pt + net.offW[1]) + lane * (HB + 1);
-    float part[HB];
-#pragma unroll
-    for (int q = 0; q < HB; ++q) {
-        const float2 w = W1P[q];
-        part[q] = fmaf(w.x, x00, w.y * x01);
-    }
+    constexpr int HS = HB + 4;                                 // hidden-layer row stride
+    constexpr int NS = ((2 * (KRT + KAT) + 7) / 8) * 8;       // slots the layer-1 sums run over
+    constexpr int NK1 = HB == 16 ? NS / 2 : NS;               // ... per lane group
+    constexpr int NKH = HB == 16 ? 8 : 32;                    // hidden inputs per lane group
+    float *xs = W.coef;
+    *reinterpret_cast<float2 *>(xs + 2 * lane) = make_float2(x00, x01);
+    __syncwarp();
+    const float *W1 = Pt + net.offW[1];
     float z;
-    if constexpr (HB == 16) {
-        z = transpose_reduce16(part, lane);  // lanes 2q, 2q+1: halves of neuron q
-        z += __shfl_xor_sync(kFull, z, 1);
-        z = __shfl_sync(kFull, z, 2 * o);
-    } else {
-        z = transpose_reduce32(part, lane);
+    {
+        const float *wr = W1 + o * kW1Stride + h * NK1, *gx = xs + h * NK1;
+        float za = 0.f, zb = 0.f;
+        // partial unrolling: all loads hoisted ahead of the FMAs would need ~100 registers
+#pragma unroll 2
+        for (int k = 0; k < NK1; k += 4) {
+            const float4 gv = *reinterpret_cast<const float4 *>(gx + k);
+            const float4 wv = *reinterpret_cast<const float4 *>(wr + k);
+            za = fmaf(wv.x, gv.x, za);
+            zb = fmaf(wv.y, gv.y, zb);
+            za = fmaf(wv.z, gv.z, za);
+            zb = fmaf(wv.w, gv.w, zb);
+        }
+        z = za + zb;
+        if constexpr (HB == 16) z += __shfl_xor_sync(kFull, z, 16);
     }
     float xl[kMaxLayers];  // this lane's neuron of every hidden layer
     xl[1] = tanhf(z + Pt[net.offB[1] + o]);
@@ -774,15 +789,21 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
 #pragma unroll
     for (int l = 2; l < kMaxLayers; ++l) {
         if (l < net.L) {
-            const float *Wl = Pt + net.offW[l] + o * (HB + 1);
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll(HB == 16 ? 4 : 2)
-            for (int j = 0; j < (HB == 16 ? 8 : 32); j += 2) {
-                const int k0 = HB == 16 ? 2 * j + h : j, k1 = HB == 16 ? 2 * j + 2 + h : j + 1;
-                a0 = fmaf(Wl[k0], __shfl_sync(kFull, xl[l - 1], k0), a0);
-                a1 = fmaf(Wl[k1], __shfl_sync(kFull, xl[l - 1], k1), a1);
+            __syncwarp();  // the previous reads of the scratch row are done
+            if (lane < HB) xs[lane] = xl[l - 1];
+            __syncwarp();
+            const float *wr = Pt + net.offW[l] + o * HS + h * NKH, *xv = xs + h * NKH;
+            float za = 0.f, zb = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < NKH; k += 4) {
+                const float4 gv = *reinterpret_cast<const float4 *>(xv + k);
+                const float4 wv = *reinterpret_cast<const float4 *>(wr + k);
+                za = fmaf(wv.x, gv.x, za);
+                zb = fmaf(wv.y, gv.y, zb);
+                za = fmaf(wv.z, gv.z, za);
+                zb = fmaf(wv.w, gv.w, zb);
             }
-            float zz = a0 + a1;
+            float zz = za + zb;
             if constexpr (HB == 16) zz += __shfl_xor_sync(kFull, zz, 16);
             xl[l] = tanhf(zz + Pt[net.offB[l] + o]);
             if (rec && lane < net.H[l]) rec[net.rec_x[l] + lane] = xl[l];
@@ -797,38 +818,56 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
 #pragma unroll
     for (int m = HB / 2; m >= 1; m >>= 1) E += __shfl_xor_sync(kFull, E, m);
     E += Pt[net.offBL];
-    // back-propagation: delta of the last hidden layer, then down to layer 1
+    // back-propagation: delta of the last hidden layer, then down to layer 1;
+    // lane k collects dx_k = sum_q W_l[q][k] delta_q over the broadcast deltas
     float delta = (1.0f - xlast * xlast) * wL;
     if (rec && lane < net.Hlast) rec[net.rec_dlast + lane] = delta;
 #pragma unroll
     for (int l = kMaxLayers - 1; l >= 2; --l) {
         if (l < net.L) {
-            const float *Wl = Pt + net.offW[l] + o;  // column o: weights from input neuron o
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll(HB == 16 ? 4 : 2)
-            for (int j = 0; j < (HB == 16 ? 8 : 32); j += 2) {
-                const int q0 = HB == 16 ? 2 * j + h : j, q1 = HB == 16 ? 2 * j + 2 + h : j + 1;
-                a0 = fmaf(Wl[q0 * (HB + 1)], __shfl_sync(kFull, delta, q0), a0);
-                a1 = fmaf(Wl[q1 * (HB + 1)], __shfl_sync(kFull, delta, q1), a1);
+            __syncwarp();
+            if (lane < HB) xs[lane] = delta;
+            __syncwarp();
+            const float *wc = Pt + net.offW[l] + h * NKH * HS + o, *dv = xs + h * NKH;
+            float da = 0.f, db = 0.f;
+#pragma unroll 2
+            for (int q = 0; q < NKH; q += 4) {
+                const float4 d4 = *reinterpret_cast<const float4 *>(dv + q);
+                da = fmaf(wc[(q + 0) * HS], d4.x, da);
+                db = fmaf(wc[(q + 1) * HS], d4.y, db);
+                da = fmaf(wc[(q + 2) * HS], d4.z, da);
+                db = fmaf(wc[(q + 3) * HS], d4.w, db);
             }
-            float dx = a0 + a1;
+            float dx = da + db;
             if constexpr (HB == 16) dx += __shfl_xor_sync(kFull, dx, 16);
             delta = (1.0f - xl[l - 1] * xl[l - 1]) * dx;
             if (rec && lane < net.H[l - 1]) rec[net.rec_d[l - 1] + lane] = delta;
         }
     }
+    // dE/dg of this lane's slots: sum_q W1[q][slot] delta1_q
+    __syncwarp();
+    if (lane < HB) xs[lane] = delta;
+    __syncwarp();
     float d0 = 0.f, d1 = 0.f, e0 = 0.f, e1 = 0.f;
-#pragma unroll(HB == 16 ? 8 : 2)
-    for (int q = 0; q < HB; q += 2) {
-        const float dq = __shfl_sync(kFull, delta, q), dr = __shfl_sync(kFull, delta, q + 1);
-        const float2 wq = W1P[q], wr = W1P[q + 1];
-        d0 = fmaf(wq.x, dq, d0);
-        d1 = fmaf(wq.y, dq, d1);
-        e0 = fmaf(wr.x, dr, e0);
-        e1 = fmaf(wr.y, dr, e1);
+#pragma unroll 2
+    for (int q = 0; q < HB; q += 4) {
+        const float4 d4 = *reinterpret_cast<const float4 *>(xs + q);
+        const float2 w0 = *reinterpret_cast<const float2 *>(W1 + (q + 0) * kW1Stride + 2 * lane);
+        const float2 w1 = *reinterpret_cast<const float2 *>(W1 + (q + 1) * kW1Stride + 2 * lane);
+        const float2 w2 = *reinterpret_cast<const float2 *>(W1 + (q + 2) * kW1Stride + 2 * lane);
+        const float2 w3 = *reinterpret_cast<const float2 *>(W1 + (q + 3) * kW1Stride + 2 * lane);
+        d0 = fmaf(w0.x, d4.x, d0);
+        d1 = fmaf(w0.y, d4.x, d1);
+        e0 = fmaf(w1.x, d4.y, e0);
+        e1 = fmaf(w1.y, d4.y, e1);
+        d0 = fmaf(w2.x, d4.z, d0);
+        d1 = fmaf(w2.y, d4.z, d1);
+        e0 = fmaf(w3.x, d4.w, e0);
+        e1 = fmaf(w3.y, d4.w, e1);
     }
     d0 += e0;
     d1 += e1;
+    __syncwarp();  // every lane has read the deltas: the row takes the coefficients
     W.coef[s0] = d0 * sc[s0];  // dE/dG = dE/dg * scale
     W.coef[s1] = d1 * sc[s1];
     if (lane == 0) {
@@ -859,9 +898,9 @@ __device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &
         const float *src = params + (size_t)t * net.n_params;
         float *dst = s_par + t * net.stride;
         const int H1 = net.H[1], hb = net.hb;
-        for (int idx = tid; idx < kSlots * (hb + 1); idx += nthreads) {  // W1P: (pair, o, slot parity)
-            const int pair = idx / (2 * (hb + 1)), rem = idx % (2 * (hb + 1)), o = rem >> 1;
-            const int col = slot_col<KRT, KAT>(2 * pair + (rem & 1), Kr, Ka);
+        for (int idx = tid; idx < hb * kW1Stride; idx += nthreads) {  // W1: (neuron, slot)
+            const int o = idx / kW1Stride, slot = idx - o * kW1Stride;
+            const int col = slot < kSlots ? slot_col<KRT, KAT>(slot, Kr, Ka) : -1;
             dst[net.offW[1] + idx] = (o < H1 && col >= 0) ? src[net.srcOff[1] + o * D + col] : 0.f;
         }
         for (int o = tid; o < hb; o += nthreads) dst[net.offB[1] + o] = o < H1 ? src[net.srcOff[1] + H1 * D + o] : 0.f;
@@ -869,8 +908,8 @@ __device__ __forceinline__ void load_net_params(const Basis &B, const FusedNet &
         for (int l = 2; l < kMaxLayers; ++l) {
             if (l >= net.L) break;
             const int Hi = net.H[l - 1], Ho = net.H[l];
-            for (int idx = tid; idx < hb * (hb + 1); idx += nthreads) {
-                const int o = idx / (hb + 1), k = idx % (hb + 1);
+            for (int idx = tid; idx < hb * (hb + 4); idx += nthreads) {
+                const int o = idx / (hb + 4), k = idx % (hb + 4);
                 dst[net.offW[l] + idx] = (o < Ho && k < Hi) ? src[net.srcOff[l] + o * Hi + k] : 0.f;
             }
             for (int o = tid; o < hb; o += nthreads)
