@@ -69,8 +69,9 @@ def network_flops(widths, n_atoms):
 # DRAM bytes per launch of the dominant kernel, from the ncu captures summarised in
 # profiles/k_potential_<workload>.md; reported only while the kernel source is the
 # one the counters were taken on (first 16 hex digits of its SHA-256).
-TRAFFIC_SOURCE_SHA256_16 = "a502f65dbc8664b2"
-TRAFFIC_CAPTURE = {("water_12288", "fp32"): 521984, ("amorphous_27000", "fp32"): 1075200}
+TRAFFIC_SOURCE_SHA256_16 = "b91ebef2066cdd63"
+TRAFFIC_CAPTURE = {("water_331776", "fp32"): 10806272, ("water_331776", "bf16x3"): 10923264,
+                   ("water_12288", "fp32"): 515584}
 
 
 def captured_traffic(workload_name, precision, skin=0.0):

@@ -216,8 +216,6 @@ struct Context {
     int *d_sp_off = nullptr;       // [kMaxSpecies]
     int *d_sp_rank = nullptr;      // [n]
     int *d_sp_list = nullptr;      // [n] sorted indices grouped by species
-    int4 *d_tiles = nullptr;       // [max tiles] (list offset, rows, species, 0)
-    int *d_n_tiles = nullptr;
 
     // staging of host arrays
     int cap_stage = 0;
@@ -378,13 +376,10 @@ cudaError_t launch_fp_backward(Context &c, const Grid &g, int n);
 // cells' virial partials, and outputs in input order.
 cudaError_t launch_finalize(Context &c, const Grid &g, int n, int n_eparts, double *forces, double *e_atom);
 
-// BF16 tensor-core network kernel (precision forms; two hidden layers <= 32).
+// BF16 tensor-core networks (precision forms; two hidden layers <= 32).
 bool bf16_supported(const Net &net);
-int bf16_max_tiles(const Context &c, int n);
-int bf16_eparts(const Context &c, int n);
-cudaError_t launch_ann_bf16(Context &c, int n);
-// The same networks on tcgen05 (TMEM accumulators), 128-atom species tiles:
-// the network kernel of the three-kernel path. Energy partials: one per CTA.
+// The three-kernel path's network kernel: tcgen05 (TMEM accumulators) over
+// 128-atom species tiles. Energy partials: one per CTA.
 int tcgen05_tiles(const Context &c, int n);
 int tcgen05_eparts(const Context &c, int n);
 cudaError_t launch_ann_tcgen05(Context &c, int n);

@@ -5,7 +5,7 @@
 // per CTA, operands in shared memory, accumulators in tensor memory (TMEM),
 // read back with tcgen05.ld for the epilogues.
 //
-// One CTA of 128 threads per tile of up to 128 atoms of one species; thread r
+// Persistent CTAs of 128 threads take tiles of up to 128 atoms of one species; thread r
 // owns row r (atom) in every epilogue, which is exactly the TMEM lane it may
 // read (warp w reads lanes 32w .. 32w + 31). Per tile, M = 128 atoms:
 //   Z1 = g W1^T          K = 64 (D padded),   N = 32 (hidden padded)
@@ -34,17 +34,19 @@ namespace {
 constexpr int kURows = 128;  // atoms per tile: the MMA's M
 constexpr int kUHid = 32;    // hidden widths padded to 32
 constexpr int kUThreads = 128;
-constexpr int kUCols = 128;  // TMEM columns of one CTA
+constexpr int kUCols = 128;  // TMEM columns of one CTA (three CTAs per SM: 384 of 512)
 
 // Byte offsets of the operands in dynamic shared memory, hi part then lo part.
+// The later layers' A operands reuse the g rows' space: layer 1 has read them
+// by the time the first of them is written.
 constexpr int kA0 = 0;                          // g rows: 128 x 64 BF16 = 16 KB per part
-constexpr int kA1 = kA0 + 2 * kURows * 64 * 2;  // x1 / delta2 / delta1 rows: 128 x 32 = 8 KB per part
-constexpr int kB1 = kA1 + 2 * kURows * 32 * 2;  // W1: 32 x 64 = 4 KB per part
+constexpr int kA1 = kA0;                        // x1 / delta2 / delta1 rows: 128 x 32 = 8 KB per part
+constexpr int kB1 = kA0 + 2 * kURows * 64 * 2;  // W1: 32 x 64 = 4 KB per part
 constexpr int kB2 = kB1 + 2 * 32 * 64 * 2;      // W2: 32 x 32 = 2 KB per part
 constexpr int kB3 = kB2 + 2 * 32 * 32 * 2;      // W2^T: 32 x 32
 constexpr int kB4 = kB3 + 2 * 32 * 32 * 2;      // W1^T: 64 x 32 = 4 KB per part
 constexpr int kBias = kB4 + 2 * 64 * 32 * 2;    // b1 [32], b2 [32], w3 [32], b3, padding: 512 B
-constexpr int kUSmem = kBias + 512;             // 72.5 KB
+constexpr int kUSmem = kBias + 512;             // 56.5 KB: three CTAs per SM (four would need <= 56 KB)
 // One species' weights as the kernel holds them (B operands hi and lo, then the
 // biases): packed once per parameter set, brought in by one bulk copy.
 constexpr int kWtcBytes = kUSmem - kB1;
@@ -113,6 +115,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     }
     return false;
 }
+
+// tanh x = 1 - 2 / (exp(2x) + 1): absolute error a few 1e-7, below the BF16
+// operands' rounding; exactly +-1 in the limits.
+__device__ __forceinline__ float tanh_exp(float x) { return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -225,7 +231,7 @@ __global__ void k_pack_tcgen05(int ns, int n_params, int D, int H1, int H2, cons
 // stride of the grid; a species' weights stay in shared memory until the CTA
 // reaches a tile of another species.
 template <bool X3>
-__global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
+__global__ void __launch_bounds__(kUThreads, 3) k_ann_tcgen05(AnnTcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t s_mbar[2];  // MMA completion, weight copy
     __shared__ uint32_t s_tmem;
@@ -306,42 +312,39 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
         float *rec = (a.act && valid) ? a.act + (size_t)s * a.rec_len : nullptr;
         const float *sh = a.shift + t * D, *sc = a.scale + t * D;
         const float *grow = valid ? a.G + (size_t)s * D : nullptr;
+        float g[64];  // the row, all loads issued before any conversion
+#pragma unroll
+        for (int k = 0; k < 64; ++k) g[k] = 0.f;
+        if (valid) {
+            if ((D & 3) == 0) {  // rows start on 16-byte boundaries
+#pragma unroll
+                for (int k = 0; k < 64; k += 4)
+                    if (k < D) {
+                        const float4 v = *reinterpret_cast<const float4 *>(grow + k);
+                        g[k] = v.x;
+                        g[k + 1] = v.y;
+                        g[k + 2] = v.z;
+                        g[k + 3] = v.w;
+                    }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 64; ++k)
+                    if (k < D) g[k] = grow[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 64; ++k) {
+                g[k] = k < D ? (g[k] - sh[k]) * sc[k] : 0.f;
+                if (rec && k < D) rec[k] = g[k];
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            float g[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) g[e] = 0.f;
-            if (valid) {
-                if ((D & 3) == 0) {  // rows start on 16-byte boundaries
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int k = 8 * c + 4 * q;
-                        if (k < D) {
-                            const float4 v = *reinterpret_cast<const float4 *>(grow + k);
-                            g[4 * q] = v.x;
-                            g[4 * q + 1] = v.y;
-                            g[4 * q + 2] = v.z;
-                            g[4 * q + 3] = v.w;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        if (8 * c + e < D) g[e] = grow[8 * c + e];
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int k = 8 * c + e;
-                    g[e] = k < D ? (g[e] - sh[k]) * sc[k] : 0.f;
-                    if (rec && k < D) rec[k] = g[e];
-                }
-            }
             uint4 hi, lo;
             uint32_t *h = &hi.x, *l = &lo.x;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                if (X3) split_bf2(g[2 * p], g[2 * p + 1], h[p], l[p]);
-                else h[p] = pack_bf2(g[2 * p], g[2 * p + 1]);
+                if (X3) split_bf2(g[8 * c + 2 * p], g[8 * c + 2 * p + 1], h[p], l[p]);
+                else h[p] = pack_bf2(g[8 * c + 2 * p], g[8 * c + 2 * p + 1]);
             }
             *reinterpret_cast<uint4 *>(smem + kA0 + uoff(tid, 8 * c, 64)) = hi;
             if (X3) *reinterpret_cast<uint4 *>(smem + kA0 + kURows * 64 * 2 + uoff(tid, 8 * c, 64)) = lo;
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
         run(0, kA0, 64, kB1, 32, 64, 32);
         tmem_ld32(lane_addr + 0, v);
 #pragma unroll
-        for (int j = 0; j < kUHid; ++j) x1[j] = j < H1 ? tanhf(v[j] + s_bias[j]) : 0.f;
+        for (int j = 0; j < kUHid; ++j) x1[j] = j < H1 ? tanh_exp(v[j] + s_bias[j]) : 0.f;
         store_row32<X3>(smem, kA1, tid, x1);
         fence_async_smem();
         tc_fence_before();
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
         float e = s_bias[3 * kUHid];
 #pragma unroll
         for (int j = 0; j < kUHid; ++j) {
-            const float x2 = j < H2 ? tanhf(v[j] + s_bias[kUHid + j]) : 0.f;
+            const float x2 = j < H2 ? tanh_exp(v[j] + s_bias[kUHid + j]) : 0.f;
             const float w = s_bias[2 * kUHid + j];
             e = fmaf(w, x2, e);
             v[j] = (1.0f - x2 * x2) * w;  // delta2
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(kUThreads, 1) k_ann_tcgen05(AnnTcArgs a) {
 
 int tcgen05_tiles(const Context &c, int n) { return (n + kURows - 1) / kURows + c.basis.n_species; }
 
-// Persistent CTAs of the network kernel: three fit an SM (72.5 KB of shared
+// Persistent CTAs of the network kernel: three fit an SM (56.5 KB of shared
 // memory and 128 TMEM columns each).
 static int tcgen05_ctas(const Context &c, int n) { return std::min(tcgen05_tiles(c, n), 3 * std::max(1, c.n_sm)); }
 

@@ -149,7 +149,6 @@ int ensure(Context &c, int n, const Grid &g) {
         CK(grow(c.d_ke_part, 0, 11 * ((N + 255) / 256 + 1)), "cudaMalloc");  // an 11-entry row per MD CTA
         CK(grow(c.d_sp_rank, 0, N), "cudaMalloc");
         CK(grow(c.d_sp_list, 0, N), "cudaMalloc");
-        CK(grow(c.d_tiles, 0, (size_t)bf16_max_tiles(c, n) + 1), "cudaMalloc");
         c.cap_atoms = n;
         ++c.buf_gen;
     }
@@ -166,7 +165,7 @@ int ensure(Context &c, int n, const Grid &g) {
         ++c.buf_gen;
     }
     const int need_e =
-        std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell * kMaxSplit), bf16_eparts(c, std::max(n, 1))) + 1;
+        std::max(std::max(ann_blocks(std::max(n, 1)), g.ncell * kMaxSplit), tcgen05_tiles(c, std::max(n, 1))) + 1;
     if (need_e > c.cap_blocks || !c.d_e_part) {
         CK(grow(c.d_e_part, 0, (size_t)need_e), "cudaMalloc");
         c.cap_blocks = need_e;
@@ -398,7 +397,6 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
     if ((e = cudaMalloc(&c.d_done, sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_sp_cnt, sizeof(int) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_sp_off, sizeof(int) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc(&c.d_n_tiles, sizeof(int))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_result, sizeof(double) * 11)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_mass, sizeof(double) * kMaxSpecies)) != cudaSuccess) return setup_fail(e, "cudaMalloc");
     if ((e = cudaMalloc(&c.d_work, 2 * sizeof(unsigned))) != cudaSuccess) return setup_fail(e, "cudaMalloc");
@@ -1428,7 +1426,7 @@ extern "C" void aenet_destroy(aenet_ctx *h) {
                     c.d_cell_of, c.d_slot, c.d_cell_count, c.d_cell_start, c.d_G, c.d_dEdG, c.d_eatom, c.d_F4,
                     c.d_vir_part, c.d_e_part, c.d_ke_part, c.d_result, c.d_err, c.d_step, c.d_done, c.d_pos, c.d_vel,
                     c.d_forces, c.d_eatom_out, c.d_types, c.d_rec, c.d_stats, c.d_sp_cnt, c.d_sp_off,
-                    c.d_sp_rank, c.d_sp_list, c.d_tiles, c.d_n_tiles, c.d_sinfo, c.d_bres, c.d_act,
+                    c.d_sp_rank, c.d_sp_list, c.d_sinfo, c.d_bres, c.d_act,
                     c.d_wpart, c.d_wpairs, c.d_dEdW, c.d_work, c.d_order, c.d_psinfo, c.d_porder,
                     c.d_vl, c.d_vl_count, c.d_vl_origin, c.d_vl_ref, c.d_vl_flag, c.d_vl_builds,
                     c.d_vl_epart, c.d_vl_vpart, c.d_lambda};
