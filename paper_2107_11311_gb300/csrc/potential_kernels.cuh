@@ -1172,6 +1172,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     __shared__ float s_vir[NW][9];
     __shared__ double s_e[NW];
     __shared__ int s_next, s_item;
+    __shared__ int s_kept, s_wcnt[NW];  // staged image-atoms of the chunk; per-warp counts while staging
     // tensor-core form: per species of the sub-item, atoms through phase A and
     // network done; the sub-item's atoms in species order, and each species'
     // first position and count in that order
@@ -1307,29 +1308,74 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     const int cnt = a_hi - a_lo;
     const int slot = order ? cell : item;  // row of this item's energy / virial partials (per cell in a batch)
     const int n_chunks = (total + tile - 1) / tile;
-    auto stage = [&](int chunk) {
-        const int base = chunk * tile;
-        const int len = min(tile, total - base);
-        for (int t = tid; t < len; t += NW * 32) {
-            const int q = base + t;
-            int lo = 0, hi = n_off - 1;  // largest o with off_prefix[o] <= q
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (off_prefix[mid] <= q) lo = mid; else hi = mid - 1;
-            }
-            const int j = off_start[lo] + (q - off_prefix[lo]);
-            const float4 p = pos4[j];
-            const float4 sh = off_shift[lo];
-            s_pos[t] = make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w);
-            if constexpr (MODE == kBuildList)
-                s_idx[t] = j | (lo << caps.vl_jbits);  // the Verlet-list entry: index and image offset
-            else
-                s_idx[t] = j | (__float_as_int(sh.w) ? kShiftBit : 0);
-        }
-    };
     // list-build mode: the entry of the atom itself (zero image offset) is excluded
     const int self_code = (g.m[0] + wx * (g.m[1] + wy * g.m[2])) << caps.vl_jbits;
     const float rc2list = caps.rc_list * caps.rc_list;
+    // Staging of chunk `chunk` of the item's neighbourhood into s_pos / s_idx;
+    // the number of staged image-atoms is in s_kept after the next barrier.
+    // In an orthorhombic cell the item's cell is the box [0, h) of the staged
+    // frame, and an image-atom farther than the cutoff from every point of that
+    // box is no atom's neighbour: it is not staged (about 28% of a 27-cell
+    // neighbourhood). The kept atoms stay in their enumeration order (a block
+    // prefix over ballots), so every atom's list is deterministic. The
+    // tensor-core modes keep every image-atom: their compact lists refer to
+    // the unfiltered enumeration.
+    const bool filter = !kTC && !g.tri;
+    // (a relative margin of 1e-5 keeps pairs at the cutoff to the last ulp)
+    const float rc2stage = (MODE == kBuildList ? rc2list : B.rc_max * B.rc_max) * 1.00001f;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    auto stage = [&](int chunk) {
+        const int base = chunk * tile;
+        const int len = min(tile, total - base);
+        int kept = 0;  // uniform across the block
+        for (int r0 = 0; r0 < len; r0 += NW * 32) {
+            const int t = r0 + tid;
+            bool keep = false;
+            float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+            int code = 0;
+            if (t < len) {
+                const int q = base + t;
+                int lo = 0, hi = n_off - 1;  // largest o with off_prefix[o] <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off_prefix[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                const int j = off_start[lo] + (q - off_prefix[lo]);
+                const float4 p = pos4[j];
+                const float4 sh = off_shift[lo];
+                sp = make_float4(p.x + sh.x, p.y + sh.y, p.z + sh.z, p.w);
+                if constexpr (MODE == kBuildList)
+                    code = j | (lo << caps.vl_jbits);  // the Verlet-list entry: index and image offset
+                else
+                    code = j | (__float_as_int(sh.w) ? kShiftBit : 0);
+                keep = true;
+                if (filter) {
+                    const float dx = fmaxf(fmaxf(-sp.x, sp.x - g.hf[0]), 0.f);
+                    const float dy = fmaxf(fmaxf(-sp.y, sp.y - g.hf[1]), 0.f);
+                    const float dz = fmaxf(fmaxf(-sp.z, sp.z - g.hf[2]), 0.f);
+                    keep = dx * dx + dy * dy + dz * dz <= rc2stage;
+                }
+            }
+            const unsigned mk = __ballot_sync(kFull, keep);
+            if (lane == 0) s_wcnt[warp] = __popc(mk);
+            __syncthreads();
+            int off = kept, round_total = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const int c = s_wcnt[w];
+                if (w < warp) off += c;
+                round_total += c;
+            }
+            if (keep) {
+                const int slot = off + __popc(mk & lt_mask);
+                s_pos[slot] = sp;
+                s_idx[slot] = code;
+            }
+            kept += round_total;
+            __syncthreads();  // s_wcnt is written again in the next round
+        }
+        if (tid == 0) s_kept = kept;
+    };
 
     float vir[9];
 #pragma unroll
@@ -1534,8 +1580,10 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         __syncthreads();
     }
     } else if (n_chunks <= 1) {
+        if (tid == 0) s_kept = 0;
         if (total > 0) stage(0);
         __syncthreads();
+        const int staged = s_kept;
         for (;;) {
             int a = 0;
             if (lane == 0) a = atomicAdd(&s_next, 1);
@@ -1545,11 +1593,11 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
             const float4 ui = pos4[i_s];
             int nnb = 0, nang = 0;
             if constexpr (MODE == kBuildList) {
-                scan_tile_build(s_pos, s_idx, total, ui, i_s | self_code, rc2list,
+                scan_tile_build(s_pos, s_idx, staged, ui, i_s | self_code, rc2list,
                                 vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
                 store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
             } else {
-                scan_tile(s_pos, s_idx, total, ui, i_s, B, caps, W, lane, nnb);
+                scan_tile(s_pos, s_idx, staged, ui, i_s, B, caps, W, lane, nnb);
                 finish_list(nnb, nang);
                 process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
                                                         eatom, G_out, dEdG_in, e_acc, vir);
@@ -1568,7 +1616,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                 stage(chunk);
                 __syncthreads();
                 if (active) {
-                    const int len = min(tile, total - chunk * tile);
+                    const int len = s_kept;
                     if constexpr (MODE == kBuildList)
                         scan_tile_build(s_pos, s_idx, len, ui, i_s | self_code, rc2list,
                                         vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
