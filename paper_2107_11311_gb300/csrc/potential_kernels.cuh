@@ -475,18 +475,46 @@ __device__ __forceinline__ void clenshaw_d(float x, float w, const float (&a0)[K
     dS = fmaf(x, d1, b1 - d2);
 }
 
+// Packed FP32: one FFMA2 instruction applies the same fused multiply-add to
+// both halves of a float2 (each half rounded exactly as fmaf), so two
+// independent recurrences advance for one issue slot.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// clenshaw_d for two arguments at once (x.x with w.x, x.y with w.y; the
+// coefficient pairs hold the same value in both halves). The derivative chain
+// is carried halved, D_q = b'_q / 2, so that every step is packed FMAs with
+// no negated operand: D_q = 2x D_{q+1} + (b_{q+1} - D_{q+2}). The results
+// equal clenshaw_d's bit for bit (scaling by 2 is exact).
+template <int KT>
+__device__ __forceinline__ void clenshaw_d2(float2 x, float2 w, const float2 (&a0)[KT], const float2 (&a1)[KT], int K,
+                                            float2 &S, float2 &dS) {
+    const float2 m1 = dup2(-1.0f), x2 = __fadd2_rn(x, x);
+    float2 b1 = dup2(0.f), b2 = b1, D1 = b1, D2 = b1;
+#pragma unroll
+    for (int q = KT - 1; q >= 1; --q) {
+        if (q < K) {
+            const float2 a = ffma2(w, a1[q], a0[q]);
+            const float2 b = ffma2(x2, b1, ffma2(m1, b2, a));
+            const float2 D = ffma2(x2, D1, ffma2(m1, D2, b1));
+            b2 = b1;
+            b1 = b;
+            D2 = D1;
+            D1 = D;
+        }
+    }
+    S = ffma2(x, b1, ffma2(m1, b2, ffma2(w, a1[0], a0[0])));
+    dS = ffma2(x2, D1, ffma2(dup2(-2.0f), D2, b1));
+}
+
 // Chain rule through one angular term T(cos th) f_c(r_j) f_c(r_k) weighted by
-// b_q = ca_q + (s_j s_k) caw_q: adds dE/dd_j to (jx, jy, jz) and returns dE/dd_k
-// in (gx, gy, gz); nothing when v is false (uk, xk then hold any valid entry).
+// b_q = ca_q + (s_j s_k) caw_q, given c = cos th, S = sum_q b_q T_q(c) and
+// dS = sum_q b_q T_q'(c): adds dE/dd_j to (jx, jy, jz) and returns dE/dd_k in
+// (gx, gy, gz); nothing when v is false (uk, xk then hold any valid entry).
 //   d/dd_j [T(cos) f_j f_k] = T' f_j f_k (u_k - cos u_j) / r_j + T f_j' f_k u_j
-template <int KAT, bool EXACT>
 __device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj, const float4 uk, const float4 xk,
-                                              bool v, const float (&ca)[KAT], const float (&caw)[KAT], int Ka,
-                                              float &jx, float &jy, float &jz, float &gx, float &gy, float &gz) {
-    const float c = uj.x * uk.x + uj.y * uk.y + uj.z * uk.z;
-    const float w = xj.z * xk.z;
-    float S, dS;  // sum_q b_q T_q(c) and sum_q b_q T_q'(c), b_q = ca_q + w caw_q
-    clenshaw_d<KAT>(c, w, ca, caw, Ka, S, dS);
+                                              bool v, float c, float S, float dS, float &jx, float &jy, float &jz,
+                                              float &gx, float &gy, float &gz) {
     const float fj = uj.w, fk = uk.w;
     const float Af = v ? dS * fj * fk : 0.f;
     const float Aj = Af * xj.x, Ak = Af * xk.x;
@@ -499,37 +527,60 @@ __device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj
     gz = Ak * (uj.z - c * uk.z) + Bk * uk.z;
 }
 
+// Slots of the descriptor a lane returns: the plain slot l and its
+// species-weighted copy l + P (P = KRT + KAT) for l < P, else the padding slots
+// 2l and 2l + 1 (zero).
+template <int KRT, int KAT>
+__device__ __forceinline__ int desc_slot0(int lane) {
+    return lane < KRT + KAT ? lane : 2 * lane;
+}
+template <int KRT, int KAT>
+__device__ __forceinline__ int desc_slot1(int lane) {
+    return lane < KRT + KAT ? lane + KRT + KAT : 2 * lane + 1;
+}
+
 // Descriptor of atom i (Sec. II.B: Eq. radial and Eq. angular with the cosine
 // cutoff, and their species-weighted copy) from its neighbour lists, reduced
-// across the warp: lane l returns the coefficients of slots 2l and 2l + 1.
-// Angular slots carry the factor 2 of the paper's ordered-pair sum.
+// across the warp: lane l returns the coefficients of slots desc_slot0(l) and
+// desc_slot1(l). A plain slot s and its weighted copy s + P take the same
+// Chebyshev value times two different weights, so they share one packed
+// accumulator (acc[2s], acc[2s + 1]) and one FFMA2 per term; the Chebyshev
+// recurrence runs duplicated in both halves. Angular slots carry the factor 2
+// of the paper's ordered-pair sum.
 template <int KRT, int KAT, bool EXACT>
 __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &B, const float *s_tw,
                                                 const WarpLists &W, int lane, float &G0, float &G1) {
-    constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
     const float inv_rcr = 1.0f / B.rc_rad;
-    const int s0 = 2 * lane, s1 = 2 * lane + 1;
-    float acc[64];
+    float acc[64];  // (slot s, slot s + P) at 2s, 2s + 1 for s < P; the rest stays zero
 #pragma unroll
     for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+    auto acc_fma = [&](int s, float2 t, float2 f) {  // acc pair s += t * f
+        const float2 r = ffma2(t, f, make_float2(acc[2 * s], acc[2 * s + 1]));
+        acc[2 * s] = r.x;
+        acc[2 * s + 1] = r.y;
+    };
+    auto acc_add = [&](int s, float2 f) {
+        const float2 r = __fadd2_rn(make_float2(acc[2 * s], acc[2 * s + 1]), f);
+        acc[2 * s] = r.x;
+        acc[2 * s + 1] = r.y;
+    };
     for (int k = lane; k < nnb; k += 32) {
         const float r = W.e_d[k].w;
         if (r <= B.rc_rad) {
             float fc, dfc;
             radial_cutoff(r, inv_rcr, fc, dfc);
             const float x = 2.0f * r * inv_rcr - 1.0f;
-            const float sfc = s_tw[W.e_j[k] >> 28] * fc;
-            float tm1 = 1.0f, t = x;
-            acc[0] += fc;
-            acc[SLOT_RADW] += sfc;
+            const float2 f = make_float2(fc, s_tw[W.e_j[k] >> 28] * fc);  // (f_c, s_j f_c)
+            const float2 x2 = dup2(2.0f * x);
+            float2 tm1 = dup2(1.0f), t = dup2(x);
+            acc_add(0, f);
 #pragma unroll
             for (int q = 1; q < KRT; ++q) {
                 if (q < Kr) {
-                    acc[q] = fmaf(t, fc, acc[q]);
-                    acc[SLOT_RADW + q] = fmaf(t, sfc, acc[SLOT_RADW + q]);
-                    const float tn = fmaf(2.0f * x, t, -tm1);
+                    acc_fma(q, t, f);
+                    const float2 tn = ffma2(x2, t, make_float2(-tm1.x, -tm1.y));
                     tm1 = t;
                     t = tn;
                 }
@@ -564,16 +615,18 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
                     const float cA = uj.x * ukA.x + uj.y * ukA.y + uj.z * ukA.z;
                     const float cB = uj.x * ukB.x + uj.y * ukB.y + uj.z * ukB.z;
                     const float wA = vA ? uj.w * ukA.w : 0.f, wB = vB ? uj.w * ukB.w : 0.f;
-                    const float wsA = wA * sj * skA, wsB = wB * sj * skB;
-                    float tA1 = 1.0f, tA = cA, tB1 = 1.0f, tB = cB;
-                    acc[SLOT_ANG] = (acc[SLOT_ANG] + wA) + wB;
-                    acc[SLOT_ANGW] = (acc[SLOT_ANGW] + wsA) + wsB;
+                    const float2 fA = make_float2(wA, wA * sj * skA), fB = make_float2(wB, wB * sj * skB);
+                    const float2 xA2 = dup2(2.0f * cA), xB2 = dup2(2.0f * cB);
+                    float2 tA1 = dup2(1.0f), tA = dup2(cA), tB1 = tA1, tB = dup2(cB);
+                    acc_add(KRT, fA);
+                    acc_add(KRT, fB);
 #pragma unroll
                     for (int q = 1; q < KAT; ++q) {
                         if (q < Ka) {
-                            acc[SLOT_ANG + q] = fmaf(tB, wB, fmaf(tA, wA, acc[SLOT_ANG + q]));
-                            acc[SLOT_ANGW + q] = fmaf(tB, wsB, fmaf(tA, wsA, acc[SLOT_ANGW + q]));
-                            const float tnA = fmaf(2.0f * cA, tA, -tA1), tnB = fmaf(2.0f * cB, tB, -tB1);
+                            acc_fma(KRT + q, tA, fA);
+                            acc_fma(KRT + q, tB, fB);
+                            const float2 tnA = ffma2(xA2, tA, make_float2(-tA1.x, -tA1.y));
+                            const float2 tnB = ffma2(xB2, tB, make_float2(-tB1.x, -tB1.y));
                             tA1 = tA;
                             tA = tnA;
                             tB1 = tB;
@@ -584,7 +637,8 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
             }
         }
     }
-    transpose_reduce64(acc, lane);
+    transpose_reduce64(acc, lane);  // lane l: acc[0], acc[1] = indices 2l, 2l + 1
+    const int s0 = desc_slot0<KRT, KAT>(lane), s1 = desc_slot1<KRT, KAT>(lane);
     G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
     G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
 }
@@ -601,7 +655,8 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
     const float inv_rcr = 1.0f / B.rc_rad;
-    float cr[KRT], crw[KRT], ca[KAT], caw[KAT];
+    float cr[KRT], crw[KRT];
+    float2 ca[KAT], caw[KAT];  // the same coefficient in both halves (packed Clenshaw of two pairs)
 #pragma unroll
     for (int q = 0; q < KRT; ++q) {
         cr[q] = coef[q];
@@ -609,8 +664,8 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
     }
 #pragma unroll
     for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
-        ca[q] = 2.0f * coef[SLOT_ANG + q];
-        caw[q] = 2.0f * coef[SLOT_ANGW + q];
+        ca[q] = dup2(2.0f * coef[SLOT_ANG + q]);
+        caw[q] = dup2(2.0f * coef[SLOT_ANGW + q]);
     }
     const float k2 = 2.0f * inv_rcr;
     for (int k = lane; k < nnb; k += 32) {
@@ -663,11 +718,14 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
                     rotation_step(diag, it, nt, nA, nB, lane, vj, ccA, vA);
                     rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
                     const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
+                    const float4 ukA = W.a_u[kA], xkA = W.a_x[kA], ukB = W.a_u[kB], xkB = W.a_x[kB];
+                    const float2 c = make_float2(uj.x * ukA.x + uj.y * ukA.y + uj.z * ukA.z,
+                                                 uj.x * ukB.x + uj.y * ukB.y + uj.z * ukB.z);
+                    float2 S, dS;  // both steps' Clenshaw sums in one packed recurrence
+                    clenshaw_d2<KAT>(c, make_float2(xj.z * xkA.z, xj.z * xkB.z), ca, caw, Ka, S, dS);
                     float gAx, gAy, gAz, gBx, gBy, gBz;
-                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kA], W.a_x[kA], vA, ca, caw, Ka, jx, jy, jz, gAx, gAy,
-                                              gAz);
-                    pair_gradient<KAT, EXACT>(uj, xj, W.a_u[kB], W.a_x[kB], vB, ca, caw, Ka, jx, jy, jz, gBx, gBy,
-                                              gBz);
+                    pair_gradient(uj, xj, ukA, xkA, vA, c.x, S.x, dS.x, jx, jy, jz, gAx, gAy, gAz);
+                    pair_gradient(uj, xj, ukB, xkB, vB, c.y, S.y, dS.y, jx, jy, jz, gBx, gBy, gBz);
                     // dE/dd_k goes to the lane that owns k: it sits t lanes to the left
                     const int srcA = rotation_source(diag, it, nA, lane);
                     const int srcB = rotation_source(diag, it + 1, nA, lane);
@@ -728,13 +786,14 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
                                              const float *__restrict__ dEdG_in, double &e_acc, float (&vir)[9]) {
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
-    const int s0 = 2 * lane, s1 = 2 * lane + 1;
+    const int s0 = 2 * lane, s1 = 2 * lane + 1;  // slots of the lane's dE/dG coefficients
     if constexpr (MODE != kForces) {
-    float G0, G1;
+    float G0, G1;  // descriptor slots g0, g1
     atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, W, lane, G0, G1);
+    const int g0 = desc_slot0<KRT, KAT>(lane), g1 = desc_slot1<KRT, KAT>(lane);
     if constexpr (MODE == kDescriptor) {
         const int D = 2 * (Kr + Ka);
-        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
+        const int c0 = slot_col<KRT, KAT>(g0, Kr, Ka), c1 = slot_col<KRT, KAT>(g1, Kr, Ka);
         if (c0 >= 0) G_out[(size_t)i_s * D + c0] = G0;
         if (c1 >= 0) G_out[(size_t)i_s * D + c1] = G1;
         return;
@@ -743,12 +802,12 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     const int t = __float_as_int(pos4[i_s].w);
     const float *Pt = s_par + t * net.stride;
     const float *sh = Pt + net.offShift, *sc = Pt + net.offScale;
-    const float x00 = (G0 - sh[s0]) * sc[s0];
-    const float x01 = (G1 - sh[s1]) * sc[s1];
+    const float x00 = (G0 - sh[g0]) * sc[g0];
+    const float x01 = (G1 - sh[g1]) * sc[g1];
     // optional activation record of this atom (G_out holds records in this mode)
     float *rec = G_out ? G_out + (size_t)i_s * net.rec_len : nullptr;
     if (rec) {
-        const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
+        const int c0 = slot_col<KRT, KAT>(g0, Kr, Ka), c1 = slot_col<KRT, KAT>(g1, Kr, Ka);
         if (c0 >= 0) rec[c0] = x00;
         if (c1 >= 0) rec[c1] = x01;
     }
@@ -763,24 +822,24 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     constexpr int NK1 = HB == 16 ? NS / 2 : NS;               // ... per lane group
     constexpr int NKH = HB == 16 ? 8 : 32;                    // hidden inputs per lane group
     float *xs = W.coef;
-    *reinterpret_cast<float2 *>(xs + 2 * lane) = make_float2(x00, x01);
+    xs[g0] = x00;
+    xs[g1] = x01;
     __syncwarp();
     const float *W1 = Pt + net.offW[1];
     float z;
     {
         const float *wr = W1 + o * kW1Stride + h * NK1, *gx = xs + h * NK1;
-        float za = 0.f, zb = 0.f;
+        // two partial sums (even and odd inputs) in the halves of one packed accumulator;
         // partial unrolling: all loads hoisted ahead of the FMAs would need ~100 registers
+        float2 zab = dup2(0.f);
 #pragma unroll 2
         for (int k = 0; k < NK1; k += 4) {
             const float4 gv = *reinterpret_cast<const float4 *>(gx + k);
             const float4 wv = *reinterpret_cast<const float4 *>(wr + k);
-            za = fmaf(wv.x, gv.x, za);
-            zb = fmaf(wv.y, gv.y, zb);
-            za = fmaf(wv.z, gv.z, za);
-            zb = fmaf(wv.w, gv.w, zb);
+            zab = ffma2(make_float2(wv.x, wv.y), make_float2(gv.x, gv.y), zab);
+            zab = ffma2(make_float2(wv.z, wv.w), make_float2(gv.z, gv.w), zab);
         }
-        z = za + zb;
+        z = zab.x + zab.y;
         if constexpr (HB == 16) z += __shfl_xor_sync(kFull, z, 16);
     }
     float xl[kMaxLayers];  // this lane's neuron of every hidden layer
@@ -793,17 +852,15 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
             if (lane < HB) xs[lane] = xl[l - 1];
             __syncwarp();
             const float *wr = Pt + net.offW[l] + o * HS + h * NKH, *xv = xs + h * NKH;
-            float za = 0.f, zb = 0.f;
+            float2 zab = dup2(0.f);
 #pragma unroll 2
             for (int k = 0; k < NKH; k += 4) {
                 const float4 gv = *reinterpret_cast<const float4 *>(xv + k);
                 const float4 wv = *reinterpret_cast<const float4 *>(wr + k);
-                za = fmaf(wv.x, gv.x, za);
-                zb = fmaf(wv.y, gv.y, zb);
-                za = fmaf(wv.z, gv.z, za);
-                zb = fmaf(wv.w, gv.w, zb);
+                zab = ffma2(make_float2(wv.x, wv.y), make_float2(gv.x, gv.y), zab);
+                zab = ffma2(make_float2(wv.z, wv.w), make_float2(gv.z, gv.w), zab);
             }
-            float zz = za + zb;
+            float zz = zab.x + zab.y;
             if constexpr (HB == 16) zz += __shfl_xor_sync(kFull, zz, 16);
             xl[l] = tanhf(zz + Pt[net.offB[l] + o]);
             if (rec && lane < net.H[l]) rec[net.rec_x[l] + lane] = xl[l];
@@ -829,44 +886,40 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
             if (lane < HB) xs[lane] = delta;
             __syncwarp();
             const float *wc = Pt + net.offW[l] + h * NKH * HS + o, *dv = xs + h * NKH;
-            float da = 0.f, db = 0.f;
+            float2 dab = dup2(0.f);
 #pragma unroll 2
             for (int q = 0; q < NKH; q += 4) {
                 const float4 d4 = *reinterpret_cast<const float4 *>(dv + q);
-                da = fmaf(wc[(q + 0) * HS], d4.x, da);
-                db = fmaf(wc[(q + 1) * HS], d4.y, db);
-                da = fmaf(wc[(q + 2) * HS], d4.z, da);
-                db = fmaf(wc[(q + 3) * HS], d4.w, db);
+                dab = ffma2(make_float2(wc[(q + 0) * HS], wc[(q + 1) * HS]), make_float2(d4.x, d4.y), dab);
+                dab = ffma2(make_float2(wc[(q + 2) * HS], wc[(q + 3) * HS]), make_float2(d4.z, d4.w), dab);
             }
-            float dx = da + db;
+            float dx = dab.x + dab.y;
             if constexpr (HB == 16) dx += __shfl_xor_sync(kFull, dx, 16);
             delta = (1.0f - xl[l - 1] * xl[l - 1]) * dx;
             if (rec && lane < net.H[l - 1]) rec[net.rec_d[l - 1] + lane] = delta;
         }
     }
-    // dE/dg of this lane's slots: sum_q W1[q][slot] delta1_q
+    // dE/dg of this lane's slots 2l, 2l + 1: sum_q W1[q][slot] delta1_q, both
+    // slots in one packed accumulator (two, over even and odd q); the row holds
+    // every delta twice, so that each 128-bit load gives two (delta, delta) pairs
     __syncwarp();
-    if (lane < HB) xs[lane] = delta;
+    if (lane < HB) *reinterpret_cast<float2 *>(xs + 2 * lane) = dup2(delta);
     __syncwarp();
-    float d0 = 0.f, d1 = 0.f, e0 = 0.f, e1 = 0.f;
+    float2 dd = dup2(0.f), ee = dd;
 #pragma unroll 2
     for (int q = 0; q < HB; q += 4) {
-        const float4 d4 = *reinterpret_cast<const float4 *>(xs + q);
+        const float4 d01 = *reinterpret_cast<const float4 *>(xs + 2 * q);
+        const float4 d23 = *reinterpret_cast<const float4 *>(xs + 2 * q + 4);
         const float2 w0 = *reinterpret_cast<const float2 *>(W1 + (q + 0) * kW1Stride + 2 * lane);
         const float2 w1 = *reinterpret_cast<const float2 *>(W1 + (q + 1) * kW1Stride + 2 * lane);
         const float2 w2 = *reinterpret_cast<const float2 *>(W1 + (q + 2) * kW1Stride + 2 * lane);
         const float2 w3 = *reinterpret_cast<const float2 *>(W1 + (q + 3) * kW1Stride + 2 * lane);
-        d0 = fmaf(w0.x, d4.x, d0);
-        d1 = fmaf(w0.y, d4.x, d1);
-        e0 = fmaf(w1.x, d4.y, e0);
-        e1 = fmaf(w1.y, d4.y, e1);
-        d0 = fmaf(w2.x, d4.z, d0);
-        d1 = fmaf(w2.y, d4.z, d1);
-        e0 = fmaf(w3.x, d4.w, e0);
-        e1 = fmaf(w3.y, d4.w, e1);
+        dd = ffma2(w0, make_float2(d01.x, d01.y), dd);
+        ee = ffma2(w1, make_float2(d01.z, d01.w), ee);
+        dd = ffma2(w2, make_float2(d23.x, d23.y), dd);
+        ee = ffma2(w3, make_float2(d23.z, d23.w), ee);
     }
-    d0 += e0;
-    d1 += e1;
+    const float d0 = dd.x + ee.x, d1 = dd.y + ee.y;
     __syncwarp();  // every lane has read the deltas: the row takes the coefficients
     W.coef[s0] = d0 * sc[s0];  // dE/dG = dE/dg * scale
     W.coef[s1] = d1 * sc[s1];
@@ -1422,10 +1475,9 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         float G0, G1;
         atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, W, lane, G0, G1);
         const float *P = s_par + __float_as_int(pos4[i_s].w) * kTcParStride;
-        float2 gv;
-        gv.x = (G0 - P[2 * lane]) * P[kSlots + 2 * lane];
-        gv.y = (G1 - P[2 * lane + 1]) * P[kSlots + 2 * lane + 1];
-        *reinterpret_cast<float2 *>(s_g + a * kSlots + 2 * lane) = gv;
+        const int g0 = desc_slot0<KRT, KAT>(lane), g1 = desc_slot1<KRT, KAT>(lane);
+        s_g[a * kSlots + g0] = (G0 - P[g0]) * P[kSlots + g0];
+        s_g[a * kSlots + g1] = (G1 - P[g1]) * P[kSlots + g1];
         if (lane == 0) s_nnb[a] = nnb;
     };
     auto tc_phase_c = [&](int a, int i_s, bool staged) {
