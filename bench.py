@@ -411,15 +411,18 @@ def run_batch(args, rank, world):
 # precision forms: the network in FP32 (fused kernel), split BF16 and plain BF16
 # on the tensor cores inside the fused kernel, and the same two as the
 # three-kernel path (descriptor kernel, network kernel, force kernel)
-FORM_DTYPE = {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16", "bf16x3_split": "bf16x3", "bf16_split": "bf16"}
+FORM_DTYPE = {"fp32": "f32", "fp32_pipelined": "f32", "bf16x3": "bf16x3", "bf16": "bf16", "bf16x3_split": "bf16x3",
+              "bf16_split": "bf16"}
 
 
 def make_gpu(m, form, stream, skin=0.0):
     """A library context for one form on the given torch stream."""
     from paper_2107_11311_gb300.aenet import AenetGPU
-    gpu = AenetGPU(m, form.replace("_split", ""), stream=stream.cuda_stream)
+    gpu = AenetGPU(m, form.replace("_split", "").replace("_pipelined", ""), stream=stream.cuda_stream)
     if form.endswith("_split"):
         gpu.fuse_network(False)
+    if form.endswith("_pipelined"):  # the FP32 fused kernel's pipelined form (AENET_OPT_PIPELINE)
+        gpu.pipeline(True)
     gpu.set_skin(skin)
     return gpu
 
@@ -569,7 +572,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="fp32,bf16x3,bf16,bf16x3_split",
                     help="precision forms timed side by side (comma-separated: fp32, bf16x3, bf16, "
-                         "bf16x3_split, bf16_split)")
+                         "bf16x3_split, bf16_split, fp32_pipelined)")
     ap.add_argument("--precision", default=None, choices=sorted(FORM_DTYPE),
                     help="time this form only (same as --forms <form>)")
     ap.add_argument("--workload", default="water_331776")

@@ -331,10 +331,12 @@ int aenet_neighbor_stats(aenet_ctx *ctx, int64_t out[3]);
  * one MD step; and path flags: AENET_PATH_FUSED when descriptor, network and
  * forces run as one fused kernel (the FP32 form with hidden widths <= 32),
  * whose time is then all reported under "forces" (descriptor and network read
- * ~0). Any output pointer except ms may be NULL. Returns AENET_E_STATE if no
- * timed step has run. Synchronises.
+ * ~0), and AENET_PATH_PIPELINED when that kernel ran in its pipelined form
+ * (AENET_OPT_PIPELINE). Any output pointer except ms may be NULL. Returns
+ * AENET_E_STATE if no timed step has run. Synchronises.
  */
 #define AENET_PATH_FUSED 1
+#define AENET_PATH_PIPELINED 2
 int aenet_md_stage_times(aenet_ctx *ctx, float ms[6], int *kernels_per_step, int *path_flags);
 
 /*
@@ -393,6 +395,20 @@ int aenet_descriptors_noalloc(int n_atoms, const double *pos, const int32_t *typ
  * compute the same products; the option exists to compare the two.
  */
 #define AENET_OPT_FUSED_NETWORK 2
+/*
+ * AENET_OPT_PIPELINE (value 0/1, default 0), FP32 fused form of a single
+ * structure: with 1 the potential kernel runs pipelined (one CTA of 16 warps
+ * per SM; warps prepare the next cells' neighbourhoods while others finish the
+ * current cell, with no CTA-wide barrier between cells); with 0 the
+ * block-synchronous form (two CTAs of 8 warps per SM, one cell at a time).
+ * Same arithmetic, so the results agree to FP32 rounding order. The pipelined
+ * form removes the barrier waits but runs slower on GB300 (its desynchronised
+ * warps miss the instruction cache more often), so it is off by default; the
+ * option exists to compare the two. It is used when its shared-memory layout
+ * fits and the descriptor basis is one of the kernel's exact forms (orders
+ * 17/9 or 21/7); otherwise the block-synchronous form runs.
+ */
+#define AENET_OPT_PIPELINE 3
 int aenet_set_option(aenet_ctx *ctx, int option, int value);
 
 /*

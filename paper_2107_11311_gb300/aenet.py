@@ -19,6 +19,9 @@ AENET_FP32, AENET_BF16, AENET_BF16X3 = 0, 1, 2
 AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING, AENET_MD_TIMING_POTENTIAL = 1, 2, 4, 8
 AENET_OPT_KEEP_ACTIVATIONS = 1
 AENET_OPT_FUSED_NETWORK = 2
+AENET_OPT_PIPELINE = 3
+AENET_PATH_FUSED = 1
+AENET_PATH_PIPELINED = 2
 AENET_BATCH_AUTOTUNE = 1
 STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
 PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
@@ -365,6 +368,11 @@ class AenetGPU:
         kernel, force kernel)."""
         self.set_option(AENET_OPT_FUSED_NETWORK, 1 if on else 0)
 
+    def pipeline(self, on=True):
+        """FP32 fused form: the pipelined potential kernel, or (default) the
+        block-synchronous one."""
+        self.set_option(AENET_OPT_PIPELINE, 1 if on else 0)
+
     def keep_activations(self, on=True):
         """Keep per-atom activation records so that grad_weights() can follow."""
         self.set_option(AENET_OPT_KEEP_ACTIVATIONS, 1 if on else 0)
@@ -404,6 +412,15 @@ class AenetGPU:
         self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), C.byref(k), C.byref(f)))
         vals = [None if np.isnan(v) else float(v) for v in ms]
         return dict(zip(STAGES, vals)), int(k.value), bool(f.value & 1)
+
+    def md_path_flags(self):
+        """Path flags of the last timed MD step: AENET_PATH_FUSED (1) when one
+        fused kernel ran descriptor, network and forces, AENET_PATH_PIPELINED (2)
+        when it was the pipelined form."""
+        ms = np.zeros(len(STAGES), dtype=np.float32)
+        f = C.c_int(0)
+        self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), None, C.byref(f)))
+        return int(f.value)
 
 
 def _energy_function():

@@ -162,6 +162,7 @@ struct Context {
     bool own_stream = false;
     int precision = AENET_FP32;
     bool fuse_network = true;      // BF16 forms: tensor-core network inside the fused kernel
+    bool pipeline = false;         // FP32 fused form: the pipelined kernel (one CTA of 16 warps per SM)
     Basis basis{};
     Net net{};
     std::vector<double> mass;      // [n_species], empty if none
@@ -285,6 +286,7 @@ struct Context {
     int *d_order = nullptr;            // [cap_order] that order for aenet_compute_batch
     int cap_order = 0;
     int last_grid = 0;                 // CTAs of the last potential launch
+    bool last_pipe = false;            // the last fused FP32 launch was the pipelined form
     int pot_parts = 0;                 // energy / virial partial rows of the last potential launch
 
     // prepared batch (aenet_batch_prepare): its own layout buffers, the tuned
@@ -398,7 +400,8 @@ int grad_max_params();
 // Work items per cell of a single-structure potential launch (persistent CTAs
 // take cell parts from a counter); partial buffers hold kMaxSplit rows per cell.
 constexpr int kMaxSplit = 4;
-int potential_split(const Context &c, const Grid &g, int *split_from);
+int potential_split(const Context &c, const Grid &g, int *split_from, int wave = 0);
+bool pipe_supported(const Context &c, const Grid &g);
 
 // Fused descriptor + network + forces kernel (FP32 form, hidden widths <= 32).
 bool fused_supported(const Context &c);

@@ -1337,7 +1337,7 @@ extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_st
             ms[k] = nanf("");  // stage not recorded in the light timing mode
     }
     if (kernels_per_step) *kernels_per_step = c.md_kernels;
-    if (path_flags) *path_flags = fused_path(c) ? AENET_PATH_FUSED : 0;
+    if (path_flags) *path_flags = (fused_path(c) ? AENET_PATH_FUSED : 0) | (c.last_pipe ? AENET_PATH_PIPELINED : 0);
     return AENET_OK;
 }
 
@@ -1353,6 +1353,13 @@ extern "C" int aenet_set_option(aenet_ctx *h, int option, int value) {
         if (c.fuse_network != (value != 0)) {
             c.fuse_network = value != 0;
             destroy_graph(c);  // the captured MD step holds the other path's kernels
+        }
+        return AENET_OK;
+    }
+    if (option == AENET_OPT_PIPELINE) {
+        if (c.pipeline != (value != 0)) {
+            c.pipeline = value != 0;
+            destroy_graph(c);
         }
         return AENET_OK;
     }

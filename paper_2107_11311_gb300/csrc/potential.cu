@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "potential_launch.cuh"
+#include "potential_pipe.cuh"
 
 namespace aenet {
 
@@ -14,15 +15,15 @@ namespace aenet {
 // persistent CTAs. Cells split_from .. ncell-1 are split into `split` parts
 // (consecutive ranges of their atoms; each part restages the cell's
 // neighbourhood), the others stay whole:
-//  * fewer cells than one wave of resident CTAs (2 per SM): every cell, into
+//  * fewer cells than one wave of resident CTAs (2 per SM, or `wave`): every cell, into
 //    enough parts to fill the wave (at most kMaxSplit, no part with fewer than 8
 //    atoms -- one per warp -- on average): 1,536 atoms in 64 cells run 23% faster;
 //  * more cells: the last wave's worth of cells into 2 parts, so that the tail
 //    is made of half-size items (also the persistent form, which stages the
 //    network parameters once per CTA: water 98,304 and 331,776 atoms run 9%
 //    and 12% faster than with one CTA per cell).
-int potential_split(const Context &c, const Grid &g, int *split_from) {
-    const int wave = 2 * std::max(1, c.n_sm);
+int potential_split(const Context &c, const Grid &g, int *split_from, int wave) {
+    if (wave <= 0) wave = 2 * std::max(1, c.n_sm);
     *split_from = 0;
     if (g.ncell <= 0) return 1;
     const double per_cell = c.cap_atoms > 0 ? (double)c.cap_atoms / g.ncell : 8.0;
@@ -50,8 +51,52 @@ bool tc_fused_supported(const Context &c) {
     return (c.basis.Kr == 17 && c.basis.Ka == 9) || (c.basis.Kr == 21 && c.basis.Ka == 7);
 }
 
+// The pipelined form (k_potential_pipe): FP32 fused evaluation of one
+// structure on the exact bases, when its layout fits one CTA per SM.
+static size_t pipe_smem_bytes(const Context &c, const Grid &g) {
+    const FusedNet net = make_fused_net(c.net);
+    return make_pipe_layout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, net.stride).total;
+}
+
+bool pipe_supported(const Context &c, const Grid &g) {
+    if (!c.pipeline || !fused_supported(c) || c.batch_sinfo || !c.d_work || c.n_sm <= 0) return false;
+    if (!((c.basis.Kr == 17 && c.basis.Ka == 9) || (c.basis.Kr == 21 && c.basis.Ka == 7))) return false;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return pipe_smem_bytes(c, g) + 1024 <= (size_t)optin;  // + the kernel's static shared memory
+}
+
+template <int KRT, int KAT, int HB>
+static cudaError_t launch_pipe_form(Context &c, const Grid &g, const FusedNet &net) {
+    auto kern = k_potential_pipe<KRT, KAT, true, HB>;
+    const size_t smem = pipe_smem_bytes(c, g);
+    cudaError_t e = allow_max_smem(kern);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM; the last wave's worth of cells in halves (short tail items)
+    int split_from = 0;
+    const int split = potential_split(c, g, &split_from, c.n_sm);
+    const int n_items = split_from + (g.ncell - split_from) * split;
+    const int grid = std::max(1, std::min(c.n_sm, n_items));
+    kern<<<grid, kPipeWarps * 32, smem, c.stream>>>(c.basis, net, g, c.caps, c.d_pos4, c.d_cell_start, c.d_params,
+                                                    c.d_shift, c.d_scale, c.d_F4, c.d_eatom,
+                                                    c.keep_act ? c.d_act : nullptr, c.d_e_part, c.d_vir_part,
+                                                    c.d_stats, c.d_err, c.d_work, n_items, split, split_from);
+    c.last_grid = grid;
+    c.pot_parts = grid;  // energy / virial partial rows: one per CTA
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_pipe(Context &c, const Grid &g) {
+    const FusedNet net = make_fused_net(c.net);
+    if (c.basis.Kr == 17 && c.basis.Ka == 9)
+        return net.hb == 16 ? launch_pipe_form<17, 9, 16>(c, g, net) : launch_pipe_form<17, 9, 32>(c, g, net);
+    return net.hb == 16 ? launch_pipe_form<21, 7, 16>(c, g, net) : launch_pipe_form<21, 7, 32>(c, g, net);
+}
+
 size_t potential_smem_bytes(const Context &c, const Grid &g) {
     const FusedNet net = make_fused_net(c.net);
+    if (pipe_supported(c, g)) return pipe_smem_bytes(c, g);
     if (tc_fused_supported(c))
         return make_playout(g.n_off, c.caps.tile, c.caps.nb, c.caps.ang, c.basis.n_species, kTcParStride, kPWarps,
                             true)
@@ -66,6 +111,8 @@ cudaError_t launch_fused_potential(Context &c, const Grid &g, int n) {
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
     if (e != cudaSuccess) return e;
+    c.last_pipe = g.ncell > 0 && pipe_supported(c, g);
+    if (c.last_pipe) return launch_pipe(c, g);
     return dispatch<kFused>(c, g);
 }
 
