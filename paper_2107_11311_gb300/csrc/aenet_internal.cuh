@@ -287,6 +287,9 @@ struct Context {
     int cap_order = 0;
     int last_grid = 0;                 // CTAs of the last potential launch
     bool last_pipe = false;            // the last fused FP32 launch was the pipelined form
+    // set while an MD step is enqueued: its kick + drift kernel has already cleared the force
+    // accumulators and the neighbour statistics, so the potential launch needs no memset
+    bool md_prezeroed = false;
     int pot_parts = 0;                 // energy / virial partial rows of the last potential launch
 
     // prepared batch (aenet_batch_prepare): its own layout buffers, the tuned
@@ -358,6 +361,7 @@ inline cudaError_t allow_max_smem(K kern) {
 // Wrap, bin and sort atoms by cell (the periodic cell list).
 cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
 // The scan + scatter half of launch_cells (after the counts are in place).
+cudaError_t launch_scatter(Context &c, int n);  // the sort after a binning kernel that also scanned
 cudaError_t launch_sort(Context &c, const Grid &g, int n);
 // Binning of a batch: every atom into the cell grid of its structure.
 cudaError_t launch_cells_batch(Context &c, int n, int total_cells, const double *pos, const int32_t *types);

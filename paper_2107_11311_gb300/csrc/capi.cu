@@ -154,6 +154,9 @@ int ensure(Context &c, int n, const Grid &g) {
     }
     if (g.ncell > c.cap_cells) {
         CK(grow(c.d_cell_count, 0, (size_t)g.ncell), "cudaMalloc");
+        // zero from the start: every scan clears the counts it reads, so the MD
+        // step's binning relies on finding them zero
+        CK(cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * (size_t)g.ncell, c.stream), "cudaMemsetAsync");
         CK(grow(c.d_cell_start, 0, (size_t)g.ncell + 1), "cudaMalloc");
         CK(grow(c.d_vir_part, 0, (size_t)g.ncell * kMaxSplit * 9), "cudaMalloc");  // a row per cell part
         c.cap_cells = g.ncell;
@@ -945,12 +948,15 @@ static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *
     int rc = check_smem(c, g);
     if (rc) return rc;
     CK(mark(c, 0), "event");
-    CK(launch_md_kick_drift_bin(c, g, n, dt, pos, vel, types), "kick + drift + binning");
+    CK(launch_md_kick_drift_bin(c, g, n, dt, pos, vel, types), "kick + drift + binning + scan");
     CK(mark(c, 1), "event");
-    CK(launch_sort(c, g, n), "cell sort");
+    CK(launch_scatter(c, n), "cell sort");
     CK(mark(c, 2), "event");
     int n_eparts = 0;
-    if ((rc = enqueue_potential(c, g, n, &n_eparts))) return rc;
+    c.md_prezeroed = true;  // the kick + drift kernel cleared the forces and statistics
+    rc = enqueue_potential(c, g, n, &n_eparts);
+    c.md_prezeroed = false;
+    if (rc) return rc;
     CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr), "kick + reductions");
     CK(mark(c, 6), "event");
     return AENET_OK;
@@ -1004,7 +1010,10 @@ static int enqueue_md_step_verlet(Context &c, const Grid &g, int n, double dt, d
     CK(mark(c, 2), "event");
     CK(mark(c, 3), "event");
     CK(mark(c, 4), "event");
-    CK(launch_potential_list(c, g, n), "potential kernel (Verlet list)");
+    c.md_prezeroed = true;  // the kick + drift kernel cleared the forces and statistics
+    const cudaError_t pe = launch_potential_list(c, g, n);
+    c.md_prezeroed = false;
+    CK(pe, "potential kernel (Verlet list)");
     CK(mark(c, 5), "event");
     CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr, true),
        "kick + reductions");

@@ -7,6 +7,7 @@
 // whatever the box size; absolute FP32 coordinates in a 150 A box would carry
 // ~1e-5 A.
 #include "aenet_internal.cuh"
+#include "cell_scan.cuh"
 
 namespace aenet {
 
@@ -58,73 +59,29 @@ __global__ void k_bin_count_batch(int n, int n_struct, int n_species, const doub
     slot[i] = atomicAdd(&cell_count[cell], 1);
 }
 
-// Exclusive scan of the cell counts by one CTA (cell counts are O(1e4-1e5)):
-// each thread takes four consecutive cells per pass (one 128-bit load and
-// store), so a pass of 1,024 threads covers 4,096 cells.
-__global__ void k_scan_cells(int ncell, const int *__restrict__ count, int *__restrict__ start) {
-    __shared__ int warp_sums[32];
-    __shared__ int carry;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < ncell; base += 4 * blockDim.x) {
-        const int i0 = base + 4 * tid;  // a multiple of 4: 16-byte aligned in both arrays
-        int v[4];
-        if (i0 + 3 < ncell) {
-            const int4 q = *reinterpret_cast<const int4 *>(count + i0);
-            v[0] = q.x;
-            v[1] = q.y;
-            v[2] = q.z;
-            v[3] = q.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = i0 + k < ncell ? count[i0 + k] : 0;
-        }
-        const int tot = (v[0] + v[1]) + (v[2] + v[3]);
-        int x = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sums[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            const int nw = blockDim.x >> 5;
-            int s = lane < nw ? warp_sums[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            if (lane < nw) warp_sums[lane] = s;
-        }
-        __syncthreads();
-        const int excl = carry + (wid ? warp_sums[wid - 1] : 0) + x - tot;
-        const int e1 = excl + v[0], e2 = e1 + v[1], e3 = e2 + v[2];
-        if (i0 + 3 < ncell) {
-            *reinterpret_cast<int4 *>(start + i0) = make_int4(excl, e1, e2, e3);
-        } else {
-            const int e[4] = {excl, e1, e2, e3};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (i0 + k < ncell) start[i0 + k] = e[k];
-        }
-        __syncthreads();  // every thread has read carry
-        if (tid == blockDim.x - 1) carry = e3 + v[3];
-        __syncthreads();
-    }
-    if (tid == 0) start[ncell] = carry;
+// Exclusive scan of the cell counts by one CTA (scan_cells_block).
+__global__ void k_scan_cells(int ncell, int *__restrict__ count, int *__restrict__ start) {
+    scan_cells_block(ncell, count, start);
 }
 
+// Atom i to its sorted position s = cell_start[cell] + rank; slot[i] then holds
+// s itself (the MD kernels read the forces of atom i at F4[slot[i]]).
 __global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__restrict__ cell_of,
-                          const int *__restrict__ slot, const int *__restrict__ cell_start,
+                          int *__restrict__ slot, const int *__restrict__ cell_start,
                           float4 *__restrict__ pos4, int *__restrict__ perm) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int s = cell_start[cell_of[i]] + slot[i];
     pos4[s] = tmp4[i];
     perm[s] = i;
+    slot[i] = s;
+}
+
+cudaError_t launch_scatter(Context &c, int n) {
+    if (n > 0)
+        k_scatter<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_tmp4, c.d_cell_of, c.d_slot, c.d_cell_start,
+                                                         c.d_pos4, c.d_perm);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sort(Context &c, const Grid &g, int n) {

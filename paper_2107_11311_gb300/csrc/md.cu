@@ -10,6 +10,7 @@
 // closing kick + all reductions (the last CTA to finish sums every partial in a
 // fixed order, so results are deterministic).
 #include "aenet_internal.cuh"
+#include "cell_scan.cuh"
 
 namespace aenet {
 
@@ -98,24 +99,22 @@ __global__ void k_unsort_G(int n, int D, const int *__restrict__ perm, const flo
     }
 }
 
-// v += dt/2 F/m c; x += dt v; then bin x (as k_bin_count). F comes from the
-// previous evaluation, in its cell-sorted order (cell_start/cell_of/slot of that
-// evaluation are still in place).
-__global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double dt, double *__restrict__ pos,
-                                    double *__restrict__ vel, const int32_t *__restrict__ types,
-                                    const float4 *__restrict__ F4, const int *__restrict__ cell_start, Grid g,
-                                    float4 *__restrict__ tmp4, int *__restrict__ cell_of, int *__restrict__ slot,
-                                    int *__restrict__ cell_count, unsigned *__restrict__ err,
-                                    const double *__restrict__ lambda) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// The per-atom part of k_md_kick_drift_bin.
+__device__ inline void md_kick_drift_bin_atom(int i, int n_species, const KickParams &kp, double dt,
+                                              double *__restrict__ pos, double *__restrict__ vel,
+                                              const int32_t *__restrict__ types, float4 *__restrict__ F4,
+                                              const Grid &g, float4 *__restrict__ tmp4, int *__restrict__ cell_of,
+                                              int *__restrict__ slot, int *__restrict__ cell_count,
+                                              unsigned *__restrict__ err, const double *__restrict__ lambda) {
     const double scale = lambda ? *lambda : 1.0;  // thermostat (1 for NVE)
     int t = types[i];
     if (t < 0 || t >= n_species) {
         atomicOr(err, kErrType);
         t = 0;
     }
-    const float4 f = F4[cell_start[cell_of[i]] + slot[i]];
+    const int s_old = slot[i];
+    const float4 f = F4[s_old];
+    F4[s_old] = make_float4(0.f, 0.f, 0.f, 0.f);
     const double k = select_species(kp.k, t);
     double x[3];
     const float fa[3] = {f.x, f.y, f.z};
@@ -135,6 +134,37 @@ __global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double 
     slot[i] = atomicAdd(&cell_count[cell], 1);
 }
 
+
+// v += dt/2 F/m c; x += dt v; then bin x (as k_bin_count), and the last CTA
+// to finish scans the cell counts into the cell starts. F comes from the
+// previous evaluation, in its cell-sorted order: slot[i] still holds atom i's
+// sorted position of that evaluation (k_scatter). Each atom's force entry is
+// read once here and cleared, so the potential kernel that follows finds F4
+// zeroed; the cell counts were cleared by the previous scan and the neighbour
+// statistics are cleared here, so the step needs no memset.
+__global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double dt, double *__restrict__ pos,
+                                    double *__restrict__ vel, const int32_t *__restrict__ types,
+                                    float4 *__restrict__ F4, Grid g, float4 *__restrict__ tmp4,
+                                    int *__restrict__ cell_of, int *__restrict__ slot, int *__restrict__ cell_count,
+                                    int *__restrict__ cell_start, unsigned *__restrict__ done,
+                                    unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
+                                    const double *__restrict__ lambda) {
+    __shared__ bool s_last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 4 && stats) stats[i] = 0ull;
+    if (i < n) md_kick_drift_bin_atom(i, n_species, kp, dt, pos, vel, types, F4, g, tmp4, cell_of, slot, cell_count,
+                                      err, lambda);
+    // the last CTA to finish binning turns the counts into the cell starts
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    scan_cells_block(g.ncell, cell_count, cell_start);
+    if (threadIdx.x == 0) *done = 0u;  // left at zero for the next user of the counter
+}
+
 // v += dt/2 F/m c with F of the current evaluation. Every CTA also sums a fixed
 // slice of the potential's energy and virial partial rows and its atoms'
 // kinetic energy into an 11-entry row of cta_part; the last CTA reduces those
@@ -143,8 +173,8 @@ __global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double 
 // do not depend on scheduling.
 __global__ void __launch_bounds__(kMdThreads)
     k_md_kick_finish(int n, KickParams kp, double *__restrict__ vel, const int32_t *__restrict__ types,
-                     const float4 *__restrict__ F4, const int *__restrict__ cell_start, const int *__restrict__ cell_of,
-                     const int *__restrict__ slot, int n_e, const double *__restrict__ e_part, int n_v,
+                     const float4 *__restrict__ F4, const int *__restrict__ slot, int n_e,
+                     const double *__restrict__ e_part, int n_v,
                      const double *__restrict__ vir_part, double *__restrict__ cta_part, unsigned *__restrict__ done,
                      double *__restrict__ result, int *__restrict__ step, double *__restrict__ rec_pot,
                      double *__restrict__ rec_kin, unsigned *__restrict__ vl_flag,
@@ -156,7 +186,7 @@ __global__ void __launch_bounds__(kMdThreads)
     double ke = 0.0;
     if (i < n) {
         const int t = types[i];
-        const float4 f = F4[cell_start[cell_of[i]] + slot[i]];
+        const float4 f = F4[slot[i]];  // sorted position of atom i (k_scatter)
         const double k = select_species(kp.k, t);
         const double vx = fma(k, (double)f.x, vel[3 * i + 0]);
         const double vy = fma(k, (double)f.y, vel[3 * i + 1]);
@@ -222,20 +252,22 @@ __global__ void __launch_bounds__(kMdThreads)
 // Verlet form of v += dt/2 F/m c; x += dt v (the list is kept, nothing is
 // binned). The FP32 coordinate of atom i is refreshed relative to the origin of
 // its cell at the last list build, u = x - origin, and written to its sorted
-// slot of that build, so the list's image offsets stay valid. An atom that moved
+// slot of that build (slot[i]), so the list's image offsets stay valid; its
+// force entry is cleared after it is read. An atom that moved
 // more than skin/2 since the build (or is not finite) raises flag[0]; the last
 // CTA to finish turns the flag into the value of the graph conditional that
 // guards the rebuild.
 __global__ void k_md_vl_kick_drift(int n, int n_species, KickParams kp, double dt, double half_skin2,
                                    double *__restrict__ pos, double *__restrict__ vel,
-                                   const int32_t *__restrict__ types, const float4 *__restrict__ F4,
-                                   const int *__restrict__ cell_start, const int *__restrict__ cell_of,
+                                   const int32_t *__restrict__ types, float4 *__restrict__ F4,
                                    const int *__restrict__ slot, const double *__restrict__ origin,
                                    const double *__restrict__ ref, float4 *__restrict__ pos4,
                                    unsigned *__restrict__ flag, cudaGraphConditionalHandle cond,
-                                   unsigned *__restrict__ err, const double *__restrict__ lambda) {
+                                   unsigned long long *__restrict__ stats, unsigned *__restrict__ err,
+                                   const double *__restrict__ lambda) {
     __shared__ bool s_last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 4 && stats) stats[i] = 0ull;  // neighbour statistics of the step's potential
     bool moved = false;
     if (i < n) {
         int t = types[i];
@@ -243,8 +275,9 @@ __global__ void k_md_vl_kick_drift(int n, int n_species, KickParams kp, double d
             atomicOr(err, kErrType);
             t = 0;
         }
-        const int s = cell_start[cell_of[i]] + slot[i];
+        const int s = slot[i];
         const float4 f = F4[s];
+        F4[s] = make_float4(0.f, 0.f, 0.f, 0.f);
         const double k = select_species(kp.k, t);
         const float fa[3] = {f.x, f.y, f.z};
         double x[3], d2 = 0.0;
@@ -402,13 +435,15 @@ cudaError_t launch_batch_reduce(Context &c, double *energies, double *virials) {
     return cudaGetLastError();
 }
 
+// Kick, drift, binning and the scan of the cell counts (the cell counts are
+// zero: every binning is followed by a scan, which clears them, and a newly
+// allocated count array is cleared once); k_scatter follows (launch_scatter).
 cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
                                      const int32_t *types) {
-    cudaError_t e = cudaMemsetAsync(c.d_cell_count, 0, sizeof(int) * g.ncell, c.stream);
-    if (e != cudaSuccess || n <= 0) return e;
+    if (n <= 0) return launch_sort(c, g, n);  // no atoms: the (all-zero) cell starts still come from a scan
     k_md_kick_drift_bin<<<(n + kMdThreads - 1) / kMdThreads, kMdThreads, 0, c.stream>>>(
-        n, c.basis.n_species, kick_params(c, dt), dt, pos, vel, types, c.d_F4, c.d_cell_start, g, c.d_tmp4,
-        c.d_cell_of, c.d_slot, c.d_cell_count, c.d_err, thermostat_on(c) ? c.d_lambda : nullptr);
+        n, c.basis.n_species, kick_params(c, dt), dt, pos, vel, types, c.d_F4, g, c.d_tmp4, c.d_cell_of, c.d_slot,
+        c.d_cell_count, c.d_cell_start, c.d_done, c.d_stats, c.d_err, thermostat_on(c) ? c.d_lambda : nullptr);
     return cudaGetLastError();
 }
 
@@ -423,7 +458,7 @@ cudaError_t launch_md_kick_finish(Context &c, int n, double dt, double *vel, con
                                   double *rec_pot, double *rec_kin, bool clear_vl) {
     const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
     k_md_kick_finish<<<blocks, kMdThreads, 0, c.stream>>>(
-        n, kick_params(c, dt), vel, types, c.d_F4, c.d_cell_start, c.d_cell_of, c.d_slot, c.last_eparts,
+        n, kick_params(c, dt), vel, types, c.d_F4, c.d_slot, c.last_eparts,
         c.last_epart, c.last_vparts, c.last_vpart, c.d_ke_part, c.d_done, c.d_result, c.d_step, rec_pot, rec_kin,
         clear_vl ? c.d_vl_flag : nullptr, c.d_vl_builds, thermostat(c, n));
     return cudaGetLastError();
@@ -434,8 +469,8 @@ cudaError_t launch_md_vl_kick_drift(Context &c, int n, double dt, double *pos, d
     const double h = 0.5 * c.skin;
     const int blocks = n > 0 ? (n + kMdThreads - 1) / kMdThreads : 1;
     k_md_vl_kick_drift<<<blocks, kMdThreads, 0, c.stream>>>(
-        n, c.basis.n_species, kick_params(c, dt), dt, h * h, pos, vel, types, c.d_F4, c.d_cell_start, c.d_cell_of,
-        c.d_slot, c.d_vl_origin, c.d_vl_ref, c.d_pos4, c.d_vl_flag, cond, c.d_err,
+        n, c.basis.n_species, kick_params(c, dt), dt, h * h, pos, vel, types, c.d_F4, c.d_slot, c.d_vl_origin,
+        c.d_vl_ref, c.d_pos4, c.d_vl_flag, cond, c.d_stats, c.d_err,
         thermostat_on(c) ? c.d_lambda : nullptr);
     return cudaGetLastError();
 }

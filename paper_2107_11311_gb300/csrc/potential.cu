@@ -107,10 +107,12 @@ size_t potential_smem_bytes(const Context &c, const Grid &g) {
 }
 
 cudaError_t launch_fused_potential(Context &c, const Grid &g, int n) {
-    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
-    if (e != cudaSuccess) return e;
+    if (!c.md_prezeroed) {
+        cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
+        if (e != cudaSuccess) return e;
+    }
     c.last_pipe = g.ncell > 0 && pipe_supported(c, g);
     if (c.last_pipe) return launch_pipe(c, g);
     return dispatch<kFused>(c, g);
@@ -151,9 +153,9 @@ __global__ void k_bin_count(int n, int n_species, const double *__restrict__ pos
                             const int32_t *__restrict__ types, Grid g, float4 *__restrict__ tmp4,
                             int *__restrict__ cell_of, int *__restrict__ slot, int *__restrict__ cell_count,
                             unsigned *__restrict__ err);
-__global__ void k_scan_cells(int ncell, const int *__restrict__ count, int *__restrict__ start);
+__global__ void k_scan_cells(int ncell, int *__restrict__ count, int *__restrict__ start);
 __global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__restrict__ cell_of,
-                          const int *__restrict__ slot, const int *__restrict__ cell_start,
+                          int *__restrict__ slot, const int *__restrict__ cell_start,
                           float4 *__restrict__ pos4, int *__restrict__ perm);
 
 namespace {

@@ -166,7 +166,7 @@ inline FusedNet make_fused_net(const Net &net) {
 
 struct PLayout {
     size_t off_start, off_count, off_prefix, off_shift, s_pos, s_idx, params, warp_base, warp_bytes, total;
-    size_t e_d, e_j, e_fx, e_fy, e_fz, a_u, a_x, coef;  // inside a warp region
+    size_t e_d, e_j, e_fx, e_fy, e_fz, a_u, a_x, a_s, coef;  // inside a warp region
     size_t tc_g, tc_cl, tc_nnb;                         // tensor-core form: rows, compact lists, counts
 };
 
@@ -213,6 +213,8 @@ __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, in
     q = align16(q + sizeof(float4) * acap);
     L.a_x = q;
     q = align16(q + sizeof(float4) * acap);
+    L.a_s = q;
+    q = align16(q + sizeof(float) * acap);
     L.coef = q;
     q = align16(q + sizeof(float) * kSlots);
     L.warp_bytes = q;
@@ -238,6 +240,7 @@ __device__ inline bool slot_is_angular(int slot) {
 
 struct WarpLists {
     float4 *e_d, *a_u, *a_x;  // e_d: (dx, dy, dz, r)
+    float *a_s;               // species weight of each angular entry (also a_x.z), unit-stride for the descriptor
     int *e_j;                 // sorted neighbour index | species << 28
     float *e_fx, *e_fy, *e_fz, *coef;
 };
@@ -332,8 +335,10 @@ __device__ __forceinline__ void complete_list(const Basis &B, const float *s_tw,
                 float sn, cs;
                 __sincosf(3.14159265358979f * (r * inv_rca), &sn, &cs);  // argument in [0, pi]
                 W.a_u[aslot] = make_float4(e.x * inv, e.y * inv, e.z * inv, 0.5f * (cs + 1.0f));
-                W.a_x[aslot] = make_float4(inv, -0.5f * 3.14159265358979f * inv_rca * sn, s_tw[W.e_j[k] >> 28],
+                const float sw = s_tw[W.e_j[k] >> 28];
+                W.a_x[aslot] = make_float4(inv, -0.5f * 3.14159265358979f * inv_rca * sn, sw,
                                            __int_as_float(k));
+                W.a_s[aslot] = sw;
             }
         }
         nang += __popc(ma);
@@ -596,7 +601,7 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
             const bool vj = lane < nA;
             const int self = 32 * A + (vj ? lane : 0);  // a valid entry: stands in for masked partners
             const float4 uj = W.a_u[self];
-            const float sj = W.a_x[self].z;
+            const float sj = W.a_s[self];
             for (int Bk = A; Bk < nbk; ++Bk) {
                 const int nB = min(32, nang - 32 * Bk);
                 const bool diag = Bk == A;
@@ -611,7 +616,7 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
                     rotation_step(diag, it + 1, nt, nA, nB, lane, vj, ccB, vB);
                     const int kA = vA ? 32 * Bk + ccA : self, kB = vB ? 32 * Bk + ccB : self;
                     const float4 ukA = W.a_u[kA], ukB = W.a_u[kB];
-                    const float skA = W.a_x[kA].z, skB = W.a_x[kB].z;
+                    const float skA = W.a_s[kA], skB = W.a_s[kB];
                     const float cA = uj.x * ukA.x + uj.y * ukA.y + uj.z * ukA.z;
                     const float cB = uj.x * ukB.x + uj.y * ukB.y + uj.z * ukB.z;
                     const float wA = vA ? uj.w * ukA.w : 0.f, wB = vB ? uj.w * ukB.w : 0.f;
@@ -1258,6 +1263,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     W.e_fz = reinterpret_cast<float *>(wb + L.e_fz);
     W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
     W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
+    W.a_s = reinterpret_cast<float *>(wb + L.a_s);
     W.coef = reinterpret_cast<float *>(wb + L.coef);
     float *s_g = reinterpret_cast<float *>(smem + L.tc_g);
     int *s_cl = reinterpret_cast<int *>(smem + L.tc_cl);
@@ -1748,6 +1754,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
     W.e_fz = reinterpret_cast<float *>(wb + L.e_fz);
     W.a_u = reinterpret_cast<float4 *>(wb + L.a_u);
     W.a_x = reinterpret_cast<float4 *>(wb + L.a_x);
+    W.a_s = reinterpret_cast<float *>(wb + L.a_s);
     W.coef = reinterpret_cast<float *>(wb + L.coef);
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)

@@ -64,10 +64,12 @@ cudaError_t launch_vl_build(Context &c, const Grid &g, int n) {
 }
 
 cudaError_t launch_potential_list(Context &c, const Grid &g, int n) {
-    cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
-    if (e != cudaSuccess) return e;
+    if (!c.md_prezeroed) {
+        cudaError_t e = cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * 4, c.stream);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(c.d_F4, 0, sizeof(float4) * (size_t)(n > 0 ? n : 1), c.stream);
+        if (e != cudaSuccess) return e;
+    }
     const int Kr = c.basis.Kr, Ka = c.basis.Ka;
     if (Kr == 17 && Ka == 9) return launch_list<17, 9, true>(c, g, n);
     if (Kr == 21 && Ka == 7) return launch_list<21, 7, true>(c, g, n);

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 1)
     W.e_fz = reinterpret_cast<float *>(wb + P.w.e_fz);
     W.a_u = reinterpret_cast<float4 *>(wb + P.w.a_u);
     W.a_x = reinterpret_cast<float4 *>(wb + P.w.a_x);
+    W.a_s = reinterpret_cast<float *>(wb + P.w.a_s);
     W.coef = reinterpret_cast<float *>(wb + P.w.coef);
     auto buf = [&](int b) { return smem + P.buf_bytes * b; };
 
