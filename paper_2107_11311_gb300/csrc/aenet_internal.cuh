@@ -34,6 +34,7 @@ struct Basis {
     int Kr, Ka, D;          // Kr = order_rad + 1, Ka = order_ang + 1, D = 2 (Kr + Ka)
     float rc_rad, rc_ang, rc_max;
     float type_weight[kMaxSpecies];
+    float sh_b[7][7];       // Legendre coefficients of T_a (a, l <= 6): the angular form through spherical harmonics
 };
 
 // Network shape (per species identical), passed by value.

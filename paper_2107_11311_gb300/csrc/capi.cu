@@ -11,6 +11,7 @@
 #include <new>
 
 #include "aenet_internal.cuh"
+#include "sh_angular.cuh"
 
 struct aenet_ctx {
     aenet::Context c;
@@ -365,6 +366,7 @@ extern "C" int aenet_setup(aenet_ctx **out, const aenet_model_desc *m, int preci
     c.basis.rc_rad = (float)m->rc_rad;
     c.basis.rc_ang = (float)m->rc_ang;
     c.basis.rc_max = (float)std::max(m->rc_rad, m->rc_ang);
+    detail::sh_legendre_of_chebyshev(c.basis.sh_b);
     for (int t = 0; t < kMaxSpecies; ++t) c.basis.type_weight[t] = t < m->n_species ? (float)m->type_weight[t] : 0.f;
     c.net.n_species = m->n_species;
     c.net.n_layers = m->n_layers;

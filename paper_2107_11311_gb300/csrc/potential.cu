@@ -283,6 +283,7 @@ extern "C" int aenet_descriptors_noalloc(int n, const double *pos, const int32_t
     B.rc_rad = (float)rc_rad;
     B.rc_ang = (float)rc_ang;
     B.rc_max = (float)(rc_rad > rc_ang ? rc_rad : rc_ang);
+    detail::sh_legendre_of_chebyshev(B.sh_b);
     for (int t = 0; t < kMaxSpecies; ++t) B.type_weight[t] = t < n_species ? (float)type_weight[t] : 0.f;
     Grid g{};
     g.ncell = 1;

@@ -38,6 +38,7 @@
 #include "aenet_internal.cuh"
 #include "bf16_mma.cuh"
 #include "fp_common.cuh"
+#include "sh_angular.cuh"
 
 namespace aenet {
 
@@ -213,8 +214,8 @@ __host__ __device__ inline PLayout make_playout(int n_off, int tile, int cap, in
     q = align16(q + sizeof(float4) * acap);
     L.a_x = q;
     q = align16(q + sizeof(float4) * acap);
-    L.a_s = q;
-    q = align16(q + sizeof(float) * acap);
+    L.a_s = q;  // also the scratch of the spherical-harmonic angular form (kShScratch floats)
+    q = align16(q + sizeof(float) * (acap > kShScratch ? acap : kShScratch));
     L.coef = q;
     q = align16(q + sizeof(float) * kSlots);
     L.warp_bytes = q;
@@ -240,7 +241,8 @@ __device__ inline bool slot_is_angular(int slot) {
 
 struct WarpLists {
     float4 *e_d, *a_u, *a_x;  // e_d: (dx, dy, dz, r)
-    float *a_s;               // species weight of each angular entry (also a_x.z), unit-stride for the descriptor
+    float *a_s;               // species weight of each angular entry (also a_x.z), unit-stride for the descriptor;
+                              // in the spherical-harmonic form the warp's scratch (kShScratch floats)
     int *e_j;                 // sorted neighbour index | species << 28
     float *e_fx, *e_fy, *e_fz, *coef;
 };
@@ -532,6 +534,36 @@ __device__ __forceinline__ void pair_gradient(const float4 &uj, const float4 &xj
     gz = Ak * (uj.z - c * uk.z) + Bk * uk.z;
 }
 
+// Spherical-harmonic form (sh_angular.cuh): the component sums of atom i's
+// angular entries, A_c = sum_j w_j v_c(u_j) (and sum_j w_j^2 at 49) into
+// scratch [0, 64) and B_c with s_j w_j into [64, 128): four passes (two copies,
+// two column groups), each lane accumulating its entries into 32 sums that
+// are then reduced across the warp (lane l: sum l).
+template <int M0, int M1, bool W2>
+__device__ __forceinline__ void sh_component_group(int nang, const WarpLists &W, int lane, int copy) {
+    float sh[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) sh[k] = 0.f;
+    for (int k = lane; k < nang; k += 32) {
+        const float4 ua = W.a_u[k];
+        const float wt = copy ? ua.w * W.a_x[k].z : ua.w;
+        sh_accumulate<M0, M1, W2>(ua.x, ua.y, ua.z, wt, sh);
+    }
+    const float v = transpose_reduce32(sh, lane);
+    constexpr int c0 = sh_comp(M0, M0, 0), n = (W2 ? kShComps + 1 : sh_comp(M1 + 1, M1 + 1, 0)) - c0;
+    __syncwarp();  // (the scratch may still be read by an earlier phase)
+    if (lane < n) W.a_s[64 * copy + c0 + lane] = v;
+}
+
+__device__ __forceinline__ void sh_component_sums(int nang, const WarpLists &W, int lane) {
+#pragma unroll 1
+    for (int copy = 0; copy < 2; ++copy) {
+        sh_component_group<0, 2, false>(nang, W, lane, copy);
+        sh_component_group<3, kShL, true>(nang, W, lane, copy);
+    }
+    __syncwarp();
+}
+
 // Slots of the descriptor a lane returns: the plain slot l and its
 // species-weighted copy l + P (P = KRT + KAT) for l < P, else the padding slots
 // 2l and 2l + 1 (zero).
@@ -554,7 +586,9 @@ __device__ __forceinline__ int desc_slot1(int lane) {
 // of the paper's ordered-pair sum.
 template <int KRT, int KAT, bool EXACT>
 __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &B, const float *s_tw,
-                                                const WarpLists &W, int lane, float &G0, float &G1) {
+                                                const float *s_sh, const WarpLists &W, int lane, float &G0,
+                                                float &G1) {
+    constexpr bool kSh = sh_angular<KRT, KAT, EXACT>();
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
     const float inv_rcr = 1.0f / B.rc_rad;
@@ -593,8 +627,9 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
         }
     }
     // angular (Eq. angular): every unordered pair once by the rotation schedule
-    // (see for the backward pass below); doubled to the ordered sum at the end
-    {
+    // (see for the backward pass below); doubled to the ordered sum at the end.
+    // (The spherical-harmonic form computes it after the radial reduction.)
+    if constexpr (!kSh) {
         const int nbk = (nang + 31) >> 5;
         for (int A = 0; A < nbk; ++A) {
             const int nA = min(32, nang - 32 * A);
@@ -646,6 +681,16 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
     const int s0 = desc_slot0<KRT, KAT>(lane), s1 = desc_slot1<KRT, KAT>(lane);
     G0 = slot_is_angular<KRT, KAT>(s0) ? 2.0f * acc[0] : acc[0];
     G1 = slot_is_angular<KRT, KAT>(s1) ? 2.0f * acc[1] : acc[1];
+    if constexpr (kSh) {
+        // the lane of angular order a = l - KRT holds slots KRT + a (plain) and
+        // 2 KRT + KAT + a (weighted): S_a = sum_l b_al Q_l - sum_j w_j^2 (the
+        // ordered-pair sum itself)
+        sh_component_sums(nang, W, lane);
+        if (lane >= KRT && lane < KRT + KAT) {
+            G0 = sh_fingerprint(W.a_s, lane - KRT, s_sh);
+            G1 = sh_fingerprint(W.a_s + 64, lane - KRT, s_sh);
+        }
+    }
 }
 
 // Chain rule of atom i's energy through every radial term and angular pair to
@@ -654,23 +699,26 @@ __device__ __forceinline__ void atom_descriptor(int nnb, int nang, const Basis &
 // without the ordered-sum factor 2, which is applied here).
 template <int KRT, int KAT, bool EXACT>
 __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, const Basis &B, const float *s_tw,
-                                                const WarpLists &W, const float *coef, int lane,
+                                                const float *s_sh, const WarpLists &W, const float *coef, int lane,
                                                 float4 *__restrict__ F4, float (&vir)[9]) {
+    constexpr bool kSh = sh_angular<KRT, KAT, EXACT>();
     constexpr int SLOT_ANG = KRT, SLOT_RADW = KRT + KAT, SLOT_ANGW = 2 * KRT + KAT;
     const int Kr = EXACT ? KRT : B.Kr;
     const int Ka = EXACT ? KAT : B.Ka;
     const float inv_rcr = 1.0f / B.rc_rad;
     float cr[KRT], crw[KRT];
-    float2 ca[KAT], caw[KAT];  // the same coefficient in both halves (packed Clenshaw of two pairs)
+    float2 ca[kSh ? 1 : KAT], caw[kSh ? 1 : KAT];  // the same coefficient in both halves (packed Clenshaw of two pairs)
 #pragma unroll
     for (int q = 0; q < KRT; ++q) {
         cr[q] = coef[q];
         crw[q] = coef[SLOT_RADW + q];
     }
+    if constexpr (!kSh) {
 #pragma unroll
-    for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
-        ca[q] = dup2(2.0f * coef[SLOT_ANG + q]);
-        caw[q] = dup2(2.0f * coef[SLOT_ANGW + q]);
+        for (int q = 0; q < KAT; ++q) {  // factor 2: ordered-pair sum
+            ca[q] = dup2(2.0f * coef[SLOT_ANG + q]);
+            caw[q] = dup2(2.0f * coef[SLOT_ANGW + q]);
+        }
     }
     const float k2 = 2.0f * inv_rcr;
     for (int k = lane; k < nnb; k += 32) {
@@ -696,6 +744,62 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
         W.e_fz[k] = fz;
     }
     __syncwarp();
+    if constexpr (kSh) {
+        // Spherical-harmonic form: the component sums (scratch [0, 64) plain with
+        // sum w^2 at 49, [64, 128) weighted) become the coefficient pairs
+        // (D_c, D'_c) = 2 N_c^2 (A_c k_l, B_c k'_l), k_l = sum_a g_a b_al, at
+        // scratch [2c], [2c + 1]; then each lane takes its entries on its own
+        // (dE/dd_j needs no partner), so every entry is written by one lane.
+        float gsum = 0.f, gwsum = 0.f;
+#pragma unroll
+        for (int a = 0; a < KAT; ++a) {
+            gsum += coef[SLOT_ANG + a];
+            gwsum += coef[SLOT_ANGW + a];
+        }
+        float dv[2], dwv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            dv[h] = dwv[h] = 0.f;
+            if (c < kShComps) {
+                const int l = (int)s_sh[kShTabL + c];
+                float kl = 0.f, klw = 0.f;
+#pragma unroll
+                for (int a = 0; a < KAT; ++a) {
+                    const float b = s_sh[kShTabB + a * (kShL + 1) + l];
+                    kl = fmaf(coef[SLOT_ANG + a], b, kl);
+                    klw = fmaf(coef[SLOT_ANGW + a], b, klw);
+                }
+                const float n2 = 2.0f * s_sh[kShTabN + c];
+                dv[h] = n2 * W.a_s[c] * kl;
+                dwv[h] = n2 * W.a_s[64 + c] * klw;
+            }
+        }
+        __syncwarp();  // every lane has read its sums
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c < kShComps) *reinterpret_cast<float2 *>(W.a_s + 2 * c) = make_float2(dv[h], dwv[h]);
+        }
+        __syncwarp();
+        // (warp-uniform trip count: sh_contract synchronises the warp; lanes past
+        // the last entry work on entry 0 and write nothing)
+        for (int base = 0; base < nang; base += 32) {
+            const int k = base + lane < nang ? base + lane : 0;
+            const float4 ua = W.a_u[k], xa = W.a_x[k];  // (u, f_c), (1/r, f_c', s, entry)
+            float E, Fx, Fy, Fz;
+            sh_contract(ua.x, ua.y, ua.z, xa.z, W.a_s, E, Fx, Fy, Fz);
+            if (base + lane < nang) {
+                const float rad = xa.y * (E - 2.0f * ua.w * fmaf(xa.z * xa.z, gwsum, gsum));
+                const float fu = Fx * ua.x + Fy * ua.y + Fz * ua.z;
+                const float t = ua.w * xa.x;
+                const int sl = __float_as_int(xa.w);  // force on neighbour = -dE_i/dd
+                W.e_fx[sl] -= fmaf(rad, ua.x, t * fmaf(-fu, ua.x, Fx));
+                W.e_fy[sl] -= fmaf(rad, ua.y, t * fmaf(-fu, ua.y, Fy));
+                W.e_fz[sl] -= fmaf(rad, ua.z, t * fmaf(-fu, ua.z, Fz));
+            }
+        }
+    } else {
     // Angular chain rule by the rotation schedule: the angular entries form
     // blocks of 32 (lane l owns entries 32b + l). Inside a diagonal block, step t
     // pairs lane l with entry (l + t) mod n_A (t = 1..n_A/2; at t = n_A/2 only the
@@ -757,6 +861,7 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
             }
         }
     }
+    }  // rotation form
     __syncwarp();
     float fix = 0.f, fiy = 0.f, fiz = 0.f;
     for (int k = lane; k < nnb; k += 32) {
@@ -785,7 +890,8 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
 
 template <int KRT, int KAT, bool EXACT, int MODE, int HB>
 __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
-                                             const float *s_par, const float *s_tw, const WarpLists &W, int lane,
+                                             const float *s_par, const float *s_tw, const float *s_sh,
+                                             const WarpLists &W, int lane,
                                              const float4 *__restrict__ pos4, float4 *__restrict__ F4,
                                              float *__restrict__ eatom, float *__restrict__ G_out,
                                              const float *__restrict__ dEdG_in, double &e_acc, float (&vir)[9]) {
@@ -794,7 +900,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
     const int s0 = 2 * lane, s1 = 2 * lane + 1;  // slots of the lane's dE/dG coefficients
     if constexpr (MODE != kForces) {
     float G0, G1;  // descriptor slots g0, g1
-    atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, W, lane, G0, G1);
+    atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, s_sh, W, lane, G0, G1);
     const int g0 = desc_slot0<KRT, KAT>(lane), g1 = desc_slot1<KRT, KAT>(lane);
     if constexpr (MODE == kDescriptor) {
         const int D = 2 * (Kr + Ka);
@@ -939,10 +1045,13 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         const int c0 = slot_col<KRT, KAT>(s0, Kr, Ka), c1 = slot_col<KRT, KAT>(s1, Kr, Ka);
         W.coef[s0] = c0 >= 0 ? dEdG_in[(size_t)i_s * D + c0] : 0.f;
         W.coef[s1] = c1 >= 0 ? dEdG_in[(size_t)i_s * D + c1] : 0.f;
+        // the spherical-harmonic chain rule needs the atom's component sums,
+        // which no descriptor pass has left in this launch
+        if constexpr (sh_angular<KRT, KAT, EXACT>()) sh_component_sums(nang, W, lane);
     }
     __syncwarp();
 
-    atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, W, W.coef, lane, F4, vir);
+    atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, s_sh, W, W.coef, lane, F4, vir);
 }
 
 // The network parameters of every species into the shared-memory layout of
@@ -1227,6 +1336,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                 int *__restrict__ vl_count, int split, int split_from, TcNet tc) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
+    __shared__ float s_sh[sh_angular<KRT, KAT, EXACT>() ? kShTab : 1];  // spherical-harmonic form's table
     __shared__ float s_vir[NW][9];
     __shared__ double s_e[NW];
     __shared__ int s_next, s_item;
@@ -1272,6 +1382,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
         if (tid == t) s_tw[t] = B.type_weight[t];
+    if constexpr (sh_angular<KRT, KAT, EXACT>()) load_sh_table(B.sh_b, s_sh, tid);
 
     // ---- network parameters of every species into the shared-memory layout
     if constexpr (MODE == kFused) load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid, NW * 32);
@@ -1479,7 +1590,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
     }
     auto tc_phase_a_finish = [&](int a, int i_s, int nnb, int nang) {
         float G0, G1;
-        atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, W, lane, G0, G1);
+        atom_descriptor<KRT, KAT, EXACT>(nnb, nang, B, s_tw, s_sh, W, lane, G0, G1);
         const float *P = s_par + __float_as_int(pos4[i_s].w) * kTcParStride;
         const int g0 = desc_slot0<KRT, KAT>(lane), g1 = desc_slot1<KRT, KAT>(lane);
         s_g[a * kSlots + g0] = (G0 - P[g0]) * P[kSlots + g0];
@@ -1517,7 +1628,10 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
         complete_list(B, s_tw, caps, W, lane, nnb, nang, err);
         nang = min(nang, caps.ang);  // an overflow was reported in phase A
         __syncwarp();
-        atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, W, s_g + a * kSlots, lane, F4, vir);
+        // (the spherical-harmonic form needs its atom's component sums again:
+        // the warp's scratch has served other atoms since phase A)
+        if constexpr (sh_angular<KRT, KAT, EXACT>()) sh_component_sums(nang, W, lane);
+        atom_chain_rule<KRT, KAT, EXACT>(i_s, nnb, nang, B, s_tw, s_sh, W, s_g + a * kSlots, lane, F4, vir);
     };
     for (int sub0 = 0; sub0 < cnt; sub0 += kTcMaxAtoms) {
         const int m = min(kTcMaxAtoms, cnt - sub0);
@@ -1657,7 +1771,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
             } else {
                 scan_tile(s_pos, s_idx, staged, ui, i_s, B, caps, W, lane, nnb);
                 finish_list(nnb, nang);
-                process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
+                process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, s_sh, W, lane, pos4, F4,
                                                         eatom, G_out, dEdG_in, e_acc, vir);
             }
         }
@@ -1687,7 +1801,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
                     store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
                 } else {
                     finish_list(nnb, nang);
-                    process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4,
+                    process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, s_sh, W, lane, pos4, F4,
                                                             eatom, G_out, dEdG_in, e_acc, vir);
                 }
             }
@@ -1739,6 +1853,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
                      unsigned *__restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
+    __shared__ float s_sh[sh_angular<KRT, KAT, EXACT>() ? kShTab : 1];  // spherical-harmonic form's table
     __shared__ float s_vir[kPWarps][9];
     __shared__ double s_e[kPWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1759,6 +1874,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
         if (tid == t) s_tw[t] = B.type_weight[t];
+    if constexpr (sh_angular<KRT, KAT, EXACT>()) load_sh_table(B.sh_b, s_sh, tid);
     load_net_params<KRT, KAT, EXACT>(B, net, params, shift, scale, s_par, tid, kPThreads);
     const int wx = 2 * g.m[0] + 1, wy = 2 * g.m[1] + 1;
     for (int o = tid; o < g.n_off; o += kPThreads) {  // image offset of every list code
@@ -1797,7 +1913,7 @@ __global__ void __launch_bounds__(kPThreads, 2)
         st_ang += nang;
         st_pairs += (unsigned long long)(nang * (nang - 1) / 2);
         __syncwarp();
-        process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+        process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, s_sh, W, lane, pos4, F4, eatom,
                                                   nullptr, nullptr, e_acc, vir);
     }
     __syncthreads();  // every warp has left the loop

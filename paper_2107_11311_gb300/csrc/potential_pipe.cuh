@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 1)
     constexpr int NW = kPipeWarps, NB = kPipeBufs;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float s_tw[kMaxSpecies];
+    __shared__ float s_sh[sh_angular<KRT, KAT, EXACT>() ? kShTab : 1];  // spherical-harmonic form's table
     __shared__ float s_vir[NW][9];
     __shared__ double s_e[NW];
     __shared__ int b_state[NB];                  // sequence number * 8 + phase
@@ -179,6 +180,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 1)
 #pragma unroll
     for (int t = 0; t < kMaxSpecies; ++t)
         if (tid == t) s_tw[t] = B.type_weight[t];
+    if constexpr (sh_angular<KRT, KAT, EXACT>()) load_sh_table(B.sh_b, s_sh, tid);
     if (tid < NB) {
         b_state[tid] = tid * 8 + kBufFree;
         b_atom[tid] = (unsigned long long)tid << 32;
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 1)
         st_ang += nang;
         st_pairs += (unsigned long long)(nang * (nang - 1) / 2);
         __syncwarp();
-        process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, W, lane, pos4, F4, eatom,
+        process_atom<KRT, KAT, EXACT, kFused, HB>(i_s, nnb, nang, B, net, s_par, s_tw, s_sh, W, lane, pos4, F4, eatom,
                                                   rec_out, nullptr, e_acc, vir);
         __syncwarp();
         if (lane == 0) {
