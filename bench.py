@@ -68,17 +68,20 @@ def network_flops(widths, n_atoms):
 
 # DRAM bytes per launch of the dominant kernel, from the ncu captures summarised in
 # profiles/k_potential_<workload>.md; reported only while the kernel source is the
-# one the counters were taken on (first 16 hex digits of its SHA-256).
-TRAFFIC_SOURCE_SHA256_16 = "b91ebef2066cdd63"
-TRAFFIC_CAPTURE = {("water_331776", "fp32"): 10806272, ("water_331776", "bf16x3"): 10923264,
-                   ("water_12288", "fp32"): 515584}
+# one the counters were taken on (first 16 hex digits of the SHA-256 of
+# potential_kernels.cuh followed by sh_angular.cuh).
+TRAFFIC_SOURCE_SHA256_16 = "c7a7609b12bc1c0c"
+TRAFFIC_CAPTURE = {("water_331776", "fp32"): 10810368, ("water_331776", "bf16x3"): 10919936,
+                   ("water_12288", "fp32"): 524032, ("amorphous_27000", "fp32"): 1105920}
 
 
 def captured_traffic(workload_name, precision, skin=0.0):
     import hashlib
-    src = os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", "potential_kernels.cuh")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("potential_kernels.cuh", "sh_angular.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_11311_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()[:16]
     if sha != TRAFFIC_SOURCE_SHA256_16 or skin != 0.0:
         return None
     return TRAFFIC_CAPTURE.get((workload_name, precision))

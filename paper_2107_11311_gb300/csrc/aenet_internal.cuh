@@ -362,6 +362,7 @@ inline cudaError_t allow_max_smem(K kern) {
 // Wrap, bin and sort atoms by cell (the periodic cell list).
 cudaError_t launch_cells(Context &c, const Grid &g, int n, const double *pos, const int32_t *types);
 // The scan + scatter half of launch_cells (after the counts are in place).
+cudaError_t launch_scan(Context &c, const Grid &g);  // cell counts -> cell starts (k_scan_cells)
 cudaError_t launch_scatter(Context &c, int n);  // the sort after a binning kernel that also scanned
 cudaError_t launch_sort(Context &c, const Grid &g, int n);
 // Binning of a batch: every atom into the cell grid of its structure.

@@ -77,6 +77,11 @@ __global__ void k_scatter(int n, const float4 *__restrict__ tmp4, const int *__r
     slot[i] = s;
 }
 
+cudaError_t launch_scan(Context &c, const Grid &g) {
+    k_scan_cells<<<1, 1024, 0, c.stream>>>(g.ncell, c.d_cell_count, c.d_cell_start);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(Context &c, int n) {
     if (n > 0)
         k_scatter<<<(n + 255) / 256, 256, 0, c.stream>>>(n, c.d_tmp4, c.d_cell_of, c.d_slot, c.d_cell_start,

@@ -155,6 +155,8 @@ __global__ void k_md_kick_drift_bin(int n, int n_species, KickParams kp, double 
     if (i < n) md_kick_drift_bin_atom(i, n_species, kp, dt, pos, vel, types, F4, g, tmp4, cell_of, slot, cell_count,
                                       err, lambda);
     // the last CTA to finish binning turns the counts into the cell starts
+    // (done == NULL: a separate scan kernel follows; the same for every thread)
+    if (!done) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -438,13 +440,20 @@ cudaError_t launch_batch_reduce(Context &c, double *energies, double *virials) {
 // Kick, drift, binning and the scan of the cell counts (the cell counts are
 // zero: every binning is followed by a scan, which clears them, and a newly
 // allocated count array is cleared once); k_scatter follows (launch_scatter).
+// The last CTA scans when one pass of its threads covers the cells (4 per
+// thread); a larger grid gets the 1,024-thread scan kernel instead (13,824
+// cells: 32 us in the kick's last CTA against 8 us as a kernel).
 cudaError_t launch_md_kick_drift_bin(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
                                      const int32_t *types) {
     if (n <= 0) return launch_sort(c, g, n);  // no atoms: the (all-zero) cell starts still come from a scan
+    const bool fold = g.ncell <= 4 * kMdThreads;
     k_md_kick_drift_bin<<<(n + kMdThreads - 1) / kMdThreads, kMdThreads, 0, c.stream>>>(
         n, c.basis.n_species, kick_params(c, dt), dt, pos, vel, types, c.d_F4, g, c.d_tmp4, c.d_cell_of, c.d_slot,
-        c.d_cell_count, c.d_cell_start, c.d_done, c.d_stats, c.d_err, thermostat_on(c) ? c.d_lambda : nullptr);
-    return cudaGetLastError();
+        c.d_cell_count, c.d_cell_start, fold ? c.d_done : nullptr, c.d_stats, c.d_err,
+        thermostat_on(c) ? c.d_lambda : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || fold) return e;
+    return launch_scan(c, g);
 }
 
 cudaError_t launch_scale(Context &c, double *x, long long count, double mu) {
