@@ -67,6 +67,21 @@ def test_verlet_md_wide_network_matches_oracle(gpu_mod, hidden):
     np.testing.assert_allclose(vel, vo, atol=1e-2)
 
 
+def test_verlet_md_solid_matches_oracle(gpu_mod):
+    """The list kernel on the 4-species solid's basis (angular order 6, whose
+    angular sum runs through spherical harmonics), 10 steps of 600 atoms with
+    a 1 A skin, against the oracle's own integration."""
+    st = inputs.amorphous(600, seed=6)
+    m = inputs.make_model("amorphous")
+    v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=4)
+    xo, vo, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 10)
+    g, pos, vel, ep, ek = _run(gpu_mod, m, st, v0, 10, 1.0)
+    assert g.md_list_builds() >= 1
+    assert np.abs(ep - epo).max() / st.n <= E_TOL
+    np.testing.assert_allclose(ek, eko, rtol=1e-5)
+    np.testing.assert_allclose(pos, xo, atol=1e-5)
+
+
 def _stepwise(gpu_mod, m, st, v0, n_steps, skin):
     """One step per call (continuing): the energy the list path records after
     each step, and a fresh cell-list evaluation (another context) of the same
