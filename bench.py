@@ -116,7 +116,9 @@ def model_overrides(args):
 
 def workload(name, hidden=None, orders=None):
     """Structure, model and initial velocities of a named workload. water_<N>
-    (N a multiple of 3) is N/3 molecules at 1.0 g/cm^3 (structure seed 10);
+    (N a multiple of 3) is N/3 molecules at 1.0 g/cm^3 (structure seed 10),
+    amorphous_<N> the 4-species solid of N atoms (structure seed 20, as the
+    27,000-atom box);
     hidden / orders override the network widths / basis orders (model-size
     sweeps)."""
     from paper_2107_11311_gb300 import inputs
@@ -130,6 +132,8 @@ def workload(name, hidden=None, orders=None):
         st, fam, vseed = inputs.amorphous_27000(), "amorphous", 22
     elif name.startswith("water_") and name[6:].isdigit() and int(name[6:]) % 3 == 0:
         st, fam, vseed = inputs.water(int(name[6:]) // 3, None, 10), "water", 12
+    elif name.startswith("amorphous_") and name[10:].isdigit() and int(name[10:]) > 0:
+        st, fam, vseed = inputs.amorphous(int(name[10:]), 20), "amorphous", 22
     else:
         raise SystemExit(f"unknown workload {name}")
     if hidden is None and name == "water_331776":
