@@ -20,8 +20,10 @@ error is within 1 meV/A; the line's ``forms`` object carries every form's rate
 and errors. The JSON line also carries the end-to-end number of that form
 through the C ABI with host buffers (host->device copy of positions,
 velocities and types, device->host copy of positions, velocities and
-energies, every step), the roofline of the dominant kernel, and the FP64 CPU
-oracle's throughput on the host cores.
+energies, every step), the roofline of the dominant kernel, the FP64 CPU
+oracle's throughput on the host cores, and (``batched``) the batched form on
+512 independent structures of 32 ... 2,048 atoms: both prepared batches
+replayed as CUDA graphs against one evaluation call per structure.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--forms fp32,bf16x3,bf16] [--workload water_331776|...]
@@ -285,21 +287,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, rank, world):
-    """--workload batch_512: 512 independent periodic structures (log-uniform 32 ...
-    2,048 atoms; 256 water at 1.0 g/cm^3 with the water model, 256 of the
-    4-species solid with its model). One step = E+F+virial of every structure.
-    Timed: the prepared batch of each model family (launch tuned once, whole
-    evaluation captured as one CUDA graph) replayed on device buffers, CUDA events
-    on the library's stream, L2 flushed between steps. For comparison (wall clock
-    around synchronous calls): the eager batched call and one call per structure."""
+def measure_batch(args, precision, world, dev, steps, warmup, clocks=None):
+    """The batched workload, batch_512: 512 independent periodic structures
+    (log-uniform 32 ... 2,048 atoms; 256 water at 1.0 g/cm^3 with the water
+    model, 256 of the 4-species solid with its model). One step = E+F+virial of
+    every structure. Timed: the prepared batch of each model family (launch
+    tuned once, whole evaluation captured as one CUDA graph) replayed on device
+    buffers, CUDA events on the library's stream, L2 flushed between steps. For
+    comparison (wall clock around synchronous calls): the eager batched call
+    and one call per structure (the plain form: one evaluation per structure)."""
     import torch
     from paper_2107_11311_gb300 import inputs
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    dev = torch.device("cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
     wat, amo = inputs.batch_structures()
     stream = torch.cuda.Stream(device=dev)
     fams = []
@@ -309,7 +307,7 @@ def run_batch(args, rank, world):
         for fam, structs in (("water", wat), ("amorphous", amo)):
             m = inputs.make_model(fam)
             off, pos, types, boxes = inputs.concat(structs)
-            g = make_gpu(m, args.precision, stream)
+            g = make_gpu(m, precision, stream)
             dpos, dtypes = torch.tensor(pos, device=dev), torch.tensor(types, device=dev)
             E = torch.zeros(len(structs), dtype=torch.float64, device=dev)
             F = torch.zeros((int(off[-1]), 3), dtype=torch.float64, device=dev)
@@ -343,13 +341,13 @@ def run_batch(args, rank, world):
             for p, t, b in single:
                 g.compute(p, t, b, energy=e1, forces=f1[:p.shape[0]], virial=v1)
 
-    def timed_wall(fn, steps):
-        for _ in range(args.warmup):
+    def timed_wall(fn, n):
+        for _ in range(warmup):
             flush.zero_()
             fn()
         torch.cuda.synchronize()
         tot = 0.0
-        for _ in range(steps):
+        for _ in range(n):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -358,56 +356,77 @@ def run_batch(args, rank, world):
             tot += time.perf_counter() - t0
         return tot
 
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start()
+    clk = None
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.zero_()
             graphs()
         torch.cuda.synchronize()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        clocks.mark()
-        for k in range(args.steps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if clocks is not None:
+            clocks.mark()
+        for k in range(steps):
             flush.zero_()
             starts[k].record(stream)
             graphs()
             ends[k].record(stream)
         torch.cuda.synchronize()
-        clk = clocks.stop()
+        if clocks is not None:
+            clk = clocks.stop()
         for g, *_ in fams:
             g.check()
         t_graph = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3, world)
-        t_eager = timed_wall(eager, max(1, args.steps // 4))
-        steps_s = max(1, args.steps // 10)
+        steps_e = max(1, steps // 4)
+        t_eager = timed_wall(eager, steps_e)
+        steps_s = max(1, steps // 10)
         t_single = timed_wall(per_structure, steps_s)
-    steps_e = max(1, args.steps // 4)
+    for g, *_ in fams:
+        g.close()
+    return {"n_atoms": n_atoms, "flops": flops, "tuning": tuning, "t_graph": t_graph, "clocks": clk,
+            "value": world * n_atoms * steps / t_graph, "ms_per_step": 1e3 * t_graph / steps,
+            "eager_batched_call": {"value": n_atoms * steps_e / t_eager, "ms_per_step": 1e3 * t_eager / steps_e},
+            "per_structure_launches": {"value": n_atoms * steps_s / t_single,
+                                       "ms_per_step": 1e3 * t_single / steps_s}}
+
+
+def run_batch(args, rank, world):
+    """--workload batch_512: the batched workload (measure_batch) as the line's
+    own workload."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    b = measure_batch(args, args.precision, world, dev, args.steps, args.warmup, clocks)
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
         peaks, peak_kind = measured_peaks()
         max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak = fp32_alu_peak_tflops(props.multi_processor_count, max_mhz)
-        achieved = flops / (t_graph / args.steps) / 1e12
-        line = {"metric": METRIC, "value": world * n_atoms * args.steps / t_graph, "unit": "atom-steps/s",
+        achieved = b["flops"] / (b["t_graph"] / args.steps) / 1e12
+        line = {"metric": METRIC, "value": b["value"], "unit": "atom-steps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * t_graph / args.steps, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": FORM_DTYPE[args.precision],
                 "data": "synthetic",
-                "config": {"workload": "batch_512", "structures": 512, "atoms": n_atoms,
+                "config": {"workload": "batch_512", "structures": 512, "atoms": b["n_atoms"],
                            "sizes": "log-uniform 32..2048; 256 water + 256 4-species solid",
                            "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                            "timing": "CUDA events around the replay of both prepared batches (one graph each)",
-                           "tuning": tuning},
-                "gpu_launches": sum(t["kernels"] for t in tuning.values()) * args.steps,
+                           "tuning": b["tuning"]},
+                "gpu_launches": sum(t["kernels"] for t in b["tuning"].values()) * args.steps,
                 "roofline": {"bound": "alu", "kernel": "whole batched evaluation (both graphs; k_potential dominant)",
                              "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                              "traffic": None,
                              "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x "
                                            f"{max_mhz:.0f} MHz (SM clock max from MEASURED_PEAKS.json, {peak_kind})"},
-                "clocks": clk,
-                "eager_batched_call": {"value": n_atoms * steps_e / t_eager, "ms_per_step": 1e3 * t_eager / steps_e},
-                "per_structure_launches": {"value": n_atoms * steps_s / t_single,
-                                           "ms_per_step": 1e3 * t_single / steps_s}}
+                "clocks": b["clocks"],
+                "eager_batched_call": b["eager_batched_call"],
+                "per_structure_launches": b["per_structure_launches"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -589,6 +608,8 @@ def main():
                     help="skip the oracle comparison of each form (sweeps); the headline is then the first form")
     ap.add_argument("--hidden", default=None, help="hidden widths, e.g. 25-25 (model-size sweeps)")
     ap.add_argument("--orders", default=None, help="basis orders N_r,N_a, e.g. 5,3 (model-size sweeps)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-form comparison (batch_512 graphs vs one call per structure)")
     ap.add_argument("--skin", type=float, default=0.0,
                     help="Verlet-list skin in A for the MD step (0, the default: cell list every step)")
     args = ap.parse_args()
@@ -650,6 +671,19 @@ def main():
     if args.e2e_steps > 0:
         e2e = e2e_rate(args, st, m, best, st.pos, v0, st.types, stream, world)
 
+    # ---- the batched form against one call per structure (batch_512, FP32)
+    batched = None
+    if not args.no_batched:
+        bsteps = max(5, args.steps // 2)
+        b = measure_batch(args, "fp32", world, dev, bsteps, args.warmup)
+        batched = {"workload": "batch_512", "structures": 512, "atoms": b["n_atoms"], "precision": "fp32",
+                   "steps": bsteps, "value": b["value"], "ms_per_step": b["ms_per_step"],
+                   "timing": "CUDA events around the replay of both prepared batches (one graph each); "
+                             "the other two: wall clock around synchronous calls",
+                   "eager_batched_call": b["eager_batched_call"],
+                   "per_structure_launches": b["per_structure_launches"],
+                   "speedup_vs_per_structure": b["value"] / b["per_structure_launches"]["value"]}
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -683,6 +717,7 @@ def main():
         # (the body of the graph's conditional node) that ran in the timed steps
         "gpu_launches": R["kernels_per_step"] * args.steps + (4 * R["builds"] if args.skin > 0 else 0),
         "e2e": e2e,
+        "batched": batched,
         "roofline": roofline_of(R, m, n, props, max_mhz, peak_kind, args.workload),
         "clocks": clk,
         "wall_s": wall,
