@@ -68,16 +68,18 @@ def network_flops(widths, n_atoms):
     return 4 * sum(widths[l] * widths[l - 1] for l in range(1, len(widths))) * n_atoms
 
 
-# DRAM bytes per launch of the dominant kernel, from the ncu captures summarised in
-# profiles/k_potential_<workload>.md; reported only while the kernel source is the
+# DRAM bytes per launch of the dominant kernel (workload, form, kernel), from the ncu
+# captures summarised in profiles/; reported only while the kernel source is the
 # one the counters were taken on (first 16 hex digits of the SHA-256 of
 # potential_kernels.cuh followed by sh_angular.cuh).
-TRAFFIC_SOURCE_SHA256_16 = "c7a7609b12bc1c0c"
-TRAFFIC_CAPTURE = {("water_331776", "fp32"): 10810368, ("water_331776", "bf16x3"): 10919936,
-                   ("water_12288", "fp32"): 524032, ("amorphous_27000", "fp32"): 1105920}
+TRAFFIC_SOURCE_SHA256_16 = "8767cb88d0b8a998"
+TRAFFIC_CAPTURE = {("water_331776", "fp32", "k_potential_list"): 146152192,
+                   ("water_331776", "fp32_cell", "k_potential"): 10810368,
+                   ("water_12288", "fp32", "k_potential_list"): 5258752,
+                   ("amorphous_27000", "fp32", "k_potential"): 1106432}
 
 
-def captured_traffic(workload_name, precision, skin=0.0):
+def captured_traffic(workload_name, precision, kernel, skin=0.0):
     import hashlib
     h = hashlib.sha256()
     for name in ("potential_kernels.cuh", "sh_angular.cuh"):
@@ -86,7 +88,7 @@ def captured_traffic(workload_name, precision, skin=0.0):
     sha = h.hexdigest()[:16]
     if sha != TRAFFIC_SOURCE_SHA256_16 or skin != 0.0:
         return None
-    return TRAFFIC_CAPTURE.get((workload_name, precision))
+    return TRAFFIC_CAPTURE.get((workload_name, precision, kernel))
 
 
 def max_over_ranks(value, world):
@@ -434,21 +436,27 @@ def run_batch(args, rank, world):
         dist.destroy_process_group()
 
 
-# precision forms: the network in FP32 (fused kernel), split BF16 and plain BF16
-# on the tensor cores inside the fused kernel, and the same two as the
-# three-kernel path (descriptor kernel, network kernel, force kernel)
-FORM_DTYPE = {"fp32": "f32", "fp32_pipelined": "f32", "bf16x3": "bf16x3", "bf16": "bf16", "bf16x3_split": "bf16x3",
-              "bf16_split": "bf16"}
+# precision forms: the network in FP32 (fp32: the library's automatic choice of
+# the MD step, which for the water basis builds the exact neighbour list in every
+# step and runs the list-driven kernel; fp32_cell: the fused kernel searching the
+# cells itself), split BF16 and plain BF16 on the tensor cores inside the fused
+# kernel, and the same two as the three-kernel path (descriptor kernel, network
+# kernel, force kernel)
+FORM_DTYPE = {"fp32": "f32", "fp32_cell": "f32", "fp32_pipelined": "f32", "bf16x3": "bf16x3", "bf16": "bf16",
+              "bf16x3_split": "bf16x3", "bf16_split": "bf16"}
 
 
 def make_gpu(m, form, stream, skin=0.0):
     """A library context for one form on the given torch stream."""
     from paper_2107_11311_gb300.aenet import AenetGPU
-    gpu = AenetGPU(m, form.replace("_split", "").replace("_pipelined", ""), stream=stream.cuda_stream)
+    gpu = AenetGPU(m, form.replace("_split", "").replace("_pipelined", "").replace("_cell", ""),
+                   stream=stream.cuda_stream)
     if form.endswith("_split"):
         gpu.fuse_network(False)
     if form.endswith("_pipelined"):  # the FP32 fused kernel's pipelined form (AENET_OPT_PIPELINE)
         gpu.pipeline(True)
+    if form.endswith("_cell"):  # MD steps: the fused kernel searches the cells (AENET_OPT_MD_LIST off)
+        gpu.md_list("off")
     gpu.set_skin(skin)
     return gpu
 
@@ -496,6 +504,8 @@ def time_form(args, st, m, v0, precision, dev, stream, flush, world):
                                                       for s in ms}
         torch.cuda.synchronize()
         gpu.check()
+        from paper_2107_11311_gb300.aenet import AENET_PATH_LIST
+        list_form = bool(gpu.md_path_flags() & AENET_PATH_LIST)
         builds = gpu.md_list_builds() - builds0
         step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
         # untimed: the full stage breakdown (every stage bracketed by events)
@@ -510,7 +520,7 @@ def time_form(args, st, m, v0, precision, dev, stream, flush, world):
     gpu.close()
     t_dev = max_over_ranks(sum(step_ms) / 1e3, world)
     return {"precision": precision, "t_dev": t_dev, "value": world * st.n * args.steps / t_dev,
-            "ms_per_step": 1e3 * t_dev / args.steps, "stats": stats, "fused": fused,
+            "ms_per_step": 1e3 * t_dev / args.steps, "stats": stats, "fused": fused, "list": list_form,
             "kernels_per_step": kernels_per_step, "builds": builds,
             "stage_ms": {s: (None if v is None else v / args.steps) for s, v in stage_sum.items()},
             "stage_full": {s: round(v / n_diag, 5) for s, v in diag.items()}}
@@ -544,7 +554,8 @@ def roofline_of(form, m, n, props, max_mhz, peak_kind, workload_name):
     f_force = force_kernel_flops(Kr, Ka, stats[0], stats[2])
     if form["fused"]:
         dom = "forces"  # descriptor, networks and forces run as one kernel, timed under "forces"
-        kernel = "k_potential (fused descriptor + network + forces)"
+        kernel = ("k_potential_list (descriptor + network + forces over the neighbour list built in the step)"
+                  if form.get("list") else "k_potential (fused neighbour search + descriptor + network + forces)")
         flops = f_desc + f_force + network_flops(m.widths, n)
     else:
         dom = max(("descriptor", "forces"), key=lambda s: form["stage_ms"][s] or 0.0)
@@ -555,7 +566,8 @@ def roofline_of(form, m, n, props, max_mhz, peak_kind, workload_name):
     peak = fp32_alu_peak_tflops(props.multi_processor_count, max_mhz)
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "flops_per_launch": flops, "launch_ms": ms,
-            "traffic": captured_traffic(workload_name, form["precision"]) if form["fused"] else None,
+            "traffic": (captured_traffic(workload_name, form["precision"], kernel.split()[0])
+                        if form["fused"] else None),
             "peak_basis": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 x 2 flops x {max_mhz:.0f} MHz "
                           f"(SM clock max from MEASURED_PEAKS.json, {peak_kind})"}
 
@@ -596,8 +608,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp32,bf16x3,bf16,bf16x3_split",
-                    help="precision forms timed side by side (comma-separated: fp32, bf16x3, bf16, "
+    ap.add_argument("--forms", default="fp32,fp32_cell,bf16x3,bf16,bf16x3_split",
+                    help="precision forms timed side by side (comma-separated: fp32, fp32_cell, bf16x3, bf16, "
                          "bf16x3_split, bf16_split, fp32_pipelined)")
     ap.add_argument("--precision", default=None, choices=sorted(FORM_DTYPE),
                     help="time this form only (same as --forms <form>)")
@@ -698,6 +710,7 @@ def main():
         r = results[f]
         rl = roofline_of(r, m, n, props, max_mhz, peak_kind, args.workload)
         forms_out[f] = dict({"value": r["value"], "ms_per_step": r["ms_per_step"], "fused": r["fused"],
+                             "neighbour_list_every_step": r["list"],
                              "kernels_per_step": r["kernels_per_step"], "roofline_frac": rl["frac"],
                              "stage_ms": {s: round(v, 5) for s, v in r["stage_ms"].items() if v is not None},
                              "meets_1meV_per_A": (f in within) if acc else None},
@@ -722,6 +735,10 @@ def main():
         "clocks": clk,
         "wall_s": wall,
     }
+    # the same algorithmic flops over the whole MD step (every kernel of it), for
+    # comparing forms whose neighbour search sits in different kernels
+    rl = line["roofline"]
+    rl["whole_step_frac"] = rl["flops_per_launch"] / (R["ms_per_step"] * 1e-3) / 1e12 / rl["peak"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)

@@ -332,11 +332,15 @@ int aenet_neighbor_stats(aenet_ctx *ctx, int64_t out[3]);
  * forces run as one fused kernel (the FP32 form with hidden widths <= 32),
  * whose time is then all reported under "forces" (descriptor and network read
  * ~0), and AENET_PATH_PIPELINED when that kernel ran in its pipelined form
- * (AENET_OPT_PIPELINE). Any output pointer except ms may be NULL. Returns
+ * (AENET_OPT_PIPELINE), and AENET_PATH_LIST when the step built the exact
+ * neighbour list in every step (AENET_OPT_MD_LIST; the list build is then
+ * reported under "cell sort" and the list-driven potential kernel under
+ * "forces"). Any output pointer except ms may be NULL. Returns
  * AENET_E_STATE if no timed step has run. Synchronises.
  */
 #define AENET_PATH_FUSED 1
 #define AENET_PATH_PIPELINED 2
+#define AENET_PATH_LIST 4
 int aenet_md_stage_times(aenet_ctx *ctx, float ms[6], int *kernels_per_step, int *path_flags);
 
 /*
@@ -409,6 +413,25 @@ int aenet_descriptors_noalloc(int n_atoms, const double *pos, const int32_t *typ
  * 17/9 or 21/7); otherwise the block-synchronous form runs.
  */
 #define AENET_OPT_PIPELINE 3
+/*
+ * AENET_OPT_MD_LIST (value AENET_MD_LIST_AUTO, _OFF or _ON; default AUTO), MD
+ * steps of the FP32 fused form without a skin (aenet_set_skin 0): the
+ * neighbours of Sec. II.B (every image-atom within the largest cutoff, the
+ * atom itself at zero shift excluded) are found in every step either by the
+ * fused potential kernel itself from the staged cells (OFF) or by a list
+ * kernel that writes each atom's exact list after the binning, which the
+ * list-driven potential kernel then reads (ON; the Verlet-list machinery with
+ * no skin and no rebuild test). The same pairs enter the same arithmetic, so
+ * the two agree to FP32 rounding order. AUTO takes ON for every basis except
+ * angular order 6 with radial order 20 (its spherical-harmonic angular sum
+ * runs faster in the fused kernel). Other evaluations (aenet_compute and the
+ * batch calls) always use the fused kernel. A change re-captures the MD step.
+ * Other values give AENET_E_ARG.
+ */
+#define AENET_OPT_MD_LIST 4
+#define AENET_MD_LIST_AUTO 0
+#define AENET_MD_LIST_OFF 1
+#define AENET_MD_LIST_ON 2
 int aenet_set_option(aenet_ctx *ctx, int option, int value);
 
 /*

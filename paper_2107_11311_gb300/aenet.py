@@ -20,8 +20,11 @@ AENET_MD_ASYNC, AENET_MD_CONTINUE, AENET_MD_TIMING, AENET_MD_TIMING_POTENTIAL = 
 AENET_OPT_KEEP_ACTIVATIONS = 1
 AENET_OPT_FUSED_NETWORK = 2
 AENET_OPT_PIPELINE = 3
+AENET_OPT_MD_LIST = 4
+AENET_MD_LIST_AUTO, AENET_MD_LIST_OFF, AENET_MD_LIST_ON = 0, 1, 2
 AENET_PATH_FUSED = 1
 AENET_PATH_PIPELINED = 2
+AENET_PATH_LIST = 4
 AENET_BATCH_AUTOTUNE = 1
 STAGES = ("kick_drift_bin", "cell_sort", "descriptor", "network", "forces", "kick_reductions")
 PRECISIONS = {"fp32": AENET_FP32, "bf16": AENET_BF16, "bf16x3": AENET_BF16X3}
@@ -373,6 +376,14 @@ class AenetGPU:
         block-synchronous one."""
         self.set_option(AENET_OPT_PIPELINE, 1 if on else 0)
 
+    def md_list(self, mode="auto"):
+        """MD steps without a skin: "on" builds the exact neighbour list in every
+        step and evaluates it with the list-driven potential kernel, "off" lets
+        the fused kernel search the cells itself, "auto" (default) takes "on"
+        except for the spherical-harmonic basis (angular order 6, radial 20)."""
+        modes = {"auto": AENET_MD_LIST_AUTO, "off": AENET_MD_LIST_OFF, "on": AENET_MD_LIST_ON}
+        self.set_option(AENET_OPT_MD_LIST, modes[mode])
+
     def keep_activations(self, on=True):
         """Keep per-atom activation records so that grad_weights() can follow."""
         self.set_option(AENET_OPT_KEEP_ACTIVATIONS, 1 if on else 0)
@@ -416,7 +427,8 @@ class AenetGPU:
     def md_path_flags(self):
         """Path flags of the last timed MD step: AENET_PATH_FUSED (1) when one
         fused kernel ran descriptor, network and forces, AENET_PATH_PIPELINED (2)
-        when it was the pipelined form."""
+        when it was the pipelined form, AENET_PATH_LIST (4) when the step built
+        the exact neighbour list and ran the list-driven kernel."""
         ms = np.zeros(len(STAGES), dtype=np.float32)
         f = C.c_int(0)
         self._check(self.lib.aenet_md_stage_times(self.h, _ptr(ms), None, C.byref(f)))

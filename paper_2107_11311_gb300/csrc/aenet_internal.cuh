@@ -240,6 +240,10 @@ struct Context {
     // built by k_potential's list mode, rebuilt inside the captured step (a graph
     // conditional node) whenever an atom moved more than skin/2 since the build.
     double skin = 0.0;
+    // MD steps without a skin: AENET_MD_LIST_AUTO (0), _OFF (1: the fused kernel searches the cells
+    // itself) or _ON (2: the exact list is built in every step and the list kernel evaluates it)
+    int md_list = 0;
+    bool last_list = false;            // the captured MD step builds the exact list in every step
     // tilt factors xy, xz, yz of the restricted triclinic cell of single-structure
     // calls (zero: orthorhombic)
     double tilt[3] = {0.0, 0.0, 0.0};
@@ -329,6 +333,7 @@ struct Context {
         bool timing = false;
         unsigned gen = 0;
         double skin = 0.0;
+        bool list_form = false;
         unsigned ev_mask = 0;
         double thermo_T0 = 0.0, thermo_tau = 0.0;
     } md_key;

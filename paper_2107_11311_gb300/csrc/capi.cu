@@ -945,20 +945,43 @@ extern "C" int aenet_descriptors(aenet_ctx *h, int n, const double *pos, const i
 // One MD step on device buffers: kick + drift + binning, cell sort, forces at
 // the new positions, closing kick with the FP64 reductions (and the record of
 // (E_pot, E_kin) when rec != NULL). With timing, events bracket the 6 stages.
+// Whether an MD step without a skin builds the exact neighbour list in every
+// step (AENET_OPT_MD_LIST): the FP32 fused form only, not the pipelined form;
+// automatic: every basis but the spherical-harmonic one (radial / angular
+// coefficient counts 21 / 7), whose fused kernel is the faster there.
+static bool md_list_form(const Context &c) {
+    if (c.skin > 0.0 || !fused_supported(c) || c.pipeline || c.md_list == AENET_MD_LIST_OFF) return false;
+    if (c.md_list == AENET_MD_LIST_ON) return true;
+    return !(c.basis.Kr == 21 && c.basis.Ka == 7);
+}
+
 static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
-                           const int32_t *types, double *rec) {
+                           const int32_t *types, double *rec, bool list_form) {
     int rc = check_smem(c, g);
     if (rc) return rc;
     CK(mark(c, 0), "event");
     CK(launch_md_kick_drift_bin(c, g, n, dt, pos, vel, types), "kick + drift + binning + scan");
     CK(mark(c, 1), "event");
     CK(launch_scatter(c, n), "cell sort");
+    // list form: every image-atom within rc_max of each atom, from this step's
+    // cells, into the atom's list row (the list kernel of the Verlet path)
+    if (list_form) CK(launch_vl_build(c, g, n), "neighbour list");
     CK(mark(c, 2), "event");
-    int n_eparts = 0;
-    c.md_prezeroed = true;  // the kick + drift kernel cleared the forces and statistics
-    rc = enqueue_potential(c, g, n, &n_eparts);
-    c.md_prezeroed = false;
-    if (rc) return rc;
+    if (list_form) {
+        CK(mark(c, 3), "event");
+        CK(mark(c, 4), "event");
+        c.md_prezeroed = true;  // the kick + drift kernel cleared the forces and statistics
+        const cudaError_t pe = launch_potential_list(c, g, n);
+        c.md_prezeroed = false;
+        CK(pe, "potential kernel (neighbour list)");
+        CK(mark(c, 5), "event");
+    } else {
+        int n_eparts = 0;
+        c.md_prezeroed = true;
+        rc = enqueue_potential(c, g, n, &n_eparts);
+        c.md_prezeroed = false;
+        if (rc) return rc;
+    }
     CK(launch_md_kick_finish(c, n, dt, vel, types, rec, rec ? rec + c.cap_rec : nullptr), "kick + reductions");
     CK(mark(c, 6), "event");
     return AENET_OK;
@@ -1088,6 +1111,7 @@ static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const in
                                                                    : 0u;
     const bool timing = ev_mask != 0;
     const bool verlet = c.skin > 0.0 && fused_supported(c);
+    const bool list_form = !verlet && md_list_form(c);
     const bool pos_dev = is_device_ptr(pos), vel_dev = is_device_ptr(vel), typ_dev = is_device_ptr(types);
     const bool rec_dev = (!e_pot || is_device_ptr(e_pot)) && (!e_kin || is_device_ptr(e_kin));
     if (async && !(pos_dev && vel_dev && typ_dev && rec_dev))
@@ -1099,8 +1123,10 @@ static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const in
     if ((rc = validate_types_host(c, n, types))) return rc;
     if ((rc = ensure(c, n, g)) || (rc = ensure_stage(c, n))) return rc;
     if (c.caps.nb == 0) c.caps = estimate_caps(c, n, g);
-    if (verlet) {
-        c.caps.rc_list = (float)(c.basis.rc_max + c.skin);
+    if (verlet || list_form) {
+        // the list form keeps a relative margin of 1e-5 over rc_max: its list is then a
+        // superset of the pairs within rc_max, which the list kernel selects exactly
+        c.caps.rc_list = (float)(verlet ? c.basis.rc_max + c.skin : c.basis.rc_max * 1.00001);
         if ((rc = ensure_verlet(c, n, g))) return rc;
     }
     double *dpos = pos_dev ? pos : c.d_pos;
@@ -1155,7 +1181,8 @@ static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const in
                           c.md_key.stream == c.stream && c.md_key.caps.nb == c.caps.nb &&
                           c.md_key.caps.ang == c.caps.ang && c.md_key.caps.tile == c.caps.tile &&
                           c.md_key.ev_mask == ev_mask && c.md_key.gen == c.buf_gen && c.md_key.skin == c.skin &&
-                          c.md_key.caps.vl_cap == c.caps.vl_cap && c.md_key.thermo_T0 == c.thermo_T0 &&
+                          c.md_key.list_form == list_form && c.md_key.caps.vl_cap == c.caps.vl_cap &&
+                          c.md_key.thermo_T0 == c.thermo_T0 &&
                           c.md_key.thermo_tau == c.thermo_tau;
         if (!same) {
             destroy_graph(c);
@@ -1163,7 +1190,7 @@ static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const in
             CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
             c.ev_mask = ev_mask;
             int src = verlet ? enqueue_md_step_verlet(c, g, n, dt, dpos, dvel, dtypes, rec)
-                             : enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec);
+                             : enqueue_md_step(c, g, n, dt, dpos, dvel, dtypes, rec, list_form);
             c.ev_mask = 0u;
             cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
             if (src) {
@@ -1202,6 +1229,8 @@ static int md_fixed_cell(aenet_ctx *h, int n, double *pos, double *vel, const in
             c.md_key.ev_mask = ev_mask;
             c.md_key.gen = c.buf_gen;
             c.md_key.skin = c.skin;
+            c.md_key.list_form = list_form;
+            c.last_list = list_form;
             c.md_key.thermo_T0 = c.thermo_T0;
             c.md_key.thermo_tau = c.thermo_tau;
         }
@@ -1348,7 +1377,9 @@ extern "C" int aenet_md_stage_times(aenet_ctx *h, float *ms, int *kernels_per_st
             ms[k] = nanf("");  // stage not recorded in the light timing mode
     }
     if (kernels_per_step) *kernels_per_step = c.md_kernels;
-    if (path_flags) *path_flags = (fused_path(c) ? AENET_PATH_FUSED : 0) | (c.last_pipe ? AENET_PATH_PIPELINED : 0);
+    if (path_flags)
+        *path_flags = (fused_path(c) ? AENET_PATH_FUSED : 0) | (c.last_pipe ? AENET_PATH_PIPELINED : 0) |
+                      (c.last_list ? AENET_PATH_LIST : 0);
     return AENET_OK;
 }
 
@@ -1370,6 +1401,15 @@ extern "C" int aenet_set_option(aenet_ctx *h, int option, int value) {
     if (option == AENET_OPT_PIPELINE) {
         if (c.pipeline != (value != 0)) {
             c.pipeline = value != 0;
+            destroy_graph(c);
+        }
+        return AENET_OK;
+    }
+    if (option == AENET_OPT_MD_LIST) {
+        if (value != AENET_MD_LIST_AUTO && value != AENET_MD_LIST_OFF && value != AENET_MD_LIST_ON)
+            return fail(&c, AENET_E_ARG, "AENET_OPT_MD_LIST takes AENET_MD_LIST_AUTO, _OFF or _ON, not %d", value);
+        if (c.md_list != value) {
+            c.md_list = value;
             destroy_graph(c);
         }
         return AENET_OK;

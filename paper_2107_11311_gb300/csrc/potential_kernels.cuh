@@ -1325,7 +1325,8 @@ __device__ __noinline__ void tc_species_network(int t, const int *order, int cnt
 }
 
 template <int KRT, int KAT, bool EXACT, int MODE, bool BATCH, int HB, int NW = kPWarps>
-__global__ void __launch_bounds__(NW * 32, NW == kPWarps ? 2 : 1)
+// (the list-build mode keeps no per-warp state: 32 registers give it eight CTAs per SM)
+__global__ void __launch_bounds__(NW * 32, MODE == kBuildList ? 8 : (NW == kPWarps ? 2 : 1))
     k_potential(Basis B, FusedNet net, Grid g_one, const StructInfo *__restrict__ sinfo, int n_struct, Caps caps,
                 const float4 *__restrict__ pos4,
                 const int *__restrict__ cell_start, const float *__restrict__ params, const float *__restrict__ shift,

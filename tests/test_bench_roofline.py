@@ -32,6 +32,10 @@ def test_fused_roofline_by_hand():
     assert abs(rl["achieved"] - by_hand / 2.0e-3 / 1e12) < 1e-9
     assert abs(rl["frac"] - by_hand / 2.0e-3 / 1e12 / peak) < 1e-12
     assert rl["bound"] == "alu" and rl["unit"] == "TFLOP/s"
+    assert rl["kernel"].startswith("k_potential ")
+    # the list form: the same algorithmic flops, charged to the list-driven kernel
+    rl2 = bench.roofline_of(dict(form, list=True), m, n, props, 2070.0, "measured", "water_331776")
+    assert rl2["flops_per_launch"] == by_hand and rl2["kernel"].startswith("k_potential_list ")
 
 
 def test_split_form_roofline_takes_the_slower_kernel():

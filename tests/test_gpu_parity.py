@@ -244,14 +244,22 @@ def test_device_types_out_of_range_reported(gpu_mod):
 
 # ------------------------------------------------------------------------ MD
 
-def test_md_matches_oracle_trajectory(gpu_mod):
+@pytest.mark.parametrize("case,mode", [("water", "auto"), ("water", "off"), ("water", "on"),
+                                       ("solid", "auto"), ("solid", "on")])
+def test_md_matches_oracle_trajectory(gpu_mod, case, mode):
     """10 velocity-Verlet steps at 0.5 fs from seeded 300 K velocities: per-frame
-    energies and final positions against the oracle's own integration."""
-    st = inputs.water_192()
-    m = inputs.make_model("water")
+    energies and final positions against the oracle's own integration; the MD
+    step with the neighbour list built in every step (on; automatic for the
+    water basis) and with the fused kernel's own cell search (off; automatic
+    for the solid's spherical-harmonic basis)."""
+    if case == "water":
+        st, m = inputs.water_192(), inputs.make_model("water")
+    else:
+        st, m = inputs.amorphous(600, seed=6), inputs.make_model("amorphous")
     v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
     xo, vo, epo, eko = O.md_nve(m, st.pos, v0, st.types, st.box, 5e-4, 10)
     g = gpu_mod.AenetGPU(m, "fp32")
+    g.md_list(mode)
     pos, vel = st.pos.copy(), v0.copy()
     ep, ek = np.zeros(11), np.zeros(11)
     g.md_nve(pos, vel, st.types, st.box, 5e-4, 10, e_pot=ep, e_kin=ek)
@@ -259,6 +267,36 @@ def test_md_matches_oracle_trajectory(gpu_mod):
     np.testing.assert_allclose(ek, eko, rtol=1e-5)
     np.testing.assert_allclose(pos, xo, atol=1e-5)
     np.testing.assert_allclose(vel, vo, atol=1e-2)
+
+
+def test_md_list_option_selects_the_path(gpu_mod):
+    """AENET_OPT_MD_LIST: the path flag of the captured step follows the mode
+    (automatic: the list for the water basis, the fused cell search for the
+    solid's), both paths give the same trajectory, and other values are
+    rejected."""
+    for fam, st, auto_list in (("water", inputs.water_192(), True),
+                               ("amorphous", inputs.amorphous(600, seed=6), False)):
+        m = inputs.make_model(fam)
+        v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
+        out = {}
+        for mode, want in (("auto", auto_list), ("on", True), ("off", False)):
+            g = gpu_mod.AenetGPU(m, "fp32")
+            g.md_list(mode)
+            pos, vel = st.pos.copy(), v0.copy()
+            g.md_nve(pos, vel, st.types, st.box, 5e-4, 3, flags=gpu_mod.AENET_MD_TIMING)
+            assert bool(g.md_path_flags() & gpu_mod.AENET_PATH_LIST) == want, (fam, mode)
+            _, kernels, fused = g.md_stage_times()
+            assert fused and kernels >= 4, (fam, mode, kernels)
+            out[mode] = pos
+            g.close()
+        # the same pairs and arithmetic: equal up to the FP32 summation order
+        np.testing.assert_allclose(out["on"], out["off"], atol=1e-6)
+    g = gpu_mod.AenetGPU(inputs.make_model("water"), "fp32")
+    for bad in (-1, 3):
+        with pytest.raises(gpu_mod.AenetError) as ei:
+            g.set_option(gpu_mod.AENET_OPT_MD_LIST, bad)
+        assert ei.value.code == -1
+    g.close()
 
 
 def test_md_device_async_continue_equals_one_call(gpu_mod):
