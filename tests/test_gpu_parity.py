@@ -245,7 +245,7 @@ def test_device_types_out_of_range_reported(gpu_mod):
 # ------------------------------------------------------------------------ MD
 
 @pytest.mark.parametrize("case,mode", [("water", "auto"), ("water", "off"), ("water", "on"),
-                                       ("solid", "auto"), ("solid", "on")])
+                                       ("water_small_box", "on"), ("solid", "auto"), ("solid", "on")])
 def test_md_matches_oracle_trajectory(gpu_mod, case, mode):
     """10 velocity-Verlet steps at 0.5 fs from seeded 300 K velocities: per-frame
     energies and final positions against the oracle's own integration; the MD
@@ -254,6 +254,8 @@ def test_md_matches_oracle_trajectory(gpu_mod, case, mode):
     for the solid's spherical-harmonic basis)."""
     if case == "water":
         st, m = inputs.water_192(), inputs.make_model("water")
+    elif case == "water_small_box":  # 6.6 A box, shorter than the cutoff: several images of each atom
+        st, m = inputs.water(8, 6.6, seed=3), inputs.make_model("water")
     else:
         st, m = inputs.amorphous(600, seed=6), inputs.make_model("amorphous")
     v0 = inputs.maxwell_boltzmann(m.masses[st.types], 300.0, seed=2)
