@@ -121,7 +121,8 @@ int aenet_compute(aenet_ctx *ctx, int n_atoms, const double *pos, const int32_t 
 /*
  * Verlet neighbour list for aenet_md_nve (the LAMMPS-style list with a skin
  * that the paper credits for ænet-LAMMPS's speed over ænet-TINKER, Sec. IV.B).
- * skin (A) >= 0; 0 (the default) rebuilds the cell list in every step. With
+ * skin (A) >= 0; 0 (the default) bins the atoms into cells and finds their
+ * neighbours anew in every step (AENET_OPT_MD_LIST says how). With
  * skin > 0 (FP32 form; the other forms ignore it) each MD step reuses a list
  * of the image-atoms within rc_max + skin of every atom and rebuilds it inside
  * the captured step only when some atom moved more than skin/2 since the last
