@@ -381,39 +381,54 @@ __device__ __forceinline__ void store_list_count(int *vl_count, int i_s, int nnb
 
 // Phase 1 of the list build from the Verlet list: the entries of atom i that
 // now lie within the largest cutoff, with the displacement computed exactly as
-// from the staged tile, (u_j + offset) - u_i.
+// from the staged tile, (u_j + offset) - u_i. The entries of kListRounds rounds
+// of 32 are loaded together, then their positions together, so that a list of
+// up to 32 kListRounds entries costs two dependent L2 round trips, not two per
+// round; the kept entries stay in list order.
+constexpr int kListRounds = 4;
+
 __device__ __forceinline__ void scan_list(const int *__restrict__ row, int cnt, const float4 *__restrict__ pos4,
                                           const float4 *off_shift, float4 ui, int jbits, const Basis &B,
                                           const Caps &caps, const WarpLists &W, int lane, int &nnb) {
     const float rc2max = B.rc_max * B.rc_max;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int jmask = (1 << jbits) - 1;
-    for (int base = 0; base < cnt; base += 32) {
-        const int k = base + lane;
-        bool in = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        int j = 0, typ = 0;
-        if (k < cnt) {
-            const int e = __ldg(row + k);
-            j = e & jmask;
-            const float4 sh = off_shift[e >> jbits];
-            const float4 p = pos4[j];
-            dx = (p.x + sh.x) - ui.x;
-            dy = (p.y + sh.y) - ui.y;
-            dz = (p.z + sh.z) - ui.z;
-            r2 = dx * dx + dy * dy + dz * dz;
-            typ = __float_as_int(p.w);
-            in = r2 <= rc2max;
+    for (int base = 0; base < cnt; base += kListRounds * 32) {
+        int e[kListRounds];
+        float4 p[kListRounds];
+#pragma unroll
+        for (int r = 0; r < kListRounds; ++r) {
+            const int k = base + 32 * r + lane;
+            e[r] = k < cnt ? __ldg(row + k) : -1;  // entries are non-negative
         }
-        const unsigned m = __ballot_sync(kFull, in);
-        if (in) {
-            const int slot = nnb + __popc(m & lt_mask);
-            if (slot < caps.nb) {
-                W.e_d[slot] = make_float4(dx, dy, dz, r2);
-                W.e_j[slot] = j | (typ << 28);
+#pragma unroll
+        for (int r = 0; r < kListRounds; ++r)
+            p[r] = e[r] >= 0 ? pos4[e[r] & jmask] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < kListRounds; ++r) {
+            bool in = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            int j = 0, typ = 0;
+            if (e[r] >= 0) {
+                j = e[r] & jmask;
+                const float4 sh = off_shift[e[r] >> jbits];
+                dx = (p[r].x + sh.x) - ui.x;
+                dy = (p[r].y + sh.y) - ui.y;
+                dz = (p[r].z + sh.z) - ui.z;
+                r2 = dx * dx + dy * dy + dz * dz;
+                typ = __float_as_int(p[r].w);
+                in = r2 <= rc2max;
             }
+            const unsigned m = __ballot_sync(kFull, in);
+            if (in) {
+                const int slot = nnb + __popc(m & lt_mask);
+                if (slot < caps.nb) {
+                    W.e_d[slot] = make_float4(dx, dy, dz, r2);
+                    W.e_j[slot] = j | (typ << 28);
+                }
+            }
+            nnb += __popc(m);
         }
-        nnb += __popc(m);
     }
 }
 
