@@ -372,6 +372,38 @@ __device__ __forceinline__ void scan_tile_build(const float4 *s_pos, const int *
     }
 }
 
+// scan_tile_build for two atoms at once (u0 and u1; the second only if two):
+// each staged image-atom is loaded once and tested against both.
+__device__ __forceinline__ void scan_tile_build2(const float4 *s_pos, const int *s_idx, int len, float4 u0, float4 u1,
+                                                 int self0, int self1, bool two, float rc2, int *__restrict__ row0,
+                                                 int *__restrict__ row1, int cap, int lane, int &n0, int &n1) {
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        bool in0 = false, in1 = false;
+        int e = 0;
+        if (q < len) {
+            const float4 p = s_pos[q];
+            e = s_idx[q];
+            const float dx0 = p.x - u0.x, dy0 = p.y - u0.y, dz0 = p.z - u0.z;
+            const float dx1 = p.x - u1.x, dy1 = p.y - u1.y, dz1 = p.z - u1.z;
+            in0 = (dx0 * dx0 + dy0 * dy0 + dz0 * dz0 <= rc2) && (e != self0);
+            in1 = two && (dx1 * dx1 + dy1 * dy1 + dz1 * dz1 <= rc2) && (e != self1);
+        }
+        const unsigned m0 = __ballot_sync(kFull, in0), m1 = __ballot_sync(kFull, in1);
+        if (in0) {
+            const int slot = n0 + __popc(m0 & lt_mask);
+            if (slot < cap) row0[slot] = e;
+        }
+        if (in1) {
+            const int slot = n1 + __popc(m1 & lt_mask);
+            if (slot < cap) row1[slot] = e;
+        }
+        n0 += __popc(m0);
+        n1 += __popc(m1);
+    }
+}
+
 __device__ __forceinline__ void store_list_count(int *vl_count, int i_s, int nnb, int cap, int lane, unsigned *err) {
     if (lane == 0) {
         vl_count[i_s] = nnb < cap ? nnb : cap;
@@ -903,6 +935,13 @@ __device__ __forceinline__ void atom_chain_rule(int i_s, int nnb, int nang, cons
     __syncwarp();
 }
 
+// tanh x = 1 - 2 / (exp(2x) + 1): the fast exponential and one division instead
+// of the full-accuracy tanhf, for the FP32 network and the tensor-core forms'
+// epilogues. Its absolute error (a few 1e-7) is below the FP32 rounding of the
+// layer sums it follows and far below the 2^-16 relative rounding of the
+// split-BF16 operands; the limits x -> +-inf give exactly +-1.
+__device__ __forceinline__ float tanh_exp(float x) { return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f); }
+
 template <int KRT, int KAT, bool EXACT, int MODE, int HB>
 __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const Basis &B, const FusedNet &net,
                                              const float *s_par, const float *s_tw, const float *s_sh,
@@ -969,7 +1008,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
         if constexpr (HB == 16) z += __shfl_xor_sync(kFull, z, 16);
     }
     float xl[kMaxLayers];  // this lane's neuron of every hidden layer
-    xl[1] = tanhf(z + Pt[net.offB[1] + o]);
+    xl[1] = tanh_exp(z + Pt[net.offB[1] + o]);
     if (rec && lane < net.H[1]) rec[net.rec_x[1] + lane] = xl[1];
 #pragma unroll
     for (int l = 2; l < kMaxLayers; ++l) {
@@ -988,7 +1027,7 @@ __device__ __forceinline__ void process_atom(int i_s, int nnb, int nang, const B
             }
             float zz = zab.x + zab.y;
             if constexpr (HB == 16) zz += __shfl_xor_sync(kFull, zz, 16);
-            xl[l] = tanhf(zz + Pt[net.offB[l] + o]);
+            xl[l] = tanh_exp(zz + Pt[net.offB[l] + o]);
             if (rec && lane < net.H[l]) rec[net.rec_x[l] + lane] = xl[l];
         }
     }
@@ -1121,12 +1160,6 @@ __device__ __forceinline__ void load_tc_params(const Basis &B, const float *__re
         s_par[t * kTcParStride + kSlots + slot] = col >= 0 ? scale[t * D + col] : 0.f;
     }
 }
-
-// tanh x = 1 - 2 / (exp(2x) + 1): the exponential and one division instead of
-// the full-accuracy tanhf. Its absolute error (a few 1e-7) is far below the
-// 2^-16 relative rounding of the split-BF16 operands it feeds; the limits
-// x -> +-inf give exactly +-1.
-__device__ __forceinline__ float tanh_exp(float x) { return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f); }
 
 // Position of the r-th set bit of mask (r from 0), or -1.
 __device__ __forceinline__ int nth_bit(unsigned mask, int r) {
@@ -1772,7 +1805,24 @@ __global__ void __launch_bounds__(NW * 32, MODE == kBuildList ? 8 : (NW == kPWar
         if (total > 0) stage(0);
         __syncthreads();
         const int staged = s_kept;
+        if constexpr (MODE == kBuildList) {  // two atoms per warp: one pass over the tile serves both
+            for (;;) {
+                int a = 0;
+                if (lane == 0) a = atomicAdd(&s_next, 2);
+                a = __shfl_sync(kFull, a, 0);
+                if (a >= cnt) break;
+                const bool two = a + 1 < cnt;
+                const int i0 = c0 + a, i1 = two ? i0 + 1 : i0;
+                int n0 = 0, n1 = 0;
+                scan_tile_build2(s_pos, s_idx, staged, pos4[i0], pos4[i1], i0 | self_code, i1 | self_code, two,
+                                 rc2list, vl_out + (size_t)i0 * caps.vl_cap, vl_out + (size_t)i1 * caps.vl_cap,
+                                 caps.vl_cap, lane, n0, n1);
+                store_list_count(vl_count, i0, n0, caps.vl_cap, lane, err);
+                if (two) store_list_count(vl_count, i1, n1, caps.vl_cap, lane, err);
+            }
+        }
         for (;;) {
+            if constexpr (MODE == kBuildList) break;
             int a = 0;
             if (lane == 0) a = atomicAdd(&s_next, 1);
             a = __shfl_sync(kFull, a, 0);
