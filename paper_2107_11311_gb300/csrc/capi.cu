@@ -942,9 +942,6 @@ extern "C" int aenet_descriptors(aenet_ctx *h, int n, const double *pos, const i
     return compute_impl(h->c, n, pos, types, box, nullptr, nullptr, nullptr, nullptr, G);
 }
 
-// One MD step on device buffers: kick + drift + binning, cell sort, forces at
-// the new positions, closing kick with the FP64 reductions (and the record of
-// (E_pot, E_kin) when rec != NULL). With timing, events bracket the 6 stages.
 // Whether an MD step without a skin builds the exact neighbour list in every
 // step (AENET_OPT_MD_LIST): the FP32 fused form only, not the pipelined form;
 // automatic: every basis but the spherical-harmonic one (radial / angular
@@ -955,6 +952,10 @@ static bool md_list_form(const Context &c) {
     return !(c.basis.Kr == 21 && c.basis.Ka == 7);
 }
 
+// One MD step on device buffers: kick + drift + binning, cell sort (and, in the
+// list form, the neighbour-list build), forces at the new positions, closing
+// kick with the FP64 reductions (and the record of (E_pot, E_kin) when rec !=
+// NULL). With timing, events bracket the 6 stages.
 static int enqueue_md_step(Context &c, const Grid &g, int n, double dt, double *pos, double *vel,
                            const int32_t *types, double *rec, bool list_form) {
     int rc = check_smem(c, g);
