@@ -1820,21 +1820,15 @@ __global__ void __launch_bounds__(NW * 32, MODE == kBuildList ? 8 : (NW == kPWar
                 store_list_count(vl_count, i0, n0, caps.vl_cap, lane, err);
                 if (two) store_list_count(vl_count, i1, n1, caps.vl_cap, lane, err);
             }
-        }
-        for (;;) {
-            if constexpr (MODE == kBuildList) break;
-            int a = 0;
-            if (lane == 0) a = atomicAdd(&s_next, 1);
-            a = __shfl_sync(kFull, a, 0);
-            if (a >= cnt) break;
-            const int i_s = c0 + a;
-            const float4 ui = pos4[i_s];
-            int nnb = 0, nang = 0;
-            if constexpr (MODE == kBuildList) {
-                scan_tile_build(s_pos, s_idx, staged, ui, i_s | self_code, rc2list,
-                                vl_out + (size_t)i_s * caps.vl_cap, caps.vl_cap, lane, nnb);
-                store_list_count(vl_count, i_s, nnb, caps.vl_cap, lane, err);
-            } else {
+        } else {
+            for (;;) {
+                int a = 0;
+                if (lane == 0) a = atomicAdd(&s_next, 1);
+                a = __shfl_sync(kFull, a, 0);
+                if (a >= cnt) break;
+                const int i_s = c0 + a;
+                const float4 ui = pos4[i_s];
+                int nnb = 0, nang = 0;
                 scan_tile(s_pos, s_idx, staged, ui, i_s, B, caps, W, lane, nnb);
                 finish_list(nnb, nang);
                 process_atom<KRT, KAT, EXACT, MODE, HB>(i_s, nnb, nang, B, net, s_par, s_tw, s_sh, W, lane, pos4, F4,
