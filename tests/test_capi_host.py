@@ -49,3 +49,26 @@ def test_setup_rejects_bad_model_before_touching_the_gpu():
     with pytest.raises(AenetError) as ei:
         AenetGPU(m, "fp32")
     assert ei.value.code == -1
+
+
+def _header_constants():
+    src = open(os.path.join(ROOT, "include", "aenet_gpu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"#define\s+(AENET_[A-Z0-9_]+)\s+(-?\d+)\b", src)}
+    consts.update({k: int(v) for k, v in re.findall(r"\b(AENET_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    """Every status code, precision, MD flag, option and path flag the binding
+    passes through the C ABI has the header's value."""
+    from paper_2107_11311_gb300 import aenet
+    consts = _header_constants()
+    names = [n for n in dir(aenet) if n.startswith("AENET_")]
+    assert len(names) >= 15
+    for n in names:
+        assert n in consts, f"{n} is not defined in include/aenet_gpu.h"
+        assert getattr(aenet, n) == consts[n], f"{n}: binding {getattr(aenet, n)} != header {consts[n]}"
+    for code, name in aenet.STATUS.items():
+        assert consts[name] == code, name
+    assert {name: consts[f"AENET_{name.upper()}"] for name in aenet.PRECISIONS} == aenet.PRECISIONS
